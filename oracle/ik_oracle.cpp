@@ -1,0 +1,824 @@
+// ORACLE — test infrastructure, not product code.
+//
+// A plain, slow, obviously-correct CPU restatement of the gap map-seeking
+// (gMS) inverse-kinematics search and its path planner (Arathorn,
+// arXiv 1906.10678), in the exact lattice form used throughout this project:
+//
+//   * joints live on voxel centres of an Nx x Ny x Nz grid (index
+//     iota = (z*Ny + y)*Nx + x), obstacles are voxels marked 1;
+//   * a segment of nominal length L may take any integer offset d with
+//     lo2 <= |d|^2 <= hi2, lo2 = max(1, ceil((L-tol)^2)), hi2 = floor((L+tol)^2)
+//     (the "shell"; it stands in for the quiver of directions times the
+//     segment length, section "Discretization of the segment articulations",
+//     and for the epsilon on the gap vector's length, section "The gap in gMS");
+//   * a segment p->q is obstacle-free when every voxel of its closed
+//     supercover (voxels whose closed unit cube meets the closed segment) is
+//     free (stands in for the n sample points of section "Testing for
+//     collisions");
+//   * Step 1 / Step 2A of "The procedure for IK solution" become forward
+//     reachable sets F_k grown from the root, the backward (cone) mapping from
+//     the target becomes backward sets B_k, the gap test becomes V_k = F_k & B_k,
+//     and Step 3's "one is chosen" becomes a minimum-linear-index traceback.
+//
+// Every set is a byte per voxel (no bit packing), every segment test walks
+// its supercover voxel by voxel, and every step follows the definitions in
+// the order they are stated.  Only tests/, the smoke check and the benchmark's
+// CPU-baseline leg load this library; the product path never does.
+//
+// Parity status: supercover, shells, F/B/V sets and the reach traceback are
+// pinned by brute-force chain enumeration, closed forms and worked examples
+// (tests/test_oracle_pins.py).  The path planner and replanner follow
+// rules that the paper states only in words (sections "Smooth sequence
+// computation", "Filtering for smoothness", "Dynamic Obstacles"); they are
+// pinned by brute force over restricted balls on tiny grids and by
+// invariants, not by any number printed in the paper.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+struct Grid {
+  int nx, ny, nz;
+  long nvox() const { return (long)nx * ny * nz; }
+  bool inside(int x, int y, int z) const {
+    return x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz;
+  }
+  long index(int x, int y, int z) const { return ((long)z * ny + y) * nx + x; }
+};
+
+struct V3 {
+  int x, y, z;
+};
+
+static inline long sq(long v) { return v * v; }
+static inline long dist2(const V3& a, const V3& b) {
+  return sq(a.x - b.x) + sq(a.y - b.y) + sq(a.z - b.z);
+}
+
+// ---------------------------------------------------------------------------
+// Shell of admissible segment offsets for one segment length.
+// ---------------------------------------------------------------------------
+
+// Integer bounds of the shell: lo2 = ceil((L - tol)^2) (at least 1, so the
+// zero offset never counts as a segment) and hi2 = floor((L + tol)^2),
+// evaluated in IEEE double precision.
+static void shell_bounds(int L, double tol, int* lo2, int* hi2) {
+  double a = (double)L - tol;
+  double b = (double)L + tol;
+  double lo = (a > 0.0) ? std::ceil(a * a) : 0.0;
+  double hi = std::floor(b * b);
+  *lo2 = std::max(1, (int)lo);
+  *hi2 = (int)hi;
+}
+
+// All d with lo2 <= |d|^2 <= hi2, ordered by (|d|^2, z, y, x).
+static std::vector<V3> shell(int lo2, int hi2) {
+  std::vector<V3> out;
+  int R = 0;
+  while ((long)(R + 1) * (R + 1) <= hi2) ++R;
+  for (int z = -R; z <= R; ++z)
+    for (int y = -R; y <= R; ++y)
+      for (int x = -R; x <= R; ++x) {
+        long n2 = (long)x * x + (long)y * y + (long)z * z;
+        if (n2 >= lo2 && n2 <= hi2) out.push_back({x, y, z});
+      }
+  std::stable_sort(out.begin(), out.end(), [](const V3& a, const V3& b) {
+    long na = (long)a.x * a.x + (long)a.y * a.y + (long)a.z * a.z;
+    long nb = (long)b.x * b.x + (long)b.y * b.y + (long)b.z * b.z;
+    if (na != nb) return na < nb;
+    if (a.z != b.z) return a.z < b.z;
+    if (a.y != b.y) return a.y < b.y;
+    return a.x < b.x;
+  });
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// Closed supercover by an exact rational slab test.
+// ---------------------------------------------------------------------------
+
+// Fraction num/den with den > 0.
+struct Frac {
+  long n, d;
+};
+static inline bool frac_lt(const Frac& a, const Frac& b) { return a.n * b.d < b.n * a.d; }
+
+// Does the closed unit cube centred on voxel c meet the closed segment a->b?
+// The segment is a + t (b - a), t in [0, 1].  Along axis i the point stays in
+// the cube's slab |a_i + t d_i - c_i| <= 1/2, i.e. 2u - 1 <= 2 t d_i <= 2u + 1
+// with u = c_i - a_i.  The cube meets the segment iff the intersection of the
+// per-axis t-intervals with [0, 1] is non-empty.
+static bool cube_meets_segment(const V3& a, const V3& b, const V3& c) {
+  Frac lo{0, 1}, hi{1, 1};
+  const int av[3] = {a.x, a.y, a.z};
+  const int bv[3] = {b.x, b.y, b.z};
+  const int cv[3] = {c.x, c.y, c.z};
+  for (int i = 0; i < 3; ++i) {
+    long d = (long)bv[i] - av[i];
+    long u = (long)cv[i] - av[i];
+    if (d == 0) {
+      if (u != 0) return false;  // |u| <= 1/2 with integer u
+      continue;
+    }
+    Frac l, h;
+    if (d > 0) {
+      l = {2 * u - 1, 2 * d};
+      h = {2 * u + 1, 2 * d};
+    } else {
+      l = {-(2 * u + 1), -2 * d};
+      h = {-(2 * u - 1), -2 * d};
+    }
+    if (frac_lt(lo, l)) lo = l;
+    if (frac_lt(h, hi)) hi = h;
+  }
+  return !frac_lt(hi, lo);
+}
+
+// Supercover of the segment a->b: every voxel of the bounding box of {a, b}
+// whose cube meets the segment, in (z, y, x) order.  (A voxel outside the
+// bounding box is at least one unit away along some axis, so its cube
+// cannot meet the segment.)
+static std::vector<V3> supercover(const V3& a, const V3& b) {
+  std::vector<V3> out;
+  for (int z = std::min(a.z, b.z); z <= std::max(a.z, b.z); ++z)
+    for (int y = std::min(a.y, b.y); y <= std::max(a.y, b.y); ++y)
+      for (int x = std::min(a.x, b.x); x <= std::max(a.x, b.x); ++x) {
+        V3 c{x, y, z};
+        if (cube_meets_segment(a, b, c)) out.push_back(c);
+      }
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// Arm: one shell per segment, each offset with its supercover from the origin.
+// SC(p, p+d) = p + SC(0, d) because the slab test depends only on
+// differences; the tests pin that identity directly.
+// ---------------------------------------------------------------------------
+
+struct Segment {
+  int lo2, hi2;
+  std::vector<V3> offs;               // the shell
+  std::vector<std::vector<V3>> sc;    // sc[i] = SC(0, offs[i])
+};
+
+static Segment make_segment(int lo2, int hi2) {
+  Segment s;
+  s.lo2 = lo2;
+  s.hi2 = hi2;
+  s.offs = shell(lo2, hi2);
+  s.sc.reserve(s.offs.size());
+  V3 o{0, 0, 0};
+  for (const V3& d : s.offs) s.sc.push_back(supercover(o, d));
+  return s;
+}
+
+struct Problem {
+  Grid g;
+  const uint8_t* occ;  // 1 = occupied
+  std::vector<Segment> seg;  // seg[k-1] is segment k
+  int S() const { return (int)seg.size(); }
+};
+
+// Segment k placed at p with offset number i: every supercover voxel free?
+// (Both endpoints are assumed inside the grid, so the supercover is too.)
+static bool edge_free(const Problem& P, const V3& p, const std::vector<V3>& sc) {
+  for (const V3& v : sc) {
+    if (P.occ[P.g.index(p.x + v.x, p.y + v.y, p.z + v.z)]) return false;
+  }
+  return true;
+}
+
+static bool is_offset_in_shell(const Segment& s, const V3& d) {
+  long n2 = (long)d.x * d.x + (long)d.y * d.y + (long)d.z * d.z;
+  return n2 >= s.lo2 && n2 <= s.hi2;
+}
+
+static inline V3 at(const Grid& g, long i) {
+  V3 v;
+  v.x = (int)(i % g.nx);
+  v.y = (int)((i / g.nx) % g.ny);
+  v.z = (int)(i / ((long)g.nx * g.ny));
+  return v;
+}
+
+using Set = std::vector<uint8_t>;  // byte per voxel
+
+// Forward sets: F_0 = {root} if free; F_k = every q reachable from some
+// p in F_{k-1} by an admissible, obstacle-free segment k (scatter form).
+static std::vector<Set> forward_sets(const Problem& P, const V3& root) {
+  const Grid& g = P.g;
+  std::vector<Set> F(P.S() + 1, Set(g.nvox(), 0));
+  if (g.inside(root.x, root.y, root.z) && !P.occ[g.index(root.x, root.y, root.z)])
+    F[0][g.index(root.x, root.y, root.z)] = 1;
+  for (int k = 1; k <= P.S(); ++k) {
+    const Segment& s = P.seg[k - 1];
+    for (long i = 0; i < g.nvox(); ++i) {
+      if (!F[k - 1][i]) continue;
+      V3 p = at(g, i);
+      for (size_t e = 0; e < s.offs.size(); ++e) {
+        V3 q{p.x + s.offs[e].x, p.y + s.offs[e].y, p.z + s.offs[e].z};
+        if (!g.inside(q.x, q.y, q.z)) continue;
+        long qi = g.index(q.x, q.y, q.z);
+        if (F[k][qi]) continue;  // already known reachable
+        if (edge_free(P, p, s.sc[e])) F[k][qi] = 1;
+      }
+    }
+  }
+  return F;
+}
+
+// Backward sets from a target set T: B_S = T & free; B_{k-1} = every p from
+// which an admissible, obstacle-free segment k lands in B_k (mirror scatter).
+// These are NOT masked by F: V_k = F_k & B_k is formed afterwards.
+static std::vector<Set> backward_sets(const Problem& P, const Set& T) {
+  const Grid& g = P.g;
+  const int S = P.S();
+  std::vector<Set> B(S + 1, Set(g.nvox(), 0));
+  for (long i = 0; i < g.nvox(); ++i) B[S][i] = (T[i] && !P.occ[i]) ? 1 : 0;
+  for (int k = S; k >= 1; --k) {
+    const Segment& s = P.seg[k - 1];
+    for (long i = 0; i < g.nvox(); ++i) {
+      if (!B[k][i]) continue;
+      V3 q = at(g, i);
+      for (size_t e = 0; e < s.offs.size(); ++e) {
+        V3 p{q.x - s.offs[e].x, q.y - s.offs[e].y, q.z - s.offs[e].z};
+        if (!g.inside(p.x, p.y, p.z)) continue;
+        long pi = g.index(p.x, p.y, p.z);
+        if (B[k - 1][pi]) continue;
+        if (edge_free(P, p, s.sc[e])) B[k - 1][pi] = 1;
+      }
+    }
+  }
+  return B;
+}
+
+static std::vector<Set> intersect(const std::vector<Set>& F, const std::vector<Set>& B) {
+  std::vector<Set> V(F.size());
+  for (size_t k = 0; k < F.size(); ++k) {
+    V[k].resize(F[k].size());
+    for (size_t i = 0; i < F[k].size(); ++i) V[k][i] = (F[k][i] && B[k][i]) ? 1 : 0;
+  }
+  return V;
+}
+
+// Reach traceback ("one is chosen"): p_0 = root; for k = 1..S, p_k is the
+// voxel of V_k with the smallest linear index among those reachable from
+// p_{k-1} by an admissible, obstacle-free segment k.  Returns false when
+// V_0 is empty.
+static bool traceback_min_index(const Problem& P, const std::vector<Set>& V, const V3& root,
+                                std::vector<V3>* pose) {
+  const Grid& g = P.g;
+  if (!g.inside(root.x, root.y, root.z) || !V[0][g.index(root.x, root.y, root.z)]) return false;
+  pose->assign(P.S() + 1, V3{0, 0, 0});
+  (*pose)[0] = root;
+  for (int k = 1; k <= P.S(); ++k) {
+    const Segment& s = P.seg[k - 1];
+    const V3 p = (*pose)[k - 1];
+    long best = -1;
+    for (size_t e = 0; e < s.offs.size(); ++e) {
+      V3 q{p.x + s.offs[e].x, p.y + s.offs[e].y, p.z + s.offs[e].z};
+      if (!g.inside(q.x, q.y, q.z)) continue;
+      long qi = g.index(q.x, q.y, q.z);
+      if (!V[k][qi]) continue;
+      if (!edge_free(P, p, s.sc[e])) continue;
+      if (best < 0 || qi < best) best = qi;
+    }
+    if (best < 0) return false;  // cannot happen when V_0 is non-empty
+    (*pose)[k] = at(g, best);
+  }
+  return true;
+}
+
+static bool any(const Set& s) {
+  for (uint8_t v : s)
+    if (v) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Path planning
+// ---------------------------------------------------------------------------
+
+// Guide waypoints on the reach polyline by the nominal arc parameter: the
+// collision sample points of section "Path Planning" become W points spaced
+// evenly in nominal length Lambda = sum L_k.  Waypoint j sits on segment k
+// with C_{k-1} <= j*Lambda/(W-1) < C_k (the last one on segment S), at
+// fraction r/den = (j*Lambda - C_{k-1}(W-1)) / (L_k (W-1)) of the segment,
+// rounded half up per component: g = p_{k-1} + floor((2 r D + den) / (2 den)).
+static long floor_div(long a, long b) {  // b > 0
+  long q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+
+static std::vector<V3> guide_points(const std::vector<int>& L, const std::vector<V3>& pose, int W) {
+  const int S = (int)L.size();
+  long Lam = 0;
+  for (int v : L) Lam += v;
+  std::vector<long> C(S + 1, 0);
+  for (int k = 1; k <= S; ++k) C[k] = C[k - 1] + L[k - 1];
+  std::vector<V3> g(W);
+  for (int j = 0; j < W; ++j) {
+    long num = (long)j * Lam;  // s_j * (W - 1)
+    int k = S;
+    for (int kk = 1; kk <= S; ++kk) {
+      if (C[kk - 1] * (W - 1) <= num && num < C[kk] * (W - 1)) {
+        k = kk;
+        break;
+      }
+    }
+    long r = num - C[k - 1] * (W - 1);
+    long den = (long)L[k - 1] * (W - 1);
+    const V3& a = pose[k - 1];
+    const V3& b = pose[k];
+    long D[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
+    long o[3];
+    for (int i = 0; i < 3; ++i) o[i] = floor_div(2 * r * D[i] + den, 2 * den);
+    g[j] = V3{a.x + (int)o[0], a.y + (int)o[1], a.z + (int)o[2]};
+  }
+  return g;
+}
+
+// Waypoint target set: free voxels within squared distance eps2 of g.  When
+// it is empty the radius grows one unit of eps2 at a time up to eps2_max.
+static Set waypoint_target(const Problem& P, const V3& gpt, int eps2, int eps2_max, int* used) {
+  const Grid& g = P.g;
+  Set T(g.nvox(), 0);
+  for (int e2 = eps2; e2 <= std::max(eps2, eps2_max); ++e2) {
+    bool found = false;
+    int R = 0;
+    while ((R + 1) * (R + 1) <= e2) ++R;
+    for (int z = gpt.z - R; z <= gpt.z + R; ++z)
+      for (int y = gpt.y - R; y <= gpt.y + R; ++y)
+        for (int x = gpt.x - R; x <= gpt.x + R; ++x) {
+          if (!g.inside(x, y, z)) continue;
+          if (dist2(V3{x, y, z}, gpt) > e2) continue;
+          long i = g.index(x, y, z);
+          if (P.occ[i]) continue;
+          T[i] = 1;
+          found = true;
+        }
+    if (found) {
+      *used = e2;
+      return T;
+    }
+  }
+  *used = -1;
+  return T;
+}
+
+// One smooth-chain step ("closest in configuration to the previously found
+// one" + "Filtering for smoothness"): with every joint k restricted to
+// C_k = V_k & Ball(ref_k, delta), find the chains root -> ... -> end in V_S,
+// by forward restriction then backward restriction, and take the
+// minimum-linear-index traceback.  Returns false when no chain fits.
+static bool smooth_step(const Problem& P, const std::vector<Set>& V, const std::vector<V3>& ref,
+                        long delta, std::vector<V3>* pose) {
+  const Grid& g = P.g;
+  const int S = P.S();
+  const long d2 = delta * delta;
+  auto in_ball = [&](int k, long i) { return dist2(at(g, i), ref[k]) <= d2; };
+  const V3 root = ref[0];
+  long root_i = g.index(root.x, root.y, root.z);
+  if (!V[0][root_i]) return false;
+  // forward restriction
+  std::vector<std::vector<long>> R(S + 1);
+  std::vector<Set> Rm(S + 1, Set(g.nvox(), 0));
+  R[0].push_back(root_i);
+  Rm[0][root_i] = 1;
+  for (int k = 1; k <= S; ++k) {
+    const Segment& s = P.seg[k - 1];
+    for (long pi : R[k - 1]) {
+      V3 p = at(g, pi);
+      for (size_t e = 0; e < s.offs.size(); ++e) {
+        V3 q{p.x + s.offs[e].x, p.y + s.offs[e].y, p.z + s.offs[e].z};
+        if (!g.inside(q.x, q.y, q.z)) continue;
+        long qi = g.index(q.x, q.y, q.z);
+        if (Rm[k][qi] || !V[k][qi] || !in_ball(k, qi)) continue;
+        if (!edge_free(P, p, s.sc[e])) continue;
+        Rm[k][qi] = 1;
+        R[k].push_back(qi);
+      }
+    }
+    if (R[k].empty()) return false;
+  }
+  // backward restriction
+  std::vector<Set> U(S + 1, Set(g.nvox(), 0));
+  for (long qi : R[S]) U[S][qi] = 1;
+  for (int k = S - 1; k >= 0; --k) {
+    const Segment& s = P.seg[k];
+    for (long pi : R[k]) {
+      V3 p = at(g, pi);
+      for (size_t e = 0; e < s.offs.size(); ++e) {
+        V3 q{p.x + s.offs[e].x, p.y + s.offs[e].y, p.z + s.offs[e].z};
+        if (!g.inside(q.x, q.y, q.z)) continue;
+        if (!U[k + 1][g.index(q.x, q.y, q.z)]) continue;
+        if (!edge_free(P, p, s.sc[e])) continue;
+        U[k][pi] = 1;
+        break;
+      }
+    }
+  }
+  if (!U[0][root_i]) return false;
+  return traceback_min_index(P, U, root, pose);
+}
+
+static bool pose_valid(const Problem& P, const std::vector<V3>& pose) {
+  const Grid& g = P.g;
+  for (int k = 0; k <= P.S(); ++k)
+    if (!g.inside(pose[k].x, pose[k].y, pose[k].z)) return false;
+  for (int k = 1; k <= P.S(); ++k) {
+    V3 d{pose[k].x - pose[k - 1].x, pose[k].y - pose[k - 1].y, pose[k].z - pose[k - 1].z};
+    if (!is_offset_in_shell(P.seg[k - 1], d)) return false;
+    for (const V3& v : supercover(pose[k - 1], pose[k]))
+      if (P.occ[g.index(v.x, v.y, v.z)]) return false;
+  }
+  return true;
+}
+
+static long diag2(const Grid& g) {
+  return sq(g.nx - 1) + sq(g.ny - 1) + sq(g.nz - 1);
+}
+
+// Relaxation ladder ("best done adaptively", section "Filtering for
+// smoothness"): delta, delta+1, ... until a chain is found or the ball
+// covers the whole grid (delta^2 >= squared grid diagonal), or max_relax
+// increments have been tried (max_relax < 0: no cap).  Returns the number
+// of increments used, or -1.
+static int smooth_ladder(const Problem& P, const std::vector<Set>& V, const std::vector<V3>& ref,
+                         int delta, int max_relax, std::vector<V3>* pose) {
+  if (!any(V[0])) return -1;
+  const long D2 = diag2(P.g);
+  for (int m = 0;; ++m) {
+    if (max_relax >= 0 && m > max_relax) return -1;
+    long d = (long)delta + m;
+    if (smooth_step(P, V, ref, d, pose)) return m;
+    if (d * d >= D2) return -1;
+  }
+}
+
+enum { PATH_OK = 0, PATH_RELAXED = 1, PATH_BROKEN = 2, PATH_UNREACHABLE = 3, PATH_KEPT = 4 };
+
+struct PathParams {
+  int W, delta, eps2, eps2_max, max_relax;
+};
+
+static std::vector<Set> waypoint_V(const Problem& P, const std::vector<Set>& F, const Set& T) {
+  return intersect(F, backward_sets(P, T));
+}
+
+static Problem make_problem(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                            const int32_t* hi2) {
+  Problem P;
+  P.g = Grid{nx, ny, nz};
+  P.occ = occ;
+  for (int k = 0; k < S; ++k) P.seg.push_back(make_segment(lo2[k], hi2[k]));
+  return P;
+}
+
+static std::vector<V3> read_pose(const int32_t* p, int S) {
+  std::vector<V3> v(S + 1);
+  for (int k = 0; k <= S; ++k) v[k] = V3{p[3 * k], p[3 * k + 1], p[3 * k + 2]};
+  return v;
+}
+static void write_pose(const std::vector<V3>& v, int32_t* p) {
+  for (size_t k = 0; k < v.size(); ++k) {
+    p[3 * k] = v[k].x;
+    p[3 * k + 1] = v[k].y;
+    p[3 * k + 2] = v[k].z;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_shell_bounds(int L, double tol, int* lo2, int* hi2) {
+  shell_bounds(L, tol, lo2, hi2);
+  return 0;
+}
+
+// Writes up to cap offsets (x,y,z int32 triples); returns the shell size.
+int orc_shell(int lo2, int hi2, int32_t* out, int cap) {
+  std::vector<V3> s = shell(lo2, hi2);
+  for (int i = 0; i < (int)s.size() && i < cap; ++i) {
+    out[3 * i] = s[i].x;
+    out[3 * i + 1] = s[i].y;
+    out[3 * i + 2] = s[i].z;
+  }
+  return (int)s.size();
+}
+
+// Supercover of a->b in (z,y,x) order; returns its size.
+int orc_supercover(const int32_t* a, const int32_t* b, int32_t* out, int cap) {
+  std::vector<V3> s = supercover(V3{a[0], a[1], a[2]}, V3{b[0], b[1], b[2]});
+  for (int i = 0; i < (int)s.size() && i < cap; ++i) {
+    out[3 * i] = s[i].x;
+    out[3 * i + 1] = s[i].y;
+    out[3 * i + 2] = s[i].z;
+  }
+  return (int)s.size();
+}
+
+// Occupancy from inclusive boxes (lo_xyz, hi_xyz), clipped to the grid.
+int orc_rasterize(int nx, int ny, int nz, const int32_t* boxes, int nbox, uint8_t* occ) {
+  Grid g{nx, ny, nz};
+  std::memset(occ, 0, (size_t)g.nvox());
+  for (int b = 0; b < nbox; ++b) {
+    const int32_t* B = boxes + 6 * b;
+    for (int z = std::max(0, B[2]); z <= std::min(nz - 1, B[5]); ++z)
+      for (int y = std::max(0, B[1]); y <= std::min(ny - 1, B[4]); ++y)
+        for (int x = std::max(0, B[0]); x <= std::min(nx - 1, B[3]); ++x) occ[g.index(x, y, z)] = 1;
+  }
+  return 0;
+}
+
+// F_0..F_S as bytes, [(S+1)][nvox].
+int orc_forward(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                const int32_t* hi2, const int32_t* root, uint8_t* fsets) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<Set> F = forward_sets(P, V3{root[0], root[1], root[2]});
+  for (int k = 0; k <= S; ++k) std::memcpy(fsets + (size_t)k * P.g.nvox(), F[k].data(), P.g.nvox());
+  return 0;
+}
+
+// Unmasked backward sets B_0..B_S from a target set T (bytes).
+int orc_backward(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                 const int32_t* hi2, const uint8_t* T, uint8_t* bsets) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  Set t(T, T + P.g.nvox());
+  std::vector<Set> B = backward_sets(P, t);
+  for (int k = 0; k <= S; ++k) std::memcpy(bsets + (size_t)k * P.g.nvox(), B[k].data(), P.g.nvox());
+  return 0;
+}
+
+// Reach for many point targets sharing one root: F once, then per target
+// B, V = F & B and the traceback.  poses_out [n][S+1][3], found_out [n],
+// vsets_out (nullable) [n][S+1][nvox].  Targets are split across n_threads.
+int orc_reach_many(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                   const int32_t* hi2, const int32_t* root, int n, const int32_t* targets,
+                   int32_t* poses_out, int32_t* found_out, uint8_t* vsets_out, int n_threads) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  const V3 r{root[0], root[1], root[2]};
+  std::vector<Set> F = forward_sets(P, r);
+  auto work = [&](int t0, int step) {
+    for (int t = t0; t < n; t += step) {
+      Set T(P.g.nvox(), 0);
+      V3 tv{targets[3 * t], targets[3 * t + 1], targets[3 * t + 2]};
+      if (P.g.inside(tv.x, tv.y, tv.z)) T[P.g.index(tv.x, tv.y, tv.z)] = 1;
+      std::vector<Set> V = intersect(F, backward_sets(P, T));
+      std::vector<V3> pose;
+      bool ok = traceback_min_index(P, V, r, &pose);
+      found_out[t] = ok ? 1 : 0;
+      if (!ok) pose.assign(S + 1, V3{0, 0, 0});
+      write_pose(pose, poses_out + (size_t)t * 3 * (S + 1));
+      if (vsets_out)
+        for (int k = 0; k <= S; ++k)
+          std::memcpy(vsets_out + ((size_t)t * (S + 1) + k) * P.g.nvox(), V[k].data(), P.g.nvox());
+    }
+  };
+  if (n_threads <= 1) {
+    work(0, 1);
+  } else {
+    std::vector<std::thread> th;
+    for (int i = 0; i < n_threads; ++i) th.emplace_back(work, i, n_threads);
+    for (auto& x : th) x.join();
+  }
+  return 0;
+}
+
+// Pose validity: joints inside the grid, offsets in the shells, every
+// supercover voxel free.  Returns 1 / 0.
+int orc_pose_valid(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                   const int32_t* hi2, const int32_t* pose) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  return pose_valid(P, read_pose(pose, S)) ? 1 : 0;
+}
+
+int orc_guide(int S, const int32_t* lens, const int32_t* pose, int W, int32_t* g_out) {
+  std::vector<int> L(lens, lens + S);
+  std::vector<V3> g = guide_points(L, read_pose(pose, S), W);
+  write_pose(g, g_out);
+  return 0;
+}
+
+// Waypoint target sets and their survivor sets V^(j) for all j (bytes):
+// T_j from the guide points (T_{W-1} = {end effector of the reach pose}),
+// eps2_used [W], vsets_out [W][S+1][nvox] (nullable).
+int orc_waypoint_sets(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
+                      const int32_t* lo2, const int32_t* hi2, const int32_t* reach_pose, int W,
+                      int eps2, int eps2_max, int32_t* eps2_used, uint8_t* vsets_out, int n_threads) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<V3> reach = read_pose(reach_pose, S);
+  std::vector<int> L(lens, lens + S);
+  std::vector<V3> g = guide_points(L, reach, W);
+  std::vector<Set> F = forward_sets(P, reach[0]);
+  auto work = [&](int t0, int step) {
+    for (int j = t0; j < W; j += step) {
+      Set T;
+      if (j == W - 1) {
+        T.assign(P.g.nvox(), 0);
+        T[P.g.index(reach[S].x, reach[S].y, reach[S].z)] = 1;
+        eps2_used[j] = 0;
+      } else {
+        T = waypoint_target(P, g[j], eps2, eps2_max, &eps2_used[j]);
+      }
+      std::vector<Set> V = waypoint_V(P, F, T);
+      if (vsets_out)
+        for (int k = 0; k <= S; ++k)
+          std::memcpy(vsets_out + ((size_t)j * (S + 1) + k) * P.g.nvox(), V[k].data(), P.g.nvox());
+    }
+  };
+  if (n_threads <= 1) {
+    work(0, 1);
+  } else {
+    std::vector<std::thread> th;
+    for (int i = 0; i < n_threads; ++i) th.emplace_back(work, i, n_threads);
+    for (auto& x : th) x.join();
+  }
+  return 0;
+}
+
+// Path planning ("Smooth sequence computation"): pose^(W-1) = reach pose;
+// for j = W-2 .. 0 the pose at waypoint j is the smooth step around
+// pose^(j+1) with the relaxation ladder.  A waypoint whose survivor set is
+// empty is skipped (its pose repeats pose^(j+1), record -1).
+// relax_out [W][2] = {delta increments or -1, eps2 used}.
+int orc_plan_path(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
+                  const int32_t* lo2, const int32_t* hi2, const int32_t* reach_pose, int W,
+                  int delta, int eps2, int eps2_max, int max_relax, int32_t* poses_out,
+                  int32_t* relax_out, int32_t* status_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<V3> reach = read_pose(reach_pose, S);
+  if (W < 2 || !pose_valid(P, reach)) {
+    *status_out = PATH_UNREACHABLE;
+    return -1;
+  }
+  std::vector<int> L(lens, lens + S);
+  std::vector<V3> g = guide_points(L, reach, W);
+  std::vector<Set> F = forward_sets(P, reach[0]);
+  std::vector<std::vector<V3>> poses(W);
+  poses[W - 1] = reach;
+  relax_out[2 * (W - 1)] = 0;
+  relax_out[2 * (W - 1) + 1] = 0;
+  bool relaxed = false, broken = false;
+  for (int j = W - 2; j >= 0; --j) {
+    int used = -1;
+    Set T = waypoint_target(P, g[j], eps2, eps2_max, &used);
+    if (used != eps2) relaxed = true;
+    std::vector<Set> V = waypoint_V(P, F, T);
+    std::vector<V3> pose;
+    int m = smooth_ladder(P, V, poses[j + 1], delta, max_relax, &pose);
+    relax_out[2 * j + 1] = used;
+    if (m < 0) {
+      broken = true;
+      poses[j] = poses[j + 1];
+      relax_out[2 * j] = -1;
+    } else {
+      if (m > 0) relaxed = true;
+      poses[j] = pose;
+      relax_out[2 * j] = m;
+    }
+  }
+  for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
+  *status_out = broken ? PATH_BROKEN : (relaxed ? PATH_RELAXED : PATH_OK);
+  return 0;
+}
+
+// Midcourse replan ("Dynamic Obstacles"), given the current occupancy:
+//  1. if every pose after the current index c is still valid, keep the path;
+//  2. else keep the reach pose if it is still valid, or re-solve it joint by
+//     joint from the root taking the successor in V_k closest to the old
+//     joint (squared distance, then linear index) -- the "least distance to
+//     the original path" objective applied to the reach pose that guides
+//     the path;
+//  3. guide points from that reach pose, survivor sets for j > c, and a
+//     forward smooth chain j = c+1 .. W-1 starting from pose^(c).
+int orc_replan(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
+               const int32_t* lo2, const int32_t* hi2, const int32_t* poses_in, int W, int c,
+               int delta, int eps2, int eps2_max, int max_relax, int32_t* poses_out,
+               int32_t* relax_out, int32_t* status_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<std::vector<V3>> old(W), poses(W);
+  for (int j = 0; j < W; ++j) old[j] = read_pose(poses_in + (size_t)j * 3 * (S + 1), S);
+  for (int j = 0; j < W; ++j) {
+    relax_out[2 * j] = 0;
+    relax_out[2 * j + 1] = 0;
+  }
+  bool cut = false;
+  for (int j = c + 1; j < W; ++j)
+    if (!pose_valid(P, old[j])) cut = true;
+  if (!cut) {
+    for (int j = 0; j < W; ++j) write_pose(old[j], poses_out + (size_t)j * 3 * (S + 1));
+    *status_out = PATH_KEPT;
+    return 0;
+  }
+  for (int j = 0; j <= c; ++j) poses[j] = old[j];
+  const V3 root = old[0][0];
+  std::vector<Set> F = forward_sets(P, root);
+  std::vector<V3> reach = old[W - 1];
+  if (!pose_valid(P, reach)) {
+    Set T(P.g.nvox(), 0);
+    const V3 t = old[W - 1][S];
+    T[P.g.index(t.x, t.y, t.z)] = 1;
+    std::vector<Set> V = intersect(F, backward_sets(P, T));
+    bool ok = V[0][P.g.index(root.x, root.y, root.z)] != 0;
+    if (ok) {
+      reach.assign(S + 1, V3{0, 0, 0});
+      reach[0] = root;
+      for (int k = 1; k <= S; ++k) {
+        const Segment& s = P.seg[k - 1];
+        const V3 p = reach[k - 1];
+        long best = -1, best_d = 0;
+        for (size_t e = 0; e < s.offs.size(); ++e) {
+          V3 q{p.x + s.offs[e].x, p.y + s.offs[e].y, p.z + s.offs[e].z};
+          if (!P.g.inside(q.x, q.y, q.z)) continue;
+          long qi = P.g.index(q.x, q.y, q.z);
+          if (!V[k][qi] || !edge_free(P, p, s.sc[e])) continue;
+          long dd = dist2(q, old[W - 1][k]);
+          if (best < 0 || dd < best_d || (dd == best_d && qi < best)) {
+            best = qi;
+            best_d = dd;
+          }
+        }
+        reach[k] = at(P.g, best);
+      }
+    } else {
+      for (int j = c + 1; j < W; ++j) {
+        poses[j] = old[c];
+        relax_out[2 * j] = -1;
+      }
+      for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
+      *status_out = PATH_UNREACHABLE;
+      return 0;
+    }
+  }
+  std::vector<int> L(lens, lens + S);
+  std::vector<V3> g = guide_points(L, reach, W);
+  bool relaxed = false, broken = false;
+  for (int j = c + 1; j < W; ++j) {
+    int used = 0;
+    Set T;
+    if (j == W - 1) {
+      T.assign(P.g.nvox(), 0);
+      T[P.g.index(reach[S].x, reach[S].y, reach[S].z)] = 1;
+    } else {
+      T = waypoint_target(P, g[j], eps2, eps2_max, &used);
+      if (used != eps2) relaxed = true;
+    }
+    std::vector<Set> V = waypoint_V(P, F, T);
+    std::vector<V3> pose;
+    int m = smooth_ladder(P, V, poses[j - 1], delta, max_relax, &pose);
+    relax_out[2 * j + 1] = used;
+    if (m < 0) {
+      broken = true;
+      poses[j] = poses[j - 1];
+      relax_out[2 * j] = -1;
+    } else {
+      if (m > 0) relaxed = true;
+      poses[j] = pose;
+      relax_out[2 * j] = m;
+    }
+  }
+  for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
+  *status_out = broken ? PATH_BROKEN : (relaxed ? PATH_RELAXED : PATH_OK);
+  return 0;
+}
+
+// Algorithmic work of one propagation D_k(X) in bitset words: over every
+// offset e of the shell and every 32-voxel word p (x-packed rows, Nx a
+// multiple of 32) whose shifted input X[p+e] is non-zero, count the word and
+// the supercover size of e.  Returns pairs; *sc_terms gets sum |SC(e)| over
+// the counted pairs.
+long orc_count_pairs(int nx, int ny, int nz, int lo2, int hi2, const uint8_t* X, long* sc_terms) {
+  Grid g{nx, ny, nz};
+  Segment s = make_segment(lo2, hi2);
+  long pairs = 0, terms = 0;
+  const int W = nx / 32;
+  for (size_t e = 0; e < s.offs.size(); ++e) {
+    const V3 d = s.offs[e];
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int w = 0; w < W; ++w) {
+          bool nz_word = false;
+          for (int b = 0; b < 32 && !nz_word; ++b) {
+            int x = 32 * w + b;
+            V3 q{x + d.x, y + d.y, z + d.z};
+            if (g.inside(q.x, q.y, q.z) && X[g.index(q.x, q.y, q.z)]) nz_word = true;
+          }
+          if (nz_word) {
+            ++pairs;
+            terms += (long)s.sc[e].size();
+          }
+        }
+  }
+  *sc_terms = terms;
+  return pairs;
+}
+
+}  // extern "C"

@@ -1,0 +1,547 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against a worked example, a closed form, an
+invariant, or brute-force enumeration on a tiny grid (``bruteforce.py``,
+which shares no code with the oracle).  The tests are chosen so that a
+dropped term, a wrong sign, a wrong index or a transposed operand in the
+oracle fails at least one of them (see ``test_planted_mistakes``).
+"""
+import os
+from fractions import Fraction
+from math import floor
+
+import numpy as np
+import pytest
+
+import bruteforce as BF
+import oracle as O
+import scenegen as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_scene(rng, shape, n_boxes, side_hi, keep=()):
+    nx, ny, nz = shape
+    boxes = []
+    while len(boxes) < n_boxes:
+        s = rng.integers(1, side_hi + 1, 3)
+        c = rng.integers(0, [nx, ny, nz])
+        b = [int(c[0]), int(c[1]), int(c[2]), int(c[0] + s[0] - 1), int(c[1] + s[1] - 1),
+             int(c[2] + s[2] - 1)]
+        if any(all(b[a] <= p[a] <= b[a + 3] for a in range(3)) for p in keep):
+            continue
+        boxes.append(b)
+    return np.asarray(boxes, np.int32).reshape(-1, 6)
+
+
+# --------------------------------------------------------------------- shells
+
+def test_shell_bounds_closed_form():
+    # tol = 1/2 with integer L: (L - 1/2)^2 = L^2 - L + 1/4, (L + 1/2)^2 = L^2 + L + 1/4
+    for L in range(1, 40):
+        assert O.shell_bounds(L, 0.5) == (L * L - L + 1, L * L + L)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 13, 20])
+def test_shell_matches_mesh_and_order(L):
+    lo, hi = O.shell_bounds(L)
+    sh = O.shell(lo, hi)
+    ref = BF.shell_offsets(lo, hi)
+    assert set(map(tuple, sh.tolist())) == set(map(tuple, ref.tolist()))
+    assert len(sh) == len(ref)
+    key = [(int(d @ d), int(d[2]), int(d[1]), int(d[0])) for d in sh.astype(np.int64)]
+    assert key == sorted(key)
+
+
+def test_shell_symmetric():
+    lo, hi = O.shell_bounds(7)
+    s = set(map(tuple, O.shell(lo, hi).tolist()))
+    assert s == {(-a, -b, -c) for a, b, c in s}
+    assert s == {(b, c, a) for a, b, c in s}
+
+
+# ----------------------------------------------------------------- supercover
+
+def test_supercover_worked_examples():
+    with open(os.path.join(GOLDEN, "supercover_examples.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            seg, vox = line.split("|")
+            a_b = [int(v) for v in seg.split()]
+            want = {tuple(int(v) for v in t.split()) for t in vox.split(";")}
+            got = set(map(tuple, O.supercover(a_b[:3], a_b[3:]).tolist()))
+            assert got == want, line
+
+
+def test_supercover_vs_chebyshev_every_small_offset():
+    for lo, hi in [(1, 12), (13, 30)]:
+        for d in BF.shell_offsets(lo, hi):
+            d = tuple(int(v) for v in d)
+            got = set(map(tuple, O.supercover((0, 0, 0), d).tolist()))
+            assert got == set(BF.supercover_from_origin(d)), d
+
+
+def test_supercover_vs_chebyshev_random_segments():
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        a = tuple(int(v) for v in rng.integers(-6, 7, 3))
+        b = tuple(int(v) for v in rng.integers(-6, 7, 3))
+        got = set(map(tuple, O.supercover(a, b).tolist()))
+        assert got == set(BF.supercover(a, b)), (a, b)
+
+
+def test_supercover_translation_and_reversal():
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        p = rng.integers(-20, 20, 3)
+        d = rng.integers(-9, 10, 3)
+        base = {tuple(v) for v in O.supercover((0, 0, 0), d).tolist()}
+        moved = {tuple(v) for v in O.supercover(p, p + d).tolist()}
+        assert moved == {tuple(np.asarray(v) + p) for v in base}
+        back = {tuple(v) for v in O.supercover(p + d, p).tolist()}
+        assert back == moved
+
+
+def test_supercover_contains_endpoints_and_is_in_bbox():
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        a = rng.integers(0, 30, 3)
+        b = rng.integers(0, 30, 3)
+        sc = O.supercover(a, b)
+        s = set(map(tuple, sc.tolist()))
+        assert tuple(a) in s and tuple(b) in s
+        assert (sc >= np.minimum(a, b)).all() and (sc <= np.maximum(a, b)).all()
+
+
+# ------------------------------------------------------------------ rasterize
+
+def test_rasterize_matches_numpy_fill():
+    rng = np.random.default_rng(1)
+    boxes = _rand_scene(rng, (20, 17, 13), 12, 7)
+    boxes[0] = [-3, -3, -3, 2, 2, 2]  # clipped at the low faces
+    boxes[1] = [15, 10, 8, 40, 40, 40]  # clipped at the high faces
+    occ = O.rasterize((20, 17, 13), boxes)
+    assert (occ.astype(bool) == BF.occupancy((20, 17, 13), boxes)).all()
+
+
+# ------------------------------------------------ sets and reach, brute force
+
+TINY = [
+    # shape, lengths, n_boxes, seed
+    ((9, 8, 7), (3, 2, 2), 4, 0),
+    ((8, 8, 8), (2, 3, 2), 6, 1),
+    ((10, 7, 6), (3, 3), 5, 2),
+    ((7, 7, 7), (2, 2, 2), 3, 3),
+    ((9, 9, 5), (4, 2, 2), 5, 4),
+]
+
+
+@pytest.mark.parametrize("shape,lengths,n_boxes,seed", TINY)
+def test_sets_and_reach_vs_enumeration(shape, lengths, n_boxes, seed):
+    rng = np.random.default_rng(100 + seed)
+    nx, ny, nz = shape
+    root = (nx // 2, ny // 2, 0)
+    boxes = _rand_scene(rng, shape, n_boxes, 3, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    ch = BF.Chains(BF.occupancy(shape, boxes), bounds)
+    F = O.forward(occ, lengths, root)
+    # several targets, including occupied and unreachable ones
+    targets = [tuple(int(v) for v in rng.integers(0, [nx, ny, nz])) for _ in range(6)]
+    targets.append(root)
+    poses, found, vs = O.reach_many(occ, lengths, root, targets, want_sets=True)
+    for i, t in enumerate(targets):
+        Fb, Vb, good = ch.joint_sets(root, [t])
+        for k in range(len(lengths) + 1):
+            assert BF.to_set(F[k]) == Fb[k], ("F", k)
+            assert BF.to_set(vs[i, k]) == Vb[k], ("V", t, k)
+        assert bool(found[i]) == bool(good), t
+        if good:
+            assert tuple(map(tuple, poses[i].tolist())) == ch.lexmin(good), t
+
+
+def test_backward_sets_vs_enumeration():
+    shape, lengths = (8, 7, 6), (3, 2, 2)
+    rng = np.random.default_rng(11)
+    boxes = _rand_scene(rng, shape, 4, 3)
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    ch = BF.Chains(BF.occupancy(shape, boxes), bounds)
+    T = np.zeros(occ.shape, np.uint8)
+    t = (4, 3, 2)
+    T[t[2], t[1], t[0]] = 1
+    B = O.backward(occ, lengths, T)
+    S = len(lengths)
+    for k in range(S + 1):
+        # B_k = voxels p from which segments k+1..S reach t
+        want = set()
+        for z in range(shape[2]):
+            for y in range(shape[1]):
+                for x in range(shape[0]):
+                    p = (x, y, z)
+                    if not ch.free(p):
+                        continue
+                    for chain in _chains_from(ch, p, k, S):
+                        if chain[-1] == t:
+                            want.add(p)
+                            break
+        assert BF.to_set(B[k]) == want, k
+
+
+def _chains_from(ch, p, k, S):
+    if k == S:
+        yield (p,)
+        return
+    for d in ch.offs[k]:
+        q = (p[0] + d[0], p[1] + d[1], p[2] + d[2])
+        if ch.inside(q) and ch.edge(p, q):
+            for rest in _chains_from(ch, q, k + 1, S):
+                yield (p,) + rest
+
+
+# --------------------------------------------------------------- closed forms
+
+def test_free_space_closed_forms():
+    shape = (24, 22, 20)
+    occ = np.zeros((20, 22, 24), np.uint8)
+    lengths = (5, 4)
+    root, t = (12, 11, 0), (15, 16, 6)
+    F = O.forward(occ, lengths, root)
+    lo1, hi1 = O.shell_bounds(5)
+    lo2, hi2 = O.shell_bounds(4)
+    sh1 = BF.shell_offsets(lo1, hi1)
+    sh2 = BF.shell_offsets(lo2, hi2)
+    inside = lambda p: 0 <= p[0] < 24 and 0 <= p[1] < 22 and 0 <= p[2] < 20
+    want_f1 = {tuple(int(v) for v in np.asarray(root) + d) for d in sh1}
+    want_f1 = {p for p in want_f1 if inside(p)}
+    assert BF.to_set(F[1]) == want_f1
+    _, found, vs = O.reach_many(occ, lengths, root, [t], want_sets=True)
+    want_v1 = want_f1 & {tuple(int(v) for v in np.asarray(t) - d) for d in sh2}
+    assert BF.to_set(vs[0, 1]) == want_v1
+    assert bool(found[0]) == bool(want_v1)
+
+
+def test_one_segment_iff():
+    rng = np.random.default_rng(9)
+    shape = (16, 16, 16)
+    boxes = _rand_scene(rng, shape, 10, 3, keep=[(8, 8, 0)])
+    occ = O.rasterize(shape, boxes)
+    occb = occ.astype(bool)
+    root = (8, 8, 0)
+    lo, hi = O.shell_bounds(6)
+    targets = [tuple(int(v) for v in rng.integers(0, 16, 3)) for _ in range(60)]
+    _, found, _ = O.reach_many(occ, (6,), root, targets)
+    for t, f in zip(targets, found):
+        d = np.asarray(t) - np.asarray(root)
+        ok = lo <= int(d @ d) <= hi and all(not occb[v[2], v[1], v[0]]
+                                             for v in BF.supercover(root, t))
+        assert bool(f) == ok, t
+
+
+def test_empty_beyond_reach_and_occupied_endpoints():
+    sc = G.c1_scene(0)
+    occ = O.rasterize(sc.shape, sc.boxes)
+    reach = sum(L + 0.5 for L in sc.lengths)
+    far = [t for t in [(0, 0, 31), (31, 31, 31), (0, 31, 31)]
+           if sum((a - b) ** 2 for a, b in zip(t, sc.root)) > reach ** 2]
+    occd = np.argwhere(occ)[:3][:, ::-1]  # occupied voxels as (x, y, z)
+    targets = far + [tuple(int(v) for v in p) for p in occd]
+    _, found, _ = O.reach_many(occ, sc.lengths, sc.root, targets)
+    assert not found.any()
+    # an occupied root: nothing is reachable
+    b = np.concatenate([sc.boxes, [[16, 16, 0, 16, 16, 0]]]).astype(np.int32)
+    occ2 = O.rasterize(sc.shape, b)
+    F = O.forward(occ2, sc.lengths, sc.root)
+    assert F.sum() == 0
+
+
+# ------------------------------------------------- dualities and monotonicity
+
+def test_reverse_arm_duality():
+    rng = np.random.default_rng(21)
+    shape = (14, 13, 12)
+    boxes = _rand_scene(rng, shape, 8, 3)
+    occ = O.rasterize(shape, boxes)
+    lengths = (4, 3, 5)
+    free = np.argwhere(occ == 0)[:, ::-1]
+    for trial in range(4):
+        r = tuple(int(v) for v in free[rng.integers(len(free))])
+        t = tuple(int(v) for v in free[rng.integers(len(free))])
+        _, f1, v1 = O.reach_many(occ, lengths, r, [t], want_sets=True)
+        _, f2, v2 = O.reach_many(occ, lengths[::-1], t, [r], want_sets=True)
+        assert f1[0] == f2[0]
+        S = len(lengths)
+        for k in range(S + 1):
+            assert (v1[0, k] == v2[0, S - k]).all(), (trial, k)
+
+
+def test_mirror_symmetry():
+    rng = np.random.default_rng(22)
+    shape = (16, 12, 10)
+    boxes = _rand_scene(rng, shape, 8, 3, keep=[(7, 6, 0)])
+    occ = O.rasterize(shape, boxes)
+    lengths = (4, 4, 3)
+    r, t = (7, 6, 0), (10, 8, 5)
+    _, _, v1 = O.reach_many(occ, lengths, r, [t], want_sets=True)
+    occ_m = occ[:, :, ::-1].copy()
+    rm, tm = (shape[0] - 1 - r[0], r[1], r[2]), (shape[0] - 1 - t[0], t[1], t[2])
+    _, _, v2 = O.reach_many(occ_m, lengths, rm, [tm], want_sets=True)
+    assert (v1[0][..., ::-1] == v2[0]).all()
+
+
+def test_monotone_in_obstacles():
+    rng = np.random.default_rng(23)
+    shape = (16, 16, 12)
+    root = (8, 8, 0)
+    boxes = _rand_scene(rng, shape, 6, 3, keep=[root])
+    more = np.concatenate([boxes, _rand_scene(rng, shape, 6, 3, keep=[root])])
+    occ_a = O.rasterize(shape, boxes)
+    occ_b = O.rasterize(shape, more)
+    lengths = (5, 4, 3)
+    t = (10, 12, 5)
+    Fa = O.forward(occ_a, lengths, root)
+    Fb = O.forward(occ_b, lengths, root)
+    assert (Fb <= Fa).all()
+    _, _, va = O.reach_many(occ_a, lengths, root, [t], want_sets=True)
+    _, _, vb = O.reach_many(occ_b, lengths, root, [t], want_sets=True)
+    assert (vb <= va).all()
+
+
+def test_v_subset_of_f_and_pose_invariants_c1():
+    for seed in range(3):
+        sc = G.c1_scene(seed)
+        occ = O.rasterize(sc.shape, sc.boxes)
+        targets = G.draw_targets(sc, 3, seed)
+        F = O.forward(occ, sc.lengths, sc.root)
+        poses, found, vs = O.reach_many(occ, sc.lengths, sc.root, targets, want_sets=True)
+        for i, t in enumerate(targets):
+            assert (vs[i] <= F).all()
+            if not found[i]:
+                continue
+            p = poses[i]
+            assert tuple(p[0]) == sc.root and tuple(p[-1]) == tuple(t)
+            assert O.pose_valid(occ, sc.lengths, p)
+            for k, L in enumerate(sc.lengths, start=1):
+                d = p[k] - p[k - 1]
+                assert L * L - L + 1 <= int(d @ d) <= L * L + L
+                assert vs[i, k, p[k][2], p[k][1], p[k][0]]
+
+
+# ----------------------------------------------------------------- guide
+
+def _guide_fraction(lengths, pose, W):
+    """Guide points by exact rational arc parameter, rounding half up."""
+    lam = sum(lengths)
+    C = np.concatenate([[0], np.cumsum(lengths)])
+    out = []
+    for j in range(W):
+        s = Fraction(j * lam, W - 1)
+        k = len(lengths)
+        for kk in range(1, len(lengths) + 1):
+            if C[kk - 1] <= s < C[kk]:
+                k = kk
+                break
+        f = (s - int(C[k - 1])) / lengths[k - 1]
+        a, b = pose[k - 1], pose[k]
+        out.append(tuple(int(a[i]) + floor(f * int(b[i] - a[i]) + Fraction(1, 2))
+                         for i in range(3)))
+    return out
+
+
+def test_guide_against_rational_rule():
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        S = int(rng.integers(2, 9))
+        lengths = [int(v) for v in rng.integers(2, 25, S)]
+        pose = np.cumsum(np.concatenate([[rng.integers(0, 50, 3)],
+                                         rng.integers(-20, 21, (S, 3))]), axis=0)
+        W = int(rng.integers(2, 40))
+        g = O.guide(lengths, pose, W)
+        assert [tuple(v) for v in g.tolist()] == _guide_fraction(lengths, pose, W)
+        assert tuple(g[0]) == tuple(pose[0]) and tuple(g[-1]) == tuple(pose[-1])
+
+
+def test_guide_straight_arm():
+    lengths = [4, 3, 5]
+    pose = np.array([[0, 0, 0], [4, 0, 0], [7, 0, 0], [12, 0, 0]])
+    g = O.guide(lengths, pose, 7)  # spacing 2 along x
+    assert g[:, 0].tolist() == [0, 2, 4, 6, 8, 10, 12]
+    assert (g[:, 1:] == 0).all()
+
+
+# ---------------------------------------------------------------- path (tiny)
+
+def _ball_chains(ch, root, ref, delta, targets):
+    """All valid chains with joint k within delta of ref[k], ending in targets."""
+    out = []
+    S = ch.S
+    d2 = delta * delta
+
+    def rec(chain, k):
+        if k > S:
+            if chain[-1] in targets:
+                out.append(tuple(chain))
+            return
+        p = chain[-1]
+        for d in ch.offs[k - 1]:
+            q = (p[0] + d[0], p[1] + d[1], p[2] + d[2])
+            if not ch.inside(q):
+                continue
+            if sum((q[i] - ref[k][i]) ** 2 for i in range(3)) > d2:
+                continue
+            if ch.edge(p, q):
+                chain.append(q)
+                rec(chain, k + 1)
+                chain.pop()
+
+    rec([root], 1)
+    return out
+
+
+def _brute_plan(ch, lengths, reach, W, delta, eps2, eps2_max):
+    """The planning rule with each smooth step solved by enumeration."""
+    S = len(lengths)
+    g = _guide_fraction(lengths, reach, W)
+    poses = [None] * W
+    relax = [[0, 0] for _ in range(W)]
+    poses[W - 1] = tuple(map(tuple, np.asarray(reach).tolist()))
+    root = poses[W - 1][0]
+    diag2 = (ch.nx - 1) ** 2 + (ch.ny - 1) ** 2 + (ch.nz - 1) ** 2
+    for j in range(W - 2, -1, -1):
+        T, used = set(), -1
+        for e2 in range(eps2, max(eps2, eps2_max) + 1):
+            T = {(x, y, z) for z in range(ch.nz) for y in range(ch.ny) for x in range(ch.nx)
+                 if (x - g[j][0]) ** 2 + (y - g[j][1]) ** 2 + (z - g[j][2]) ** 2 <= e2
+                 and ch.free((x, y, z))}
+            if T:
+                used = e2
+                break
+        relax[j][1] = used
+        ref = poses[j + 1]
+        m = 0
+        while True:
+            d = delta + m
+            good = _ball_chains(ch, root, ref, d, T)
+            if good:
+                poses[j] = ch.lexmin(good)
+                relax[j][0] = m
+                break
+            if d * d >= diag2:
+                poses[j] = ref
+                relax[j][0] = -1
+                break
+            m += 1
+    return poses, relax
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plan_path_vs_enumeration(seed):
+    rng = np.random.default_rng(300 + seed)
+    shape = (10, 10, 8)
+    lengths = (3, 3, 2)
+    root = (5, 5, 0)
+    boxes = _rand_scene(rng, shape, 5, 2, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    ch = BF.Chains(BF.occupancy(shape, boxes), bounds)
+    free = np.argwhere(occ == 0)[:, ::-1]
+    # a reachable target
+    for _ in range(50):
+        t = tuple(int(v) for v in free[rng.integers(len(free))])
+        poses, found, _ = O.reach_many(occ, lengths, root, [t])
+        if found[0]:
+            break
+    assert found[0]
+    reach = poses[0]
+    W, delta = 6, 1
+    p_o, r_o, st = O.plan_path(occ, lengths, reach, W, delta=delta, eps2=1, eps2_max=4)
+    p_b, r_b = _brute_plan(ch, lengths, reach, W, delta, 1, 4)
+    assert [tuple(map(tuple, p.tolist())) for p in p_o] == p_b
+    assert r_o.tolist() == r_b
+    want = (O.PATH_BROKEN if any(r[0] < 0 for r in r_b) else
+            O.PATH_RELAXED if any(r[0] > 0 or (r[1] != 1) for r in r_b[:-1]) else O.PATH_OK)
+    assert st == want
+
+
+def test_plan_path_invariants_c1():
+    sc = G.c1_scene(1)
+    occ = O.rasterize(sc.shape, sc.boxes)
+    targets = G.draw_targets(sc, 2, 1)
+    poses, found, _ = O.reach_many(occ, sc.lengths, sc.root, targets)
+    for i in range(len(targets)):
+        if not found[i]:
+            continue
+        W = 8
+        path, relax, st = O.plan_path(occ, sc.lengths, poses[i], W, delta=3)
+        g = O.guide(sc.lengths, poses[i], W)
+        assert (path[-1] == poses[i]).all()
+        for j in range(W):
+            assert O.pose_valid(occ, sc.lengths, path[j])
+            assert tuple(path[j][0]) == sc.root
+            if j < W - 1 and relax[j][0] >= 0:
+                e = path[j][-1] - g[j]
+                assert int(e @ e) <= relax[j][1]
+                step = path[j] - path[j + 1]
+                d = 3 + relax[j][0]
+                assert (np.sum(step * step, axis=1) <= d * d).all()
+
+
+# -------------------------------------------------------------------- replan
+
+def test_replan_keeps_valid_path_and_fixes_cut():
+    sc = G.c1_scene(2)
+    occ = O.rasterize(sc.shape, sc.boxes)
+    targets = G.draw_targets(sc, 4, 2)
+    poses, found, _ = O.reach_many(occ, sc.lengths, sc.root, targets)
+    i = int(np.argmax(found))
+    W = 8
+    path, relax, st = O.plan_path(occ, sc.lengths, poses[i], W)
+    kept, _, st2 = O.replan(occ, sc.lengths, path, 2)
+    assert st2 == O.PATH_KEPT and (kept == path).all()
+    # cut the path: put a small box on a mid-path joint of a later pose
+    j = W - 3
+    v = path[j][2]
+    box = np.array([[v[0], v[1], v[2], v[0], v[1], v[2]]], np.int32)
+    occ2 = O.rasterize(sc.shape, np.concatenate([sc.boxes, box]))
+    assert not O.pose_valid(occ2, sc.lengths, path[j])
+    new, relax2, st3 = O.replan(occ2, sc.lengths, path, 2)
+    assert st3 != O.PATH_KEPT
+    assert (new[:3] == path[:3]).all()
+    if st3 in (O.PATH_OK, O.PATH_RELAXED):
+        for jj in range(3, W):
+            assert O.pose_valid(occ2, sc.lengths, new[jj])
+            step = new[jj] - new[jj - 1]
+            d = 3 + relax2[jj][0]
+            assert (np.sum(step * step, axis=1) <= d * d).all()
+
+
+# ---------------------------------------------------------------- generators
+
+def test_splitmix64_published_outputs():
+    # splitmix64 from state 0: published first outputs of the generator
+    r = G.SplitMix64(0, 0)
+    assert [r.next_u64() for _ in range(3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_lemire_uniform_and_range():
+    r = G.SplitMix64(5, 1)
+    xs = [r.below(7) for _ in range(7000)]
+    assert min(xs) == 0 and max(xs) == 6
+    counts = np.bincount(xs, minlength=7)
+    assert (np.abs(counts - 1000) < 150).all()
+
+
+def test_scene_shapes():
+    sc = G.c2_scene(1)
+    assert sc.boxes.shape == (200, 6) and sc.shape == (128, 128, 128)
+    assert not sc.point_occupied(sc.root)
+    sides = sc.boxes[:, 3:] - sc.boxes[:, :3] + 1
+    assert sides.min() >= 1 and sides.max() <= 24
+    t = G.draw_targets(sc, 16, 1)
+    reach = sum(sc.lengths)
+    for p in t:
+        assert not sc.point_occupied(tuple(p))
+        assert int(((p - np.asarray(sc.root)) ** 2).sum()) <= reach * reach
