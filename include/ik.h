@@ -1,0 +1,239 @@
+/*
+ * ik.h -- C ABI of the B300 gap map-seeking inverse-kinematics library.
+ *
+ * The library solves the problem stated in the paper's Introduction (eq 1):
+ * find a chain of segment translations that takes the arm root p_root to the
+ * end-effector target p_end, among obstacles, then a smooth sequence of poses
+ * along the way (section "Path Planning") and, when obstacles move, a new
+ * remainder of that sequence (section "Dynamic Obstacles").
+ *
+ * Lattice form used throughout (the paper's quiver and n-point collision
+ * test restated exactly on the voxel grid):
+ *   - the grid is nx * ny * nz unit voxels, nx a multiple of 32; a voxel set
+ *     is a bit-packed array of uint32 words, x fastest: voxel (x, y, z) is bit
+ *     (x % 32) of word (z * ny + y) * (nx / 32) + x / 32;
+ *   - occupancy uses 1 = occupied (the paper's mask, section "The
+ *     representations of the arm and obstacles", stores 0 for obstacles; the
+ *     meaning is the same);
+ *   - segment k of nominal length L_k may take any integer offset d with
+ *     lo2 <= |d|^2 <= hi2, lo2 = max(1, ceil((L_k - tol)^2)),
+ *     hi2 = floor((L_k + tol)^2), evaluated in double precision ("shell";
+ *     stands in for the quiver of section "Discretization of the segment
+ *     articulations" and the epsilon on the gap vector of "The gap in gMS");
+ *   - a segment p->q is obstacle-free when every voxel whose closed unit cube
+ *     meets the closed segment is free (closed supercover; stands in for the
+ *     n sample points of "Testing for collisions");
+ *   - a pose is int32 [n_seg + 1][3] joint positions (x, y, z), p_0 = root.
+ *
+ * Conventions for every call:
+ *   - return value: IK_OK (0) or a negative IK_ERR_* code; nothing throws
+ *     across the ABI; "no solution" is not an error (found = 0, or a path
+ *     status);
+ *   - ownership: the caller owns every buffer it passes; the library owns the
+ *     grid's device state (occupancy, shell tables, edge masks, reachable
+ *     sets, scratch) from ik_create_grid until ik_destroy_grid;
+ *   - pointers are host pointers unless a call takes an `on_device` flag and
+ *     it is non-zero, in which case the listed arrays are device pointers of
+ *     the grid's device;
+ *   - calls are synchronous on the grid's CUDA stream; a handle must not be
+ *     used from two threads at once;
+ *   - on a GPU fault or a failed allocation the call returns IK_ERR_CUDA or
+ *     IK_ERR_OOM; ik_last_error_message() gives the CUDA error text.
+ */
+#ifndef IK_B300_H
+#define IK_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IK_API __attribute__((visibility("default")))
+#else
+#define IK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- return codes */
+#define IK_OK 0
+#define IK_ERR_ARG -1         /* invalid argument (sizes, coordinates, NULL) */
+#define IK_ERR_OOM -2         /* device or host allocation failed */
+#define IK_ERR_CUDA -3        /* a CUDA call failed */
+#define IK_ERR_TIMEOUT -4     /* a bounded device-side wait ran out */
+#define IK_ERR_STATE -5       /* call made in the wrong state (e.g. no obstacles set) */
+#define IK_ERR_UNSUPPORTED -6 /* valid request beyond this build's limits */
+
+/* ------------------------------------------------------------ path status */
+#define IK_PATH_OK 0          /* every waypoint solved with the nominal filter */
+#define IK_PATH_RELAXED 1     /* some waypoint needed a wider filter or target ball */
+#define IK_PATH_BROKEN 2      /* some waypoint had no solution; it repeats its neighbour */
+#define IK_PATH_UNREACHABLE 3 /* no reach pose exists (or the given one is invalid) */
+#define IK_PATH_KEPT 4        /* replan: the remainder is still valid and unchanged */
+
+typedef struct ik_grid_s* ik_grid;
+
+/* An arm: n_seg segments (1..IK_MAX_SEG) of integer nominal lengths
+ * len[k] >= 1 voxels (k = 0 is the segment at the root), and the shell
+ * tolerance tol (0.5 by default: the shell of L is then exactly
+ * L^2 - L + 1 <= |d|^2 <= L^2 + L). */
+#define IK_MAX_SEG 16
+#define IK_MAX_LEN 100
+typedef struct {
+  int32_t n_seg;
+  const int32_t* len;
+  float tol;
+} ik_arm;
+
+/* Path parameters (sections "Smooth sequence computation", "Filtering for
+ * smoothness"):
+ *   n_way      number of waypoints W >= 2; waypoint 0 is the root, W-1 the target;
+ *   delta      each joint moves at most delta voxels (Euclidean) between
+ *              consecutive poses; on failure at a waypoint the bound grows by
+ *              one voxel at a time ("best done adaptively");
+ *   eps2       the end effector lands within squared distance eps2 of the
+ *              waypoint ("a greater epsilon"); if no free voxel is that close
+ *              the radius grows by one unit of eps2 up to eps2_max;
+ *   max_relax  cap on the number of delta increments, -1 = until the ball
+ *              covers the grid. */
+typedef struct {
+  int32_t n_way;
+  int32_t delta;
+  int32_t eps2;
+  int32_t eps2_max;
+  int32_t max_relax;
+} ik_path_params;
+
+/* ---------------------------------------------------------- housekeeping */
+IK_API int ik_version(void);
+IK_API const char* ik_strerror(int code);
+/* Text of the last CUDA error seen by this process ("" if none). */
+IK_API const char* ik_last_error_message(void);
+
+/* Create a grid on the current CUDA device.  nx % 32 == 0, each extent in
+ * [32, 1024] for nx and [1, 1024] for ny, nz.  cuda_stream may be NULL (the
+ * legacy default stream).  The occupancy starts all free. */
+IK_API int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out);
+IK_API int ik_destroy_grid(ik_grid g);
+/* Number of uint32 words of one voxel set of this grid. */
+IK_API size_t ik_grid_words(ik_grid g);
+
+/* ---------------------------------------------------- obstacles (step a1) */
+/* Replace the occupancy with a bit-packed set (1 = occupied), n_words =
+ * ik_grid_words(g).  Bits of x >= nx do not exist (nx % 32 == 0). */
+IK_API int ik_set_obstacles(ik_grid g, const uint32_t* occ_words, size_t n_words, int on_device);
+/* Replace the occupancy with the union of n_boxes inclusive boxes
+ * boxes[i] = {lo_x, lo_y, lo_z, hi_x, hi_y, hi_z}, clipped to the grid (empty
+ * boxes are allowed).  The boxes are rasterised on the GPU. */
+IK_API int ik_set_boxes(ik_grid g, const int32_t* boxes, int n_boxes, int on_device);
+IK_API int ik_get_obstacles(ik_grid g, uint32_t* occ_words, size_t n_words, int on_device);
+
+/* ------------------------------------------------- reach IK (steps a3-a5) */
+/* Forward reachable sets F_0..F_S (section "The procedure for IK solution",
+ * Steps 1 and 2A): F_0 = {root} if free, F_k = every voxel reachable from
+ * F_{k-1} by an admissible obstacle-free segment k.  fsets_out is
+ * [n_seg + 1][ik_grid_words(g)].  F is cached per (occupancy, root, arm). */
+IK_API int ik_forward_sets(ik_grid g, const ik_arm* arm, const int32_t root[3], uint32_t* fsets_out,
+                    int on_device);
+
+/* Reach pose for one target (Steps 1, 2A, 2B and 3): the survivor sets
+ * V_k = F_k & B_k (joint-k positions on some valid chain root -> target,
+ * B_k the backward sets from the target) and the chosen pose: p_0 = root,
+ * p_k = the voxel of V_k with the smallest linear index reachable from
+ * p_{k-1} by a valid segment.  pose_out [n_seg + 1][3]; vsets_out nullable,
+ * [n_seg + 1][words]; *found = 1 when a pose exists.  Root and target must be
+ * inside the grid (else IK_ERR_ARG); an occupied root or target gives
+ * found = 0. */
+IK_API int ik_solve_reach(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t target[3],
+                   int32_t* pose_out, uint32_t* vsets_out, int* found);
+
+/* The same for n targets sharing one root, solved together in batched
+ * launches (one backward launch per segment for all targets).  targets
+ * [n][3]; poses_out [n][n_seg + 1][3]; found_out [n]; vsets_out nullable
+ * [n][n_seg + 1][words].  With on_device != 0 all four arrays are device
+ * pointers. */
+IK_API int ik_solve_reach_many(ik_grid g, const ik_arm* arm, const int32_t root[3],
+                        const int32_t* targets, int n, int32_t* poses_out, int32_t* found_out,
+                        uint32_t* vsets_out, int on_device);
+
+/* -------------------------------------------------- path (steps a6 - a8) */
+/* Guide waypoints on a reach pose (section "Path Planning"): W points spaced
+ * evenly in nominal arc length Lambda = sum L_k along the polyline
+ * p_0 .. p_S.  Waypoint j lies on segment k with
+ * C_{k-1} <= j Lambda / (W-1) < C_k (C_k the cumulative nominal length; the
+ * last waypoint on segment S) at fraction r / den,
+ * r = j Lambda - C_{k-1} (W-1), den = L_k (W-1), rounded half up per
+ * component: g_j = p_{k-1} + floor((2 r (p_k - p_{k-1}) + den) / (2 den)).
+ * g_0 = root, g_{W-1} = end effector.  g_out [n_way][3]. */
+IK_API int ik_guide(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way, int32_t* g_out);
+
+/* Survivor sets of every waypoint of one path in one batched pass (one
+ * full IK per waypoint, section "Implementation Performance"):
+ * T_j = free voxels within squared distance eps2 of g_j (grown up to
+ * eps2_max when empty; T_{W-1} = {end effector of the reach pose}),
+ * V^(j)_k = F_k & B^(j)_k.  eps2_used [n_way] (-1: no free voxel even at
+ * eps2_max); vsets_out nullable [n_way][n_seg + 1][words]. */
+IK_API int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way, int eps2,
+                     int eps2_max, int32_t* eps2_used, uint32_t* vsets_out);
+
+/* Smooth path to a reach pose (sections "Smooth sequence computation" and
+ * "Filtering for smoothness"): pose^(W-1) = reach pose; for j = W-2 .. 0,
+ * pose^(j) is the minimum-linear-index chain (joint by joint from the root)
+ * among the chains with every joint k in V^(j)_k and within delta + m of
+ * joint k of pose^(j+1), for the smallest m >= 0 that admits one.  A
+ * waypoint whose survivor set is empty (or whose m would pass max_relax)
+ * repeats pose^(j+1) and records m = -1.
+ * poses_out [n_way][n_seg + 1][3]; relax_out [n_way][2] = {m, eps2 used};
+ * *status = IK_PATH_OK / RELAXED / BROKEN, or UNREACHABLE when the reach
+ * pose is not a valid pose of this arm and grid. */
+IK_API int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const ik_path_params* pp,
+                 int32_t* poses_out, int32_t* relax_out, int* status);
+
+/* Reach + path for n targets sharing one root, all in batched launches with
+ * no host round trip between steps: reach survivor sets and poses for all
+ * targets, then the survivor sets of all n * n_way waypoints in one batched
+ * backward pass per segment, then one smooth-chain block per path.
+ * targets [n][3]; reach_out [n][n_seg + 1][3]; found_out [n];
+ * poses_out [n][n_way][n_seg + 1][3]; relax_out [n][n_way][2];
+ * status_out [n] (IK_PATH_UNREACHABLE when no reach pose exists).  With
+ * on_device != 0 every array is a device pointer. */
+IK_API int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* targets,
+                       int n, const ik_path_params* pp, int32_t* reach_out, int32_t* found_out,
+                       int32_t* poses_out, int32_t* relax_out, int32_t* status_out, int on_device);
+
+/* ------------------------------------------------------- replan (step a9) */
+/* Validity of n poses under the current occupancy: every joint inside the
+ * grid, every offset in its shell, every segment obstacle-free.
+ * poses [n][n_seg + 1][3]; valid_out [n] (1 / 0). */
+IK_API int ik_validate_poses(ik_grid g, const ik_arm* arm, const int32_t* poses, int n, int32_t* valid_out);
+
+/* Midcourse replan under the current occupancy (section "Dynamic
+ * Obstacles").  The arm is at waypoint current_idx of poses_in
+ * [n_way][n_seg + 1][3].  If every later pose is still valid the path is
+ * kept (IK_PATH_KEPT).  Otherwise poses 0..current_idx are kept; the reach
+ * pose is kept if valid, else re-solved joint by joint from the root taking
+ * the successor in V_k closest to the old joint (squared distance, then
+ * linear index), the path's least-distance objective; guide points come
+ * from that reach pose; and poses current_idx+1 .. n_way-1 are chained
+ * forward from pose^(current_idx) by the smooth-step rule of ik_plan_path.
+ * IK_PATH_UNREACHABLE (poses after current_idx repeat it, m = -1) when the
+ * target cannot be reached now. */
+IK_API int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, int current_idx,
+              const ik_path_params* pp, int32_t* poses_out, int32_t* relax_out, int* status);
+
+/* ------------------------------------------------------- host utilities */
+/* Shell bounds and offsets of one segment length, as the library builds
+ * them (offsets ordered by |d|^2, then z, y, x).  Writes up to cap offsets
+ * (x, y, z) and returns the shell size, or a negative error code. */
+IK_API int ik_shell_offsets(int len, float tol, int32_t* lo2_hi2, int32_t* offs_out, int cap);
+/* Closed supercover of the segment 0 -> d as the library builds it (by an
+ * incremental integer traversal of the segment's boundary crossings),
+ * ordered by (z, y, x).  Returns its size or a negative error code. */
+IK_API int ik_supercover_offsets(const int32_t d[3], int32_t* vox_out, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IK_B300_H */

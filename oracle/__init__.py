@@ -72,7 +72,9 @@ def _u8(a) -> np.ndarray:
 def shell_bounds(L: int, tol: float = 0.5) -> Tuple[int, int]:
     lo = ctypes.c_int()
     hi = ctypes.c_int()
-    _load().orc_shell_bounds(int(L), ctypes.c_double(tol), ctypes.byref(lo), ctypes.byref(hi))
+    # the C ABI carries tol as a float; round it the same way
+    _load().orc_shell_bounds(int(L), ctypes.c_double(float(np.float32(tol))), ctypes.byref(lo),
+                             ctypes.byref(hi))
     return lo.value, hi.value
 
 
@@ -177,6 +179,36 @@ def waypoint_sets(occ, lengths, reach_pose, W: int, eps2: int = 2, eps2_max: int
                               _p(_i32(reach_pose)), int(W), int(eps2), int(eps2_max),
                               _p(used), _p(vs) if want_sets else None, int(threads))
     return used, vs
+
+
+def waypoint_sets_range(occ, lengths, reach_pose, W: int, j_lo: int, j_hi: int, eps2: int = 2,
+                        eps2_max: int = 8, tol: float = 0.5):
+    """Survivor sets of waypoints j_lo..j_hi-1 only: (eps2_used, vsets)."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    lo2, hi2 = arm_bounds(lengths, tol)
+    S = len(lengths)
+    n = j_hi - j_lo
+    used = np.zeros(n, np.int32)
+    vs = np.zeros((n, S + 1, nz, ny, nx), np.uint8)
+    _load().orc_waypoint_sets_range(nx, ny, nz, _p(occ), S, _p(_i32(lengths)), _p(lo2), _p(hi2),
+                                    _p(_i32(reach_pose)), int(W), int(j_lo), int(j_hi), int(eps2),
+                                    int(eps2_max), _p(used), _p(vs))
+    return used, vs
+
+
+def smooth_step(occ, lengths, vsets, ref_pose, delta: int = 3, max_relax: int = -1,
+                tol: float = 0.5):
+    """One smooth step from given survivor sets: (pose [S+1][3] or None, m)."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    lo2, hi2 = arm_bounds(lengths, tol)
+    S = len(lengths)
+    pose = np.zeros((S + 1, 3), np.int32)
+    m = ctypes.c_int32()
+    _load().orc_smooth_step(nx, ny, nz, _p(occ), S, _p(lo2), _p(hi2), _p(_u8(vsets)),
+                            _p(_i32(ref_pose)), int(delta), int(max_relax), _p(pose), ctypes.byref(m))
+    return (pose if m.value >= 0 else None), m.value
 
 
 def plan_path(occ, lengths, reach_pose, W: int, delta: int = 3, eps2: int = 2,

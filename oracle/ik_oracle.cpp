@@ -790,6 +790,51 @@ int orc_replan(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t*
   return 0;
 }
 
+// Survivor sets of waypoints j_lo .. j_hi-1 only (same rules as
+// orc_waypoint_sets); vsets_out [j_hi - j_lo][S+1][nvox].
+int orc_waypoint_sets_range(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
+                            const int32_t* lo2, const int32_t* hi2, const int32_t* reach_pose, int W,
+                            int j_lo, int j_hi, int eps2, int eps2_max, int32_t* eps2_used,
+                            uint8_t* vsets_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<V3> reach = read_pose(reach_pose, S);
+  std::vector<int> L(lens, lens + S);
+  std::vector<V3> g = guide_points(L, reach, W);
+  std::vector<Set> F = forward_sets(P, reach[0]);
+  for (int j = j_lo; j < j_hi; ++j) {
+    Set T;
+    int used = 0;
+    if (j == W - 1) {
+      T.assign(P.g.nvox(), 0);
+      T[P.g.index(reach[S].x, reach[S].y, reach[S].z)] = 1;
+    } else {
+      T = waypoint_target(P, g[j], eps2, eps2_max, &used);
+    }
+    eps2_used[j - j_lo] = used;
+    std::vector<Set> V = waypoint_V(P, F, T);
+    for (int k = 0; k <= S; ++k)
+      std::memcpy(vsets_out + ((size_t)(j - j_lo) * (S + 1) + k) * P.g.nvox(), V[k].data(), P.g.nvox());
+  }
+  return 0;
+}
+
+// One smooth step with its relaxation ladder, given survivor sets V (bytes,
+// [S+1][nvox]) and the reference pose.  Returns the number of increments
+// used (written to *m_out, -1 when none fits) and the pose.
+int orc_smooth_step(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                    const int32_t* hi2, const uint8_t* vsets, const int32_t* ref_pose, int delta,
+                    int max_relax, int32_t* pose_out, int32_t* m_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<Set> V(S + 1);
+  for (int k = 0; k <= S; ++k)
+    V[k].assign(vsets + (size_t)k * P.g.nvox(), vsets + (size_t)(k + 1) * P.g.nvox());
+  std::vector<V3> pose;
+  int m = smooth_ladder(P, V, read_pose(ref_pose, S), delta, max_relax, &pose);
+  *m_out = m;
+  if (m >= 0) write_pose(pose, pose_out);
+  return 0;
+}
+
 // Algorithmic work of one propagation D_k(X) in bitset words: over every
 // offset e of the shell and every 32-voxel word p (x-packed rows, Nx a
 // multiple of 32) whose shifted input X[p+e] is non-zero, count the word and

@@ -1,0 +1,774 @@
+// C ABI of the library: argument checks, device-resident state per grid, and
+// the launch sequences of the hot path.  No step of the method runs on the
+// host: the host builds the integer shell/supercover tables once per segment
+// length and then only enqueues kernels and copies.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ik_internal.h"
+
+using namespace ikb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct GridState;
+
+}  // namespace
+
+struct ik_grid_s {
+  int device = 0;
+  Dims d{};
+  cudaStream_t st = nullptr;
+  uint32_t* d_occ = nullptr;
+  uint64_t version = 1;
+  std::map<std::pair<int, int>, ShellDev*> shells;
+  // forward-set cache
+  bool f_valid = false;
+  int f_root[3] = {0, 0, 0};
+  std::vector<std::pair<int, int>> f_key;
+  uint64_t f_version = 0;
+  DevBuf F;
+  // scratch
+  DevBuf V, Vw, chain, boxes;
+  DevBuf b_root, b_targets, b_reach, b_found, b_poses, b_relax, b_status, b_eps, b_g, b_valid;
+  DevBuf b_old;
+};
+
+namespace {
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) return fail_cuda(_e);      \
+  } while (0)
+
+int fail_cuda(cudaError_t e) {
+  g_last_error = cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return IK_ERR_OOM;
+  }
+  return IK_ERR_CUDA;
+}
+
+// Grow a device buffer to at least `bytes`; contents are not kept.  With
+// `zero`, a newly allocated buffer is cleared.
+int ensure(ik_grid g, DevBuf& b, size_t bytes, bool zero = false) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return IK_OK;
+  if (b.p) {
+    CK(cudaStreamSynchronize(g->st));
+    CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return fail_cuda(e);
+  }
+  b.bytes = bytes;
+  if (zero) CK(cudaMemsetAsync(b.p, 0, bytes, g->st));
+  return IK_OK;
+}
+
+template <typename T>
+T* ptr(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+int to_device(ik_grid g, DevBuf& b, const void* src, size_t bytes) {
+  int rc = ensure(g, b, bytes);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, g->st));
+  return IK_OK;
+}
+
+int check_arm(const ik_arm* arm) {
+  if (!arm || !arm->len || arm->n_seg < 1 || arm->n_seg > IK_MAX_SEG) return IK_ERR_ARG;
+  if (!(arm->tol >= 0.0f && arm->tol < 1.0f)) return IK_ERR_ARG;
+  for (int k = 0; k < arm->n_seg; ++k)
+    if (arm->len[k] < 1 || arm->len[k] > IK_MAX_LEN) return IK_ERR_ARG;
+  return IK_OK;
+}
+
+// Shell table for (lo2, hi2), built on the host and uploaded once.
+int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
+  auto key = std::make_pair(lo2, hi2);
+  auto it = g->shells.find(key);
+  if (it != g->shells.end()) {
+    *out = it->second;
+    return IK_OK;
+  }
+  ShellDev* s = new ShellDev();
+  build_shell(lo2, hi2, &s->host);
+  const size_t n = s->host.off.size();
+  if (n == 0) {
+    delete s;
+    return IK_ERR_ARG;
+  }
+  int reach = 0;
+  for (int32_t o : s->host.off)
+    reach = std::max(reach, std::max(std::abs(unpack_x(o)), std::max(std::abs(unpack_y(o)), std::abs(unpack_z(o)))));
+  s->reach = reach;
+  cudaError_t e = cudaMalloc(&s->d_off, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_off);
+    cudaFree(s->d_sc_start);
+    cudaFree(s->d_sc);
+    delete s;
+    return fail_cuda(e);
+  }
+  CK(cudaMemcpyAsync(s->d_off, s->host.off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+  CK(cudaMemcpyAsync(s->d_sc_start, s->host.sc_start.data(), (n + 1) * 4, cudaMemcpyHostToDevice, g->st));
+  CK(cudaMemcpyAsync(s->d_sc, s->host.sc.data(), s->host.sc.size() * 4, cudaMemcpyHostToDevice, g->st));
+  CK(cudaStreamSynchronize(g->st));
+  g->shells[key] = s;
+  *out = s;
+  return IK_OK;
+}
+
+// Edge masks of a shell for the current occupancy (recomputed when stale).
+int ensure_masks(ik_grid g, ShellDev* s) {
+  if (s->mask_version == g->version && s->d_mask) return IK_OK;
+  if (!s->d_mask) {
+    const size_t bytes = s->host.off.size() * (size_t)g->d.nw * 4;
+    cudaError_t e = cudaMalloc(&s->d_mask, bytes);
+    if (e != cudaSuccess) {
+      s->d_mask = nullptr;
+      return fail_cuda(e);
+    }
+  }
+  CK(launch_edge_masks(g->d, g->d_occ, *s, s->d_mask, g->st));
+  s->mask_version = g->version;
+  return IK_OK;
+}
+
+int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<int, int>>* key) {
+  int rc = check_arm(arm);
+  if (rc) return rc;
+  memset(ad, 0, sizeof(*ad));
+  ad->S = arm->n_seg;
+  if (key) key->clear();
+  for (int k = 0; k < arm->n_seg; ++k) {
+    int lo2, hi2;
+    shell_bounds(arm->len[k], (double)arm->tol, &lo2, &hi2);
+    if (hi2 < lo2) return IK_ERR_ARG;
+    ShellDev* s = nullptr;
+    rc = get_shell(g, lo2, hi2, &s);
+    if (rc) return rc;
+    rc = ensure_masks(g, s);
+    if (rc) return rc;
+    SegDev& sd = ad->seg[k];
+    sd.off = s->d_off;
+    sd.sc_start = s->d_sc_start;
+    sd.sc = s->d_sc;
+    sd.mask = s->d_mask;
+    sd.n = (int)s->host.off.size();
+    sd.lo2 = lo2;
+    sd.hi2 = hi2;
+    sd.reach = s->reach;
+    ad->len[k] = arm->len[k];
+    if (key) key->push_back(std::make_pair(lo2, hi2));
+  }
+  return IK_OK;
+}
+
+bool point_inside(const Dims& d, const int32_t* p) {
+  return p[0] >= 0 && p[1] >= 0 && p[2] >= 0 && p[0] < d.nx && p[1] < d.ny && p[2] < d.nz;
+}
+
+// Forward sets F_0..F_S for `root` (host int[3]), cached.
+int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int, int>>& key,
+                   const int32_t* root) {
+  if (g->f_valid && g->f_version == g->version && g->f_key == key && g->f_root[0] == root[0] &&
+      g->f_root[1] == root[1] && g->f_root[2] == root[2])
+    return IK_OK;
+  g->f_valid = false;
+  const Dims& d = g->d;
+  const int S = ad.S;
+  int rc = ensure(g, g->F, (size_t)(S + 1) * d.nw * 4);
+  if (rc) return rc;
+  rc = to_device(g, g->b_root, root, 12);
+  if (rc) return rc;
+  uint32_t* F = ptr<uint32_t>(g->F);
+  CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, g->st));
+  for (int k = 1; k <= S; ++k)
+    CK(launch_propagate(d, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
+                        0, 1, g->st));
+  g->f_valid = true;
+  g->f_version = g->version;
+  g->f_key = key;
+  memcpy(g->f_root, root, 12);
+  return IK_OK;
+}
+
+// Backward pass for Q queries whose last set (index S) is already seeded in
+// V (query stride (S+1) * nw): V_{k-1} = F_{k-1} & D_k(V_k) for k = S..1.
+int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q) {
+  const Dims& d = g->d;
+  const int S = ad.S;
+  const long qs = (long)(S + 1) * d.nw;
+  const uint32_t* F = ptr<uint32_t>(g->F);
+  for (int k = S; k >= 1; --k)
+    CK(launch_propagate(d, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
+                        g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, g->st));
+  return IK_OK;
+}
+
+int copy_out(ik_grid g, void* dst, const void* src, size_t bytes, int on_device) {
+  if (!dst || bytes == 0) return IK_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     g->st));
+  return IK_OK;
+}
+
+int sync(ik_grid g) {
+  CK(cudaStreamSynchronize(g->st));
+  CK(cudaGetLastError());
+  return IK_OK;
+}
+
+int set_device(ik_grid g) {
+  if (!g) return IK_ERR_ARG;
+  CK(cudaSetDevice(g->device));
+  return IK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ik_version(void) { return 1; }
+
+const char* ik_strerror(int code) {
+  switch (code) {
+    case IK_OK: return "ok";
+    case IK_ERR_ARG: return "invalid argument";
+    case IK_ERR_OOM: return "out of memory";
+    case IK_ERR_CUDA: return "CUDA error";
+    case IK_ERR_TIMEOUT: return "device wait timed out";
+    case IK_ERR_STATE: return "invalid state";
+    case IK_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown error";
+  }
+}
+
+const char* ik_last_error_message(void) { return g_last_error.c_str(); }
+
+int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out) {
+  if (!out) return IK_ERR_ARG;
+  *out = nullptr;
+  if (nx < 32 || nx > 1024 || nx % 32 != 0 || ny < 1 || ny > 1024 || nz < 1 || nz > 1024)
+    return IK_ERR_ARG;
+  ik_grid g = new ik_grid_s();
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    return fail_cuda(e);
+  }
+  g->d.nx = nx;
+  g->d.ny = ny;
+  g->d.nz = nz;
+  g->d.wx = nx / 32;
+  g->d.nw = (long)g->d.wx * ny * nz;
+  g->st = (cudaStream_t)cuda_stream;
+  e = cudaMalloc(&g->d_occ, g->d.nw * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ, 0, g->d.nw * 4, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) {
+    cudaFree(g->d_occ);
+    delete g;
+    return fail_cuda(e);
+  }
+  *out = g;
+  return IK_OK;
+}
+
+int ik_destroy_grid(ik_grid g) {
+  if (!g) return IK_ERR_ARG;
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->st);
+  for (auto& kv : g->shells) {
+    ShellDev* s = kv.second;
+    cudaFree(s->d_off);
+    cudaFree(s->d_sc_start);
+    cudaFree(s->d_sc);
+    cudaFree(s->d_mask);
+    delete s;
+  }
+  DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->b_root, &g->b_targets,
+                    &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
+                    &g->b_g, &g->b_valid, &g->b_old};
+  for (DevBuf* b : bufs) cudaFree(b->p);
+  cudaFree(g->d_occ);
+  delete g;
+  return IK_OK;
+}
+
+size_t ik_grid_words(ik_grid g) { return g ? (size_t)g->d.nw : 0; }
+
+int ik_set_obstacles(ik_grid g, const uint32_t* occ_words, size_t n_words, int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!occ_words || n_words != (size_t)g->d.nw) return IK_ERR_ARG;
+  CK(cudaMemcpyAsync(g->d_occ, occ_words, n_words * 4,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
+  ++g->version;
+  return sync(g);
+}
+
+int ik_set_boxes(ik_grid g, const int32_t* boxes, int n_boxes, int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (n_boxes < 0 || (n_boxes > 0 && !boxes)) return IK_ERR_ARG;
+  const int32_t* db = boxes;
+  if (n_boxes > 0 && !on_device) {
+    rc = to_device(g, g->boxes, boxes, (size_t)n_boxes * 24);
+    if (rc) return rc;
+    db = ptr<int32_t>(g->boxes);
+  }
+  CK(launch_rasterize(g->d, db, n_boxes, g->d_occ, g->st));
+  ++g->version;
+  return sync(g);
+}
+
+int ik_get_obstacles(ik_grid g, uint32_t* occ_words, size_t n_words, int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!occ_words || n_words != (size_t)g->d.nw) return IK_ERR_ARG;
+  rc = copy_out(g, occ_words, g->d_occ, n_words * 4, on_device);
+  if (rc) return rc;
+  return sync(g);
+}
+
+int ik_forward_sets(ik_grid g, const ik_arm* arm, const int32_t root[3], uint32_t* fsets_out,
+                    int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!root || !point_inside(g->d, root)) return IK_ERR_ARG;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = ensure_forward(g, ad, key, root))) return rc;
+  if ((rc = copy_out(g, fsets_out, g->F.p, (size_t)(ad.S + 1) * g->d.nw * 4, on_device))) return rc;
+  return sync(g);
+}
+
+// Reach for n targets; every array is a device pointer when on_device.
+static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int, int>>& key,
+                           const int32_t* root, const int32_t* targets, int n, int32_t* poses_out,
+                           int32_t* found_out, uint32_t* vsets_out, int on_device,
+                           int32_t** d_poses, int32_t** d_found) {
+  const Dims& d = g->d;
+  const int S = ad.S;
+  int rc = ensure_forward(g, ad, key, root);
+  if (rc) return rc;
+  const long qs = (long)(S + 1) * d.nw;
+  if ((rc = ensure(g, g->V, (size_t)n * qs * 4))) return rc;
+  uint32_t* V = ptr<uint32_t>(g->V);
+  const int32_t* dt = targets;
+  if (!on_device) {
+    if ((rc = to_device(g, g->b_targets, targets, (size_t)n * 12))) return rc;
+    dt = ptr<int32_t>(g->b_targets);
+  }
+  if ((rc = to_device(g, g->b_root, root, 12))) return rc;
+  const uint32_t* F = ptr<uint32_t>(g->F);
+  CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr, g->st));
+  if ((rc = backward_sets(g, ad, V, n))) return rc;
+  int32_t* dp = poses_out;
+  int32_t* df = found_out;
+  if (!on_device || !poses_out || !found_out) {
+    if ((rc = ensure(g, g->b_reach, (size_t)n * 12 * (S + 1)))) return rc;
+    if ((rc = ensure(g, g->b_found, (size_t)n * 4))) return rc;
+    dp = ptr<int32_t>(g->b_reach);
+    df = ptr<int32_t>(g->b_found);
+  }
+  CK(launch_traceback(d, ad, ptr<int32_t>(g->b_root), V, qs, n, dp, df, g->st));
+  if (!on_device) {
+    if ((rc = copy_out(g, poses_out, dp, (size_t)n * 12 * (S + 1), 0))) return rc;
+    if ((rc = copy_out(g, found_out, df, (size_t)n * 4, 0))) return rc;
+  }
+  if (vsets_out && (rc = copy_out(g, vsets_out, V, (size_t)n * qs * 4, on_device))) return rc;
+  if (d_poses) *d_poses = dp;
+  if (d_found) *d_found = df;
+  return IK_OK;
+}
+
+int ik_solve_reach_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* targets,
+                        int n, int32_t* poses_out, int32_t* found_out, uint32_t* vsets_out,
+                        int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!root || !point_inside(g->d, root) || n < 0 || (n > 0 && !targets)) return IK_ERR_ARG;
+  if (n == 0) return IK_OK;
+  if (!on_device) {
+    for (int i = 0; i < n; ++i)
+      if (!point_inside(g->d, targets + 3 * i)) return IK_ERR_ARG;
+  }
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = reach_many_impl(g, ad, key, root, targets, n, poses_out, found_out, vsets_out, on_device,
+                            nullptr, nullptr)))
+    return rc;
+  return sync(g);
+}
+
+int ik_solve_reach(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t target[3],
+                   int32_t* pose_out, uint32_t* vsets_out, int* found) {
+  if (!pose_out || !found || !target) return IK_ERR_ARG;
+  int32_t f = 0;
+  int rc = ik_solve_reach_many(g, arm, root, target, 1, pose_out, &f, vsets_out, 0);
+  *found = f;
+  return rc;
+}
+
+int ik_guide(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way, int32_t* g_out) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!reach_pose || !g_out || n_way < 2) return IK_ERR_ARG;
+  if ((rc = check_arm(arm))) return rc;
+  ArmDev ad;
+  memset(&ad, 0, sizeof(ad));
+  ad.S = arm->n_seg;
+  for (int k = 0; k < ad.S; ++k) ad.len[k] = arm->len[k];
+  const int S = ad.S;
+  if ((rc = to_device(g, g->b_reach, reach_pose, (size_t)12 * (S + 1)))) return rc;
+  if ((rc = ensure(g, g->b_g, (size_t)12 * n_way))) return rc;
+  if ((rc = ensure(g, g->b_eps, (size_t)4 * n_way))) return rc;
+  CK(launch_guide_targets(g->d, ad, g->d_occ, nullptr, ptr<int32_t>(g->b_reach), nullptr, 1, n_way, 0,
+                          0, 0, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), nullptr, g->st));
+  if ((rc = copy_out(g, g_out, g->b_g.p, (size_t)12 * n_way, 0))) return rc;
+  return sync(g);
+}
+
+// Survivor sets of P paths x W waypoints (waypoints j >= j_lo) whose reach
+// poses are on the device (d_reach [P][S+1][3], d_found nullable).
+static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reach,
+                              const int32_t* d_found, int P, int W, int j_lo, int eps2,
+                              int eps2_max) {
+  const Dims& d = g->d;
+  const int S = ad.S;
+  const long qs = (long)(S + 1) * d.nw;
+  int rc = ensure(g, g->Vw, (size_t)P * W * qs * 4);
+  if (rc) return rc;
+  if ((rc = ensure(g, g->b_g, (size_t)12 * P * W))) return rc;
+  if ((rc = ensure(g, g->b_eps, (size_t)4 * P * W))) return rc;
+  uint32_t* Vw = ptr<uint32_t>(g->Vw);
+  // zero the seeded (last) set of every waypoint
+  CK(cudaMemset2DAsync(Vw + (long)S * d.nw, (size_t)qs * 4, 0, (size_t)d.nw * 4, (size_t)P * W, g->st));
+  const uint32_t* F = ptr<uint32_t>(g->F);
+  CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
+                          eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, g->st));
+  if (j_lo == 0) return backward_sets(g, ad, Vw, P * W);
+  // only waypoints j >= j_lo (P == 1 in that case)
+  for (int p = 0; p < P; ++p)
+    if ((rc = backward_sets(g, ad, Vw + ((long)p * W + j_lo) * qs, W - j_lo))) return rc;
+  return IK_OK;
+}
+
+static int check_path_params(const ik_path_params* pp) {
+  if (!pp || pp->n_way < 2 || pp->n_way > 4096 || pp->delta < 0 || pp->delta > 4096 ||
+      pp->eps2 < 0 || pp->eps2 > 4096 || pp->eps2_max < 0 || pp->eps2_max > 4096 ||
+      pp->max_relax < -1)
+    return IK_ERR_ARG;
+  return IK_OK;
+}
+
+int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way, int eps2,
+                     int eps2_max, int32_t* eps2_used, uint32_t* vsets_out) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!reach_pose || n_way < 2 || n_way > 4096 || eps2 < 0 || eps2 > 4096 || eps2_max < 0 ||
+      eps2_max > 4096)
+    return IK_ERR_ARG;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  const int S = ad.S;
+  for (int k = 0; k <= S; ++k)
+    if (!point_inside(g->d, reach_pose + 3 * k)) return IK_ERR_ARG;
+  if ((rc = ensure_forward(g, ad, key, reach_pose))) return rc;
+  if ((rc = to_device(g, g->b_reach, reach_pose, (size_t)12 * (S + 1)))) return rc;
+  if ((rc = waypoint_sets_impl(g, ad, ptr<int32_t>(g->b_reach), nullptr, 1, n_way, 0, eps2, eps2_max)))
+    return rc;
+  if ((rc = copy_out(g, eps2_used, g->b_eps.p, (size_t)4 * n_way, 0))) return rc;
+  if ((rc = copy_out(g, vsets_out, g->Vw.p, (size_t)n_way * (S + 1) * g->d.nw * 4, 0))) return rc;
+  return sync(g);
+}
+
+// Smooth chains for P paths whose waypoint survivor sets are in g->Vw and
+// whose preset poses are in d_poses.
+static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int P, int mode, int c,
+                      const int32_t* d_found, int32_t* d_poses, int32_t* d_relax, int32_t* d_status) {
+  const Dims& d = g->d;
+  const int S = ad.S;
+  int rc = ensure(g, g->chain, (size_t)P * 2 * (S + 1) * d.nw * 4, true);
+  if (rc) return rc;
+  ChainArgs a;
+  a.P = P;
+  a.W = pp->n_way;
+  a.c = c;
+  a.mode = mode;
+  a.delta = pp->delta;
+  a.max_relax = pp->max_relax;
+  a.found = d_found;
+  a.Vw = ptr<uint32_t>(g->Vw);
+  a.eps_used = ptr<int32_t>(g->b_eps);
+  a.poses = d_poses;
+  a.relax = d_relax;
+  a.status = d_status;
+  a.scratch = ptr<uint32_t>(g->chain);
+  a.relaxed_eps_base = pp->eps2;
+  CK(launch_smooth_chain(d, ad, a, g->st));
+  return IK_OK;
+}
+
+static int validate_impl(ik_grid g, const ArmDev& ad, const int32_t* d_poses, int n, int32_t* d_valid) {
+  CK(launch_validate(g->d, ad, g->d_occ, d_poses, n, d_valid, g->st));
+  return IK_OK;
+}
+
+int ik_validate_poses(ik_grid g, const ik_arm* arm, const int32_t* poses, int n, int32_t* valid_out) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!poses || !valid_out))) return IK_ERR_ARG;
+  if (n == 0) return IK_OK;
+  ArmDev ad;
+  if ((rc = resolve_arm(g, arm, &ad, nullptr))) return rc;
+  const int S = ad.S;
+  if ((rc = to_device(g, g->b_poses, poses, (size_t)n * 12 * (S + 1)))) return rc;
+  if ((rc = ensure(g, g->b_valid, (size_t)4 * n))) return rc;
+  if ((rc = validate_impl(g, ad, ptr<int32_t>(g->b_poses), n, ptr<int32_t>(g->b_valid)))) return rc;
+  if ((rc = copy_out(g, valid_out, g->b_valid.p, (size_t)4 * n, 0))) return rc;
+  return sync(g);
+}
+
+int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const ik_path_params* pp,
+                 int32_t* poses_out, int32_t* relax_out, int* status) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!reach_pose || !poses_out || !relax_out || !status) return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  const int S = ad.S, W = pp->n_way;
+  const size_t pose_bytes = (size_t)12 * (S + 1);
+  // the reach pose must be a valid pose of this arm in this grid
+  if ((rc = to_device(g, g->b_reach, reach_pose, pose_bytes))) return rc;
+  if ((rc = ensure(g, g->b_valid, 4))) return rc;
+  if ((rc = validate_impl(g, ad, ptr<int32_t>(g->b_reach), 1, ptr<int32_t>(g->b_valid)))) return rc;
+  int32_t valid = 0;
+  if ((rc = copy_out(g, &valid, g->b_valid.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  if (!valid) {
+    *status = IK_PATH_UNREACHABLE;
+    return IK_OK;
+  }
+  if ((rc = ensure_forward(g, ad, key, reach_pose))) return rc;
+  if ((rc = waypoint_sets_impl(g, ad, ptr<int32_t>(g->b_reach), nullptr, 1, W, 0, pp->eps2, pp->eps2_max)))
+    return rc;
+  if ((rc = ensure(g, g->b_poses, pose_bytes * W))) return rc;
+  if ((rc = ensure(g, g->b_relax, (size_t)8 * W))) return rc;
+  if ((rc = ensure(g, g->b_status, 4))) return rc;
+  int32_t* dposes = ptr<int32_t>(g->b_poses);
+  CK(cudaMemcpyAsync(dposes + (long)(W - 1) * 3 * (S + 1), g->b_reach.p, pose_bytes,
+                     cudaMemcpyDeviceToDevice, g->st));
+  if ((rc = chain_impl(g, ad, pp, 1, 0, 0, nullptr, dposes, ptr<int32_t>(g->b_relax),
+                       ptr<int32_t>(g->b_status))))
+    return rc;
+  int32_t st = 0;
+  if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W, 0))) return rc;
+  if ((rc = copy_out(g, relax_out, g->b_relax.p, (size_t)8 * W, 0))) return rc;
+  if ((rc = copy_out(g, &st, g->b_status.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  *status = st;
+  return IK_OK;
+}
+
+int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* targets,
+                       int n, const ik_path_params* pp, int32_t* reach_out, int32_t* found_out,
+                       int32_t* poses_out, int32_t* relax_out, int32_t* status_out, int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!root || !point_inside(g->d, root) || n < 0 || (n > 0 && !targets)) return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  if (n == 0) return IK_OK;
+  if (!on_device)
+    for (int i = 0; i < n; ++i)
+      if (!point_inside(g->d, targets + 3 * i)) return IK_ERR_ARG;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  const int S = ad.S, W = pp->n_way;
+  const size_t pose_bytes = (size_t)12 * (S + 1);
+  int32_t *d_reach = nullptr, *d_found = nullptr;
+  if ((rc = reach_many_impl(g, ad, key, root, targets, n, on_device ? reach_out : nullptr,
+                            on_device ? found_out : nullptr, nullptr, on_device, &d_reach, &d_found)))
+    return rc;
+  if ((rc = waypoint_sets_impl(g, ad, d_reach, d_found, n, W, 0, pp->eps2, pp->eps2_max))) return rc;
+  int32_t *dposes = poses_out, *drelax = relax_out, *dstatus = status_out;
+  if (!on_device) {
+    if ((rc = ensure(g, g->b_poses, pose_bytes * W * n))) return rc;
+    if ((rc = ensure(g, g->b_relax, (size_t)8 * W * n))) return rc;
+    if ((rc = ensure(g, g->b_status, (size_t)4 * n))) return rc;
+    dposes = ptr<int32_t>(g->b_poses);
+    drelax = ptr<int32_t>(g->b_relax);
+    dstatus = ptr<int32_t>(g->b_status);
+  }
+  // pose W-1 of each path is its reach pose
+  CK(cudaMemcpy2DAsync(dposes + (long)(W - 1) * 3 * (S + 1), pose_bytes * W, d_reach, pose_bytes,
+                       pose_bytes, n, cudaMemcpyDeviceToDevice, g->st));
+  if ((rc = chain_impl(g, ad, pp, n, 0, 0, d_found, dposes, drelax, dstatus))) return rc;
+  if (!on_device) {
+    if ((rc = copy_out(g, reach_out, d_reach, pose_bytes * n, 0))) return rc;
+    if ((rc = copy_out(g, found_out, d_found, (size_t)4 * n, 0))) return rc;
+    if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W * n, 0))) return rc;
+    if ((rc = copy_out(g, relax_out, drelax, (size_t)8 * W * n, 0))) return rc;
+    if ((rc = copy_out(g, status_out, dstatus, (size_t)4 * n, 0))) return rc;
+  }
+  return sync(g);
+}
+
+int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, int current_idx,
+              const ik_path_params* pp, int32_t* poses_out, int32_t* relax_out, int* status) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!poses_in || !poses_out || !relax_out || !status || n_way < 2 || current_idx < 0 ||
+      current_idx >= n_way)
+    return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  if (pp->n_way != n_way) return IK_ERR_ARG;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  const int S = ad.S, W = n_way, c = current_idx;
+  const size_t pose_bytes = (size_t)12 * (S + 1);
+  const int32_t* root = poses_in;
+  for (int j = 0; j < W; ++j)
+    if (poses_in[3 * (S + 1) * j] != root[0] || poses_in[3 * (S + 1) * j + 1] != root[1] ||
+        poses_in[3 * (S + 1) * j + 2] != root[2])
+      return IK_ERR_ARG;
+  if (!point_inside(g->d, root)) return IK_ERR_ARG;
+  // 1. is the remainder still valid?
+  if ((rc = ensure(g, g->b_poses, pose_bytes * W))) return rc;
+  int32_t* dposes = ptr<int32_t>(g->b_poses);
+  CK(cudaMemcpyAsync(dposes, poses_in, pose_bytes * W, cudaMemcpyHostToDevice, g->st));
+  if ((rc = ensure(g, g->b_valid, (size_t)4 * W))) return rc;
+  if ((rc = validate_impl(g, ad, dposes, W, ptr<int32_t>(g->b_valid)))) return rc;
+  std::vector<int32_t> valid(W);
+  if ((rc = copy_out(g, valid.data(), g->b_valid.p, (size_t)4 * W, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  bool cut = false;
+  for (int j = c + 1; j < W; ++j)
+    if (!valid[j]) cut = true;
+  for (int j = 0; j < 2 * W; ++j) relax_out[j] = 0;
+  if (!cut) {
+    memcpy(poses_out, poses_in, pose_bytes * W);
+    *status = IK_PATH_KEPT;
+    return IK_OK;
+  }
+  // 2. forward sets on the new occupancy; 3. the guiding reach pose
+  if ((rc = ensure_forward(g, ad, key, root))) return rc;
+  if ((rc = ensure(g, g->b_reach, pose_bytes))) return rc;
+  int32_t* dreach = ptr<int32_t>(g->b_reach);
+  const int32_t* old_reach = poses_in + (size_t)3 * (S + 1) * (W - 1);
+  if (valid[W - 1]) {
+    CK(cudaMemcpyAsync(dreach, old_reach, pose_bytes, cudaMemcpyHostToDevice, g->st));
+  } else {
+    const long qs = (long)(S + 1) * g->d.nw;
+    if ((rc = ensure(g, g->V, (size_t)qs * 4))) return rc;
+    if ((rc = to_device(g, g->b_targets, old_reach + 3 * S, 12))) return rc;
+    if ((rc = to_device(g, g->b_old, old_reach, pose_bytes))) return rc;
+    if ((rc = to_device(g, g->b_root, root, 12))) return rc;
+    if ((rc = ensure(g, g->b_found, 4))) return rc;
+    uint32_t* V = ptr<uint32_t>(g->V);
+    const uint32_t* F = ptr<uint32_t>(g->F);
+    CK(launch_seed_points(g->d, ptr<int32_t>(g->b_targets), 1, F + (long)S * g->d.nw, nullptr,
+                          V + (long)S * g->d.nw, qs, nullptr, g->st));
+    if ((rc = backward_sets(g, ad, V, 1))) return rc;
+    CK(launch_traceback_nearest(g->d, ad, ptr<int32_t>(g->b_root), V, ptr<int32_t>(g->b_old), dreach,
+                                ptr<int32_t>(g->b_found), g->st));
+    int32_t found = 0;
+    if ((rc = copy_out(g, &found, g->b_found.p, 4, 0))) return rc;
+    if ((rc = sync(g))) return rc;
+    if (!found) {
+      memcpy(poses_out, poses_in, pose_bytes * (c + 1));
+      for (int j = c + 1; j < W; ++j) {
+        memcpy(poses_out + (size_t)3 * (S + 1) * j, poses_in + (size_t)3 * (S + 1) * c, pose_bytes);
+        relax_out[2 * j] = -1;
+      }
+      *status = IK_PATH_UNREACHABLE;
+      return IK_OK;
+    }
+  }
+  // 4. guide + survivor sets of waypoints c+1 .. W-1; 5. forward chain
+  if ((rc = waypoint_sets_impl(g, ad, dreach, nullptr, 1, W, c + 1, pp->eps2, pp->eps2_max))) return rc;
+  if ((rc = ensure(g, g->b_relax, (size_t)8 * W))) return rc;
+  if ((rc = ensure(g, g->b_status, 4))) return rc;
+  if ((rc = chain_impl(g, ad, pp, 1, 1, c, nullptr, dposes, ptr<int32_t>(g->b_relax),
+                       ptr<int32_t>(g->b_status))))
+    return rc;
+  int32_t st = 0;
+  if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W, 0))) return rc;
+  if ((rc = copy_out(g, relax_out, g->b_relax.p, (size_t)8 * W, 0))) return rc;
+  if ((rc = copy_out(g, &st, g->b_status.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  *status = st;
+  return IK_OK;
+}
+
+int ik_shell_offsets(int len, float tol, int32_t* lo2_hi2, int32_t* offs_out, int cap) {
+  if (len < 1 || len > IK_MAX_LEN || !(tol >= 0.0f && tol < 1.0f)) return IK_ERR_ARG;
+  int lo2, hi2;
+  shell_bounds(len, (double)tol, &lo2, &hi2);
+  if (lo2_hi2) {
+    lo2_hi2[0] = lo2;
+    lo2_hi2[1] = hi2;
+  }
+  ShellHost sh;
+  build_shell(lo2, hi2, &sh);
+  const int n = (int)sh.off.size();
+  for (int i = 0; i < n && i < cap && offs_out; ++i) {
+    offs_out[3 * i] = unpack_x(sh.off[i]);
+    offs_out[3 * i + 1] = unpack_y(sh.off[i]);
+    offs_out[3 * i + 2] = unpack_z(sh.off[i]);
+  }
+  return n;
+}
+
+int ik_supercover_offsets(const int32_t d[3], int32_t* vox_out, int cap) {
+  if (!d) return IK_ERR_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (d[i] < -127 || d[i] > 127) return IK_ERR_ARG;
+  std::vector<int32_t> sc;
+  supercover_traverse(d[0], d[1], d[2], &sc);
+  const int n = (int)sc.size();
+  for (int i = 0; i < n && i < cap && vox_out; ++i) {
+    vox_out[3 * i] = unpack_x(sc[i]);
+    vox_out[3 * i + 1] = unpack_y(sc[i]);
+    vox_out[3 * i + 2] = unpack_z(sc[i]);
+  }
+  return n;
+}
+
+}  // extern "C"

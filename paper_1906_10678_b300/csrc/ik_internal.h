@@ -1,0 +1,129 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ik.h"
+
+namespace ikb {
+
+// Offsets are packed as three signed bytes: x | y << 8 | z << 16.
+__host__ __device__ inline int32_t pack3(int x, int y, int z) {
+  return (int32_t)((uint32_t)(x & 0xff) | ((uint32_t)(y & 0xff) << 8) | ((uint32_t)(z & 0xff) << 16));
+}
+__host__ __device__ inline int unpack_x(int32_t v) { return (int)(int8_t)(v & 0xff); }
+__host__ __device__ inline int unpack_y(int32_t v) { return (int)(int8_t)((v >> 8) & 0xff); }
+__host__ __device__ inline int unpack_z(int32_t v) { return (int)(int8_t)((v >> 16) & 0xff); }
+
+struct Dims {
+  int nx, ny, nz;  // voxels
+  int wx;          // words per row = nx / 32
+  long nw;         // words per set
+};
+
+// One admissible-offset table on the host, built by tables.cpp.
+struct ShellHost {
+  int lo2 = 0, hi2 = 0;
+  std::vector<int32_t> off;       // packed offsets, ordered by (|d|^2, z, y, x)
+  std::vector<int32_t> sc_start;  // size n + 1, into sc
+  std::vector<int32_t> sc;        // packed supercover voxels of 0 -> off[i], (z, y, x) order
+  int max_sc = 0;
+};
+
+void shell_bounds(int len, double tol, int* lo2, int* hi2);
+void build_shell(int lo2, int hi2, ShellHost* out);
+// Closed supercover of 0 -> d by incremental traversal; (z, y, x) order.
+void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
+
+// Device view of one segment's tables.
+struct SegDev {
+  const int32_t* off;      // [n] packed offsets
+  const int32_t* sc_start; // [n + 1]
+  const int32_t* sc;       // packed supercover voxels
+  const uint32_t* mask;    // [n][nw] edge masks: bit of voxel p in row e = segment p -> p + off[e] free
+  int n;
+  int lo2, hi2;
+  int reach;               // max |component| of an offset
+};
+
+struct ArmDev {
+  SegDev seg[IK_MAX_SEG];
+  int S;
+  int len[IK_MAX_SEG];
+};
+
+// Device-resident shell table with its edge masks for one occupancy version.
+struct ShellDev {
+  ShellHost host;
+  int32_t* d_off = nullptr;
+  int32_t* d_sc_start = nullptr;
+  int32_t* d_sc = nullptr;
+  uint32_t* d_mask = nullptr;
+  uint64_t mask_version = ~0ull;
+  int reach = 0;
+};
+
+// ------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return the launch error (cudaSuccess).
+cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, uint32_t* occ,
+                             cudaStream_t st);
+cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev& s, uint32_t* mask,
+                              cudaStream_t st);
+// out[q] = (mask ? mask[q] : ~0) & D_seg(X[q]) for q < Q; sets are nw words
+// apart with stride `x_stride` / `out_stride` / `mask_stride` words between
+// queries (mask_stride 0: one mask shared by all queries).
+cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
+                             const uint32_t* mask, long mask_stride, const uint32_t* occ,
+                             uint32_t* out, long out_stride, int Q, cudaStream_t st);
+// Single-voxel seeds: set q = {p_q} & (and_set ? and_set : all) & ~excl,
+// p_q from points[q] (int32 x, y, z) -- a point outside the grid gives the
+// empty set.  found_gate (nullable): query q is seeded only when
+// found_gate[q] != 0.
+cudaError_t launch_seed_points(const Dims& d, const int32_t* points, int Q, const uint32_t* and_set,
+                               const uint32_t* excl, uint32_t* out, long out_stride,
+                               const int32_t* found_gate, cudaStream_t st);
+cudaError_t launch_and(const uint32_t* a, const uint32_t* b, uint32_t* out, long n, cudaStream_t st);
+// Reach traceback over Q queries: V sets [Q][S+1][nw] (query stride vstride).
+cudaError_t launch_traceback(const Dims& d, const ArmDev& arm, const int32_t* root,
+                             const uint32_t* V, long vstride, int Q, int32_t* poses,
+                             int32_t* found, cudaStream_t st);
+// Replan re-solve: like traceback but minimising squared distance to
+// old_pose first (old_pose [S+1][3]).
+cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int32_t* root,
+                                     const uint32_t* V, const int32_t* old_pose, int32_t* pose,
+                                     int32_t* found, cudaStream_t st);
+// Guide points + waypoint target seeds for P paths of W waypoints:
+// reach [P][S+1][3], found [P] (nullable: all found), writes
+// g [P][W][3], eps_used [P][W] and V_S^(p,j) = F_S & T_j into
+// Vw + ((p*W + j) * (S+1) + S) * nw.  Waypoints j < j_lo are skipped.
+cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
+                                 const uint32_t* F_S, const int32_t* reach, const int32_t* found,
+                                 int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
+                                 int32_t* eps_used, uint32_t* Vw, cudaStream_t st);
+// Smooth chains for P paths (one block each).  mode 0 = plan (backward from
+// the reach pose), mode 1 = forward from pose c (replan).  scratch: per path
+// 2 * (S+1) * nw zeroed words.
+struct ChainArgs {
+  int P, W, c, mode;
+  int delta, max_relax;
+  const int32_t* found;     // [P] nullable
+  const uint32_t* Vw;       // [P][W][S+1][nw]
+  const int32_t* eps_used;  // [P][W]
+  int32_t* poses;           // [P][W][S+1][3]; plan: pose W-1 preset; replan: poses 0..c preset
+  int32_t* relax;           // [P][W][2]
+  int32_t* status;          // [P]
+  uint32_t* scratch;
+  int relaxed_eps_base;     // eps2 requested (to flag eps growth)
+};
+cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
+                                cudaStream_t st);
+cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* occ,
+                            const int32_t* poses, int n, int32_t* valid, cudaStream_t st);
+
+}  // namespace ikb

@@ -1,0 +1,831 @@
+// sm_103a kernels of the lattice gap map-seeking IK hot path.
+//
+// Voxel sets are x-packed bitsets: bit b of word (z*ny + y)*wx + w is voxel
+// (32w + b, y, z).  A set shifted by an offset (dx, dy, dz) is read 32 voxels
+// at a time with one or two word loads and a funnel shift; voxels outside the
+// grid read as 0.  Everything here is exact boolean arithmetic.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ik_internal.h"
+
+namespace ikb {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ void word_coords(const Dims& d, long w, int* wx, int* y, int* z) {
+  *wx = (int)(w % d.wx);
+  long r = w / d.wx;
+  *y = (int)(r % d.ny);
+  *z = (int)(r / d.ny);
+}
+
+// Bits of voxels (32*wx + b + dx, y + dy, z + dz), b = 0..31, of set s.
+__device__ __forceinline__ uint32_t ld_shifted(const uint32_t* __restrict__ s, const Dims& d, int wx,
+                                               int y, int z, int dx, int dy, int dz) {
+  const int yy = y + dy, zz = z + dz;
+  if ((unsigned)yy >= (unsigned)d.ny || (unsigned)zz >= (unsigned)d.nz) return 0u;
+  const uint32_t* row = s + ((long)zz * d.ny + yy) * d.wx;
+  const int w0 = wx + (dx >> 5);
+  const int sh = dx & 31;
+  const uint32_t lo = ((unsigned)w0 < (unsigned)d.wx) ? __ldg(row + w0) : 0u;
+  if (sh == 0) return lo;
+  const uint32_t hi = ((unsigned)(w0 + 1) < (unsigned)d.wx) ? __ldg(row + w0 + 1) : 0u;
+  return __funnelshift_r(lo, hi, sh);
+}
+
+__device__ __forceinline__ bool inside(const Dims& d, int x, int y, int z) {
+  return (unsigned)x < (unsigned)d.nx && (unsigned)y < (unsigned)d.ny && (unsigned)z < (unsigned)d.nz;
+}
+
+__device__ __forceinline__ long lin(const Dims& d, int x, int y, int z) {
+  return ((long)z * d.ny + y) * d.nx + x;
+}
+
+__device__ __forceinline__ bool test_bit(const uint32_t* s, long i) {
+  return (__ldg(s + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+static inline int grid_for(long n, int block) { return (int)((n + block - 1) / block); }
+
+// ------------------------------------------------------- a1: rasterise boxes
+
+// One thread per occupancy word: OR of the x-runs of every box that covers
+// the word's row.  Boxes are staged through shared memory in chunks.
+constexpr int kBoxChunk = 512;
+
+__global__ void k_rasterize(Dims d, const int32_t* __restrict__ boxes, int nb, uint32_t* occ) {
+  __shared__ int32_t sb[kBoxChunk * 6];
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int wx = 0, y = 0, z = 0;
+  if (w < d.nw) word_coords(d, w, &wx, &y, &z);
+  uint32_t acc = 0;
+  for (int base = 0; base < nb; base += kBoxChunk) {
+    const int cnt = min(kBoxChunk, nb - base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * 6; i += blockDim.x) sb[i] = boxes[(long)base * 6 + i];
+    __syncthreads();
+    if (w < d.nw) {
+      for (int b = 0; b < cnt; ++b) {
+        const int32_t* B = sb + 6 * b;
+        if (y < B[1] || y > B[4] || z < B[2] || z > B[5]) continue;
+        const int x0 = max(B[0], 32 * wx), x1 = min(B[3], 32 * wx + 31);
+        if (x0 > x1) continue;
+        const int lo = x0 - 32 * wx, hi = x1 - 32 * wx;
+        const uint32_t upto = hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u);
+        acc |= upto & ~((1u << lo) - 1u);
+      }
+    }
+  }
+  if (w < d.nw) occ[w] = acc;
+}
+
+cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, uint32_t* occ,
+                             cudaStream_t st) {
+  k_rasterize<<<grid_for(d.nw, 256), 256, 0, st>>>(d, boxes, n_boxes, occ);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------- edge masks (per-offset M_e)
+
+// M_e[p] = AND over v in SC(0, e) of free(p + v): the segment p -> p + e is
+// obstacle-free.  One thread per (offset, word); the offset's supercover list
+// is uniform across the block (blockIdx.y = offset).
+__global__ void k_edge_masks(Dims d, const uint32_t* __restrict__ occ,
+                             const int32_t* __restrict__ sc_start, const int32_t* __restrict__ sc,
+                             int n_off, uint32_t* __restrict__ mask) {
+  for (int e = blockIdx.y; e < n_off; e += gridDim.y) {
+    const int s0 = __ldg(sc_start + e), s1 = __ldg(sc_start + e + 1);
+    for (long w = blockIdx.x * (long)blockDim.x + threadIdx.x; w < d.nw;
+         w += (long)gridDim.x * blockDim.x) {
+      int wx, y, z;
+      word_coords(d, w, &wx, &y, &z);
+      uint32_t blocked = 0;
+      for (int i = s0; i < s1 && blocked != 0xffffffffu; ++i) {
+        const int32_t v = __ldg(sc + i);
+        blocked |= ld_shifted(occ, d, wx, y, z, unpack_x(v), unpack_y(v), unpack_z(v));
+      }
+      mask[(long)e * d.nw + w] = ~blocked;
+    }
+  }
+}
+
+cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev& s, uint32_t* mask,
+                              cudaStream_t st) {
+  const int n = (int)s.host.off.size();
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  const int gx = max(1, min(grid_for(d.nw, block), 64));
+  dim3 grid(gx, min(n, 65535));
+  k_edge_masks<<<grid, block, 0, st>>>(d, occ, s.d_sc_start, s.d_sc, n, mask);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- a3/a4: one propagation D_k
+
+// out[p] = mask[p] & OR_e X[p + e] & M_e[p] over the shell of segment k.
+// Gather form of the scatter "every p reachable from X by a valid segment":
+// the shell is symmetric and SC(p, p+e) = p + SC(0, e).  An output word stops
+// early once every free voxel it may hold is set; the edge mask is read only
+// when the shifted input could add new bits.
+__global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uint32_t* __restrict__ X,
+                                                   long xs, const uint32_t* __restrict__ mask, long ms,
+                                                   const uint32_t* __restrict__ occ,
+                                                   uint32_t* __restrict__ out, long os) {
+  const int q = blockIdx.y;
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (w >= d.nw) return;
+  const uint32_t* Xq = X + q * xs;
+  uint32_t m = mask ? __ldg(mask + q * ms + w) : 0xffffffffu;
+  m &= ~__ldg(occ + w);
+  uint32_t acc = 0;
+  if (m) {
+    int wx, y, z;
+    word_coords(d, w, &wx, &y, &z);
+    const uint32_t* M = seg.mask + w;
+    for (int e = 0; e < seg.n; ++e) {
+      const int32_t o = __ldg(seg.off + e);
+      const uint32_t x = ld_shifted(Xq, d, wx, y, z, unpack_x(o), unpack_y(o), unpack_z(o));
+      if (x & m & ~acc) {
+        acc |= x & __ldg(M + (long)e * d.nw);
+        if ((acc & m) == m) break;
+      }
+    }
+  }
+  out[q * os + w] = acc & m;
+}
+
+cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
+                             const uint32_t* mask, long mask_stride, const uint32_t* occ,
+                             uint32_t* out, long out_stride, int Q, cudaStream_t st) {
+  if (Q <= 0) return cudaSuccess;
+  dim3 grid(grid_for(d.nw, 256), Q);
+  k_propagate<<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out, out_stride);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- seeds, and
+
+__global__ void k_seed_points(Dims d, const int32_t* __restrict__ pts, const uint32_t* __restrict__ and_set,
+                              const uint32_t* __restrict__ excl, uint32_t* __restrict__ out, long os,
+                              const int32_t* __restrict__ gate) {
+  const int q = blockIdx.y;
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (w >= d.nw) return;
+  uint32_t v = 0;
+  const int x = pts[3 * q], y = pts[3 * q + 1], z = pts[3 * q + 2];
+  if ((!gate || gate[q]) && inside(d, x, y, z)) {
+    const long i = lin(d, x, y, z);
+    if ((i >> 5) == w) v = 1u << (i & 31);
+  }
+  if (and_set) v &= __ldg(and_set + w);
+  if (excl) v &= ~__ldg(excl + w);
+  out[q * os + w] = v;
+}
+
+cudaError_t launch_seed_points(const Dims& d, const int32_t* points, int Q, const uint32_t* and_set,
+                               const uint32_t* excl, uint32_t* out, long out_stride,
+                               const int32_t* found_gate, cudaStream_t st) {
+  if (Q <= 0) return cudaSuccess;
+  dim3 grid(grid_for(d.nw, 256), Q);
+  k_seed_points<<<grid, 256, 0, st>>>(d, points, and_set, excl, out, out_stride, found_gate);
+  return cudaGetLastError();
+}
+
+__global__ void k_and(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* out,
+                      long n) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] & b[i];
+}
+
+cudaError_t launch_and(const uint32_t* a, const uint32_t* b, uint32_t* out, long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_and<<<grid_for(n, 256), 256, 0, st>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- a5: reach traceback
+
+// One block per query.  p_0 = root; p_k = min linear index over the offsets
+// e of segment k with q = p_{k-1} + e inside the grid, q in V_k and the
+// segment p_{k-1} -> q free (edge-mask bit of p_{k-1} in row e).
+// nearest != nullptr: minimise (|q - nearest_k|^2, index) instead.
+__device__ void traceback_block(const Dims& d, const ArmDev& arm, int rx, int ry, int rz,
+                                const uint32_t* V, const int32_t* nearest, int32_t* pose,
+                                int32_t* found) {
+  __shared__ unsigned long long best;
+  __shared__ int p[3];
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = inside(d, rx, ry, rz) && test_bit(V, lin(d, rx, ry, rz));
+    p[0] = rx;
+    p[1] = ry;
+    p[2] = rz;
+    *found = ok;
+    pose[0] = ok ? rx : 0;
+    pose[1] = ok ? ry : 0;
+    pose[2] = ok ? rz : 0;
+  }
+  __syncthreads();
+  if (!ok) {
+    for (int i = threadIdx.x; i < 3 * arm.S; i += blockDim.x) pose[3 + i] = 0;
+    return;
+  }
+  for (int k = 1; k <= arm.S; ++k) {
+    const SegDev& sg = arm.seg[k - 1];
+    const uint32_t* Vk = V + (long)k * d.nw;
+    const int px = p[0], py = p[1], pz = p[2];
+    const long pi = lin(d, px, py, pz);
+    const uint32_t* M = sg.mask + (pi >> 5);
+    const int pb = (int)(pi & 31);
+    if (threadIdx.x == 0) best = ~0ull;
+    __syncthreads();
+    for (int e = threadIdx.x; e < sg.n; e += blockDim.x) {
+      const int32_t o = __ldg(sg.off + e);
+      const int qx = px + unpack_x(o), qy = py + unpack_y(o), qz = pz + unpack_z(o);
+      if (!inside(d, qx, qy, qz)) continue;
+      const long qi = lin(d, qx, qy, qz);
+      if (!test_bit(Vk, qi)) continue;
+      if (!((__ldg(M + (long)e * d.nw) >> pb) & 1u)) continue;
+      unsigned long long key = (unsigned long long)qi;
+      if (nearest) {
+        const long dx = qx - nearest[3 * k], dy = qy - nearest[3 * k + 1], dz = qz - nearest[3 * k + 2];
+        key |= (unsigned long long)(dx * dx + dy * dy + dz * dz) << 32;
+      }
+      atomicMin(&best, key);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const long qi = (long)(best & 0xffffffffull);
+      p[0] = (int)(qi % d.nx);
+      p[1] = (int)((qi / d.nx) % d.ny);
+      p[2] = (int)(qi / ((long)d.nx * d.ny));
+      pose[3 * k] = p[0];
+      pose[3 * k + 1] = p[1];
+      pose[3 * k + 2] = p[2];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_traceback(Dims d, ArmDev arm, const int32_t* __restrict__ root,
+                                                   const uint32_t* __restrict__ V, long vs,
+                                                   int32_t* poses, int32_t* found) {
+  const int q = blockIdx.x;
+  traceback_block(d, arm, root[0], root[1], root[2], V + q * vs, nullptr,
+                  poses + (long)q * 3 * (arm.S + 1), found + q);
+}
+
+cudaError_t launch_traceback(const Dims& d, const ArmDev& arm, const int32_t* root, const uint32_t* V,
+                             long vstride, int Q, int32_t* poses, int32_t* found, cudaStream_t st) {
+  if (Q <= 0) return cudaSuccess;
+  k_traceback<<<Q, 256, 0, st>>>(d, arm, root, V, vstride, poses, found);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_traceback_nearest(Dims d, ArmDev arm, const int32_t* root,
+                                                           const uint32_t* V, const int32_t* old_pose,
+                                                           int32_t* pose, int32_t* found) {
+  traceback_block(d, arm, root[0], root[1], root[2], V, old_pose, pose, found);
+}
+
+cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int32_t* root,
+                                     const uint32_t* V, const int32_t* old_pose, int32_t* pose,
+                                     int32_t* found, cudaStream_t st) {
+  k_traceback_nearest<<<1, 256, 0, st>>>(d, arm, root, V, old_pose, pose, found);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ a9: validate poses (G7)
+
+// Shell index of offset (x, y, z) by binary search over the table's order
+// (|d|^2, z, y, x); -1 when the offset is not in the shell.
+__device__ int shell_index(const SegDev& sg, int x, int y, int z) {
+  const int n2 = x * x + y * y + z * z;
+  if (n2 < sg.lo2 || n2 > sg.hi2) return -1;
+  int lo = 0, hi = sg.n - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int32_t o = __ldg(sg.off + mid);
+    const int ox = unpack_x(o), oy = unpack_y(o), oz = unpack_z(o);
+    const int on2 = ox * ox + oy * oy + oz * oz;
+    int c;
+    if (on2 != n2) c = on2 < n2 ? -1 : 1;
+    else if (oz != z) c = oz < z ? -1 : 1;
+    else if (oy != y) c = oy < y ? -1 : 1;
+    else if (ox != x) c = ox < x ? -1 : 1;
+    else return mid;
+    if (c < 0) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// One thread per (pose, segment); valid[pose] starts at 1 and is cleared by
+// any segment that leaves the grid, leaves its shell or meets an obstacle.
+__global__ void k_validate(Dims d, ArmDev arm, const uint32_t* __restrict__ occ,
+                           const int32_t* __restrict__ poses, int n, int32_t* valid) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)n * arm.S) return;
+  const int i = (int)(t / arm.S), k = (int)(t % arm.S) + 1;
+  const int32_t* P = poses + (long)i * 3 * (arm.S + 1);
+  const int ax = P[3 * (k - 1)], ay = P[3 * (k - 1) + 1], az = P[3 * (k - 1) + 2];
+  const int bx = P[3 * k], by = P[3 * k + 1], bz = P[3 * k + 2];
+  bool ok = inside(d, ax, ay, az) && inside(d, bx, by, bz);
+  if (ok) {
+    const SegDev& sg = arm.seg[k - 1];
+    const int e = shell_index(sg, bx - ax, by - ay, bz - az);
+    ok = e >= 0;
+    if (ok) {
+      const int s0 = __ldg(sg.sc_start + e), s1 = __ldg(sg.sc_start + e + 1);
+      for (int j = s0; j < s1 && ok; ++j) {
+        const int32_t v = __ldg(sg.sc + j);
+        ok = !test_bit(occ, lin(d, ax + unpack_x(v), ay + unpack_y(v), az + unpack_z(v)));
+      }
+    }
+  }
+  if (!ok) atomicAnd(valid + i, 0);
+}
+
+__global__ void k_fill_i32(int32_t* p, long n, int32_t v) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* occ,
+                            const int32_t* poses, int n, int32_t* valid, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_i32<<<grid_for(n, 256), 256, 0, st>>>(valid, n, 1);
+  const long t = (long)n * arm.S;
+  k_validate<<<grid_for(t, 256), 256, 0, st>>>(d, arm, occ, poses, n, valid);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------- a6: guide points + targets
+
+__device__ __forceinline__ long floor_div(long a, long b) {  // b > 0
+  long q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+
+__device__ __forceinline__ int isqrt_dev(int v) {  // floor(sqrt(v)), v >= 0
+  int r = (int)sqrtf((float)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+// One block per (path, waypoint).  Guide point by the nominal-arc rule, then
+// the waypoint target set T_j (free voxels within squared distance eps2,
+// grown to eps2_max when empty; T_{W-1} = {end effector}) intersected with
+// F_S, OR-ed into the (pre-zeroed) last survivor set of the waypoint.
+__global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__ occ,
+                                const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
+                                const int32_t* __restrict__ found, int W, int j_lo, int eps2,
+                                int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw) {
+  const int p = blockIdx.y;
+  const int j = blockIdx.x + j_lo;
+  const int S = arm.S;
+  const int32_t* R = reach + (long)p * 3 * (S + 1);
+  __shared__ int gp[3];
+  __shared__ int used;
+  const bool ok = !found || found[p];
+  if (threadIdx.x == 0) {
+    long lam = 0;
+    for (int k = 0; k < S; ++k) lam += arm.len[k];
+    const long num = (long)j * lam;
+    long Cprev = 0;
+    int k = S;
+    long c0 = 0;
+    for (int kk = 1; kk <= S; ++kk) {
+      const long c1 = Cprev + arm.len[kk - 1];
+      if (Cprev * (W - 1) <= num && num < c1 * (W - 1)) {
+        k = kk;
+        c0 = Cprev;
+        break;
+      }
+      Cprev = c1;
+    }
+    if (k == S) c0 = lam - arm.len[S - 1];
+    const long r = num - c0 * (W - 1);
+    const long den = (long)arm.len[k - 1] * (W - 1);
+    for (int i = 0; i < 3; ++i) {
+      const long a = ok ? R[3 * (k - 1) + i] : 0, b = ok ? R[3 * k + i] : 0;
+      gp[i] = (int)(a + floor_div(2 * r * (b - a) + den, 2 * den));
+      g[((long)p * W + j) * 3 + i] = gp[i];
+    }
+    used = -1;
+  }
+  __syncthreads();
+  if (!Vw) return;  // guide points only
+  uint32_t* VS = Vw + (((long)p * W + j) * (S + 1) + S) * d.nw;
+  if (!ok) {
+    if (threadIdx.x == 0) eps_used[(long)p * W + j] = -1;
+    return;
+  }
+  if (j == W - 1) {
+    if (threadIdx.x == 0) {
+      const int tx = R[3 * S], ty = R[3 * S + 1], tz = R[3 * S + 2];
+      if (inside(d, tx, ty, tz)) {
+        const long i = lin(d, tx, ty, tz);
+        if (test_bit(F_S, i)) atomicOr(VS + (i >> 5), 1u << (i & 31));
+      }
+      eps_used[(long)p * W + j] = 0;
+    }
+    return;
+  }
+  const int top = max(eps2, eps2_max);
+  for (int e2 = eps2; e2 <= top; ++e2) {
+    const int Rb = isqrt_dev(e2);
+    const int side = 2 * Rb + 1;
+    int any = 0;
+    for (int t = threadIdx.x; t < side * side * side; t += blockDim.x) {
+      const int x = gp[0] - Rb + t % side, y = gp[1] - Rb + (t / side) % side,
+                z = gp[2] - Rb + t / (side * side);
+      const int dx = x - gp[0], dy = y - gp[1], dz = z - gp[2];
+      if (dx * dx + dy * dy + dz * dz > e2 || !inside(d, x, y, z)) continue;
+      if (!test_bit(occ, lin(d, x, y, z))) any = 1;
+    }
+    if (__syncthreads_or(any)) {
+      if (threadIdx.x == 0) used = e2;
+      break;
+    }
+  }
+  __syncthreads();
+  const int e2 = used;
+  if (threadIdx.x == 0) eps_used[(long)p * W + j] = e2;
+  if (e2 < 0) return;
+  const int Rb = isqrt_dev(e2);
+  const int side = 2 * Rb + 1;
+  for (int t = threadIdx.x; t < side * side * side; t += blockDim.x) {
+    const int x = gp[0] - Rb + t % side, y = gp[1] - Rb + (t / side) % side,
+              z = gp[2] - Rb + t / (side * side);
+    const int dx = x - gp[0], dy = y - gp[1], dz = z - gp[2];
+    if (dx * dx + dy * dy + dz * dz > e2 || !inside(d, x, y, z)) continue;
+    const long i = lin(d, x, y, z);
+    if (!test_bit(occ, i) && test_bit(F_S, i)) atomicOr(VS + (i >> 5), 1u << (i & 31));
+  }
+}
+
+cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
+                                 const uint32_t* F_S, const int32_t* reach, const int32_t* found,
+                                 int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
+                                 int32_t* eps_used, uint32_t* Vw, cudaStream_t st) {
+  if (P <= 0 || W - j_lo <= 0) return cudaSuccess;
+  dim3 grid(W - j_lo, P);
+  k_guide_targets<<<grid, 128, 0, st>>>(d, arm, occ, F_S, reach, found, W, j_lo, eps2, eps2_max, g,
+                                        eps_used, Vw);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- a8: smooth chain per path
+
+// Sets written earlier in the same kernel are read with plain loads (the
+// read-only path is not coherent with in-kernel writes).
+__device__ __forceinline__ uint32_t ld_shifted_rw(const uint32_t* s, const Dims& d, int wx, int y, int z,
+                                                  int dx, int dy, int dz) {
+  const int yy = y + dy, zz = z + dz;
+  if ((unsigned)yy >= (unsigned)d.ny || (unsigned)zz >= (unsigned)d.nz) return 0u;
+  const uint32_t* row = s + ((long)zz * d.ny + yy) * d.wx;
+  const int w0 = wx + (dx >> 5);
+  const int sh = dx & 31;
+  const uint32_t lo = ((unsigned)w0 < (unsigned)d.wx) ? row[w0] : 0u;
+  if (sh == 0) return lo;
+  const uint32_t hi = ((unsigned)(w0 + 1) < (unsigned)d.wx) ? row[w0 + 1] : 0u;
+  return __funnelshift_r(lo, hi, sh);
+}
+
+// Bits of word (wx, y, z) inside the ball |v - c|^2 <= d2.
+__device__ __forceinline__ uint32_t ball_bits(int wx, int y, int z, const int* c, int d2) {
+  const int dy = y - c[1], dz = z - c[2];
+  const int rem = d2 - dy * dy - dz * dz;
+  if (rem < 0) return 0u;
+  const int r = isqrt_dev(rem);
+  const int lo = max(c[0] - r, 32 * wx) - 32 * wx, hi = min(c[0] + r, 32 * wx + 31) - 32 * wx;
+  if (lo > hi) return 0u;
+  const uint32_t upto = hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u);
+  return upto & ~((1u << lo) - 1u);
+}
+
+struct Box {
+  int x0, x1, y0, y1, z0, z1;  // inclusive voxel ranges, clipped to the grid
+};
+
+constexpr int kChainThreads = 512;
+
+__device__ __forceinline__ bool covers_full(long D2, int delta) { return (long)delta * delta >= D2; }
+
+struct ChainShared {
+  int ref[IK_MAX_SEG + 1][3];
+  Box box[IK_MAX_SEG + 1];
+  unsigned long long best;
+  int cur[3];
+};
+
+__device__ void chain_boxes(const Dims& d, ChainShared& sh, int S, int delta) {
+  if (threadIdx.x <= S) {
+    const int k = threadIdx.x;
+    Box b;
+    b.x0 = max(0, sh.ref[k][0] - delta);
+    b.x1 = min(d.nx - 1, sh.ref[k][0] + delta);
+    b.y0 = max(0, sh.ref[k][1] - delta);
+    b.y1 = min(d.ny - 1, sh.ref[k][1] + delta);
+    b.z0 = max(0, sh.ref[k][2] - delta);
+    b.z1 = min(d.nz - 1, sh.ref[k][2] + delta);
+    sh.box[k] = b;
+  }
+  __syncthreads();
+}
+
+// Number of words of a box and the coordinates of its t-th word.
+__device__ __forceinline__ long box_words(const Box& b) {
+  return (long)((b.x1 >> 5) - (b.x0 >> 5) + 1) * (b.y1 - b.y0 + 1) * (b.z1 - b.z0 + 1);
+}
+__device__ __forceinline__ void box_word(const Box& b, long t, int* wx, int* y, int* z) {
+  const int nwx = (b.x1 >> 5) - (b.x0 >> 5) + 1, ny = b.y1 - b.y0 + 1;
+  *wx = (b.x0 >> 5) + (int)(t % nwx);
+  *y = b.y0 + (int)((t / nwx) % ny);
+  *z = b.z0 + (int)(t / ((long)nwx * ny));
+}
+
+__device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, uint32_t* U) {
+  for (int k = 0; k <= S; ++k) {
+    const Box b = sh.box[k];
+    const long n = box_words(b);
+    for (long t = threadIdx.x; t < n; t += blockDim.x) {
+      int wx, y, z;
+      box_word(b, t, &wx, &y, &z);
+      const long w = ((long)z * d.ny + y) * d.wx + wx;
+      R[(long)k * d.nw + w] = 0u;
+      U[(long)k * d.nw + w] = 0u;
+    }
+  }
+  __syncthreads();
+}
+
+// One restricted propagation word: OR over the segment's offsets of the
+// source set shifted by the offset, limited to offsets whose source voxels
+// can fall in the source box, AND edge mask, within `m`.
+__device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const uint32_t* src,
+                                                    const Box& sb, int wx, int y, int z, long w,
+                                                    uint32_t m) {
+  uint32_t acc = 0;
+  for (int e = 0; e < sg.n; ++e) {
+    const int32_t o = __ldg(sg.off + e);
+    const int oy = unpack_y(o), oz = unpack_z(o);
+    const int sy = y + oy, sz = z + oz;
+    if (sy < sb.y0 || sy > sb.y1 || sz < sb.z0 || sz > sb.z1) continue;
+    const int ox = unpack_x(o);
+    const int sx = 32 * wx + ox;
+    if (sx + 31 < sb.x0 || sx > sb.x1) continue;
+    const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ox, oy, oz);
+    if (x & m & ~acc) {
+      acc |= x & __ldg(sg.mask + (long)e * d.nw + w);
+      if ((acc & m) == m) break;
+    }
+  }
+  return acc & m;
+}
+
+// Forward restriction: R_0 = {root}, R_k = (V_k & Ball(ref_k, delta)) & D_k(R_{k-1}).
+__device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* V,
+                              uint32_t* R, int delta2) {
+  const int S = arm.S;
+  if (threadIdx.x == 0) {
+    const long i = lin(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]);
+    R[i >> 5] = 1u << (i & 31);
+  }
+  __syncthreads();
+  for (int k = 1; k <= S; ++k) {
+    const Box b = sh.box[k], sb = sh.box[k - 1];
+    const SegDev& sg = arm.seg[k - 1];
+    const uint32_t* src = R + (long)(k - 1) * d.nw;
+    const uint32_t* Vk = V + (long)k * d.nw;
+    uint32_t* dst = R + (long)k * d.nw;
+    const long n = box_words(b);
+    int any = 0;
+    for (long t = threadIdx.x; t < n; t += blockDim.x) {
+      int wx, y, z;
+      box_word(b, t, &wx, &y, &z);
+      const long w = ((long)z * d.ny + y) * d.wx + wx;
+      const uint32_t m = ball_bits(wx, y, z, sh.ref[k], delta2) & __ldg(Vk + w);
+      if (!m) continue;
+      const uint32_t acc = restricted_word(d, sg, src, sb, wx, y, z, w, m);
+      if (acc) {
+        dst[w] = acc;
+        any = 1;
+      }
+    }
+    if (!__syncthreads_or(any)) return false;
+  }
+  return true;
+}
+
+// Backward restriction: U_S = R_S, U_k = R_k & D_{k+1}(U_{k+1}).
+__device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* R,
+                               uint32_t* U) {
+  const int S = arm.S;
+  {
+    const Box b = sh.box[S];
+    const long n = box_words(b);
+    for (long t = threadIdx.x; t < n; t += blockDim.x) {
+      int wx, y, z;
+      box_word(b, t, &wx, &y, &z);
+      const long w = ((long)z * d.ny + y) * d.wx + wx;
+      U[(long)S * d.nw + w] = R[(long)S * d.nw + w];
+    }
+  }
+  __syncthreads();
+  for (int k = S - 1; k >= 0; --k) {
+    const Box b = sh.box[k], sb = sh.box[k + 1];
+    const SegDev& sg = arm.seg[k];
+    const uint32_t* src = U + (long)(k + 1) * d.nw;
+    const uint32_t* Rk = R + (long)k * d.nw;
+    uint32_t* dst = U + (long)k * d.nw;
+    const long n = box_words(b);
+    for (long t = threadIdx.x; t < n; t += blockDim.x) {
+      int wx, y, z;
+      box_word(b, t, &wx, &y, &z);
+      const long w = ((long)z * d.ny + y) * d.wx + wx;
+      const uint32_t m = Rk[w];
+      if (!m) continue;
+      const uint32_t acc = restricted_word(d, sg, src, sb, wx, y, z, w, m);
+      if (acc) dst[w] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Minimum-index traceback through sets X_0..X_S (X_0 holds the root):
+// p_k = min linear index q in X_k with p_{k-1} -> q a valid segment k.
+// `coherent` selects plain loads for sets written in this kernel.
+template <bool kCoherent>
+__device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* X,
+                            int32_t* pose) {
+  const int S = arm.S;
+  if (threadIdx.x == 0) {
+    sh.cur[0] = sh.ref[0][0];
+    sh.cur[1] = sh.ref[0][1];
+    sh.cur[2] = sh.ref[0][2];
+    pose[0] = sh.cur[0];
+    pose[1] = sh.cur[1];
+    pose[2] = sh.cur[2];
+  }
+  __syncthreads();
+  for (int k = 1; k <= S; ++k) {
+    const SegDev& sg = arm.seg[k - 1];
+    const uint32_t* Xk = X + (long)k * d.nw;
+    const int px = sh.cur[0], py = sh.cur[1], pz = sh.cur[2];
+    const long pi = lin(d, px, py, pz);
+    const uint32_t* M = sg.mask + (pi >> 5);
+    const int pb = (int)(pi & 31);
+    if (threadIdx.x == 0) sh.best = ~0ull;
+    __syncthreads();
+    for (int e = threadIdx.x; e < sg.n; e += blockDim.x) {
+      const int32_t o = __ldg(sg.off + e);
+      const int qx = px + unpack_x(o), qy = py + unpack_y(o), qz = pz + unpack_z(o);
+      if (!inside(d, qx, qy, qz)) continue;
+      const long qi = lin(d, qx, qy, qz);
+      const uint32_t word = kCoherent ? Xk[qi >> 5] : __ldg(Xk + (qi >> 5));
+      if (!((word >> (qi & 31)) & 1u)) continue;
+      if (!((__ldg(M + (long)e * d.nw) >> pb) & 1u)) continue;
+      atomicMin(&sh.best, (unsigned long long)qi);
+    }
+    __syncthreads();
+    const unsigned long long best = sh.best;
+    if (best == ~0ull) return false;
+    if (threadIdx.x == 0) {
+      const long qi = (long)best;
+      sh.cur[0] = (int)(qi % d.nx);
+      sh.cur[1] = (int)((qi / d.nx) % d.ny);
+      sh.cur[2] = (int)(qi / ((long)d.nx * d.ny));
+      pose[3 * k] = sh.cur[0];
+      pose[3 * k + 1] = sh.cur[1];
+      pose[3 * k + 2] = sh.cur[2];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+__device__ bool chain_feasible(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* V,
+                               uint32_t* R, uint32_t* U, int delta) {
+  chain_boxes(d, sh, arm.S, delta);
+  const bool ok = chain_forward(d, arm, sh, V, R, delta * delta);
+  chain_clear(d, sh, arm.S, R, U);
+  return ok;
+}
+
+__global__ void __launch_bounds__(kChainThreads) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
+  __shared__ ChainShared sh;
+  const int p = blockIdx.x, S = arm.S, W = a.W;
+  const long pose_sz = 3L * (S + 1);
+  int32_t* poses = a.poses + (long)p * W * pose_sz;
+  int32_t* relax = a.relax + (long)p * W * 2;
+  uint32_t* R = a.scratch + (long)p * 2 * (S + 1) * d.nw;
+  uint32_t* U = R + (long)(S + 1) * d.nw;
+  const long D2 = (long)(d.nx - 1) * (d.nx - 1) + (long)(d.ny - 1) * (d.ny - 1) +
+                  (long)(d.nz - 1) * (d.nz - 1);
+  if (a.found && !a.found[p]) {
+    for (long i = threadIdx.x; i < W * pose_sz; i += blockDim.x) poses[i] = 0;
+    for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) relax[i] = -1;
+    if (threadIdx.x == 0) a.status[p] = IK_PATH_UNREACHABLE;
+    return;
+  }
+  bool relaxed = false, broken = false;
+  const int n_steps = a.mode == 0 ? W - 1 : W - 1 - a.c;
+  if (threadIdx.x == 0) {
+    if (a.mode == 0) {
+      relax[2 * (W - 1)] = 0;
+      relax[2 * (W - 1) + 1] = 0;
+    } else {
+      for (int j = 0; j <= a.c; ++j) relax[2 * j] = relax[2 * j + 1] = 0;
+    }
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    const int j = a.mode == 0 ? W - 2 - s : a.c + 1 + s;
+    const int rj = a.mode == 0 ? j + 1 : j - 1;
+    const uint32_t* V = a.Vw + ((long)p * W + j) * (S + 1) * d.nw;
+    int32_t* pose = poses + (long)j * pose_sz;
+    const int32_t* refp = poses + (long)rj * pose_sz;
+    if (threadIdx.x < (S + 1) * 3) sh.ref[threadIdx.x / 3][threadIdx.x % 3] = refp[threadIdx.x];
+    const int eps = a.eps_used[(long)p * W + j];
+    if (j < W - 1 && eps != a.relaxed_eps_base) relaxed = true;
+    __syncthreads();
+    if (threadIdx.x == 0) relax[2 * j + 1] = eps;
+    const bool vok = inside(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]) &&
+                     test_bit(V, lin(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]));
+    int m_star = -1;
+    if (vok) {
+      // smallest m with a chain inside the balls of radius delta + m; the
+      // ball covers the grid once (delta + m)^2 >= D2, and then a chain exists
+      // because V is non-empty.  Feasibility grows with m, so a doubling then
+      // bisecting search finds the same m as trying m = 0, 1, 2, ... in turn.
+      auto covers = [&](int m) { return (long)(a.delta + m) * (a.delta + m) >= D2; };
+      int lo = -1, hi = -1;
+      for (int m = 0; m <= 3; ++m) {
+        if (covers(m) || chain_feasible(d, arm, sh, V, R, U, a.delta + m)) {
+          hi = m;
+          break;
+        }
+        lo = m;
+      }
+      if (hi < 0) {
+        int step = 4;
+        for (;;) {
+          const int m = lo + step;
+          if (covers(m) || chain_feasible(d, arm, sh, V, R, U, a.delta + m)) {
+            hi = m;
+            break;
+          }
+          lo = m;
+          step *= 2;
+        }
+        while (hi - lo > 1) {
+          const int mid = lo + (hi - lo) / 2;
+          if (covers(mid) || chain_feasible(d, arm, sh, V, R, U, a.delta + mid)) hi = mid;
+          else lo = mid;
+        }
+      }
+      m_star = hi;
+      if (a.max_relax >= 0 && m_star > a.max_relax) m_star = -1;
+    }
+    bool done = false;
+    if (m_star >= 0) {
+      if (covers_full(D2, a.delta + m_star)) {
+        done = chain_trace<false>(d, arm, sh, V, pose);
+      } else {
+        chain_boxes(d, sh, S, a.delta + m_star);
+        const int dm = a.delta + m_star;
+        const bool ok = chain_forward(d, arm, sh, V, R, dm * dm);
+        if (ok) {
+          chain_backward(d, arm, sh, R, U);
+          done = chain_trace<true>(d, arm, sh, U, pose);
+        }
+        chain_clear(d, sh, S, R, U);
+      }
+    }
+    if (done) {
+      if (m_star > 0) relaxed = true;
+      if (threadIdx.x == 0) relax[2 * j] = m_star;
+    } else {
+      broken = true;
+      for (int i = threadIdx.x; i < pose_sz; i += blockDim.x) pose[i] = refp[i];
+      if (threadIdx.x == 0) relax[2 * j] = -1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    a.status[p] = broken ? IK_PATH_BROKEN : (relaxed ? IK_PATH_RELAXED : IK_PATH_OK);
+}
+
+cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
+                                cudaStream_t st) {
+  if (a.P <= 0) return cudaSuccess;
+  k_smooth_chain<<<a.P, kChainThreads, 0, st>>>(d, arm, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ikb

@@ -1,0 +1,133 @@
+// Host-side construction of the per-segment tables: the shell of admissible
+// offsets and each offset's closed supercover.
+//
+// The shell replaces the paper's quiver (section "Discretization of the
+// segment articulations": unit directions times the segment length) by every
+// integer offset whose length is within tol of the segment length; the
+// supercover replaces the n equispaced collision sample points of section
+// "Testing for collisions" by every voxel whose closed cube meets the
+// segment, so that no obstacle voxel can slip between sample points.
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+
+#include "ik_internal.h"
+
+namespace ikb {
+
+void shell_bounds(int len, double tol, int* lo2, int* hi2) {
+  double a = (double)len - tol;
+  double b = (double)len + tol;
+  double lo = (a > 0.0) ? std::ceil(a * a) : 0.0;
+  *lo2 = std::max(1, (int)lo);
+  *hi2 = (int)std::floor(b * b);
+}
+
+static int isqrt_floor(long v) {  // largest r with r*r <= v, v >= 0
+  long r = (long)std::sqrt((double)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return (int)r;
+}
+
+static int isqrt_ceil(long v) {  // smallest r >= 0 with r*r >= v
+  if (v <= 0) return 0;
+  int r = isqrt_floor(v);
+  return (long)r * r == v ? r : r + 1;
+}
+
+// Closed supercover of the segment 0 -> d by walking its boundary
+// crossings.  Along axis i the segment t*d crosses the voxel faces
+// x_i = s_i (k + 1/2), k = 0 .. |d_i| - 1, at t = (2k + 1) / (2 |d_i|).
+// Crossings are visited in increasing t (exact integer comparison).  At a
+// crossing time shared by the axes in A, the segment point lies on the faces
+// of every voxel cur + sum_{i in B} s_i e_i for B a subset of A, so all of
+// them are touched; then the walk steps to cur + sum_{i in A} s_i e_i.
+void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out) {
+  const int d[3] = {dx, dy, dz};
+  int n[3], s[3], k[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i) {
+    n[i] = d[i] < 0 ? -d[i] : d[i];
+    s[i] = d[i] < 0 ? -1 : 1;
+  }
+  std::vector<std::array<int, 3>> vox;
+  int cur[3] = {0, 0, 0};
+  vox.push_back({0, 0, 0});
+  for (;;) {
+    // earliest pending crossing: compare (2k_i+1)/(2n_i) by cross-multiplying
+    int best = -1;
+    for (int i = 0; i < 3; ++i) {
+      if (k[i] >= n[i]) continue;
+      if (best < 0 || (long)(2 * k[i] + 1) * n[best] < (long)(2 * k[best] + 1) * n[i]) best = i;
+    }
+    if (best < 0) break;
+    int A[3], na = 0;
+    for (int i = 0; i < 3; ++i) {
+      if (k[i] >= n[i]) continue;
+      if ((long)(2 * k[i] + 1) * n[best] == (long)(2 * k[best] + 1) * n[i]) A[na++] = i;
+    }
+    for (int mask = 1; mask < (1 << na); ++mask) {
+      std::array<int, 3> v = {cur[0], cur[1], cur[2]};
+      for (int b = 0; b < na; ++b)
+        if (mask & (1 << b)) v[A[b]] += s[A[b]];
+      vox.push_back(v);
+    }
+    for (int b = 0; b < na; ++b) {
+      cur[A[b]] += s[A[b]];
+      ++k[A[b]];
+    }
+  }
+  std::sort(vox.begin(), vox.end(), [](const std::array<int, 3>& a, const std::array<int, 3>& b) {
+    if (a[2] != b[2]) return a[2] < b[2];
+    if (a[1] != b[1]) return a[1] < b[1];
+    return a[0] < b[0];
+  });
+  vox.erase(std::unique(vox.begin(), vox.end()), vox.end());
+  out->clear();
+  for (auto& v : vox) out->push_back(pack3(v[0], v[1], v[2]));
+}
+
+void build_shell(int lo2, int hi2, ShellHost* sh) {
+  struct Off {
+    int x, y, z, n2;
+  };
+  std::vector<Off> offs;
+  const int R = isqrt_floor(hi2);
+  for (int z = -R; z <= R; ++z) {
+    for (int y = -R; y <= R; ++y) {
+      long yz = (long)y * y + (long)z * z;
+      if (yz > hi2) continue;
+      int xmin = isqrt_ceil(std::max(0L, (long)lo2 - yz));
+      int xmax = isqrt_floor(hi2 - yz);
+      if (xmin > xmax) continue;
+      for (int x = -xmax; x <= xmax; ++x) {
+        int ax = x < 0 ? -x : x;
+        if (ax < xmin) continue;
+        offs.push_back({x, y, z, (int)(x * x + yz)});
+      }
+    }
+  }
+  std::sort(offs.begin(), offs.end(), [](const Off& a, const Off& b) {
+    if (a.n2 != b.n2) return a.n2 < b.n2;
+    if (a.z != b.z) return a.z < b.z;
+    if (a.y != b.y) return a.y < b.y;
+    return a.x < b.x;
+  });
+  sh->lo2 = lo2;
+  sh->hi2 = hi2;
+  sh->off.clear();
+  sh->sc.clear();
+  sh->sc_start.assign(1, 0);
+  sh->max_sc = 0;
+  std::vector<int32_t> sc;
+  for (const Off& o : offs) {
+    sh->off.push_back(pack3(o.x, o.y, o.z));
+    supercover_traverse(o.x, o.y, o.z, &sc);
+    sh->sc.insert(sh->sc.end(), sc.begin(), sc.end());
+    sh->sc_start.push_back((int32_t)sh->sc.size());
+    sh->max_sc = std::max(sh->max_sc, (int)sc.size());
+  }
+}
+
+}  // namespace ikb

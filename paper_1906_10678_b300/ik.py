@@ -1,0 +1,373 @@
+"""Python binding of the C ABI in ``include/ik.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+part of the method itself: it converts arguments to pointers, calls the
+library, checks the return code and shapes the outputs.  Host arrays are
+numpy; device arrays are ``torch`` CUDA tensors (PyTorch supplies device
+memory and streams, nothing else).
+
+The library must have been built (``python -m paper_1906_10678_b300.build``);
+importing this module without it raises ``ImportError``: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libik_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1906_10678_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+IK_OK, IK_ERR_ARG, IK_ERR_OOM, IK_ERR_CUDA, IK_ERR_TIMEOUT, IK_ERR_STATE, IK_ERR_UNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6)
+IK_PATH_OK, IK_PATH_RELAXED, IK_PATH_BROKEN, IK_PATH_UNREACHABLE, IK_PATH_KEPT = range(5)
+IK_MAX_SEG = 16
+IK_MAX_LEN = 100
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+
+
+class IkArm(ctypes.Structure):
+    _fields_ = [("n_seg", ctypes.c_int32), ("len", ctypes.POINTER(ctypes.c_int32)),
+                ("tol", ctypes.c_float)]
+
+
+class IkPathParams(ctypes.Structure):
+    _fields_ = [("n_way", ctypes.c_int32), ("delta", ctypes.c_int32), ("eps2", ctypes.c_int32),
+                ("eps2_max", ctypes.c_int32), ("max_relax", ctypes.c_int32)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("ik_version", _i, [])
+_sig("ik_strerror", ctypes.c_char_p, [_i])
+_sig("ik_last_error_message", ctypes.c_char_p, [])
+_sig("ik_create_grid", _i, [_i, _i, _i, _vp, ctypes.POINTER(_vp)])
+_sig("ik_destroy_grid", _i, [_vp])
+_sig("ik_grid_words", ctypes.c_size_t, [_vp])
+_sig("ik_set_obstacles", _i, [_vp, _vp, ctypes.c_size_t, _i])
+_sig("ik_set_boxes", _i, [_vp, _vp, _i, _i])
+_sig("ik_get_obstacles", _i, [_vp, _vp, ctypes.c_size_t, _i])
+_sig("ik_forward_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i])
+_sig("ik_solve_reach", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _vp, _vp, ctypes.POINTER(_i)])
+_sig("ik_solve_reach_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _vp, _vp, _i])
+_sig("ik_guide", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
+_sig("ik_waypoint_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, _i, _vp, _vp])
+_sig("ik_plan_path", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPathParams), _vp, _vp,
+                          ctypes.POINTER(_i)])
+_sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
+                                ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp, _i])
+_sig("ik_validate_poses", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
+_sig("ik_replan", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, ctypes.POINTER(IkPathParams), _vp,
+                       _vp, ctypes.POINTER(_i)])
+_sig("ik_shell_offsets", _i, [_i, ctypes.c_float, _vp, _vp, _i])
+_sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
+
+EXPORTED = [
+    "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
+    "ik_grid_words", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
+    "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
+    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_shell_offsets",
+    "ik_supercover_offsets",
+]
+
+
+class IkError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.ik_strerror(code).decode()
+        extra = _lib.ik_last_error_message().decode()
+        super().__init__(f"{where}: {msg} ({code}){': ' + extra if extra else ''}")
+        self.code = code
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != IK_OK:
+        raise IkError(rc, where)
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _dev_ptr(t) -> int:
+    """Device pointer of a contiguous CUDA tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+class Arm:
+    """Keeps the length array alive while the C struct points at it."""
+
+    def __init__(self, lengths: Sequence[int], tol: float = 0.5):
+        self.lengths = _i32(lengths)
+        self.c = IkArm(len(self.lengths), self.lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                       float(tol))
+
+    @property
+    def S(self) -> int:
+        return len(self.lengths)
+
+
+def _arm(a) -> Arm:
+    return a if isinstance(a, Arm) else Arm(a)
+
+
+def path_params(n_way: int, delta: int = 3, eps2: int = 2, eps2_max: int = 8,
+                max_relax: int = -1) -> IkPathParams:
+    return IkPathParams(int(n_way), int(delta), int(eps2), int(eps2_max), int(max_relax))
+
+
+# ------------------------------------------------------------------ layout
+
+def pack_bits(mask: np.ndarray) -> np.ndarray:
+    """bool/uint8 [nz][ny][nx] -> uint32 words (x-packed, bit b = x % 32)."""
+    m = np.ascontiguousarray(np.asarray(mask).astype(bool))
+    nz, ny, nx = m.shape
+    b = np.packbits(m.reshape(nz, ny, nx // 32, 32), axis=-1, bitorder="little")
+    return np.ascontiguousarray(b).view(np.uint32).reshape(-1)
+
+
+def unpack_bits(words: np.ndarray, shape) -> np.ndarray:
+    """uint32 words -> bool [nz][ny][nx] for grid ``shape`` = (nx, ny, nz)."""
+    nx, ny, nz = shape
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32)).reshape(-1, nz, ny, nx // 32)
+    b = np.unpackbits(w.view(np.uint8).reshape(w.shape[0], nz, ny, nx // 32, 4), axis=-1,
+                      bitorder="little")
+    return b.reshape(w.shape[0], nz, ny, nx).astype(bool)
+
+
+# --------------------------------------------------------------- functions
+
+def ik_version() -> int:
+    return _lib.ik_version()
+
+
+def ik_create_grid(nx: int, ny: int, nz: int, stream: int = 0) -> int:
+    h = _vp()
+    _check(_lib.ik_create_grid(nx, ny, nz, _vp(stream) if stream else None, ctypes.byref(h)),
+           "ik_create_grid")
+    return h.value
+
+
+def ik_destroy_grid(g: int) -> None:
+    _check(_lib.ik_destroy_grid(g), "ik_destroy_grid")
+
+
+def ik_grid_words(g: int) -> int:
+    return int(_lib.ik_grid_words(g))
+
+
+def ik_set_boxes(g: int, boxes) -> None:
+    if hasattr(boxes, "is_cuda"):
+        _check(_lib.ik_set_boxes(g, _dev_ptr(boxes), boxes.shape[0], 1), "ik_set_boxes")
+        return
+    b = _i32(boxes).reshape(-1, 6)
+    _check(_lib.ik_set_boxes(g, _np_ptr(b), len(b), 0), "ik_set_boxes")
+
+
+def ik_set_obstacles(g: int, words) -> None:
+    if hasattr(words, "is_cuda"):
+        _check(_lib.ik_set_obstacles(g, _dev_ptr(words), words.numel(), 1), "ik_set_obstacles")
+        return
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    _check(_lib.ik_set_obstacles(g, _np_ptr(w), w.size, 0), "ik_set_obstacles")
+
+
+def ik_get_obstacles(g: int) -> np.ndarray:
+    out = np.zeros(ik_grid_words(g), np.uint32)
+    _check(_lib.ik_get_obstacles(g, _np_ptr(out), out.size, 0), "ik_get_obstacles")
+    return out
+
+
+def ik_forward_sets(g: int, arm, root) -> np.ndarray:
+    arm = _arm(arm)
+    out = np.zeros((arm.S + 1, ik_grid_words(g)), np.uint32)
+    _check(_lib.ik_forward_sets(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _np_ptr(out), 0),
+           "ik_forward_sets")
+    return out
+
+
+def ik_solve_reach(g: int, arm, root, target, want_sets: bool = False):
+    """Returns (pose [S+1][3], found, vsets [S+1][words] or None)."""
+    arm = _arm(arm)
+    pose = np.zeros((arm.S + 1, 3), np.int32)
+    vs = np.zeros((arm.S + 1, ik_grid_words(g)), np.uint32) if want_sets else None
+    f = _i()
+    _check(_lib.ik_solve_reach(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _np_ptr(_i32(target)),
+                               _np_ptr(pose), _np_ptr(vs), ctypes.byref(f)), "ik_solve_reach")
+    return pose, bool(f.value), vs
+
+
+def ik_solve_reach_many(g: int, arm, root, targets, want_sets: bool = False):
+    """Host form.  Returns (poses [n][S+1][3], found [n], vsets or None)."""
+    arm = _arm(arm)
+    t = _i32(targets).reshape(-1, 3)
+    n = len(t)
+    poses = np.zeros((n, arm.S + 1, 3), np.int32)
+    found = np.zeros(n, np.int32)
+    vs = np.zeros((n, arm.S + 1, ik_grid_words(g)), np.uint32) if want_sets else None
+    _check(_lib.ik_solve_reach_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _np_ptr(t), n,
+                                    _np_ptr(poses), _np_ptr(found), _np_ptr(vs), 0),
+           "ik_solve_reach_many")
+    return poses, found, vs
+
+
+def ik_solve_reach_many_device(g: int, arm, root, targets, poses, found) -> None:
+    """Device form: ``targets`` int32 [n][3], ``poses`` int32 [n][S+1][3] and
+    ``found`` int32 [n] are CUDA tensors."""
+    arm = _arm(arm)
+    n = targets.shape[0]
+    _check(_lib.ik_solve_reach_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _dev_ptr(targets),
+                                    n, _dev_ptr(poses), _dev_ptr(found), None, 1),
+           "ik_solve_reach_many")
+
+
+def ik_guide(g: int, arm, reach_pose, n_way: int) -> np.ndarray:
+    arm = _arm(arm)
+    out = np.zeros((n_way, 3), np.int32)
+    _check(_lib.ik_guide(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), n_way, _np_ptr(out)),
+           "ik_guide")
+    return out
+
+
+def ik_waypoint_sets(g: int, arm, reach_pose, n_way: int, eps2: int = 2, eps2_max: int = 8,
+                     want_sets: bool = True):
+    """Returns (eps2_used [W], vsets [W][S+1][words] or None)."""
+    arm = _arm(arm)
+    used = np.zeros(n_way, np.int32)
+    vs = np.zeros((n_way, arm.S + 1, ik_grid_words(g)), np.uint32) if want_sets else None
+    _check(_lib.ik_waypoint_sets(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), n_way, eps2,
+                                 eps2_max, _np_ptr(used), _np_ptr(vs)), "ik_waypoint_sets")
+    return used, vs
+
+
+def ik_plan_path(g: int, arm, reach_pose, n_way: int, delta: int = 3, eps2: int = 2,
+                 eps2_max: int = 8, max_relax: int = -1):
+    """Returns (poses [W][S+1][3], relax [W][2], status)."""
+    arm = _arm(arm)
+    pp = path_params(n_way, delta, eps2, eps2_max, max_relax)
+    poses = np.zeros((n_way, arm.S + 1, 3), np.int32)
+    relax = np.zeros((n_way, 2), np.int32)
+    st = _i()
+    _check(_lib.ik_plan_path(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), ctypes.byref(pp),
+                             _np_ptr(poses), _np_ptr(relax), ctypes.byref(st)), "ik_plan_path")
+    return poses, relax, st.value
+
+
+def ik_reach_path_many(g: int, arm, root, targets, n_way: int, delta: int = 3, eps2: int = 2,
+                       eps2_max: int = 8, max_relax: int = -1):
+    """Host form.  Returns (reach [n][S+1][3], found [n], poses [n][W][S+1][3],
+    relax [n][W][2], status [n])."""
+    arm = _arm(arm)
+    pp = path_params(n_way, delta, eps2, eps2_max, max_relax)
+    t = _i32(targets).reshape(-1, 3)
+    n, S = len(t), arm.S
+    reach = np.zeros((n, S + 1, 3), np.int32)
+    found = np.zeros(n, np.int32)
+    poses = np.zeros((n, n_way, S + 1, 3), np.int32)
+    relax = np.zeros((n, n_way, 2), np.int32)
+    status = np.zeros(n, np.int32)
+    _check(_lib.ik_reach_path_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _np_ptr(t), n,
+                                   ctypes.byref(pp), _np_ptr(reach), _np_ptr(found), _np_ptr(poses),
+                                   _np_ptr(relax), _np_ptr(status), 0), "ik_reach_path_many")
+    return reach, found, poses, relax, status
+
+
+def ik_reach_path_many_device(g: int, arm, root, targets, n_way: int, reach, found, poses, relax,
+                              status, delta: int = 3, eps2: int = 2, eps2_max: int = 8,
+                              max_relax: int = -1) -> None:
+    """Device form: every array argument is a contiguous int32 CUDA tensor."""
+    arm = _arm(arm)
+    pp = path_params(n_way, delta, eps2, eps2_max, max_relax)
+    _check(_lib.ik_reach_path_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _dev_ptr(targets),
+                                   targets.shape[0], ctypes.byref(pp), _dev_ptr(reach),
+                                   _dev_ptr(found), _dev_ptr(poses), _dev_ptr(relax),
+                                   _dev_ptr(status), 1), "ik_reach_path_many")
+
+
+def ik_validate_poses(g: int, arm, poses) -> np.ndarray:
+    arm = _arm(arm)
+    p = _i32(poses).reshape(-1, arm.S + 1, 3)
+    out = np.zeros(len(p), np.int32)
+    _check(_lib.ik_validate_poses(g, ctypes.byref(arm.c), _np_ptr(p), len(p), _np_ptr(out)),
+           "ik_validate_poses")
+    return out
+
+
+def ik_replan(g: int, arm, poses, current: int, delta: int = 3, eps2: int = 2, eps2_max: int = 8,
+              max_relax: int = -1):
+    """Returns (poses [W][S+1][3], relax [W][2], status)."""
+    arm = _arm(arm)
+    p = _i32(poses)
+    W = p.shape[0]
+    pp = path_params(W, delta, eps2, eps2_max, max_relax)
+    out = np.zeros_like(p)
+    relax = np.zeros((W, 2), np.int32)
+    st = _i()
+    _check(_lib.ik_replan(g, ctypes.byref(arm.c), _np_ptr(p), W, current, ctypes.byref(pp),
+                          _np_ptr(out), _np_ptr(relax), ctypes.byref(st)), "ik_replan")
+    return out, relax, st.value
+
+
+def ik_shell_offsets(length: int, tol: float = 0.5) -> Tuple[Tuple[int, int], np.ndarray]:
+    b = np.zeros(2, np.int32)
+    n = _lib.ik_shell_offsets(length, tol, _np_ptr(b), None, 0)
+    if n < 0:
+        raise IkError(n, "ik_shell_offsets")
+    out = np.zeros((max(n, 1), 3), np.int32)
+    _lib.ik_shell_offsets(length, tol, _np_ptr(b), _np_ptr(out), n)
+    return (int(b[0]), int(b[1])), out[:n]
+
+
+def ik_supercover_offsets(d) -> np.ndarray:
+    d = _i32(d)
+    cap = int(np.prod(np.abs(d) + 1)) + 8
+    out = np.zeros((cap, 3), np.int32)
+    n = _lib.ik_supercover_offsets(_np_ptr(d), _np_ptr(out), cap)
+    if n < 0:
+        raise IkError(n, "ik_supercover_offsets")
+    return out[:n]
+
+
+class Grid:
+    """Owning wrapper of an ``ik_grid`` handle."""
+
+    def __init__(self, nx: int, ny: int, nz: int, stream: int = 0):
+        self.shape = (nx, ny, nz)
+        self.h = ik_create_grid(nx, ny, nz, stream)
+
+    def close(self) -> None:
+        if self.h:
+            ik_destroy_grid(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,87 @@
+"""CPU checks of the CUDA library: it loads, exports every symbol its header
+declares, and its host-built tables (shell offsets, incremental supercover)
+agree with the oracle's independent constructions.  No compute call needs a
+GPU here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ik():
+    from paper_1906_10678_b300 import build
+    build.build()
+    from paper_1906_10678_b300 import ik as mod
+    return mod
+
+
+def _declared_symbols():
+    with open(os.path.join(ROOT, "include", "ik.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"IK_API\s+[\w\s\*]+?\b(ik_\w+)\s*\(", text)))
+
+
+def test_header_symbols_exported(ik):
+    declared = _declared_symbols()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(ik._lib, name), name
+    assert set(declared) == set(ik.EXPORTED)
+
+
+@pytest.mark.parametrize("L", list(range(1, 25)) + [40, 64, 100])
+def test_shell_tables_match_oracle(ik, L):
+    (lo, hi), off = ik.ik_shell_offsets(L, 0.5)
+    assert (lo, hi) == O.shell_bounds(L, 0.5)
+    assert (off == O.shell(lo, hi)).all()
+
+
+def test_shell_bounds_other_tolerances(ik):
+    for tol in (0.0, 0.25, 0.3, 0.75, 0.9):
+        for L in (1, 2, 5, 11):
+            (lo, hi), _ = ik.ik_shell_offsets(L, tol)
+            assert (lo, hi) == O.shell_bounds(L, float(np.float32(tol))), (L, tol)
+
+
+def test_supercover_traversal_matches_slab_test_every_offset(ik):
+    n = 0
+    for L in range(1, 25):
+        lo, hi = O.shell_bounds(L)
+        for d in O.shell(lo, hi):
+            a = ik.ik_supercover_offsets(d)
+            b = O.supercover((0, 0, 0), d)
+            assert a.shape == b.shape and (a == b).all(), (L, d)
+            n += 1
+    assert n == sum(len(O.shell(*O.shell_bounds(L))) for L in range(1, 25))
+
+
+def test_supercover_worked_examples(ik):
+    got = {tuple(v) for v in ik.ik_supercover_offsets([1, 1, 0]).tolist()}
+    assert got == {(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0)}
+    assert len(ik.ik_supercover_offsets([1, 1, 1])) == 8
+    assert len(ik.ik_supercover_offsets([2, 1, 0])) == 4
+
+
+def test_bit_layout_roundtrip(ik):
+    rng = np.random.default_rng(0)
+    m = rng.random((5, 7, 64)) < 0.3
+    w = ik.pack_bits(m)
+    assert w.dtype == np.uint32 and w.size == 5 * 7 * 2
+    # voxel (x, y, z) is bit x % 32 of word (z*ny + y)*(nx/32) + x // 32
+    x, y, z = 37, 4, 3
+    assert bool((w[(z * 7 + y) * 2 + x // 32] >> (x % 32)) & 1) == bool(m[z, y, x])
+    assert (ik.unpack_bits(w, (64, 7, 5))[0] == m).all()
+
+
+def test_argument_errors_without_gpu(ik):
+    with pytest.raises(ik.IkError):
+        ik.ik_shell_offsets(0)
+    with pytest.raises(ik.IkError):
+        ik.ik_supercover_offsets([300, 0, 0])
+    assert ik._lib.ik_strerror(-1) == b"invalid argument"
