@@ -97,6 +97,117 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def roofline(prof, work, sc, n_targets):
+    """Roofline of the dominant kernel (the batched backward propagation).
+
+    Algorithmic bytes of one propagation launch = 4 B for every edge-mask
+    word the launch must read (an offset-word pair whose shifted input can
+    add an output bit) + 4 B x (input + output) per word of every query set
+    + 4 B x (mask + occupancy) per word once per launch.  Both counts come from the kernel's own work
+    counters on an identical step.
+    """
+    cls = max((k for k in prof if k.startswith("propagate")), key=lambda k: prof[k]["ms"])
+    p, w = prof[cls], work[cls]
+    launches = max(1, p["launches"])
+    words = (sc.nx // 32) * sc.ny * sc.nz
+    q_per_launch = {"propagate_backward_waypoints": n_targets * N_WAY,
+                    "propagate_backward_reach": n_targets, "propagate_forward": 1}[cls]
+    # per query: input set read + output set written; mask (F) and occupancy
+    # are shared by the launch's queries
+    alg_bytes = 4.0 * w["mask_words"] + 4.0 * words * (2 * q_per_launch + 2) * launches
+    per_launch = alg_bytes / launches
+    ms = p["ms"] / launches
+    peak = measured_peaks().get("hbm_gbs", 6400.0)
+    achieved = per_launch / (ms / 1000.0) / 1e9
+    return {"kernel": "k_propagate (" + cls + ")", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "alg_bytes_per_launch": round(per_launch), "ms_per_launch": round(ms, 4),
+            "pairs_visited": w["visited"], "pairs_nonzero": w["nonzero"],
+            "mask_words_read": w["mask_words"], "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+
+def oracle_sample(threads: int):
+    """CPU oracle, as it stands, on a bounded sample of the workload.
+
+    The oracle's unit of work for this workload is one backward pass: the
+    unmasked backward sets from a target (its reach IK) or from a waypoint
+    target (each waypoint IK); a reach + 32-waypoint path needs 32 of them
+    plus the forward sets once per 64-target batch.  The sample runs
+    ``threads`` such passes from ``threads`` seeded target voxels, one per
+    host thread, and scales: solves/s = passes/s / 32.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle as O
+    import scenegen as G
+
+    sc = workload()
+    occ = O.rasterize(sc.shape, sc.boxes)
+    targets = G.draw_targets(sc, threads, 77)
+    O.shell_bounds(1)  # load the library before timing
+
+    def one(t):
+        T = np.zeros(occ.shape, np.uint8)
+        T[t[2], t[1], t[0]] = 1
+        O.backward(occ, sc.lengths, T)
+
+    a = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(one, targets))
+    wall = time.perf_counter() - a
+    passes_per_s = threads / wall
+    return passes_per_s / 32.0, wall
+
+
+def cpu_baseline():
+    cores = os.cpu_count() or 1
+    value, wall = oracle_sample(cores)
+    return {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} unmasked backward passes (one per host thread) from seeded "
+                      f"target voxels of the 128^3 scene, {wall:.1f} s wall; solves/s = passes/s "
+                      f"/ 32 (1 reach + 31 waypoint passes per reach+path; forward sets and "
+                      f"smooth steps not included)"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    # warm-up steps: load and touch the oracle library (no oracle state to warm)
+    import oracle as O
+    for _ in range(args.warmup):
+        O.shell_bounds(1)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        v, wall = oracle_sample(cores)
+        vals.append(v)
+        walls.append(wall)
+    value = float(np.mean(vals))
+    ms = float(np.mean(walls)) * 1000.0
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "C3: 128^3 grid, 200 boxes (seed 1), arm {20,18,16,14,12,10,8,6}, "
+                               "reach + 32-waypoint path"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step {cores} unmasked backward passes (one per host "
+                                   f"thread); solves/s = passes/s / 32"},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
 def workload():
     import scenegen as G
     sc = G.c2_scene(1)
@@ -177,6 +288,17 @@ def run_ours(args):
     h2d = sc.boxes.nbytes + targets_np.nbytes
     d2h = sum(x.nbytes for x in out)
 
+    # per-kernel times: one more step with the library's event profiler on
+    # (events recorded on the grid's stream around each launch), then one
+    # with its work counters on (slower; counts only)
+    ik.ik_profile_enable(g.h, timing=True, counting=False)
+    step()
+    prof = ik.ik_profile_read(g.h)
+    ik.ik_profile_enable(g.h, timing=False, counting=True)
+    step()
+    work = ik.ik_profile_read(g.h)
+    ik.ik_profile_enable(g.h, timing=False, counting=False)
+
     # plain single-query form on a sample of targets
     plain_ms = []
     for i in range(min(8, N_TARGETS)):
@@ -205,7 +327,12 @@ def run_ours(args):
             "path_status_counts": {str(k): int((status_np == k).sum()) for k in range(5)},
             "max_relax": int(relax_np[..., 0].max()),
             "clocks": clk,
+            "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
+                        for k, v in prof.items() if v["launches"]},
         }
+        line["roofline"] = roofline(prof, work, sc, N_TARGETS)
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
     g.close()
     if world > 1:
@@ -218,9 +345,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
-        print(json.dumps({"impl": "reference", "unavailable": "not yet wired"}))
+        run_reference(args)
         return
     run_ours(args)
 

@@ -222,6 +222,22 @@ IK_API int ik_validate_poses(ik_grid g, const ik_arm* arm, const int32_t* poses,
 IK_API int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, int current_idx,
               const ik_path_params* pp, int32_t* poses_out, int32_t* relax_out, int* status);
 
+/* ------------------------------------------------------------- profiling */
+/* Per-kernel-class timing: with timing != 0 every launch is bracketed by two
+ * CUDA events recorded on the grid's stream; with counting != 0 the
+ * propagation kernels also count their work (slower; for measurement runs
+ * only).  Off by default. */
+IK_API int ik_profile_enable(ik_grid g, int timing, int counting);
+/* Totals since the last read, per kernel class i < cap: ms_out[i] summed
+ * event time, launches_out[i] number of launches, counters_out[4*i + 0..3]
+ * = (offset-word pairs visited, pairs with a non-zero shifted input word,
+ * edge-mask words read, output words with a non-empty mask); any output may
+ * be NULL.  Returns the number of kernel classes, or a negative error. */
+IK_API int ik_profile_read(ik_grid g, double* ms_out, int64_t* launches_out, uint64_t* counters_out,
+                           int cap);
+/* Name of kernel class i ("" when out of range). */
+IK_API const char* ik_profile_name(int i);
+
 /* ------------------------------------------------------- host utilities */
 /* Shell bounds and offsets of one segment length, as the library builds
  * them (offsets ordered by |d|^2, then z, y, x).  Writes up to cap offsets

@@ -47,6 +47,16 @@ struct ik_grid_s {
   DevBuf V, Vw, chain, boxes;
   DevBuf b_root, b_targets, b_reach, b_found, b_poses, b_relax, b_status, b_eps, b_g, b_valid;
   DevBuf b_old;
+  // per-kernel profiling: events recorded on st around each launch
+  bool prof_on = false, count_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  unsigned long long* d_counters = nullptr;
 };
 
 namespace {
@@ -64,6 +74,61 @@ int fail_cuda(cudaError_t e) {
     return IK_ERR_OOM;
   }
   return IK_ERR_CUDA;
+}
+
+enum ProfId {
+  P_RASTER,
+  P_MASKS,
+  P_FWD,
+  P_BWD_REACH,
+  P_BWD_WAY,
+  P_SEED,
+  P_TRACE,
+  P_GUIDE,
+  P_CHAIN,
+  P_VALIDATE,
+  P_N
+};
+const char* kProfNames[P_N] = {"rasterize",
+                               "edge_masks",
+                               "propagate_forward",
+                               "propagate_backward_reach",
+                               "propagate_backward_waypoints",
+                               "seed",
+                               "traceback",
+                               "guide_targets",
+                               "smooth_chain",
+                               "validate"};
+
+cudaEvent_t take_event(ik_grid g) {
+  if (g->ev_used == g->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g->ev_pool.push_back(e);
+  }
+  return g->ev_pool[g->ev_used++];
+}
+
+// Records an event before and after the launches in its scope when
+// profiling is on; the pair is resolved by ik_profile_read.
+struct ProfScope {
+  ik_grid g;
+  int id;
+  cudaEvent_t a = nullptr;
+  ProfScope(ik_grid g_, int id_) : g(g_), id(id_) {
+    if (g->prof_on && (a = take_event(g))) cudaEventRecord(a, g->st);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = take_event(g);
+    if (!b) return;
+    cudaEventRecord(b, g->st);
+    g->recs.push_back({id, a, b});
+  }
+};
+
+unsigned long long* counters(ik_grid g, int id) {
+  return (g->count_on && g->d_counters) ? g->d_counters + 4 * id : nullptr;
 }
 
 // Grow a device buffer to at least `bytes`; contents are not kept.  With
@@ -156,7 +221,10 @@ int ensure_masks(ik_grid g, ShellDev* s) {
       return fail_cuda(e);
     }
   }
-  CK(launch_edge_masks(g->d, g->d_occ, *s, s->d_mask, g->st));
+  {
+    ProfScope ps(g, P_MASKS);
+    CK(launch_edge_masks(g->d, g->d_occ, *s, s->d_mask, g->st));
+  }
   s->mask_version = g->version;
   return IK_OK;
 }
@@ -209,10 +277,15 @@ int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int,
   rc = to_device(g, g->b_root, root, 12);
   if (rc) return rc;
   uint32_t* F = ptr<uint32_t>(g->F);
-  CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, g->st));
-  for (int k = 1; k <= S; ++k)
+  {
+    ProfScope ps(g, P_SEED);
+    CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, g->st));
+  }
+  for (int k = 1; k <= S; ++k) {
+    ProfScope ps(g, P_FWD);
     CK(launch_propagate(d, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
-                        0, 1, g->st));
+                        0, 1, g->st, counters(g, P_FWD)));
+  }
   g->f_valid = true;
   g->f_version = g->version;
   g->f_key = key;
@@ -222,14 +295,16 @@ int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int,
 
 // Backward pass for Q queries whose last set (index S) is already seeded in
 // V (query stride (S+1) * nw): V_{k-1} = F_{k-1} & D_k(V_k) for k = S..1.
-int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q) {
+int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id) {
   const Dims& d = g->d;
   const int S = ad.S;
   const long qs = (long)(S + 1) * d.nw;
   const uint32_t* F = ptr<uint32_t>(g->F);
-  for (int k = S; k >= 1; --k)
+  for (int k = S; k >= 1; --k) {
+    ProfScope ps(g, prof_id);
     CK(launch_propagate(d, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
-                        g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, g->st));
+                        g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, g->st, counters(g, prof_id)));
+  }
   return IK_OK;
 }
 
@@ -251,6 +326,7 @@ int set_device(ik_grid g) {
   CK(cudaSetDevice(g->device));
   return IK_OK;
 }
+
 
 }  // namespace
 
@@ -318,6 +394,8 @@ int ik_destroy_grid(ik_grid g) {
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
                     &g->b_g, &g->b_valid, &g->b_old};
   for (DevBuf* b : bufs) cudaFree(b->p);
+  for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+  cudaFree(g->d_counters);
   cudaFree(g->d_occ);
   delete g;
   return IK_OK;
@@ -345,7 +423,10 @@ int ik_set_boxes(ik_grid g, const int32_t* boxes, int n_boxes, int on_device) {
     if (rc) return rc;
     db = ptr<int32_t>(g->boxes);
   }
-  CK(launch_rasterize(g->d, db, n_boxes, g->d_occ, g->st));
+  {
+    ProfScope ps(g, P_RASTER);
+    CK(launch_rasterize(g->d, db, n_boxes, g->d_occ, g->st));
+  }
   ++g->version;
   return sync(g);
 }
@@ -391,8 +472,11 @@ static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::p
   }
   if ((rc = to_device(g, g->b_root, root, 12))) return rc;
   const uint32_t* F = ptr<uint32_t>(g->F);
-  CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr, g->st));
-  if ((rc = backward_sets(g, ad, V, n))) return rc;
+  {
+    ProfScope ps(g, P_SEED);
+    CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr, g->st));
+  }
+  if ((rc = backward_sets(g, ad, V, n, P_BWD_REACH))) return rc;
   int32_t* dp = poses_out;
   int32_t* df = found_out;
   if (!on_device || !poses_out || !found_out) {
@@ -401,7 +485,10 @@ static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::p
     dp = ptr<int32_t>(g->b_reach);
     df = ptr<int32_t>(g->b_found);
   }
-  CK(launch_traceback(d, ad, ptr<int32_t>(g->b_root), V, qs, n, dp, df, g->st));
+  {
+    ProfScope ps(g, P_TRACE);
+    CK(launch_traceback(d, ad, ptr<int32_t>(g->b_root), V, qs, n, dp, df, g->st));
+  }
   if (!on_device) {
     if ((rc = copy_out(g, poses_out, dp, (size_t)n * 12 * (S + 1), 0))) return rc;
     if ((rc = copy_out(g, found_out, df, (size_t)n * 4, 0))) return rc;
@@ -476,12 +563,15 @@ static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reac
   // zero the seeded (last) set of every waypoint
   CK(cudaMemset2DAsync(Vw + (long)S * d.nw, (size_t)qs * 4, 0, (size_t)d.nw * 4, (size_t)P * W, g->st));
   const uint32_t* F = ptr<uint32_t>(g->F);
-  CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
-                          eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, g->st));
-  if (j_lo == 0) return backward_sets(g, ad, Vw, P * W);
+  {
+    ProfScope ps(g, P_GUIDE);
+    CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
+                            eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, g->st));
+  }
+  if (j_lo == 0) return backward_sets(g, ad, Vw, P * W, P_BWD_WAY);
   // only waypoints j >= j_lo (P == 1 in that case)
   for (int p = 0; p < P; ++p)
-    if ((rc = backward_sets(g, ad, Vw + ((long)p * W + j_lo) * qs, W - j_lo))) return rc;
+    if ((rc = backward_sets(g, ad, Vw + ((long)p * W + j_lo) * qs, W - j_lo, P_BWD_WAY))) return rc;
   return IK_OK;
 }
 
@@ -538,12 +628,18 @@ static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int
   a.status = d_status;
   a.scratch = ptr<uint32_t>(g->chain);
   a.relaxed_eps_base = pp->eps2;
-  CK(launch_smooth_chain(d, ad, a, g->st));
+  {
+    ProfScope ps(g, P_CHAIN);
+    CK(launch_smooth_chain(d, ad, a, g->st));
+  }
   return IK_OK;
 }
 
 static int validate_impl(ik_grid g, const ArmDev& ad, const int32_t* d_poses, int n, int32_t* d_valid) {
-  CK(launch_validate(g->d, ad, g->d_occ, d_poses, n, d_valid, g->st));
+  {
+    ProfScope ps(g, P_VALIDATE);
+    CK(launch_validate(g->d, ad, g->d_occ, d_poses, n, d_valid, g->st));
+  }
   return IK_OK;
 }
 
@@ -705,7 +801,7 @@ int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, 
     const uint32_t* F = ptr<uint32_t>(g->F);
     CK(launch_seed_points(g->d, ptr<int32_t>(g->b_targets), 1, F + (long)S * g->d.nw, nullptr,
                           V + (long)S * g->d.nw, qs, nullptr, g->st));
-    if ((rc = backward_sets(g, ad, V, 1))) return rc;
+    if ((rc = backward_sets(g, ad, V, 1, P_BWD_REACH))) return rc;
     CK(launch_traceback_nearest(g->d, ad, ptr<int32_t>(g->b_root), V, ptr<int32_t>(g->b_old), dreach,
                                 ptr<int32_t>(g->b_found), g->st));
     int32_t found = 0;
@@ -736,6 +832,50 @@ int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, 
   *status = st;
   return IK_OK;
 }
+
+int ik_profile_enable(ik_grid g, int timing, int counting) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (counting && !g->d_counters) {
+    CK(cudaMalloc(&g->d_counters, sizeof(unsigned long long) * 4 * P_N));
+    CK(cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned long long) * 4 * P_N, g->st));
+  }
+  g->prof_on = timing != 0;
+  g->count_on = counting != 0;
+  return sync(g);
+}
+
+int ik_profile_read(ik_grid g, double* ms_out, int64_t* launches_out, uint64_t* counters_out,
+                    int cap) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if ((rc = sync(g))) return rc;
+  std::vector<double> ms(P_N, 0.0);
+  std::vector<int64_t> n(P_N, 0);
+  for (auto& r : g->recs) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.id] += t;
+    n[r.id] += 1;
+  }
+  g->recs.clear();
+  g->ev_used = 0;
+  std::vector<unsigned long long> cnt(4 * P_N, 0);
+  if (g->d_counters) {
+    CK(cudaMemcpy(cnt.data(), g->d_counters, sizeof(unsigned long long) * 4 * P_N,
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemset(g->d_counters, 0, sizeof(unsigned long long) * 4 * P_N));
+  }
+  for (int i = 0; i < P_N && i < cap; ++i) {
+    if (ms_out) ms_out[i] = ms[i];
+    if (launches_out) launches_out[i] = n[i];
+    if (counters_out)
+      for (int j = 0; j < 4; ++j) counters_out[4 * i + j] = cnt[4 * i + j];
+  }
+  return P_N;
+}
+
+const char* ik_profile_name(int i) { return (i >= 0 && i < P_N) ? kProfNames[i] : ""; }
 
 int ik_shell_offsets(int len, float tol, int32_t* lo2_hi2, int32_t* offs_out, int cap) {
   if (len < 1 || len > IK_MAX_LEN || !(tol >= 0.0f && tol < 1.0f)) return IK_ERR_ARG;

@@ -80,7 +80,11 @@ cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev
 // queries (mask_stride 0: one mask shared by all queries).
 cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
                              const uint32_t* mask, long mask_stride, const uint32_t* occ,
-                             uint32_t* out, long out_stride, int Q, cudaStream_t st);
+                             uint32_t* out, long out_stride, int Q, cudaStream_t st,
+                             unsigned long long* counters = nullptr);
+// counters (nullable, 4 x u64, accumulated): offset-word pairs visited,
+// pairs whose shifted input word is non-zero, edge-mask words read, output
+// words with a non-empty mask.
 // Single-voxel seeds: set q = {p_q} & (and_set ? and_set : all) & ~excl,
 // p_q from points[q] (int32 x, y, z) -- a point outside the grid gives the
 // empty set.  found_gate (nullable): query q is seeded only when

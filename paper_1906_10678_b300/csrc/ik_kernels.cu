@@ -129,10 +129,12 @@ cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev
 // the shell is symmetric and SC(p, p+e) = p + SC(0, e).  An output word stops
 // early once every free voxel it may hold is set; the edge mask is read only
 // when the shifted input could add new bits.
+template <bool kCount>
 __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uint32_t* __restrict__ X,
                                                    long xs, const uint32_t* __restrict__ mask, long ms,
                                                    const uint32_t* __restrict__ occ,
-                                                   uint32_t* __restrict__ out, long os) {
+                                                   uint32_t* __restrict__ out, long os,
+                                                   unsigned long long* __restrict__ counters) {
   const int q = blockIdx.y;
   const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (w >= d.nw) return;
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
   uint32_t m = mask ? __ldg(mask + q * ms + w) : 0xffffffffu;
   m &= ~__ldg(occ + w);
   uint32_t acc = 0;
+  unsigned long long visited = 0, nonzero = 0, mloads = 0;
   if (m) {
     int wx, y, z;
     word_coords(d, w, &wx, &y, &z);
@@ -147,21 +150,38 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
     for (int e = 0; e < seg.n; ++e) {
       const int32_t o = __ldg(seg.off + e);
       const uint32_t x = ld_shifted(Xq, d, wx, y, z, unpack_x(o), unpack_y(o), unpack_z(o));
+      if (kCount) {
+        ++visited;
+        nonzero += x != 0;
+      }
       if (x & m & ~acc) {
+        if (kCount) ++mloads;
         acc |= x & __ldg(M + (long)e * d.nw);
         if ((acc & m) == m) break;
       }
     }
   }
   out[q * os + w] = acc & m;
+  if (kCount) {
+    atomicAdd(counters + 0, visited);
+    atomicAdd(counters + 1, nonzero);
+    atomicAdd(counters + 2, mloads);
+    atomicAdd(counters + 3, (unsigned long long)(m != 0));
+  }
 }
 
 cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
                              const uint32_t* mask, long mask_stride, const uint32_t* occ,
-                             uint32_t* out, long out_stride, int Q, cudaStream_t st) {
+                             uint32_t* out, long out_stride, int Q, cudaStream_t st,
+                             unsigned long long* counters) {
   if (Q <= 0) return cudaSuccess;
   dim3 grid(grid_for(d.nw, 256), Q);
-  k_propagate<<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out, out_stride);
+  if (counters)
+    k_propagate<true><<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out,
+                                            out_stride, counters);
+  else
+    k_propagate<false><<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out,
+                                             out_stride, nullptr);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,9 @@ _sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
 _sig("ik_validate_poses", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_replan", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, ctypes.POINTER(IkPathParams), _vp,
                        _vp, ctypes.POINTER(_i)])
+_sig("ik_profile_enable", _i, [_vp, _i, _i])
+_sig("ik_profile_read", _i, [_vp, _vp, _vp, _vp, _i])
+_sig("ik_profile_name", ctypes.c_char_p, [_i])
 _sig("ik_shell_offsets", _i, [_i, ctypes.c_float, _vp, _vp, _i])
 _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 
@@ -81,8 +84,8 @@ EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
-    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_shell_offsets",
-    "ik_supercover_offsets",
+    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_profile_enable",
+    "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
 ]
 
 
@@ -326,6 +329,31 @@ def ik_replan(g: int, arm, poses, current: int, delta: int = 3, eps2: int = 2, e
     _check(_lib.ik_replan(g, ctypes.byref(arm.c), _np_ptr(p), W, current, ctypes.byref(pp),
                           _np_ptr(out), _np_ptr(relax), ctypes.byref(st)), "ik_replan")
     return out, relax, st.value
+
+
+def ik_profile_enable(g: int, timing: bool = True, counting: bool = False) -> None:
+    _check(_lib.ik_profile_enable(g, int(timing), int(counting)), "ik_profile_enable")
+
+
+def ik_profile_read(g: int) -> dict:
+    """{kernel class: {"ms", "launches", "visited", "nonzero", "mask_words", "out_words"}}."""
+    cap = 32
+    ms = np.zeros(cap, np.float64)
+    n = np.zeros(cap, np.int64)
+    c = np.zeros((cap, 4), np.uint64)
+    k = _lib.ik_profile_read(g, _np_ptr(ms), _np_ptr(n), _np_ptr(c), cap)
+    if k < 0:
+        raise IkError(k, "ik_profile_read")
+    out = {}
+    for i in range(k):
+        out[_lib.ik_profile_name(i).decode()] = {
+            "ms": float(ms[i]), "launches": int(n[i]), "visited": int(c[i, 0]),
+            "nonzero": int(c[i, 1]), "mask_words": int(c[i, 2]), "out_words": int(c[i, 3])}
+    return out
+
+
+def ik_profile_name(i: int) -> str:
+    return _lib.ik_profile_name(i).decode()
 
 
 def ik_shell_offsets(length: int, tol: float = 0.5) -> Tuple[Tuple[int, int], np.ndarray]:

@@ -184,7 +184,8 @@ def test_plan_path_relax_cap_and_invalid_reach(ik):
         po, ro, so = O.plan_path(occ, sc.lengths, reach[0], 10, delta=1, max_relax=1)
         assert sg == so and (rg == ro).all() and (pg == po).all()
         bad = reach[0].copy()
-        bad[1] += 1
+        bad[1] = bad[0]  # a zero-length first segment is never admissible
+        assert not O.pose_valid(occ, sc.lengths, bad)
         _, _, st = ik.ik_plan_path(g.h, sc.lengths, bad, 8)
         assert st == ik.IK_PATH_UNREACHABLE
 
