@@ -208,10 +208,13 @@ def run_reference(args):
     }))
 
 
-def workload():
+def workload(grid: int = 128):
     import scenegen as G
-    sc = G.c2_scene(1)
-    return sc
+    if grid == 128:
+        return G.c2_scene(1)
+    # smaller grid of the same construction, for profiler captures only
+    return G.scaled_scene(grid, G.C2_LENGTHS, max(1, 200 * grid ** 3 // 128 ** 3), 4, 24, 1,
+                          f"C2@{grid}")
 
 
 def run_ours(args):
@@ -226,7 +229,9 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = workload()
+    global N_TARGETS
+    N_TARGETS = args.targets
+    sc = workload(args.grid)
     # each rank solves its own batch of targets (replicas, no collective)
     targets_np = G.draw_targets(sc, N_TARGETS, 1 + 1000 * rank)
     S = len(sc.lengths)
@@ -275,6 +280,11 @@ def run_ours(args):
     status_np = status.cpu().numpy()
     relax_np = relax.cpu().numpy()
 
+    if args.no_extras:
+        g.close()
+        print(json.dumps({"ms_per_step": ms / args.steps, "grid": args.grid,
+                          "targets": N_TARGETS}))
+        return
     # end to end through the public API with host buffers
     reach_h = np.zeros((N_TARGETS, S + 1, 3), np.int32)
     e2e_ms = []
@@ -346,6 +356,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the batched step only (for profiler captures)")
+    ap.add_argument("--grid", type=int, default=128,
+                    help="grid edge; 128 is the benchmark workload, smaller only for captures")
+    ap.add_argument("--targets", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

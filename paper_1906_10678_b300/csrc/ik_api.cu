@@ -45,6 +45,7 @@ struct ik_grid_s {
   DevBuf F;
   // scratch
   DevBuf V, Vw, chain, boxes;
+  DevBuf F_box, V_box, Vw_box;  // word boxes of every set (min form)
   DevBuf b_root, b_targets, b_reach, b_found, b_poses, b_relax, b_status, b_eps, b_g, b_valid;
   DevBuf b_old;
   // per-kernel profiling: events recorded on st around each launch
@@ -187,21 +188,22 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
     delete s;
     return IK_ERR_ARG;
   }
-  int reach = 0;
-  for (int32_t o : s->host.off)
-    reach = std::max(reach, std::max(std::abs(unpack_x(o)), std::max(std::abs(unpack_y(o)), std::abs(unpack_z(o)))));
-  s->reach = reach;
+  s->reach = s->host.R;
   cudaError_t e = cudaMalloc(&s->d_off, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
   if (e != cudaSuccess) {
     cudaFree(s->d_off);
+    cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
     delete s;
     return fail_cuda(e);
   }
-  CK(cudaMemcpyAsync(s->d_off, s->host.off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+  CK(cudaMemcpyAsync(s->d_off, s->host.dev_off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+  CK(cudaMemcpyAsync(s->d_rows, s->host.rows.data(), s->host.rows.size() * 4, cudaMemcpyHostToDevice,
+                     g->st));
   CK(cudaMemcpyAsync(s->d_sc_start, s->host.sc_start.data(), (n + 1) * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_sc, s->host.sc.data(), s->host.sc.size() * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaStreamSynchronize(g->st));
@@ -246,13 +248,14 @@ int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<
     if (rc) return rc;
     SegDev& sd = ad->seg[k];
     sd.off = s->d_off;
+    sd.rows = s->d_rows;
     sd.sc_start = s->d_sc_start;
     sd.sc = s->d_sc;
     sd.mask = s->d_mask;
     sd.n = (int)s->host.off.size();
     sd.lo2 = lo2;
     sd.hi2 = hi2;
-    sd.reach = s->reach;
+    sd.R = s->reach;
     ad->len[k] = arm->len[k];
     if (key) key->push_back(std::make_pair(lo2, hi2));
   }
@@ -274,17 +277,21 @@ int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int,
   const int S = ad.S;
   int rc = ensure(g, g->F, (size_t)(S + 1) * d.nw * 4);
   if (rc) return rc;
+  if ((rc = ensure(g, g->F_box, (size_t)(S + 1) * 24))) return rc;
   rc = to_device(g, g->b_root, root, 12);
   if (rc) return rc;
   uint32_t* F = ptr<uint32_t>(g->F);
+  int32_t* fb = ptr<int32_t>(g->F_box);
+  CK(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, g->st));
   {
     ProfScope ps(g, P_SEED);
-    CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, g->st));
+    CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, fb, 0,
+                          g->st));
   }
   for (int k = 1; k <= S; ++k) {
     ProfScope ps(g, P_FWD);
     CK(launch_propagate(d, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
-                        0, 1, g->st, counters(g, P_FWD)));
+                        0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, g->st, counters(g, P_FWD)));
   }
   g->f_valid = true;
   g->f_version = g->version;
@@ -295,7 +302,7 @@ int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int,
 
 // Backward pass for Q queries whose last set (index S) is already seeded in
 // V (query stride (S+1) * nw): V_{k-1} = F_{k-1} & D_k(V_k) for k = S..1.
-int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id) {
+int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id, int32_t* box) {
   const Dims& d = g->d;
   const int S = ad.S;
   const long qs = (long)(S + 1) * d.nw;
@@ -303,7 +310,8 @@ int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id) 
   for (int k = S; k >= 1; --k) {
     ProfScope ps(g, prof_id);
     CK(launch_propagate(d, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
-                        g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, g->st, counters(g, prof_id)));
+                        g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, box + 6 * k, box + 6 * (k - 1),
+                        6L * (S + 1), g->st, counters(g, prof_id)));
   }
   return IK_OK;
 }
@@ -385,12 +393,14 @@ int ik_destroy_grid(ik_grid g) {
   for (auto& kv : g->shells) {
     ShellDev* s = kv.second;
     cudaFree(s->d_off);
+    cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
     cudaFree(s->d_mask);
     delete s;
   }
-  DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->b_root, &g->b_targets,
+  DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->F_box, &g->V_box, &g->Vw_box,
+                    &g->b_root, &g->b_targets,
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
                     &g->b_g, &g->b_valid, &g->b_old};
   for (DevBuf* b : bufs) cudaFree(b->p);
@@ -471,12 +481,16 @@ static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::p
     dt = ptr<int32_t>(g->b_targets);
   }
   if ((rc = to_device(g, g->b_root, root, 12))) return rc;
+  if ((rc = ensure(g, g->V_box, (size_t)n * (S + 1) * 24))) return rc;
+  int32_t* vb = ptr<int32_t>(g->V_box);
+  CK(cudaMemsetAsync(vb, kBoxEmptyByte, (size_t)n * (S + 1) * 24, g->st));
   const uint32_t* F = ptr<uint32_t>(g->F);
   {
     ProfScope ps(g, P_SEED);
-    CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr, g->st));
+    CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr,
+                          vb + 6 * S, 6L * (S + 1), g->st));
   }
-  if ((rc = backward_sets(g, ad, V, n, P_BWD_REACH))) return rc;
+  if ((rc = backward_sets(g, ad, V, n, P_BWD_REACH, vb))) return rc;
   int32_t* dp = poses_out;
   int32_t* df = found_out;
   if (!on_device || !poses_out || !found_out) {
@@ -542,7 +556,8 @@ int ik_guide(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way,
   if ((rc = ensure(g, g->b_g, (size_t)12 * n_way))) return rc;
   if ((rc = ensure(g, g->b_eps, (size_t)4 * n_way))) return rc;
   CK(launch_guide_targets(g->d, ad, g->d_occ, nullptr, ptr<int32_t>(g->b_reach), nullptr, 1, n_way, 0,
-                          0, 0, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), nullptr, g->st));
+                          0, 0, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), nullptr, nullptr,
+                          g->st));
   if ((rc = copy_out(g, g_out, g->b_g.p, (size_t)12 * n_way, 0))) return rc;
   return sync(g);
 }
@@ -560,18 +575,23 @@ static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reac
   if ((rc = ensure(g, g->b_g, (size_t)12 * P * W))) return rc;
   if ((rc = ensure(g, g->b_eps, (size_t)4 * P * W))) return rc;
   uint32_t* Vw = ptr<uint32_t>(g->Vw);
+  if ((rc = ensure(g, g->Vw_box, (size_t)P * W * (S + 1) * 24))) return rc;
+  int32_t* wb = ptr<int32_t>(g->Vw_box);
+  CK(cudaMemsetAsync(wb, kBoxEmptyByte, (size_t)P * W * (S + 1) * 24, g->st));
   // zero the seeded (last) set of every waypoint
   CK(cudaMemset2DAsync(Vw + (long)S * d.nw, (size_t)qs * 4, 0, (size_t)d.nw * 4, (size_t)P * W, g->st));
   const uint32_t* F = ptr<uint32_t>(g->F);
   {
     ProfScope ps(g, P_GUIDE);
     CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
-                            eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, g->st));
+                            eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, wb, g->st));
   }
-  if (j_lo == 0) return backward_sets(g, ad, Vw, P * W, P_BWD_WAY);
+  if (j_lo == 0) return backward_sets(g, ad, Vw, P * W, P_BWD_WAY, wb);
   // only waypoints j >= j_lo (P == 1 in that case)
   for (int p = 0; p < P; ++p)
-    if ((rc = backward_sets(g, ad, Vw + ((long)p * W + j_lo) * qs, W - j_lo, P_BWD_WAY))) return rc;
+    if ((rc = backward_sets(g, ad, Vw + ((long)p * W + j_lo) * qs, W - j_lo, P_BWD_WAY,
+                            wb + ((long)p * W + j_lo) * (S + 1) * 6)))
+      return rc;
   return IK_OK;
 }
 
@@ -799,9 +819,12 @@ int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, 
     if ((rc = ensure(g, g->b_found, 4))) return rc;
     uint32_t* V = ptr<uint32_t>(g->V);
     const uint32_t* F = ptr<uint32_t>(g->F);
+    if ((rc = ensure(g, g->V_box, (size_t)(S + 1) * 24))) return rc;
+    int32_t* vb = ptr<int32_t>(g->V_box);
+    CK(cudaMemsetAsync(vb, kBoxEmptyByte, (size_t)(S + 1) * 24, g->st));
     CK(launch_seed_points(g->d, ptr<int32_t>(g->b_targets), 1, F + (long)S * g->d.nw, nullptr,
-                          V + (long)S * g->d.nw, qs, nullptr, g->st));
-    if ((rc = backward_sets(g, ad, V, 1, P_BWD_REACH))) return rc;
+                          V + (long)S * g->d.nw, qs, nullptr, vb + 6 * S, 0, g->st));
+    if ((rc = backward_sets(g, ad, V, 1, P_BWD_REACH, vb))) return rc;
     CK(launch_traceback_nearest(g->d, ad, ptr<int32_t>(g->b_root), V, ptr<int32_t>(g->b_old), dreach,
                                 ptr<int32_t>(g->b_found), g->st));
     int32_t found = 0;

@@ -31,8 +31,14 @@ struct Dims {
 struct ShellHost {
   int lo2 = 0, hi2 = 0;
   std::vector<int32_t> off;       // packed offsets, ordered by (|d|^2, z, y, x)
-  std::vector<int32_t> sc_start;  // size n + 1, into sc
-  std::vector<int32_t> sc;        // packed supercover voxels of 0 -> off[i], (z, y, x) order
+  // device order: offsets sorted by (z, y, x), so that the offsets of one
+  // (dz, dy) row are contiguous; rows[(dz+R)*(2R+1) + (dy+R)] .. rows[.. + 1]
+  // is the range of row (dy, dz).
+  int R = 0;
+  std::vector<int32_t> dev_off;
+  std::vector<int32_t> rows;      // size (2R+1)^2 + 1
+  std::vector<int32_t> sc_start;  // size n + 1, into sc, device order
+  std::vector<int32_t> sc;        // packed supercover voxels of 0 -> dev_off[i], (z, y, x) order
   int max_sc = 0;
 };
 
@@ -43,14 +49,20 @@ void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
 
 // Device view of one segment's tables.
 struct SegDev {
-  const int32_t* off;      // [n] packed offsets
+  const int32_t* off;      // [n] packed offsets, device order (z, y, x)
+  const int32_t* rows;     // [(2R+1)^2 + 1] row starts, see ShellHost
   const int32_t* sc_start; // [n + 1]
   const int32_t* sc;       // packed supercover voxels
   const uint32_t* mask;    // [n][nw] edge masks: bit of voxel p in row e = segment p -> p + off[e] free
   int n;
   int lo2, hi2;
-  int reach;               // max |component| of an offset
+  int R;                   // max |component| of an offset
 };
+
+// Bounding box of a voxel set in word coordinates, kept in "min form" so
+// that every component accumulates with atomicMin: {wx0, y0, z0, -wx1, -y1,
+// -z1}.  A box whose bytes are all 0x7f is empty (wx0 > wx1).
+constexpr int kBoxEmptyByte = 0x7f;
 
 struct ArmDev {
   SegDev seg[IK_MAX_SEG];
@@ -62,6 +74,7 @@ struct ArmDev {
 struct ShellDev {
   ShellHost host;
   int32_t* d_off = nullptr;
+  int32_t* d_rows = nullptr;
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;
@@ -78,9 +91,12 @@ cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev
 // out[q] = (mask ? mask[q] : ~0) & D_seg(X[q]) for q < Q; sets are nw words
 // apart with stride `x_stride` / `out_stride` / `mask_stride` words between
 // queries (mask_stride 0: one mask shared by all queries).
+// xbox / obox: boxes of X[q] and out[q] at q * box_stride ints; obox must
+// be set empty beforehand and receives the box of the output.
 cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
                              const uint32_t* mask, long mask_stride, const uint32_t* occ,
-                             uint32_t* out, long out_stride, int Q, cudaStream_t st,
+                             uint32_t* out, long out_stride, int Q, const int32_t* xbox,
+                             int32_t* obox, long box_stride, cudaStream_t st,
                              unsigned long long* counters = nullptr);
 // counters (nullable, 4 x u64, accumulated): offset-word pairs visited,
 // pairs whose shifted input word is non-zero, edge-mask words read, output
@@ -89,9 +105,11 @@ cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X
 // p_q from points[q] (int32 x, y, z) -- a point outside the grid gives the
 // empty set.  found_gate (nullable): query q is seeded only when
 // found_gate[q] != 0.
+// obox (set empty beforehand, stride box_stride) receives each seed's box.
 cudaError_t launch_seed_points(const Dims& d, const int32_t* points, int Q, const uint32_t* and_set,
                                const uint32_t* excl, uint32_t* out, long out_stride,
-                               const int32_t* found_gate, cudaStream_t st);
+                               const int32_t* found_gate, int32_t* obox, long box_stride,
+                               cudaStream_t st);
 cudaError_t launch_and(const uint32_t* a, const uint32_t* b, uint32_t* out, long n, cudaStream_t st);
 // Reach traceback over Q queries: V sets [Q][S+1][nw] (query stride vstride).
 cudaError_t launch_traceback(const Dims& d, const ArmDev& arm, const int32_t* root,
@@ -106,10 +124,12 @@ cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int
 // reach [P][S+1][3], found [P] (nullable: all found), writes
 // g [P][W][3], eps_used [P][W] and V_S^(p,j) = F_S & T_j into
 // Vw + ((p*W + j) * (S+1) + S) * nw.  Waypoints j < j_lo are skipped.
+// wbox: boxes [P][W][S+1][6]; the box of each seeded set (index S) is
+// accumulated (set empty beforehand).
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
-                                 int32_t* eps_used, uint32_t* Vw, cudaStream_t st);
+                                 int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st);
 // Smooth chains for P paths (one block each).  mode 0 = plan (backward from
 // the reach pose), mode 1 = forward from pose c (replan).  scratch: per path
 // 2 * (S+1) * nw zeroed words.

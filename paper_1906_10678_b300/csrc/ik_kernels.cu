@@ -129,39 +129,89 @@ cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev
 // the shell is symmetric and SC(p, p+e) = p + SC(0, e).  An output word stops
 // early once every free voxel it may hold is set; the edge mask is read only
 // when the shifted input could add new bits.
+// Warp-level accumulation of the word box of the lanes whose output word is
+// non-empty: one atomicMin per component per warp.  Every lane still active
+// in the warp must call it.
+__device__ __forceinline__ void box_accumulate(int32_t* box, bool nz, int wx, int y, int z) {
+  const unsigned act = __activemask();
+  if (!__ballot_sync(act, nz)) return;
+  const int big = 0x7fffffff;
+  const int v0 = __reduce_min_sync(act, nz ? wx : big);
+  const int v1 = __reduce_min_sync(act, nz ? y : big);
+  const int v2 = __reduce_min_sync(act, nz ? z : big);
+  const int v3 = __reduce_min_sync(act, nz ? -wx : big);
+  const int v4 = __reduce_min_sync(act, nz ? -y : big);
+  const int v5 = __reduce_min_sync(act, nz ? -z : big);
+  if ((threadIdx.x & 31) == __ffs(act) - 1) {
+    atomicMin(box + 0, v0);
+    atomicMin(box + 1, v1);
+    atomicMin(box + 2, v2);
+    atomicMin(box + 3, v3);
+    atomicMin(box + 4, v4);
+    atomicMin(box + 5, v5);
+  }
+}
+
+// out[p] = mask[p] & OR_e X[p + e] & M_e[p] over the shell of segment k.
+// Gather form of the scatter "every p reachable from X by a valid segment":
+// the shell is symmetric and SC(p, p+e) = p + SC(0, e).  Only the offsets
+// whose source voxels can fall inside the word box of X are visited: the
+// (dz, dy) rows of the shell table are walked over the box's z and y ranges
+// and each row's x offsets are checked against its x range.  An output
+// word stops early once every free voxel it may hold is set; the edge mask
+// is read only when the shifted input could add new bits.
 template <bool kCount>
 __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uint32_t* __restrict__ X,
                                                    long xs, const uint32_t* __restrict__ mask, long ms,
                                                    const uint32_t* __restrict__ occ,
                                                    uint32_t* __restrict__ out, long os,
+                                                   const int32_t* __restrict__ xbox,
+                                                   int32_t* __restrict__ obox, long bs,
                                                    unsigned long long* __restrict__ counters) {
   const int q = blockIdx.y;
   const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (w >= d.nw) return;
   const uint32_t* Xq = X + q * xs;
+  const int32_t* xb = xbox + q * bs;
+  const int bx0 = __ldg(xb + 0), by0 = __ldg(xb + 1), bz0 = __ldg(xb + 2);
+  const int bx1 = -__ldg(xb + 3), by1 = -__ldg(xb + 4), bz1 = -__ldg(xb + 5);
   uint32_t m = mask ? __ldg(mask + q * ms + w) : 0xffffffffu;
   m &= ~__ldg(occ + w);
+  int wx, y, z;
+  word_coords(d, w, &wx, &y, &z);
   uint32_t acc = 0;
   unsigned long long visited = 0, nonzero = 0, mloads = 0;
-  if (m) {
-    int wx, y, z;
-    word_coords(d, w, &wx, &y, &z);
+  if (m && bx0 <= bx1) {
+    const int R = seg.R, side = 2 * R + 1;
+    const int ez0 = max(bz0 - z, -R), ez1 = min(bz1 - z, R);
+    const int ey0 = max(by0 - y, -R), ey1 = min(by1 - y, R);
+    const int exlo = 32 * (bx0 - wx) - 31, exhi = 32 * (bx1 - wx) + 31;
     const uint32_t* M = seg.mask + w;
-    for (int e = 0; e < seg.n; ++e) {
-      const int32_t o = __ldg(seg.off + e);
-      const uint32_t x = ld_shifted(Xq, d, wx, y, z, unpack_x(o), unpack_y(o), unpack_z(o));
-      if (kCount) {
-        ++visited;
-        nonzero += x != 0;
-      }
-      if (x & m & ~acc) {
-        if (kCount) ++mloads;
-        acc |= x & __ldg(M + (long)e * d.nw);
-        if ((acc & m) == m) break;
+    for (int ez = ez0; ez <= ez1; ++ez) {
+      const int32_t* rowp = seg.rows + (ez + R) * side + R;
+      for (int ey = ey0; ey <= ey1; ++ey) {
+        const int r1 = __ldg(rowp + ey + 1);
+        for (int e = __ldg(rowp + ey); e < r1; ++e) {
+          const int ex = unpack_x(__ldg(seg.off + e));
+          if (ex < exlo || ex > exhi) continue;
+          const uint32_t x = ld_shifted(Xq, d, wx, y, z, ex, ey, ez);
+          if (kCount) {
+            ++visited;
+            nonzero += x != 0;
+          }
+          if (x & m & ~acc) {
+            if (kCount) ++mloads;
+            acc |= x & __ldg(M + (long)e * d.nw);
+            if ((acc & m) == m) goto done;
+          }
+        }
       }
     }
   }
-  out[q * os + w] = acc & m;
+done:
+  acc &= m;
+  out[q * os + w] = acc;
+  box_accumulate(obox + q * bs, acc != 0, wx, y, z);
   if (kCount) {
     atomicAdd(counters + 0, visited);
     atomicAdd(counters + 1, nonzero);
@@ -172,16 +222,17 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
 
 cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
                              const uint32_t* mask, long mask_stride, const uint32_t* occ,
-                             uint32_t* out, long out_stride, int Q, cudaStream_t st,
+                             uint32_t* out, long out_stride, int Q, const int32_t* xbox,
+                             int32_t* obox, long box_stride, cudaStream_t st,
                              unsigned long long* counters) {
   if (Q <= 0) return cudaSuccess;
   dim3 grid(grid_for(d.nw, 256), Q);
   if (counters)
     k_propagate<true><<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out,
-                                            out_stride, counters);
+                                            out_stride, xbox, obox, box_stride, counters);
   else
     k_propagate<false><<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out,
-                                             out_stride, nullptr);
+                                             out_stride, xbox, obox, box_stride, nullptr);
   return cudaGetLastError();
 }
 
@@ -189,7 +240,7 @@ cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X
 
 __global__ void k_seed_points(Dims d, const int32_t* __restrict__ pts, const uint32_t* __restrict__ and_set,
                               const uint32_t* __restrict__ excl, uint32_t* __restrict__ out, long os,
-                              const int32_t* __restrict__ gate) {
+                              const int32_t* __restrict__ gate, int32_t* __restrict__ obox, long bs) {
   const int q = blockIdx.y;
   const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (w >= d.nw) return;
@@ -202,14 +253,25 @@ __global__ void k_seed_points(Dims d, const int32_t* __restrict__ pts, const uin
   if (and_set) v &= __ldg(and_set + w);
   if (excl) v &= ~__ldg(excl + w);
   out[q * os + w] = v;
+  if (v) {
+    int32_t* b = obox + q * bs;
+    atomicMin(b + 0, x >> 5);
+    atomicMin(b + 1, y);
+    atomicMin(b + 2, z);
+    atomicMin(b + 3, -(x >> 5));
+    atomicMin(b + 4, -y);
+    atomicMin(b + 5, -z);
+  }
 }
 
 cudaError_t launch_seed_points(const Dims& d, const int32_t* points, int Q, const uint32_t* and_set,
                                const uint32_t* excl, uint32_t* out, long out_stride,
-                               const int32_t* found_gate, cudaStream_t st) {
+                               const int32_t* found_gate, int32_t* obox, long box_stride,
+                               cudaStream_t st) {
   if (Q <= 0) return cudaSuccess;
   dim3 grid(grid_for(d.nw, 256), Q);
-  k_seed_points<<<grid, 256, 0, st>>>(d, points, and_set, excl, out, out_stride, found_gate);
+  k_seed_points<<<grid, 256, 0, st>>>(d, points, and_set, excl, out, out_stride, found_gate, obox,
+                                      box_stride);
   return cudaGetLastError();
 }
 
@@ -319,26 +381,16 @@ cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int
 
 // ------------------------------------------------ a9: validate poses (G7)
 
-// Shell index of offset (x, y, z) by binary search over the table's order
-// (|d|^2, z, y, x); -1 when the offset is not in the shell.
+// Shell index of offset (x, y, z) in device order (row (z, y), then a scan
+// of the row's x offsets); -1 when the offset is not in the shell.
 __device__ int shell_index(const SegDev& sg, int x, int y, int z) {
   const int n2 = x * x + y * y + z * z;
   if (n2 < sg.lo2 || n2 > sg.hi2) return -1;
-  int lo = 0, hi = sg.n - 1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const int32_t o = __ldg(sg.off + mid);
-    const int ox = unpack_x(o), oy = unpack_y(o), oz = unpack_z(o);
-    const int on2 = ox * ox + oy * oy + oz * oz;
-    int c;
-    if (on2 != n2) c = on2 < n2 ? -1 : 1;
-    else if (oz != z) c = oz < z ? -1 : 1;
-    else if (oy != y) c = oy < y ? -1 : 1;
-    else if (ox != x) c = ox < x ? -1 : 1;
-    else return mid;
-    if (c < 0) lo = mid + 1;
-    else hi = mid - 1;
-  }
+  if (y < -sg.R || y > sg.R || z < -sg.R || z > sg.R) return -1;
+  const int r = (z + sg.R) * (2 * sg.R + 1) + (y + sg.R);
+  const int r1 = __ldg(sg.rows + r + 1);
+  for (int e = __ldg(sg.rows + r); e < r1; ++e)
+    if (unpack_x(__ldg(sg.off + e)) == x) return e;
   return -1;
 }
 
@@ -384,6 +436,16 @@ cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* oc
 
 // -------------------------------------------- a6: guide points + targets
 
+// Adds voxel (x, y, z) to a min-form word box.
+__device__ __forceinline__ void box_point(int32_t* b, int x, int y, int z) {
+  atomicMin(b + 0, x >> 5);
+  atomicMin(b + 1, y);
+  atomicMin(b + 2, z);
+  atomicMin(b + 3, -(x >> 5));
+  atomicMin(b + 4, -y);
+  atomicMin(b + 5, -z);
+}
+
 __device__ __forceinline__ long floor_div(long a, long b) {  // b > 0
   long q = a / b;
   if ((a % b != 0) && (a < 0)) --q;
@@ -404,7 +466,8 @@ __device__ __forceinline__ int isqrt_dev(int v) {  // floor(sqrt(v)), v >= 0
 __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__ occ,
                                 const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
                                 const int32_t* __restrict__ found, int W, int j_lo, int eps2,
-                                int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw) {
+                                int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw,
+                                int32_t* wbox) {
   const int p = blockIdx.y;
   const int j = blockIdx.x + j_lo;
   const int S = arm.S;
@@ -441,6 +504,7 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
   __syncthreads();
   if (!Vw) return;  // guide points only
   uint32_t* VS = Vw + (((long)p * W + j) * (S + 1) + S) * d.nw;
+  int32_t* vb = wbox + (((long)p * W + j) * (S + 1) + S) * 6;
   if (!ok) {
     if (threadIdx.x == 0) eps_used[(long)p * W + j] = -1;
     return;
@@ -450,7 +514,10 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
       const int tx = R[3 * S], ty = R[3 * S + 1], tz = R[3 * S + 2];
       if (inside(d, tx, ty, tz)) {
         const long i = lin(d, tx, ty, tz);
-        if (test_bit(F_S, i)) atomicOr(VS + (i >> 5), 1u << (i & 31));
+        if (test_bit(F_S, i)) {
+          atomicOr(VS + (i >> 5), 1u << (i & 31));
+          box_point(vb, tx, ty, tz);
+        }
       }
       eps_used[(long)p * W + j] = 0;
     }
@@ -485,18 +552,21 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
     const int dx = x - gp[0], dy = y - gp[1], dz = z - gp[2];
     if (dx * dx + dy * dy + dz * dz > e2 || !inside(d, x, y, z)) continue;
     const long i = lin(d, x, y, z);
-    if (!test_bit(occ, i) && test_bit(F_S, i)) atomicOr(VS + (i >> 5), 1u << (i & 31));
+    if (!test_bit(occ, i) && test_bit(F_S, i)) {
+      atomicOr(VS + (i >> 5), 1u << (i & 31));
+      box_point(vb, x, y, z);
+    }
   }
 }
 
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
-                                 int32_t* eps_used, uint32_t* Vw, cudaStream_t st) {
+                                 int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st) {
   if (P <= 0 || W - j_lo <= 0) return cudaSuccess;
   dim3 grid(W - j_lo, P);
   k_guide_targets<<<grid, 128, 0, st>>>(d, arm, occ, F_S, reach, found, W, j_lo, eps2, eps2_max, g,
-                                        eps_used, Vw);
+                                        eps_used, Vw, wbox);
   return cudaGetLastError();
 }
 
@@ -591,19 +661,24 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
 __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const uint32_t* src,
                                                     const Box& sb, int wx, int y, int z, long w,
                                                     uint32_t m) {
+  const int R = sg.R, side = 2 * R + 1;
+  const int ez0 = max(sb.z0 - z, -R), ez1 = min(sb.z1 - z, R);
+  const int ey0 = max(sb.y0 - y, -R), ey1 = min(sb.y1 - y, R);
+  const int exlo = sb.x0 - 32 * wx - 31, exhi = sb.x1 - 32 * wx;
   uint32_t acc = 0;
-  for (int e = 0; e < sg.n; ++e) {
-    const int32_t o = __ldg(sg.off + e);
-    const int oy = unpack_y(o), oz = unpack_z(o);
-    const int sy = y + oy, sz = z + oz;
-    if (sy < sb.y0 || sy > sb.y1 || sz < sb.z0 || sz > sb.z1) continue;
-    const int ox = unpack_x(o);
-    const int sx = 32 * wx + ox;
-    if (sx + 31 < sb.x0 || sx > sb.x1) continue;
-    const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ox, oy, oz);
-    if (x & m & ~acc) {
-      acc |= x & __ldg(sg.mask + (long)e * d.nw + w);
-      if ((acc & m) == m) break;
+  for (int ez = ez0; ez <= ez1; ++ez) {
+    const int32_t* rowp = sg.rows + (ez + R) * side + R;
+    for (int ey = ey0; ey <= ey1; ++ey) {
+      const int r1 = __ldg(rowp + ey + 1);
+      for (int e = __ldg(rowp + ey); e < r1; ++e) {
+        const int ex = unpack_x(__ldg(sg.off + e));
+        if (ex < exlo || ex > exhi) continue;
+        const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ex, ey, ez);
+        if (x & m & ~acc) {
+          acc |= x & __ldg(sg.mask + (long)e * d.nw + w);
+          if ((acc & m) == m) return acc & m;
+        }
+      }
     }
   }
   return acc & m;

@@ -117,12 +117,27 @@ void build_shell(int lo2, int hi2, ShellHost* sh) {
   sh->lo2 = lo2;
   sh->hi2 = hi2;
   sh->off.clear();
+  for (const Off& o : offs) sh->off.push_back(pack3(o.x, o.y, o.z));
+  // device order (z, y, x) with a row table over (dz, dy)
+  std::vector<Off> dev = offs;
+  std::sort(dev.begin(), dev.end(), [](const Off& a, const Off& b) {
+    if (a.z != b.z) return a.z < b.z;
+    if (a.y != b.y) return a.y < b.y;
+    return a.x < b.x;
+  });
+  sh->R = R;
+  const int side = 2 * R + 1;
+  sh->rows.assign((size_t)side * side + 1, 0);
+  std::vector<int32_t> count((size_t)side * side, 0);
+  for (const Off& o : dev) ++count[(size_t)(o.z + R) * side + (o.y + R)];
+  for (size_t r = 0; r < count.size(); ++r) sh->rows[r + 1] = sh->rows[r] + count[r];
+  sh->dev_off.clear();
   sh->sc.clear();
   sh->sc_start.assign(1, 0);
   sh->max_sc = 0;
   std::vector<int32_t> sc;
-  for (const Off& o : offs) {
-    sh->off.push_back(pack3(o.x, o.y, o.z));
+  for (const Off& o : dev) {
+    sh->dev_off.push_back(pack3(o.x, o.y, o.z));
     supercover_traverse(o.x, o.y, o.z, &sc);
     sh->sc.insert(sh->sc.end(), sc.begin(), sc.end());
     sh->sc_start.push_back((int32_t)sh->sc.size());
