@@ -124,11 +124,6 @@ cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev
 
 // ------------------------------------------------- a3/a4: one propagation D_k
 
-// out[p] = mask[p] & OR_e X[p + e] & M_e[p] over the shell of segment k.
-// Gather form of the scatter "every p reachable from X by a valid segment":
-// the shell is symmetric and SC(p, p+e) = p + SC(0, e).  An output word stops
-// early once every free voxel it may hold is set; the edge mask is read only
-// when the shifted input could add new bits.
 // Warp-level accumulation of the word box of the lanes whose output word is
 // non-empty: one atomicMin per component per warp.  Every lane still active
 // in the warp must call it.
@@ -154,12 +149,16 @@ __device__ __forceinline__ void box_accumulate(int32_t* box, bool nz, int wx, in
 
 // out[p] = mask[p] & OR_e X[p + e] & M_e[p] over the shell of segment k.
 // Gather form of the scatter "every p reachable from X by a valid segment":
-// the shell is symmetric and SC(p, p+e) = p + SC(0, e).  Only the offsets
-// whose source voxels can fall inside the word box of X are visited: the
-// (dz, dy) rows of the shell table are walked over the box's z and y ranges
-// and each row's x offsets are checked against its x range.  An output
-// word stops early once every free voxel it may hold is set; the edge mask
-// is read only when the shifted input could add new bits.
+// the shell is symmetric and SC(p, p+e) = p + SC(0, e).
+//
+// Only offsets whose source voxels can fall inside the word box of X are
+// visited.  The walk is warp-uniform: a warp covers 32 consecutive output
+// words, takes the union of its lanes' z and y ranges, and for each dz walks
+// the one contiguous run of the (z, y, x)-ordered shell table whose dy lies
+// in that union; each lane predicates on its own box test.  A lane's edge
+// mask word is read only when its shifted input could add new bits, and the
+// warp leaves a dz early once every lane holds every free voxel its mask
+// allows.
 template <bool kCount>
 __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uint32_t* __restrict__ X,
                                                    long xs, const uint32_t* __restrict__ mask, long ms,
@@ -168,32 +167,44 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
                                                    const int32_t* __restrict__ xbox,
                                                    int32_t* __restrict__ obox, long bs,
                                                    unsigned long long* __restrict__ counters) {
+  constexpr unsigned kFull = 0xffffffffu;
   const int q = blockIdx.y;
   const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (w >= d.nw) return;
+  const bool valid = w < d.nw;
   const uint32_t* Xq = X + q * xs;
   const int32_t* xb = xbox + q * bs;
   const int bx0 = __ldg(xb + 0), by0 = __ldg(xb + 1), bz0 = __ldg(xb + 2);
   const int bx1 = -__ldg(xb + 3), by1 = -__ldg(xb + 4), bz1 = -__ldg(xb + 5);
-  uint32_t m = mask ? __ldg(mask + q * ms + w) : 0xffffffffu;
-  m &= ~__ldg(occ + w);
-  int wx, y, z;
-  word_coords(d, w, &wx, &y, &z);
+  int wx = 0, y = 0, z = 0;
+  uint32_t m = 0;
+  if (valid) {
+    word_coords(d, w, &wx, &y, &z);
+    m = (mask ? __ldg(mask + q * ms + w) : 0xffffffffu) & ~__ldg(occ + w);
+  }
   uint32_t acc = 0;
   unsigned long long visited = 0, nonzero = 0, mloads = 0;
-  if (m && bx0 <= bx1) {
+  if (bx0 <= bx1 && __any_sync(kFull, m != 0)) {
     const int R = seg.R, side = 2 * R + 1;
-    const int ez0 = max(bz0 - z, -R), ez1 = min(bz1 - z, R);
-    const int ey0 = max(by0 - y, -R), ey1 = min(by1 - y, R);
+    const int big = 0x7fffffff;
+    const int zlo = __reduce_min_sync(kFull, m ? z : big), zhi = -__reduce_min_sync(kFull, m ? -z : big);
+    const int ylo = __reduce_min_sync(kFull, m ? y : big), yhi = -__reduce_min_sync(kFull, m ? -y : big);
+    const int ez0 = max(bz0 - zhi, -R), ez1 = min(bz1 - zlo, R);
+    const int ey0 = max(by0 - yhi, -R), ey1 = min(by1 - ylo, R);
     const int exlo = 32 * (bx0 - wx) - 31, exhi = 32 * (bx1 - wx) + 31;
     const uint32_t* M = seg.mask + w;
-    for (int ez = ez0; ez <= ez1; ++ez) {
+    bool live = m != 0;
+    for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
+      const int sz = z + ez;
+      const bool zok = live && sz >= bz0 && sz <= bz1;
+      if (!__any_sync(kFull, zok)) continue;
       const int32_t* rowp = seg.rows + (ez + R) * side + R;
-      for (int ey = ey0; ey <= ey1; ++ey) {
-        const int r1 = __ldg(rowp + ey + 1);
-        for (int e = __ldg(rowp + ey); e < r1; ++e) {
-          const int ex = unpack_x(__ldg(seg.off + e));
-          if (ex < exlo || ex > exhi) continue;
+      const int e1 = __ldg(rowp + ey1 + 1);
+      for (int e = __ldg(rowp + ey0); e < e1; ++e) {
+        const int32_t o = __ldg(seg.off + e);
+        const int ex = unpack_x(o), ey = unpack_y(o);
+        const int sy = y + ey;
+        const bool ok = zok && sy >= by0 && sy <= by1 && ex >= exlo && ex <= exhi;
+        if (ok) {
           const uint32_t x = ld_shifted(Xq, d, wx, y, z, ex, ey, ez);
           if (kCount) {
             ++visited;
@@ -202,17 +213,17 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
           if (x & m & ~acc) {
             if (kCount) ++mloads;
             acc |= x & __ldg(M + (long)e * d.nw);
-            if ((acc & m) == m) goto done;
           }
         }
       }
+      live = live && (acc & m) != m;
+      if (!__any_sync(kFull, live)) break;
     }
   }
-done:
   acc &= m;
-  out[q * os + w] = acc;
+  if (valid) out[q * os + w] = acc;
   box_accumulate(obox + q * bs, acc != 0, wx, y, z);
-  if (kCount) {
+  if (kCount && valid) {
     atomicAdd(counters + 0, visited);
     atomicAdd(counters + 1, nonzero);
     atomicAdd(counters + 2, mloads);
@@ -658,30 +669,37 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
 // One restricted propagation word: OR over the segment's offsets of the
 // source set shifted by the offset, limited to offsets whose source voxels
 // can fall in the source box, AND edge mask, within `m`.
+// One restricted propagation word, its offset walk shared by the kG lanes
+// of a lane group (lane g of the group takes every kG-th offset of each
+// row run); the group's partial results are OR-reduced.  Sources are limited
+// to offsets whose source voxels can fall in the source box.  Every lane of
+// the group must call it (idle lanes pass m = 0).
+constexpr int kG = 8;
+
 __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const uint32_t* src,
                                                     const Box& sb, int wx, int y, int z, long w,
                                                     uint32_t m) {
-  const int R = sg.R, side = 2 * R + 1;
-  const int ez0 = max(sb.z0 - z, -R), ez1 = min(sb.z1 - z, R);
-  const int ey0 = max(sb.y0 - y, -R), ey1 = min(sb.y1 - y, R);
-  const int exlo = sb.x0 - 32 * wx - 31, exhi = sb.x1 - 32 * wx;
+  const int g = threadIdx.x % kG;
+  const unsigned gmask = ((1u << kG) - 1u) << ((threadIdx.x & 31) & ~(kG - 1));
   uint32_t acc = 0;
-  for (int ez = ez0; ez <= ez1; ++ez) {
-    const int32_t* rowp = sg.rows + (ez + R) * side + R;
-    for (int ey = ey0; ey <= ey1; ++ey) {
-      const int r1 = __ldg(rowp + ey + 1);
-      for (int e = __ldg(rowp + ey); e < r1; ++e) {
-        const int ex = unpack_x(__ldg(sg.off + e));
+  if (m) {
+    const int R = sg.R, side = 2 * R + 1;
+    const int ez0 = max(sb.z0 - z, -R), ez1 = min(sb.z1 - z, R);
+    const int ey0 = max(sb.y0 - y, -R), ey1 = min(sb.y1 - y, R);
+    const int exlo = sb.x0 - 32 * wx - 31, exhi = sb.x1 - 32 * wx;
+    for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
+      const int32_t* rowp = sg.rows + (ez + R) * side + R;
+      const int e1 = __ldg(rowp + ey1 + 1);
+      for (int e = __ldg(rowp + ey0) + g; e < e1; e += kG) {
+        const int32_t o = __ldg(sg.off + e);
+        const int ex = unpack_x(o);
         if (ex < exlo || ex > exhi) continue;
-        const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ex, ey, ez);
-        if (x & m & ~acc) {
-          acc |= x & __ldg(sg.mask + (long)e * d.nw + w);
-          if ((acc & m) == m) return acc & m;
-        }
+        const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ex, unpack_y(o), ez);
+        if (x & m & ~acc) acc |= x & __ldg(sg.mask + (long)e * d.nw + w);
       }
     }
   }
-  return acc & m;
+  return __reduce_or_sync(gmask, acc) & m;
 }
 
 // Forward restriction: R_0 = {root}, R_k = (V_k & Ball(ref_k, delta)) & D_k(R_{k-1}).
@@ -701,14 +719,19 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
     uint32_t* dst = R + (long)k * d.nw;
     const long n = box_words(b);
     int any = 0;
-    for (long t = threadIdx.x; t < n; t += blockDim.x) {
-      int wx, y, z;
-      box_word(b, t, &wx, &y, &z);
-      const long w = ((long)z * d.ny + y) * d.wx + wx;
-      const uint32_t m = ball_bits(wx, y, z, sh.ref[k], delta2) & __ldg(Vk + w);
-      if (!m) continue;
+    // kG lanes per word; the loop bound is uniform per lane group
+    for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
+      const long t = t0 + threadIdx.x / kG;
+      int wx = 0, y = 0, z = 0;
+      long w = 0;
+      uint32_t m = 0;
+      if (t < n) {
+        box_word(b, t, &wx, &y, &z);
+        w = ((long)z * d.ny + y) * d.wx + wx;
+        m = ball_bits(wx, y, z, sh.ref[k], delta2) & __ldg(Vk + w);
+      }
       const uint32_t acc = restricted_word(d, sg, src, sb, wx, y, z, w, m);
-      if (acc) {
+      if (acc && threadIdx.x % kG == 0) {
         dst[w] = acc;
         any = 1;
       }
@@ -740,14 +763,18 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
     const uint32_t* Rk = R + (long)k * d.nw;
     uint32_t* dst = U + (long)k * d.nw;
     const long n = box_words(b);
-    for (long t = threadIdx.x; t < n; t += blockDim.x) {
-      int wx, y, z;
-      box_word(b, t, &wx, &y, &z);
-      const long w = ((long)z * d.ny + y) * d.wx + wx;
-      const uint32_t m = Rk[w];
-      if (!m) continue;
+    for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
+      const long t = t0 + threadIdx.x / kG;
+      int wx = 0, y = 0, z = 0;
+      long w = 0;
+      uint32_t m = 0;
+      if (t < n) {
+        box_word(b, t, &wx, &y, &z);
+        w = ((long)z * d.ny + y) * d.wx + wx;
+        m = Rk[w];
+      }
       const uint32_t acc = restricted_word(d, sg, src, sb, wx, y, z, w, m);
-      if (acc) dst[w] = acc;
+      if (acc && threadIdx.x % kG == 0) dst[w] = acc;
     }
     __syncthreads();
   }
