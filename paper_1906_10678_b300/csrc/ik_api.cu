@@ -33,6 +33,7 @@ struct GridState;
 struct ik_grid_s {
   int device = 0;
   Dims d{};
+  TileCfg tc{};
   cudaStream_t st = nullptr;
   uint32_t* d_occ = nullptr;
   uint64_t version = 1;
@@ -189,18 +190,29 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
     return IK_ERR_ARG;
   }
   s->reach = s->host.R;
+  // shared-memory deltas of the tiled propagation for this grid's pitch
+  std::vector<int32_t> tab(n);
+  for (size_t i = 0; i < n; ++i) {
+    const int32_t o = s->host.dev_off[i];
+    const int dx = unpack_x(o), dy = unpack_y(o);
+    const int delta = dy * g->tc.P + (dx >> 5);
+    tab[i] = (int32_t)(((uint32_t)delta & 0xffffu) | ((uint32_t)(dx & 31) << 16));
+  }
   cudaError_t e = cudaMalloc(&s->d_off, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_tab, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
   if (e != cudaSuccess) {
     cudaFree(s->d_off);
+    cudaFree(s->d_tab);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
     delete s;
     return fail_cuda(e);
   }
+  CK(cudaMemcpyAsync(s->d_tab, tab.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_off, s->host.dev_off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_rows, s->host.rows.data(), s->host.rows.size() * 4, cudaMemcpyHostToDevice,
                      g->st));
@@ -249,6 +261,7 @@ int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<
     SegDev& sd = ad->seg[k];
     sd.off = s->d_off;
     sd.rows = s->d_rows;
+    sd.tab = s->d_tab;
     sd.sc_start = s->d_sc_start;
     sd.sc = s->d_sc;
     sd.mask = s->d_mask;
@@ -290,7 +303,7 @@ int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int,
   }
   for (int k = 1; k <= S; ++k) {
     ProfScope ps(g, P_FWD);
-    CK(launch_propagate(d, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
+    CK(launch_propagate(d, g->tc, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
                         0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, g->st, counters(g, P_FWD)));
   }
   g->f_valid = true;
@@ -309,7 +322,7 @@ int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id, 
   const uint32_t* F = ptr<uint32_t>(g->F);
   for (int k = S; k >= 1; --k) {
     ProfScope ps(g, prof_id);
-    CK(launch_propagate(d, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
+    CK(launch_propagate(d, g->tc, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
                         g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, box + 6 * k, box + 6 * (k - 1),
                         6L * (S + 1), g->st, counters(g, prof_id)));
   }
@@ -373,6 +386,7 @@ int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out) {
   g->d.nz = nz;
   g->d.wx = nx / 32;
   g->d.nw = (long)g->d.wx * ny * nz;
+  g->tc = make_tile_cfg(g->d);
   g->st = (cudaStream_t)cuda_stream;
   e = cudaMalloc(&g->d_occ, g->d.nw * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ, 0, g->d.nw * 4, g->st);
@@ -393,6 +407,7 @@ int ik_destroy_grid(ik_grid g) {
   for (auto& kv : g->shells) {
     ShellDev* s = kv.second;
     cudaFree(s->d_off);
+    cudaFree(s->d_tab);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);

@@ -57,7 +57,22 @@ struct SegDev {
   int n;
   int lo2, hi2;
   int R;                   // max |component| of an offset
+  const int32_t* tab;      // [n] shared-memory deltas for the tiled kernel, see TileCfg
 };
+
+// Output tiling of the shared-memory propagation kernel: a block of 8 warps
+// covers all wx words of TY rows in each of TZ = 8 z slices (warp i = slice
+// z0 + i, lane = (word lane % wx, row lane / wx)); its source halo of reach R
+// is staged in shared memory as (TZ + 2R) x (TY + 2R) rows of P words (word
+// -1 .. wx, zero-padded), P chosen so that a warp's 32 row-word addresses hit
+// distinct banks.  tab[e] packs (dy * P + (dx >> 5)) in the low 16 bits
+// (signed) and dx & 31 in bits 16..20.
+struct TileCfg {
+  int TY, TZ, P, lanes, tiles_y, tiles_z;
+};
+TileCfg make_tile_cfg(const Dims& d);
+// Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).
+size_t tile_smem_bytes(const TileCfg& tc, int R);
 
 // Bounding box of a voxel set in word coordinates, kept in "min form" so
 // that every component accumulates with atomicMin: {wx0, y0, z0, -wx1, -y1,
@@ -75,6 +90,7 @@ struct ShellDev {
   ShellHost host;
   int32_t* d_off = nullptr;
   int32_t* d_rows = nullptr;
+  int32_t* d_tab = nullptr;
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;
@@ -93,10 +109,12 @@ cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev
 // queries (mask_stride 0: one mask shared by all queries).
 // xbox / obox: boxes of X[q] and out[q] at q * box_stride ints; obox must
 // be set empty beforehand and receives the box of the output.
-cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
-                             const uint32_t* mask, long mask_stride, const uint32_t* occ,
-                             uint32_t* out, long out_stride, int Q, const int32_t* xbox,
-                             int32_t* obox, long box_stride, cudaStream_t st,
+// The tiled shared-memory kernel runs when tile_smem_bytes(tc, seg.R) > 0,
+// the global-load kernel otherwise.
+cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,
+                             long x_stride, const uint32_t* mask, long mask_stride,
+                             const uint32_t* occ, uint32_t* out, long out_stride, int Q,
+                             const int32_t* xbox, int32_t* obox, long box_stride, cudaStream_t st,
                              unsigned long long* counters = nullptr);
 // counters (nullable, 4 x u64, accumulated): offset-word pairs visited,
 // pairs whose shifted input word is non-zero, edge-mask words read, output

@@ -231,12 +231,119 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
   }
 }
 
-cudaError_t launch_propagate(const Dims& d, const SegDev& seg, const uint32_t* X, long x_stride,
-                             const uint32_t* mask, long mask_stride, const uint32_t* occ,
-                             uint32_t* out, long out_stride, int Q, const int32_t* xbox,
-                             int32_t* obox, long box_stride, cudaStream_t st,
+// Shared-memory form of the same propagation.  The block's output tile is
+// all wx words of TY rows in TZ slices; its source halo (reach R in y and z,
+// one word in x) is copied from X into shared memory once, with everything
+// outside the word box of X (and outside the grid) left zero, so the offset
+// walk reads two shared words per offset with no bounds test: the per-offset
+// address delta and funnel shift come from the precomputed table tab.  The
+// walk visits, per warp (one z slice), the dz range that can reach the box
+// of X and, per dz, the one contiguous run of offsets whose dy can reach it
+// from any of the warp's rows.
+template <bool kCount>
+__global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, TileCfg tc,
+                                                        const uint32_t* __restrict__ X, long xs,
+                                                        const uint32_t* __restrict__ mask, long ms,
+                                                        const uint32_t* __restrict__ occ,
+                                                        uint32_t* __restrict__ out, long os,
+                                                        const int32_t* __restrict__ xbox,
+                                                        int32_t* __restrict__ obox, long bs,
+                                                        unsigned long long* __restrict__ counters) {
+  extern __shared__ uint32_t sx[];
+  constexpr unsigned kFull = 0xffffffffu;
+  const int q = blockIdx.y;
+  const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = seg.R, RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R, P = tc.P;
+  const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
+  const bool valid = warp < tc.TZ && lane < tc.lanes && y < d.ny && z < d.nz;
+  const long w = valid ? ((long)z * d.ny + y) * d.wx + wx : 0;
+  const uint32_t* Xq = X + q * xs;
+  const int32_t* xb = xbox + q * bs;
+  const int bx0 = __ldg(xb + 0), by0 = __ldg(xb + 1), bz0 = __ldg(xb + 2);
+  const int bx1 = -__ldg(xb + 3), by1 = -__ldg(xb + 4), bz1 = -__ldg(xb + 5);
+  uint32_t m = 0;
+  if (valid) m = (mask ? __ldg(mask + q * ms + w) : 0xffffffffu) & ~__ldg(occ + w);
+  const bool touches = bx0 <= bx1 && by1 >= y0 - R && by0 <= y0 + tc.TY - 1 + R &&
+                       bz1 >= z0 - R && bz0 <= z0 + tc.TZ - 1 + R;
+  if (!__syncthreads_or(touches && m != 0)) {
+    if (valid) out[q * os + w] = 0u;
+    return;
+  }
+  // stage the source halo
+  const int total = RZ * RY * P;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int c = i % P, r = i / P;
+    const int sy = y0 - R + r % RY, sz = z0 - R + r / RY, sw = c - 1;
+    uint32_t v = 0u;
+    if (sy >= by0 && sy <= by1 && sz >= bz0 && sz <= bz1 && sw >= bx0 && sw <= bx1)
+      v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
+    sx[i] = v;
+  }
+  __syncthreads();
+  uint32_t acc = 0;
+  unsigned long long visited = 0, nonzero = 0, mloads = 0;
+  if (__any_sync(kFull, m != 0)) {
+    const int side = 2 * R + 1;
+    const int ylast = min(y0 + tc.TY, d.ny) - 1;
+    const int ez0 = max(bz0 - z, -R), ez1 = min(bz1 - z, R);
+    const int ey0 = max(by0 - ylast, -R), ey1 = min(by1 - y0, R);
+    // lanes without a word read a harmless in-range spot
+    const int base = valid ? ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1) : (R * RY + R) * P + 1;
+    const uint32_t* M = seg.mask + w;
+    bool live = m != 0;
+    for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
+      const int32_t* rowp = seg.rows + (ez + R) * side + R;
+      const int e1 = __ldg(rowp + ey1 + 1);
+      const int zb = base + ez * RY * P;
+      for (int e = __ldg(rowp + ey0); e < e1; ++e) {
+        const int32_t t = __ldg(seg.tab + e);
+        const int a = zb + (int)(int16_t)(t & 0xffff);
+        const uint32_t x = __funnelshift_r(sx[a], sx[a + 1], (t >> 16) & 31);
+        if (kCount && live) {
+          ++visited;
+          nonzero += x != 0;
+        }
+        if (x & m & ~acc) {
+          if (kCount) ++mloads;
+          acc |= x & __ldg(M + (long)e * d.nw);
+        }
+      }
+      live = live && (acc & m) != m;
+      if (!__any_sync(kFull, live)) break;
+    }
+  }
+  acc &= m;
+  if (valid) out[q * os + w] = acc;
+  box_accumulate(obox + q * bs, acc != 0, wx, y, z);
+  if (kCount && valid) {
+    atomicAdd(counters + 0, visited);
+    atomicAdd(counters + 1, nonzero);
+    atomicAdd(counters + 2, mloads);
+    atomicAdd(counters + 3, (unsigned long long)(m != 0));
+  }
+}
+
+cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,
+                             long x_stride, const uint32_t* mask, long mask_stride,
+                             const uint32_t* occ, uint32_t* out, long out_stride, int Q,
+                             const int32_t* xbox, int32_t* obox, long box_stride, cudaStream_t st,
                              unsigned long long* counters) {
   if (Q <= 0) return cudaSuccess;
+  const size_t smem = tile_smem_bytes(tc, seg.R);
+  if (smem > 0 && seg.tab) {
+    // per device and per function; cheap enough to repeat on every launch
+    cudaFuncSetAttribute(counters ? (const void*)k_propagate_tile<true> : (const void*)k_propagate_tile<false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(tc.tiles_y * tc.tiles_z, Q);
+    if (counters)
+      k_propagate_tile<true><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
+                                                      out, out_stride, xbox, obox, box_stride, counters);
+    else
+      k_propagate_tile<false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
+                                                       out, out_stride, xbox, obox, box_stride, nullptr);
+    return cudaGetLastError();
+  }
   dim3 grid(grid_for(d.nw, 256), Q);
   if (counters)
     k_propagate<true><<<grid, 256, 0, st>>>(d, seg, X, x_stride, mask, mask_stride, occ, out,

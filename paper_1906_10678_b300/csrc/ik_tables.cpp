@@ -145,4 +145,37 @@ void build_shell(int lo2, int hi2, ShellHost* sh) {
   }
 }
 
+TileCfg make_tile_cfg(const Dims& d) {
+  TileCfg tc;
+  tc.TY = 32 / d.wx;
+  tc.lanes = tc.TY * d.wx;
+  tc.TZ = 8;
+  tc.tiles_y = (d.ny + tc.TY - 1) / tc.TY;
+  tc.tiles_z = (d.nz + tc.TZ - 1) / tc.TZ;
+  // smallest pitch >= wx + 2 whose lane addresses (lo and hi words) spread
+  // over the banks with the fewest collisions
+  int best = d.wx + 2, best_conf = 1 << 30;
+  for (int P = d.wx + 2; P <= d.wx + 2 + 32; ++P) {
+    int hits[32] = {0};
+    int conf = 0;
+    for (int l = 0; l < tc.lanes; ++l) {
+      const int b = ((l / d.wx) * P + (l % d.wx)) & 31;
+      conf = std::max(conf, ++hits[b]);
+    }
+    if (conf < best_conf) {
+      best_conf = conf;
+      best = P;
+    }
+    if (conf == 1) break;
+  }
+  tc.P = best;
+  return tc;
+}
+
+size_t tile_smem_bytes(const TileCfg& tc, int R) {
+  if (R > 31) return 0;  // the x halo would exceed one word
+  const size_t bytes = (size_t)(tc.TZ + 2 * R) * (tc.TY + 2 * R) * tc.P * 4;
+  return bytes <= 200 * 1024 ? bytes : 0;
+}
+
 }  // namespace ikb
