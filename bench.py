@@ -131,7 +131,8 @@ def roofline(prof, work, sc, n_targets):
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
             "alg_bytes_per_launch": round(per_launch), "ms_per_launch": round(ms, 4),
             "pairs_visited": w["visited"], "pairs_nonzero": w["nonzero"],
-            "mask_words_read": w["mask_words"], "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+            "mask_words_read": w["mask_words"], "warp_iters": w["warp_iters"],
+            "active_blocks": w["blocks"], "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
 
 def oracle_sample(threads: int):

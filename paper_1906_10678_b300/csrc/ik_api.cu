@@ -129,8 +129,10 @@ struct ProfScope {
   }
 };
 
+constexpr int kCounters = 8;
+
 unsigned long long* counters(ik_grid g, int id) {
-  return (g->count_on && g->d_counters) ? g->d_counters + 4 * id : nullptr;
+  return (g->count_on && g->d_counters) ? g->d_counters + kCounters * id : nullptr;
 }
 
 // Grow a device buffer to at least `bytes`; contents are not kept.  With
@@ -875,8 +877,8 @@ int ik_profile_enable(ik_grid g, int timing, int counting) {
   int rc = set_device(g);
   if (rc) return rc;
   if (counting && !g->d_counters) {
-    CK(cudaMalloc(&g->d_counters, sizeof(unsigned long long) * 4 * P_N));
-    CK(cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned long long) * 4 * P_N, g->st));
+    CK(cudaMalloc(&g->d_counters, sizeof(unsigned long long) * kCounters * P_N));
+    CK(cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned long long) * kCounters * P_N, g->st));
   }
   g->prof_on = timing != 0;
   g->count_on = counting != 0;
@@ -898,17 +900,17 @@ int ik_profile_read(ik_grid g, double* ms_out, int64_t* launches_out, uint64_t* 
   }
   g->recs.clear();
   g->ev_used = 0;
-  std::vector<unsigned long long> cnt(4 * P_N, 0);
+  std::vector<unsigned long long> cnt(kCounters * P_N, 0);
   if (g->d_counters) {
-    CK(cudaMemcpy(cnt.data(), g->d_counters, sizeof(unsigned long long) * 4 * P_N,
+    CK(cudaMemcpy(cnt.data(), g->d_counters, sizeof(unsigned long long) * kCounters * P_N,
                   cudaMemcpyDeviceToHost));
-    CK(cudaMemset(g->d_counters, 0, sizeof(unsigned long long) * 4 * P_N));
+    CK(cudaMemset(g->d_counters, 0, sizeof(unsigned long long) * kCounters * P_N));
   }
   for (int i = 0; i < P_N && i < cap; ++i) {
     if (ms_out) ms_out[i] = ms[i];
     if (launches_out) launches_out[i] = n[i];
     if (counters_out)
-      for (int j = 0; j < 4; ++j) counters_out[4 * i + j] = cnt[4 * i + j];
+      for (int j = 0; j < kCounters; ++j) counters_out[kCounters * i + j] = cnt[kCounters * i + j];
   }
   return P_N;
 }

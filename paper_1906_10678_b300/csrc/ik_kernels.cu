@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
   const int q = blockIdx.y;
   const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int R = seg.R, RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R, P = tc.P;
+  const int R = seg.R, RY = tc.TY + 2 * R, P = tc.P;
   const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
   const bool valid = warp < tc.TZ && lane < tc.lanes && y < d.ny && z < d.nz;
   const long w = valid ? ((long)z * d.ny + y) * d.wx + wx : 0;
@@ -270,19 +270,30 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
     if (valid) out[q * os + w] = 0u;
     return;
   }
-  // stage the source halo
-  const int total = RZ * RY * P;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int c = i % P, r = i / P;
-    const int sy = y0 - R + r % RY, sz = z0 - R + r / RY, sw = c - 1;
-    uint32_t v = 0u;
-    if (sy >= by0 && sy <= by1 && sz >= bz0 && sz <= bz1 && sw >= bx0 && sw <= bx1)
-      v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
-    sx[i] = v;
+  // Stage the source halo.  The walk below only reads slices inside the z
+  // range of the box of X, and rows at most TY - 1 outside its y range (the
+  // warp's union of rows), so only that part of the halo is written: words
+  // inside the box are copied, the rest of it is zeroed.  A warp writes
+  // 32 / P rows per pass, one word per lane.
+  {
+    const int sz0 = max(bz0, z0 - R), sz1 = min(bz1, z0 + tc.TZ - 1 + R);
+    const int sy0 = max(by0 - tc.TY + 1, y0 - R), sy1 = min(by1 + tc.TY - 1, y0 + tc.TY - 1 + R);
+    const int ny_rows = sy1 - sy0 + 1, n_rows = (sz1 - sz0 + 1) * ny_rows;
+    const int per_pass = 32 / P;
+    const int sub = lane / P, c = lane % P, sw = c - 1;
+    const bool col_in = sw >= bx0 && sw <= bx1;
+    if (ny_rows > 0 && sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+        const int sy = sy0 + r % ny_rows, sz = sz0 + r / ny_rows;
+        uint32_t v = 0u;
+        if (col_in && sy >= by0 && sy <= by1) v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
+        sx[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
+      }
+    }
   }
   __syncthreads();
   uint32_t acc = 0;
-  unsigned long long visited = 0, nonzero = 0, mloads = 0;
+  unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0;
   if (__any_sync(kFull, m != 0)) {
     const int side = 2 * R + 1;
     const int ylast = min(y0 + tc.TY, d.ny) - 1;
@@ -296,6 +307,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
       const int32_t* rowp = seg.rows + (ez + R) * side + R;
       const int e1 = __ldg(rowp + ey1 + 1);
       const int zb = base + ez * RY * P;
+      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + ey0));
       for (int e = __ldg(rowp + ey0); e < e1; ++e) {
         const int32_t t = __ldg(seg.tab + e);
         const int a = zb + (int)(int16_t)(t & 0xffff);
@@ -322,6 +334,8 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
     atomicAdd(counters + 2, mloads);
     atomicAdd(counters + 3, (unsigned long long)(m != 0));
   }
+  if (kCount && lane == 0) atomicAdd(counters + 4, warp_iters);
+  if (kCount && threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
 }
 
 cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,

@@ -340,7 +340,7 @@ def ik_profile_read(g: int) -> dict:
     cap = 32
     ms = np.zeros(cap, np.float64)
     n = np.zeros(cap, np.int64)
-    c = np.zeros((cap, 4), np.uint64)
+    c = np.zeros((cap, 8), np.uint64)
     k = _lib.ik_profile_read(g, _np_ptr(ms), _np_ptr(n), _np_ptr(c), cap)
     if k < 0:
         raise IkError(k, "ik_profile_read")
@@ -348,7 +348,8 @@ def ik_profile_read(g: int) -> dict:
     for i in range(k):
         out[_lib.ik_profile_name(i).decode()] = {
             "ms": float(ms[i]), "launches": int(n[i]), "visited": int(c[i, 0]),
-            "nonzero": int(c[i, 1]), "mask_words": int(c[i, 2]), "out_words": int(c[i, 3])}
+            "nonzero": int(c[i, 1]), "mask_words": int(c[i, 2]), "out_words": int(c[i, 3]),
+            "warp_iters": int(c[i, 4]), "blocks": int(c[i, 5])}
     return out
 
 
