@@ -200,14 +200,25 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
     const int delta = dy * g->tc.P + (dx >> 5);
     tab[i] = (int32_t)(((uint32_t)delta & 0xffffu) | ((uint32_t)(dx & 31) << 16));
   }
+  // shared-memory deltas of every supercover voxel for the tiled edge masks
+  const int RY = g->tc.TY + 2 * s->reach;
+  std::vector<int32_t> sctab(s->host.sc.size());
+  for (size_t i = 0; i < sctab.size(); ++i) {
+    const int32_t v = s->host.sc[i];
+    const int vx = unpack_x(v), vy = unpack_y(v), vz = unpack_z(v);
+    const int delta = (vz * RY + vy) * g->tc.P + (vx >> 5);
+    sctab[i] = (int32_t)((uint32_t)delta << 5) | (vx & 31);
+  }
   cudaError_t e = cudaMalloc(&s->d_off, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_tab, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_sctab, sctab.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
   if (e != cudaSuccess) {
     cudaFree(s->d_off);
     cudaFree(s->d_tab);
+    cudaFree(s->d_sctab);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -215,6 +226,7 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
     return fail_cuda(e);
   }
   CK(cudaMemcpyAsync(s->d_tab, tab.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+  CK(cudaMemcpyAsync(s->d_sctab, sctab.data(), sctab.size() * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_off, s->host.dev_off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_rows, s->host.rows.data(), s->host.rows.size() * 4, cudaMemcpyHostToDevice,
                      g->st));
@@ -239,7 +251,7 @@ int ensure_masks(ik_grid g, ShellDev* s) {
   }
   {
     ProfScope ps(g, P_MASKS);
-    CK(launch_edge_masks(g->d, g->d_occ, *s, s->d_mask, g->st));
+    CK(launch_edge_masks(g->d, g->tc, g->d_occ, *s, s->d_mask, g->st));
   }
   s->mask_version = g->version;
   return IK_OK;
@@ -264,6 +276,7 @@ int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<
     sd.off = s->d_off;
     sd.rows = s->d_rows;
     sd.tab = s->d_tab;
+    sd.sctab = s->d_sctab;
     sd.sc_start = s->d_sc_start;
     sd.sc = s->d_sc;
     sd.mask = s->d_mask;
@@ -410,6 +423,7 @@ int ik_destroy_grid(ik_grid g) {
     ShellDev* s = kv.second;
     cudaFree(s->d_off);
     cudaFree(s->d_tab);
+    cudaFree(s->d_sctab);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);

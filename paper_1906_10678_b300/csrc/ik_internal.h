@@ -58,6 +58,7 @@ struct SegDev {
   int lo2, hi2;
   int R;                   // max |component| of an offset
   const int32_t* tab;      // [n] shared-memory deltas for the tiled kernel, see TileCfg
+  const int32_t* sctab;    // [sc_start[n]] shared-memory deltas of the supercover voxels
 };
 
 // Output tiling of the shared-memory propagation kernel: a block of 8 warps
@@ -91,6 +92,7 @@ struct ShellDev {
   int32_t* d_off = nullptr;
   int32_t* d_rows = nullptr;
   int32_t* d_tab = nullptr;
+  int32_t* d_sctab = nullptr;  // per supercover voxel: (shared-memory delta << 5) | (dx & 31)
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;
@@ -102,8 +104,8 @@ struct ShellDev {
 // All launchers enqueue on `st` and return the launch error (cudaSuccess).
 cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, uint32_t* occ,
                              cudaStream_t st);
-cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev& s, uint32_t* mask,
-                              cudaStream_t st);
+cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
+                              uint32_t* mask, cudaStream_t st);
 // out[q] = (mask ? mask[q] : ~0) & D_seg(X[q]) for q < Q; sets are nw words
 // apart with stride `x_stride` / `out_stride` / `mask_stride` words between
 // queries (mask_stride 0: one mask shared by all queries).

@@ -111,10 +111,74 @@ __global__ void k_edge_masks(Dims d, const uint32_t* __restrict__ occ,
   }
 }
 
-cudaError_t launch_edge_masks(const Dims& d, const uint32_t* occ, const ShellDev& s, uint32_t* mask,
-                              cudaStream_t st) {
+// Shared-memory form: a block covers one output tile (TileCfg) and a chunk
+// of kMaskChunk offsets.  The occupancy halo of the tile (reach R, zero
+// outside the grid, where a segment cannot end anyway) is staged once and
+// reused for every offset of the chunk; each supercover voxel is then two
+// shared loads and a funnel shift at a precomputed delta.
+constexpr int kMaskChunk = 64;
+
+__global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, int R, int n_off,
+                                                         const uint32_t* __restrict__ occ,
+                                                         const int32_t* __restrict__ sc_start,
+                                                         const int32_t* __restrict__ sctab,
+                                                         uint32_t* __restrict__ mask) {
+  extern __shared__ uint32_t so[];
+  const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R, P = tc.P;
+  {
+    const int n_rows = RZ * RY, per_pass = 32 / P;
+    const int sub = lane / P, c = lane % P, sw = c - 1;
+    if (sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+        const int sy = y0 - R + r % RY, sz = z0 - R + r / RY;
+        uint32_t v = 0u;
+        if (sw >= 0 && sw < d.wx && sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz)
+          v = __ldg(occ + ((long)sz * d.ny + sy) * d.wx + sw);
+        so[r * P + c] = v;
+      }
+    }
+  }
+  __syncthreads();
+  const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
+  if (warp >= tc.TZ || lane >= tc.lanes || y >= d.ny || z >= d.nz) return;
+  const long w = ((long)z * d.ny + y) * d.wx + wx;
+  const int base = ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1);
+  const int e_end = min(n_off, (int)(blockIdx.y + 1) * kMaskChunk);
+  for (int e = blockIdx.y * kMaskChunk; e < e_end; ++e) {
+    const int s1 = __ldg(sc_start + e + 1);
+    uint32_t blocked = 0;
+    int i = __ldg(sc_start + e);
+    for (; i + 4 <= s1; i += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t t = __ldg(sctab + i + u);
+        const int a = base + (t >> 5);
+        blocked |= __funnelshift_r(so[a], so[a + 1], t & 31);
+      }
+    }
+    for (; i < s1; ++i) {
+      const int32_t t = __ldg(sctab + i);
+      const int a = base + (t >> 5);
+      blocked |= __funnelshift_r(so[a], so[a + 1], t & 31);
+    }
+    mask[(long)e * d.nw + w] = ~blocked;
+  }
+}
+
+cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
+                              uint32_t* mask, cudaStream_t st) {
   const int n = (int)s.host.off.size();
   if (n == 0) return cudaSuccess;
+  const size_t smem = tile_smem_bytes(tc, s.reach);
+  if (smem > 0 && s.d_sctab) {
+    cudaFuncSetAttribute((const void*)k_edge_masks_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    dim3 grid(tc.tiles_y * tc.tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
+    k_edge_masks_tile<<<grid, 256, smem, st>>>(d, tc, s.reach, n, occ, s.d_sc_start, s.d_sctab, mask);
+    return cudaGetLastError();
+  }
   const int block = 256;
   const int gx = max(1, min(grid_for(d.nw, block), 64));
   dim3 grid(gx, min(n, 65535));
@@ -308,7 +372,31 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
       const int e1 = __ldg(rowp + ey1 + 1);
       const int zb = base + ez * RY * P;
       if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + ey0));
-      for (int e = __ldg(rowp + ey0); e < e1; ++e) {
+      int e = __ldg(rowp + ey0);
+      // four offsets per pass: eight independent shared loads in flight
+      for (; e + 4 <= e1; e += 4) {
+        uint32_t xv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int32_t t = __ldg(seg.tab + e + i);
+          const int a = zb + (int)(int16_t)(t & 0xffff);
+          xv[i] = __funnelshift_r(sx[a], sx[a + 1], (t >> 16) & 31);
+        }
+        if (kCount && live) {
+          visited += 4;
+          nonzero += (xv[0] != 0) + (xv[1] != 0) + (xv[2] != 0) + (xv[3] != 0);
+        }
+        if ((xv[0] | xv[1] | xv[2] | xv[3]) & m & ~acc) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (xv[i] & m & ~acc) {
+              if (kCount) ++mloads;
+              acc |= xv[i] & __ldg(M + (long)(e + i) * d.nw);
+            }
+          }
+        }
+      }
+      for (; e < e1; ++e) {
         const int32_t t = __ldg(seg.tab + e);
         const int a = zb + (int)(int16_t)(t & 0xffff);
         const uint32_t x = __funnelshift_r(sx[a], sx[a + 1], (t >> 16) & 31);
