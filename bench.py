@@ -115,7 +115,13 @@ def roofline(prof, work, sc, n_targets):
     counters on an identical step.
     """
     cls = max((k for k in prof if k.startswith("propagate")), key=lambda k: prof[k]["ms"])
-    p, w = prof[cls], work[cls]
+    p = prof[cls]
+    if cls == "propagate_backward_waypoints":
+        # the waypoint pass keeps its work counters per segment level
+        w = {f: sum(v[f] for k, v in work.items() if k.startswith("way_k"))
+             for f in ("visited", "nonzero", "mask_words", "out_words", "warp_iters", "blocks")}
+    else:
+        w = work[cls]
     launches = max(1, p["launches"])
     words = (sc.nx // 32) * sc.ny * sc.nz
     q_per_launch = {"propagate_backward_waypoints": n_targets * N_WAY,
@@ -319,6 +325,30 @@ def run_ours(args):
             ik.ik_plan_path(g.h, arm, p, N_WAY, delta=DELTA)
         plain_ms.append((time.perf_counter() - a) * 1000.0)
 
+    # midcourse replans: 16 moving boxes (sides 6-16, 0.5-2 voxels per tick)
+    # added to the static scene; each tick updates the occupancy once, then
+    # every path with a reach pose is replanned from waypoint c = 8.  The
+    # first request after an update also pays the edge-mask and forward-set
+    # rebuild of the new occupancy.
+    mv = G.make_moving_boxes(sc.shape, 16, 3)
+    paths = out[2]
+    rep_ms, rep_status = [], []
+    for tick in range(args.replan_ticks):
+        for _ in range(4):
+            mv.step()
+        ik.ik_set_boxes(g.h, np.concatenate([sc.boxes, mv.boxes()]))
+        for i in range(N_TARGETS):
+            if not out[1][i]:
+                continue
+            a = time.perf_counter()
+            _, _, st = ik.ik_replan(g.h, arm, paths[i], 8, delta=DELTA)
+            rep_ms.append((time.perf_counter() - a) * 1000.0)
+            rep_status.append(st)
+    ik.ik_set_boxes(g.h, sc.boxes)
+    rep_ms = np.asarray(rep_ms)
+    rep_status = np.asarray(rep_status)
+    cut = rep_status != ik.IK_PATH_KEPT
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -334,12 +364,23 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h)},
             "plain": {"value": round(1000.0 / float(np.mean(plain_ms)), 3), "unit": UNIT,
                       "ms_per_solve": round(float(np.mean(plain_ms)), 3), "sample": len(plain_ms)},
+            "replan": {"p50_ms": round(float(np.percentile(rep_ms, 50)), 3),
+                       "p99_ms": round(float(np.percentile(rep_ms, 99)), 3),
+                       "cut_p50_ms": round(float(np.percentile(rep_ms[cut], 50)), 3) if cut.any() else None,
+                       "cut_p99_ms": round(float(np.percentile(rep_ms[cut], 99)), 3) if cut.any() else None,
+                       "requests": int(len(rep_ms)), "cut": int(cut.sum()),
+                       "status_counts": {str(k): int((rep_status == k).sum()) for k in range(5)},
+                       "note": "host wall time per ik_replan call (C ABI, host buffers)"},
             "found": int(found_np.sum()),
             "path_status_counts": {str(k): int((status_np == k).sum()) for k in range(5)},
             "max_relax": int(relax_np[..., 0].max()),
             "clocks": clk,
             "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
-                        for k, v in prof.items() if v["launches"]},
+                        for k, v in prof.items() if v["launches"] and not k.startswith("way_k")},
+            "waypoint_levels": {k: {"ms": round(prof[k]["ms"], 3), "warp_iters": work[k]["warp_iters"],
+                                    "visited": work[k]["visited"], "nonzero": work[k]["nonzero"],
+                                    "blocks": work[k]["blocks"]}
+                                for k in prof if k.startswith("way_k") and prof[k]["launches"]},
         }
         line["roofline"] = roofline(prof, work, sc, N_TARGETS)
         if world == 1 and not args.no_cpu_baseline:
@@ -362,6 +403,7 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="grid edge; 128 is the benchmark workload, smaller only for captures")
     ap.add_argument("--targets", type=int, default=64)
+    ap.add_argument("--replan-ticks", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

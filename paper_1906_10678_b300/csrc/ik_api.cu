@@ -89,7 +89,8 @@ enum ProfId {
   P_GUIDE,
   P_CHAIN,
   P_VALIDATE,
-  P_N
+  P_WAY_K1,  // waypoint backward pass per segment level k = 1 .. IK_MAX_SEG
+  P_N = P_WAY_K1 + IK_MAX_SEG
 };
 const char* kProfNames[P_N] = {"rasterize",
                                "edge_masks",
@@ -100,7 +101,10 @@ const char* kProfNames[P_N] = {"rasterize",
                                "traceback",
                                "guide_targets",
                                "smooth_chain",
-                               "validate"};
+                               "validate",
+                               "way_k1", "way_k2", "way_k3", "way_k4", "way_k5", "way_k6",
+                               "way_k7", "way_k8", "way_k9", "way_k10", "way_k11", "way_k12",
+                               "way_k13", "way_k14", "way_k15", "way_k16"};
 
 cudaEvent_t take_event(ik_grid g) {
   if (g->ev_used == g->ev_pool.size()) {
@@ -118,7 +122,7 @@ struct ProfScope {
   int id;
   cudaEvent_t a = nullptr;
   ProfScope(ik_grid g_, int id_) : g(g_), id(id_) {
-    if (g->prof_on && (a = take_event(g))) cudaEventRecord(a, g->st);
+    if (id >= 0 && g->prof_on && (a = take_event(g))) cudaEventRecord(a, g->st);
   }
   ~ProfScope() {
     if (!a) return;
@@ -337,9 +341,12 @@ int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id, 
   const uint32_t* F = ptr<uint32_t>(g->F);
   for (int k = S; k >= 1; --k) {
     ProfScope ps(g, prof_id);
+    // the waypoint pass is also recorded per level (work counters go there)
+    ProfScope pl(g, prof_id == P_BWD_WAY ? P_WAY_K1 + k - 1 : -1);
+    unsigned long long* cnt = counters(g, prof_id == P_BWD_WAY ? P_WAY_K1 + k - 1 : prof_id);
     CK(launch_propagate(d, g->tc, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
                         g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, box + 6 * k, box + 6 * (k - 1),
-                        6L * (S + 1), g->st, counters(g, prof_id)));
+                        6L * (S + 1), g->st, cnt));
   }
   return IK_OK;
 }
