@@ -373,26 +373,35 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
       const int zb = base + ez * RY * P;
       if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + ey0));
       int e = __ldg(rowp + ey0);
-      // four offsets per pass: eight independent shared loads in flight
-      for (; e + 4 <= e1; e += 4) {
-        uint32_t xv[4];
+      // Eight offsets per pass.  The edge-mask words a pass needs are decided
+      // against the accumulator as it stood when the pass began and then
+      // loaded together, so their (HBM) latencies overlap instead of each
+      // load waiting for the previous one to update the accumulator.
+      for (; e + 8 <= e1; e += 8) {
+        uint32_t xv[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 8; ++i) {
           const int32_t t = __ldg(seg.tab + e + i);
           const int a = zb + (int)(int16_t)(t & 0xffff);
           xv[i] = __funnelshift_r(sx[a], sx[a + 1], (t >> 16) & 31);
         }
-        if (kCount && live) {
-          visited += 4;
-          nonzero += (xv[0] != 0) + (xv[1] != 0) + (xv[2] != 0) + (xv[3] != 0);
-        }
-        if ((xv[0] | xv[1] | xv[2] | xv[3]) & m & ~acc) {
+        const uint32_t want = m & ~acc;
+        uint32_t any = 0;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (xv[i] & m & ~acc) {
-              if (kCount) ++mloads;
-              acc |= xv[i] & __ldg(M + (long)(e + i) * d.nw);
-            }
+        for (int i = 0; i < 8; ++i) any |= xv[i];
+        if (kCount && live) {
+          visited += 8;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) nonzero += xv[i] != 0;
+        }
+        if (any & want) {
+          uint32_t mv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) mv[i] = (xv[i] & want) ? __ldg(M + (long)(e + i) * d.nw) : 0u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (kCount) mloads += (xv[i] & want) != 0;
+            acc |= xv[i] & mv[i];
           }
         }
       }
