@@ -222,6 +222,34 @@ IK_API int ik_validate_poses(ik_grid g, const ik_arm* arm, const int32_t* poses,
 IK_API int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, int current_idx,
               const ik_path_params* pp, int32_t* poses_out, int32_t* relax_out, int* status);
 
+/* ------------------------------------------------ allocation-free variant */
+/* Forward reachable sets F_0..F_S, like ik_forward_sets, for callers that
+ * cannot allocate GPU memory when they need the answer (a caching or arena
+ * allocator owns the device, a real-time loop must not pay cudaMalloc's
+ * synchronisation, or allocation is forbidden after start-up).  The paper
+ * has no counterpart: this is a deployment interface only.
+ *
+ * occ_words (device, bit-packed occupancy, 1 = occupied) and fsets_out
+ * (device, [n_seg + 1][(nx/32) * ny * nz] words) belong to the caller; arm
+ * and root are host memory.  The grid rules are those of ik_create_grid.
+ * The call allocates nothing: its scratch -- the arm's shell offsets and
+ * supercover lists -- is one fixed array of 4.25 MiB in the library's device
+ * memory (held by every GPU that loads the library until the process ends).
+ * Limits: at most 32768 shell offsets over all segments and 2^20 supercover
+ * voxels (the arms {8,7,6,5} and {20,18,16,14,12,10,8,6} fit, six segments
+ * of length 20 fit); larger arms return IK_ERR_UNSUPPORTED.  Segment tests walk the supercover
+ * against the occupancy instead of reading stored edge masks.
+ *
+ * The first call on a device looks up the array's device address (with
+ * that device current) and should come before any stream capture.  Every
+ * call shares the array and overwrites the part it uses; calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it.  The call
+ * is synchronous on cuda_stream (NULL: the legacy default stream).  Returns
+ * IK_OK, IK_ERR_ARG, IK_ERR_UNSUPPORTED or IK_ERR_CUDA. */
+IK_API int ik_forward_sets_noalloc(const uint32_t* occ_words, int nx, int ny, int nz,
+                                   const ik_arm* arm, const int32_t root[3], uint32_t* fsets_out,
+                                   void* cuda_stream);
+
 /* ------------------------------------------------------------- profiling */
 /* Per-kernel-class timing: with timing != 0 every launch is bracketed by two
  * CUDA events recorded on the grid's stream; with counting != 0 the

@@ -74,6 +74,7 @@ _sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
 _sig("ik_validate_poses", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_replan", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, ctypes.POINTER(IkPathParams), _vp,
                        _vp, ctypes.POINTER(_i)])
+_sig("ik_forward_sets_noalloc", _i, [_vp, _i, _i, _i, ctypes.POINTER(IkArm), _vp, _vp, _vp])
 _sig("ik_profile_enable", _i, [_vp, _i, _i])
 _sig("ik_profile_read", _i, [_vp, _vp, _vp, _vp, _i])
 _sig("ik_profile_name", ctypes.c_char_p, [_i])
@@ -84,7 +85,8 @@ EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
-    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_profile_enable",
+    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_forward_sets_noalloc",
+    "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
 ]
 
@@ -329,6 +331,18 @@ def ik_replan(g: int, arm, poses, current: int, delta: int = 3, eps2: int = 2, e
     _check(_lib.ik_replan(g, ctypes.byref(arm.c), _np_ptr(p), W, current, ctypes.byref(pp),
                           _np_ptr(out), _np_ptr(relax), ctypes.byref(st)), "ik_replan")
     return out, relax, st.value
+
+
+def ik_forward_sets_noalloc(occ_words, shape, arm, root, fsets_out, stream: int = 0) -> None:
+    """Device form only: ``occ_words`` uint32/int32 CUDA tensor of the
+    occupancy words, ``fsets_out`` CUDA tensor of (S+1) * words uint32/int32;
+    no allocation happens inside the call."""
+    arm = _arm(arm)
+    nx, ny, nz = shape
+    _check(_lib.ik_forward_sets_noalloc(_dev_ptr(occ_words), nx, ny, nz, ctypes.byref(arm.c),
+                                        _np_ptr(_i32(root)), _dev_ptr(fsets_out),
+                                        _vp(stream) if stream else None),
+           "ik_forward_sets_noalloc")
 
 
 def ik_profile_enable(g: int, timing: bool = True, counting: bool = False) -> None:
