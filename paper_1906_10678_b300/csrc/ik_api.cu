@@ -202,7 +202,7 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
     const int32_t o = s->host.dev_off[i];
     const int dx = unpack_x(o), dy = unpack_y(o);
     const int delta = dy * g->tc.P + (dx >> 5);
-    tab[i] = (int32_t)(((uint32_t)delta & 0xffffu) | ((uint32_t)(dx & 31) << 16));
+    tab[i] = (int32_t)(((uint32_t)delta << 5) | (uint32_t)(dx & 31));
   }
   // shared-memory deltas of every supercover voxel for the tiled edge masks
   const int RY = g->tc.TY + 2 * s->reach;

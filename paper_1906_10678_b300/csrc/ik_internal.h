@@ -66,8 +66,8 @@ struct SegDev {
 // z0 + i, lane = (word lane % wx, row lane / wx)); its source halo of reach R
 // is staged in shared memory as (TZ + 2R) x (TY + 2R) rows of P words (word
 // -1 .. wx, zero-padded), P chosen so that a warp's 32 row-word addresses hit
-// distinct banks.  tab[e] packs (dy * P + (dx >> 5)) in the low 16 bits
-// (signed) and dx & 31 in bits 16..20.
+// distinct banks.  tab[e] = ((dy * P + (dx >> 5)) << 5) | (dx & 31): the
+// shared-memory word delta and the funnel shift of offset e.
 struct TileCfg {
   int TY, TZ, P, lanes, tiles_y, tiles_z;
 };
