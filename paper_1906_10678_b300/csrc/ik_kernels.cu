@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
   const int q = blockIdx.y;
   const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int R = seg.R, RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R, P = tc.P;
+  const int R = seg.R, RY = tc.TY + 2 * R, P = tc.P;
   const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
   const bool valid = warp < tc.TZ && lane < tc.lanes && y < d.ny && z < d.nz;
   const long w = valid ? ((long)z * d.ny + y) * d.wx + wx : 0;
@@ -339,12 +339,6 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
   // warp's union of rows), so only that part of the halo is written: words
   // inside the box are copied, the rest of it is zeroed.  A warp writes
   // 32 / P rows per pass, one word per lane.
-  // rowbits[slice]: bit r set when staged row r of that slice has a
-  // non-zero word (only used when the halo has at most 64 rows)
-  unsigned long long* rowbits = reinterpret_cast<unsigned long long*>(sx + (RZ * RY * P + 1) / 2 * 2);
-  const bool use_rows = RY <= 64;
-  for (int i = threadIdx.x; i < RZ; i += blockDim.x) rowbits[i] = use_rows ? 0ull : ~0ull;
-  __syncthreads();
   {
     const int sz0 = max(bz0, z0 - R), sz1 = min(bz1, z0 + tc.TZ - 1 + R);
     const int sy0 = max(by0 - tc.TY + 1, y0 - R), sy1 = min(by1 + tc.TY - 1, y0 + tc.TY - 1 + R);
@@ -352,23 +346,12 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
     const int per_pass = 32 / P;
     const int sub = lane / P, c = lane % P, sw = c - 1;
     const bool col_in = sw >= bx0 && sw <= bx1;
-    if (ny_rows > 0) {
-      // every lane runs the same number of passes so the row ballot is full
-      const int passes = (n_rows + 8 * per_pass - 1) / (8 * per_pass);
-      for (int k = 0; k < passes; ++k) {
-        const int r = k * 8 * per_pass + warp * per_pass + sub;
-        const bool act = sub < per_pass && r < n_rows;
+    if (ny_rows > 0 && sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+        const int sy = sy0 + r % ny_rows, sz = sz0 + r / ny_rows;
         uint32_t v = 0u;
-        int sy = 0, sz = 0;
-        if (act) {
-          sy = sy0 + r % ny_rows;
-          sz = sz0 + r / ny_rows;
-          if (col_in && sy >= by0 && sy <= by1) v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
-          sx[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
-        }
-        const unsigned nzb = __ballot_sync(kFull, act && v != 0u);
-        if (act && use_rows && c == 0 && ((nzb >> (sub * P)) & ((1u << P) - 1u)))
-          atomicOr(rowbits + (sz - z0 + R), 1ull << (sy - y0 + R));
+        if (col_in && sy >= by0 && sy <= by1) v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
+        sx[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
       }
     }
   }
@@ -386,22 +369,10 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
     bool live = m != 0;
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
       const int32_t* rowp = seg.rows + (ez + R) * side + R;
+      const int e1 = __ldg(rowp + ey1 + 1);
       const int zb = base + ez * RY * P;
-      // shell rows dy whose source rows (the warp's TY rows shifted by dy)
-      // are all zero are skipped; the rest form runs of consecutive dy,
-      // each a contiguous run of the offset table
-      unsigned long long wmask = rowbits[z - z0 + R + ez];
-      for (int sh = 1; sh < tc.TY; sh <<= 1) wmask |= wmask >> sh;
-      const int nb = ey1 - ey0 + 1;
-      unsigned long long bits = (wmask >> (R + ey0)) & (nb >= 64 ? ~0ull : ((1ull << nb) - 1ull));
-      while (bits) {
-        const int first = __ffsll((long long)bits) - 1;
-        const unsigned long long rest = ~(bits >> first);
-        const int len = rest ? __ffsll((long long)rest) - 1 : 64 - first;
-        bits &= (len + first >= 64) ? 0ull : (~0ull << (first + len));
-        const int e1 = __ldg(rowp + ey0 + first + len);
-      int e = __ldg(rowp + ey0 + first);
-      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - e);
+      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + ey0));
+      int e = __ldg(rowp + ey0);
       // Eight offsets per pass.  The edge-mask words a pass needs are decided
       // against the accumulator as it stood when the pass began and then
       // loaded together, so their (HBM) latencies overlap instead of each
@@ -446,7 +417,6 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
           if (kCount) ++mloads;
           acc |= x & __ldg(M + (long)e * d.nw);
         }
-      }
       }
       live = live && (acc & m) != m;
       if (!__any_sync(kFull, live)) break;

@@ -175,9 +175,7 @@ TileCfg make_tile_cfg(const Dims& d) {
 size_t tile_smem_bytes(const TileCfg& tc, int R) {
   if (R > 31) return 0;     // the x halo would exceed one word
   if (tc.P > 31) return 0;  // a staged row must fit in one warp's lanes
-  // halo words, then one 64-bit row mask per slice (8-byte aligned)
-  size_t bytes = (size_t)(tc.TZ + 2 * R) * (tc.TY + 2 * R) * tc.P * 4;
-  bytes = (bytes + 7) / 8 * 8 + (size_t)(tc.TZ + 2 * R) * 8;
+  const size_t bytes = (size_t)(tc.TZ + 2 * R) * (tc.TY + 2 * R) * tc.P * 4;
   return bytes <= 200 * 1024 ? bytes : 0;
 }
 
