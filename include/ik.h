@@ -202,6 +202,29 @@ IK_API int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3
                        int n, const ik_path_params* pp, int32_t* reach_out, int32_t* found_out,
                        int32_t* poses_out, int32_t* relax_out, int32_t* status_out, int on_device);
 
+/* --------------------------------------------- batched graph (step a10) */
+/* A reach + path batch recorded once as a CUDA graph and replayed.  The
+ * graph reads n_boxes boxes from boxes_dev and n targets from targets_dev
+ * (device, [n][3]) each time it runs, rasterises the occupancy, rebuilds
+ * every edge mask and the forward sets, and writes the same outputs as
+ * ik_reach_path_many (device arrays, fixed at capture).  A target outside
+ * the grid marks an empty slot (found 0, status IK_PATH_UNREACHABLE), so a
+ * fixed-size graph serves a varying number of requests.
+ * ik_batch_capture runs the batch once normally (sizing every buffer), then
+ * records it on the grid's stream, which must not be the legacy default
+ * stream (IK_ERR_STATE).  ik_batch_launch enqueues one replay and returns
+ * without waiting; the outputs are ready when the grid's stream is.  A
+ * replay replaces the grid's occupancy; later ordinary calls on the grid
+ * see it. */
+typedef struct ik_batch_s* ik_batch;
+IK_API int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3],
+                            const int32_t* boxes_dev, int n_boxes, const int32_t* targets_dev, int n,
+                            const ik_path_params* pp, int32_t* reach_dev, int32_t* found_dev,
+                            int32_t* poses_dev, int32_t* relax_dev, int32_t* status_dev,
+                            ik_batch* out);
+IK_API int ik_batch_launch(ik_batch b);
+IK_API int ik_batch_destroy(ik_batch b);
+
 /* ------------------------------------------------------- replan (step a9) */
 /* Validity of n poses under the current occupancy: every joint inside the
  * grid, every offset in its shell, every segment obstacle-free.
@@ -266,6 +289,17 @@ IK_API int ik_profile_read(ik_grid g, double* ms_out, int64_t* launches_out, uin
                            int cap);
 /* Name of kernel class i ("" when out of range). */
 IK_API const char* ik_profile_name(int i);
+
+/* Replans of n live paths at once, with every decision taken on the GPU
+ * (the rules of ik_replan, applied per slot): poses_in [n][n_way][n_seg+1][3]
+ * (every pose starting at root), current [n] (the arm's waypoint per slot;
+ * a value outside [0, n_way) marks an empty slot, whose status is -1).
+ * Outputs poses_out [n][n_way][n_seg+1][3], relax_out [n][n_way][2],
+ * status_out [n].  With on_device != 0 every array is a device pointer (and
+ * the root is not checked against the poses). */
+IK_API int ik_replan_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* poses_in,
+                          const int32_t* current, int n, const ik_path_params* pp,
+                          int32_t* poses_out, int32_t* relax_out, int32_t* status_out, int on_device);
 
 /* ------------------------------------------------------- host utilities */
 /* Shell bounds and offsets of one segment length, as the library builds

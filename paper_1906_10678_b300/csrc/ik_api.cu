@@ -49,6 +49,7 @@ struct ik_grid_s {
   DevBuf F_box, V_box, Vw_box;  // word boxes of every set (min form)
   DevBuf b_root, b_targets, b_reach, b_found, b_poses, b_relax, b_status, b_eps, b_g, b_valid;
   DevBuf b_old;
+  DevBuf b_rp, b_rin, b_rc;  // batched replan: bookkeeping, host-form inputs
   // per-kernel profiling: events recorded on st around each launch
   bool prof_on = false, count_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -59,6 +60,15 @@ struct ik_grid_s {
   };
   std::vector<Rec> recs;
   unsigned long long* d_counters = nullptr;
+  bool capturing = false;  // inside ik_batch_capture: no allocation, no host transfer
+};
+
+struct ik_batch_s {
+  ik_grid g = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int root[3] = {0, 0, 0};
+  std::vector<std::pair<int, int>> key;  // the arm's shells
 };
 
 namespace {
@@ -76,6 +86,14 @@ int fail_cuda(cudaError_t e) {
     return IK_ERR_OOM;
   }
   return IK_ERR_CUDA;
+}
+
+// The occupancy, edge masks and forward sets were rewritten by a replayed
+// graph: forget what the host knew about them.
+void forget_device_state(ik_grid g) {
+  ++g->version;
+  g->f_valid = false;
+  for (auto& kv : g->shells) kv.second->mask_version = ~0ull;
 }
 
 enum ProfId {
@@ -144,6 +162,7 @@ unsigned long long* counters(ik_grid g, int id) {
 int ensure(ik_grid g, DevBuf& b, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return IK_OK;
+  if (g->capturing) return IK_ERR_STATE;  // buffers are sized by the warm-up run
   if (b.p) {
     CK(cudaStreamSynchronize(g->st));
     CK(cudaFree(b.p));
@@ -410,7 +429,8 @@ int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out) {
   g->d.nw = (long)g->d.wx * ny * nz;
   g->tc = make_tile_cfg(g->d);
   g->st = (cudaStream_t)cuda_stream;
-  e = cudaMalloc(&g->d_occ, g->d.nw * 4);
+  e = set_kernel_attributes();
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_occ, g->d.nw * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ, 0, g->d.nw * 4, g->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
   if (e != cudaSuccess) {
@@ -438,7 +458,7 @@ int ik_destroy_grid(ik_grid g) {
     delete s;
   }
   DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->F_box, &g->V_box, &g->Vw_box,
-                    &g->b_root, &g->b_targets,
+                    &g->b_rp, &g->b_rin, &g->b_rc, &g->b_root, &g->b_targets,
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
                     &g->b_g, &g->b_valid, &g->b_old};
   for (DevBuf* b : bufs) cudaFree(b->p);
@@ -604,7 +624,7 @@ int ik_guide(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way,
 // poses are on the device (d_reach [P][S+1][3], d_found nullable).
 static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reach,
                               const int32_t* d_found, int P, int W, int j_lo, int eps2,
-                              int eps2_max) {
+                              int eps2_max, const int32_t* c_arr = nullptr) {
   const Dims& d = g->d;
   const int S = ad.S;
   const long qs = (long)(S + 1) * d.nw;
@@ -622,7 +642,8 @@ static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reac
   {
     ProfScope ps(g, P_GUIDE);
     CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
-                            eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, wb, g->st));
+                            eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, wb, g->st,
+                            c_arr));
   }
   if (j_lo == 0) return backward_sets(g, ad, Vw, P * W, P_BWD_WAY, wb);
   // only waypoints j >= j_lo (P == 1 in that case)
@@ -666,7 +687,8 @@ int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, in
 // Smooth chains for P paths whose waypoint survivor sets are in g->Vw and
 // whose preset poses are in d_poses.
 static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int P, int mode, int c,
-                      const int32_t* d_found, int32_t* d_poses, int32_t* d_relax, int32_t* d_status) {
+                      const int32_t* d_found, int32_t* d_poses, int32_t* d_relax, int32_t* d_status,
+                      const int32_t* c_arr = nullptr) {
   const Dims& d = g->d;
   const int S = ad.S;
   int rc = ensure(g, g->chain, (size_t)P * 2 * (S + 1) * d.nw * 4, true);
@@ -686,6 +708,7 @@ static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int
   a.status = d_status;
   a.scratch = ptr<uint32_t>(g->chain);
   a.relaxed_eps_base = pp->eps2;
+  a.c_arr = c_arr;
   {
     ProfScope ps(g, P_CHAIN);
     CK(launch_smooth_chain(d, ad, a, g->st));
@@ -803,6 +826,134 @@ int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], cons
   return sync(g);
 }
 
+// The whole reach + path pipeline for n slots, enqueued on the grid's stream
+// with no host transfer, allocation or synchronisation (every buffer was
+// sized by a warm-up call): rasterise the boxes, rebuild every edge mask and
+// the forward sets, then reach, waypoint sets and smooth chains.
+static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int, int>>& key,
+                              const int32_t* d_boxes, int n_boxes, const int32_t* d_targets, int n,
+                              const ik_path_params* pp, int32_t* d_reach, int32_t* d_found,
+                              int32_t* d_poses, int32_t* d_relax, int32_t* d_status) {
+  const Dims& d = g->d;
+  const int S = ad.S, W = pp->n_way;
+  const long qs = (long)(S + 1) * d.nw;
+  const size_t pose_bytes = (size_t)12 * (S + 1);
+  int rc;
+  CK(launch_rasterize(d, d_boxes, n_boxes, g->d_occ, g->st));
+  std::vector<std::pair<int, int>> done;
+  for (const auto& k : key) {
+    if (std::find(done.begin(), done.end(), k) != done.end()) continue;
+    done.push_back(k);
+    ShellDev* sh = g->shells[k];
+    CK(launch_edge_masks(d, g->tc, g->d_occ, *sh, sh->d_mask, g->st));
+  }
+  uint32_t* F = ptr<uint32_t>(g->F);
+  int32_t* fb = ptr<int32_t>(g->F_box);
+  CK(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, g->st));
+  CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, fb, 0, g->st));
+  for (int k = 1; k <= S; ++k)
+    CK(launch_propagate(d, g->tc, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ,
+                        F + k * d.nw, 0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, g->st));
+  uint32_t* V = ptr<uint32_t>(g->V);
+  int32_t* vb = ptr<int32_t>(g->V_box);
+  CK(cudaMemsetAsync(vb, kBoxEmptyByte, (size_t)n * (S + 1) * 24, g->st));
+  CK(launch_seed_points(d, d_targets, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr,
+                        vb + 6 * S, 6L * (S + 1), g->st));
+  if ((rc = backward_sets(g, ad, V, n, P_BWD_REACH, vb))) return rc;
+  CK(launch_traceback(d, ad, ptr<int32_t>(g->b_root), V, qs, n, d_reach, d_found, g->st));
+  if ((rc = waypoint_sets_impl(g, ad, d_reach, d_found, n, W, 0, pp->eps2, pp->eps2_max))) return rc;
+  CK(cudaMemcpy2DAsync(d_poses + (long)(W - 1) * 3 * (S + 1), pose_bytes * W, d_reach, pose_bytes,
+                       pose_bytes, n, cudaMemcpyDeviceToDevice, g->st));
+  return chain_impl(g, ad, pp, n, 0, 0, d_found, d_poses, d_relax, d_status);
+}
+
+int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* boxes_dev,
+                     int n_boxes, const int32_t* targets_dev, int n, const ik_path_params* pp,
+                     int32_t* reach_dev, int32_t* found_dev, int32_t* poses_dev, int32_t* relax_dev,
+                     int32_t* status_dev, ik_batch* out) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!out || !root || !point_inside(g->d, root) || n < 1 || !targets_dev || n_boxes < 0 ||
+      (n_boxes > 0 && !boxes_dev) || !reach_dev || !found_dev || !poses_dev || !relax_dev ||
+      !status_dev)
+    return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  if (!g->st) return IK_ERR_STATE;  // the legacy default stream cannot be captured
+  *out = nullptr;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  // warm-up: size every buffer and build every table with one ordinary run
+  if ((rc = ik_set_boxes(g, boxes_dev, n_boxes, 1))) return rc;
+  if ((rc = ik_reach_path_many(g, arm, root, targets_dev, n, pp, reach_dev, found_dev, poses_dev,
+                               relax_dev, status_dev, 1)))
+    return rc;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = to_device(g, g->b_root, root, 12))) return rc;
+  if ((rc = sync(g))) return rc;
+  const bool prof = g->prof_on, cnt = g->count_on;
+  g->prof_on = g->count_on = false;
+  g->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = enqueue_reach_path(g, ad, key, boxes_dev, n_boxes, targets_dev, n, pp, reach_dev, found_dev,
+                            poses_dev, relax_dev, status_dev);
+  } else {
+    rc = fail_cuda(e);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(g->st, &graph);
+  g->capturing = false;
+  g->prof_on = prof;
+  g->count_on = cnt;
+  forget_device_state(g);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e2 != cudaSuccess) return fail_cuda(e2);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail_cuda(e);
+  }
+  ik_batch b = new ik_batch_s();
+  b->g = g;
+  b->graph = graph;
+  b->exec = exec;
+  memcpy(b->root, root, 12);
+  b->key = key;
+  *out = b;
+  return IK_OK;
+}
+
+int ik_batch_launch(ik_batch b) {
+  if (!b) return IK_ERR_ARG;
+  ik_grid g = b->g;
+  int rc = set_device(g);
+  if (rc) return rc;
+  CK(cudaGraphLaunch(b->exec, g->st));
+  // the replay leaves a new occupancy with its edge masks and forward sets:
+  // later calls on this stream may use them as they are
+  forget_device_state(g);
+  for (const auto& k : b->key) g->shells[k]->mask_version = g->version;
+  g->f_valid = true;
+  g->f_version = g->version;
+  g->f_key = b->key;
+  memcpy(g->f_root, b->root, 12);
+  return IK_OK;
+}
+
+int ik_batch_destroy(ik_batch b) {
+  if (!b) return IK_ERR_ARG;
+  cudaSetDevice(b->g->device);
+  cudaStreamSynchronize(b->g->st);
+  cudaGraphExecDestroy(b->exec);
+  cudaGraphDestroy(b->graph);
+  delete b;
+  return IK_OK;
+}
+
 int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, int current_idx,
               const ik_path_params* pp, int32_t* poses_out, int32_t* relax_out, int* status) {
   int rc = set_device(g);
@@ -892,6 +1043,102 @@ int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, 
   if ((rc = sync(g))) return rc;
   *status = st;
   return IK_OK;
+}
+
+// Batched replan for R slots, enqueued with no host synchronisation:
+// validate every pose, decide per slot (live, cut, reach pose to re-solve),
+// re-solve the cut reach poses, then survivor sets of the waypoints after
+// each slot's current index and the forward smooth chains.  All pointers are
+// device pointers; the forward sets of `root` must be current (g->F, b_root).
+static int enqueue_replan(ik_grid g, const ArmDev& ad, const int32_t* d_poses_in, const int32_t* d_c,
+                          int R, const ik_path_params* pp, int32_t* d_poses_out, int32_t* d_relax,
+                          int32_t* d_status) {
+  const Dims& d = g->d;
+  const int S = ad.S, W = pp->n_way;
+  const long ps = 3L * (S + 1), qs = (long)(S + 1) * d.nw;
+  int rc;
+  if ((rc = ensure(g, g->b_rp, (size_t)4 * ((size_t)R * W + 3 * R + 3 * R + R * ps + 2 * R)))) return rc;
+  if ((rc = ensure(g, g->V, (size_t)R * qs * 4))) return rc;
+  if ((rc = ensure(g, g->V_box, (size_t)R * (S + 1) * 24))) return rc;
+  int32_t* valid = ptr<int32_t>(g->b_rp);
+  int32_t* cut = valid + (long)R * W;
+  int32_t* need = cut + R;
+  int32_t* gate = need + R;
+  int32_t* tgt = gate + R;
+  int32_t* reach = tgt + 3L * R;
+  int32_t* rfound = reach + (long)R * ps;
+  uint32_t* V = ptr<uint32_t>(g->V);
+  int32_t* vb = ptr<int32_t>(g->V_box);
+  const uint32_t* F = ptr<uint32_t>(g->F);
+  CK(cudaMemcpyAsync(d_poses_out, d_poses_in, (size_t)R * W * ps * 4, cudaMemcpyDeviceToDevice, g->st));
+  CK(cudaMemsetAsync(d_status, 0xff, (size_t)R * 4, g->st));
+  CK(cudaMemsetAsync(rfound, 0, (size_t)R * 4, g->st));
+  {
+    ProfScope ps_(g, P_VALIDATE);
+    CK(launch_validate(d, ad, g->d_occ, d_poses_in, R * W, valid, g->st));
+  }
+  CK(launch_replan_prepare(R, W, S, d_poses_in, d_c, valid, cut, need, tgt, d_relax, g->st));
+  CK(cudaMemsetAsync(vb, kBoxEmptyByte, (size_t)R * (S + 1) * 24, g->st));
+  CK(launch_seed_points(d, tgt, R, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, need,
+                        vb + 6 * S, 6L * (S + 1), g->st));
+  if ((rc = backward_sets(g, ad, V, R, P_BWD_REACH, vb))) return rc;
+  CK(launch_traceback_nearest_many(d, ad, ptr<int32_t>(g->b_root), V, qs, d_poses_in + (long)(W - 1) * ps,
+                                   (long)W * ps, reach, rfound, need, R, g->st));
+  CK(launch_replan_fix(R, W, S, d_poses_in, cut, need, reach, rfound, gate, g->st));
+  if ((rc = waypoint_sets_impl(g, ad, reach, gate, R, W, 0, pp->eps2, pp->eps2_max, d_c))) return rc;
+  if ((rc = chain_impl(g, ad, pp, R, 1, 0, gate, d_poses_out, d_relax, d_status, d_c))) return rc;
+  CK(launch_replan_finalize(R, W, S, d_c, cut, gate, d_poses_out, d_relax, d_status, g->st));
+  return IK_OK;
+}
+
+int ik_replan_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* poses_in,
+                   const int32_t* current, int n, const ik_path_params* pp, int32_t* poses_out,
+                   int32_t* relax_out, int32_t* status_out, int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!root || !point_inside(g->d, root) || n < 0 ||
+      (n > 0 && (!poses_in || !current || !poses_out || !relax_out || !status_out)))
+    return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  if (n == 0) return IK_OK;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  const int S = ad.S, W = pp->n_way;
+  const size_t path_bytes = (size_t)12 * (S + 1) * W;
+  if (!on_device) {
+    for (int r = 0; r < n; ++r) {
+      if (current[r] < 0 || current[r] >= W) continue;
+      const int32_t* P = poses_in + (size_t)3 * (S + 1) * W * r;
+      for (int j = 0; j < W; ++j)
+        if (P[3 * (S + 1) * j] != root[0] || P[3 * (S + 1) * j + 1] != root[1] ||
+            P[3 * (S + 1) * j + 2] != root[2])
+          return IK_ERR_ARG;
+    }
+  }
+  if ((rc = ensure_forward(g, ad, key, root))) return rc;
+  if ((rc = to_device(g, g->b_root, root, 12))) return rc;
+  const int32_t *dpin = poses_in, *dc = current;
+  int32_t *dpout = poses_out, *drelax = relax_out, *dstatus = status_out;
+  if (!on_device) {
+    if ((rc = to_device(g, g->b_rin, poses_in, path_bytes * n))) return rc;
+    if ((rc = to_device(g, g->b_rc, current, (size_t)4 * n))) return rc;
+    if ((rc = ensure(g, g->b_poses, path_bytes * n))) return rc;
+    if ((rc = ensure(g, g->b_relax, (size_t)8 * W * n))) return rc;
+    if ((rc = ensure(g, g->b_status, (size_t)4 * n))) return rc;
+    dpin = ptr<int32_t>(g->b_rin);
+    dc = ptr<int32_t>(g->b_rc);
+    dpout = ptr<int32_t>(g->b_poses);
+    drelax = ptr<int32_t>(g->b_relax);
+    dstatus = ptr<int32_t>(g->b_status);
+  }
+  if ((rc = enqueue_replan(g, ad, dpin, dc, n, pp, dpout, drelax, dstatus))) return rc;
+  if (!on_device) {
+    if ((rc = copy_out(g, poses_out, dpout, path_bytes * n, 0))) return rc;
+    if ((rc = copy_out(g, relax_out, drelax, (size_t)8 * W * n, 0))) return rc;
+    if ((rc = copy_out(g, status_out, dstatus, (size_t)4 * n, 0))) return rc;
+  }
+  return sync(g);
 }
 
 int ik_profile_enable(ik_grid g, int timing, int counting) {

@@ -149,7 +149,8 @@ cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
-                                 int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st);
+                                 int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st,
+                                 const int32_t* c_arr = nullptr);
 // Smooth chains for P paths (one block each).  mode 0 = plan (backward from
 // the reach pose), mode 1 = forward from pose c (replan).  scratch: per path
 // 2 * (S+1) * nw zeroed words.
@@ -164,9 +165,26 @@ struct ChainArgs {
   int32_t* status;          // [P]
   uint32_t* scratch;
   int relaxed_eps_base;     // eps2 requested (to flag eps growth)
+  const int32_t* c_arr = nullptr;  // replan: per-path current waypoint (else c)
 };
 cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
                                 cudaStream_t st);
+// Opt-in to large dynamic shared memory for the tiled kernels (current device).
+cudaError_t set_kernel_attributes();
+cudaError_t launch_traceback_nearest_many(const Dims& d, const ArmDev& arm, const int32_t* root,
+                                          const uint32_t* V, long vstride, const int32_t* old_pose,
+                                          long old_stride, int32_t* pose, int32_t* found,
+                                          const int32_t* gate, int Q, cudaStream_t st);
+// Batched replan bookkeeping (see ik_kernels.cu).
+cudaError_t launch_replan_prepare(int R, int W, int S, const int32_t* poses_in, const int32_t* c,
+                                  const int32_t* valid, int32_t* cut, int32_t* need, int32_t* tgt,
+                                  int32_t* relax, cudaStream_t st);
+cudaError_t launch_replan_fix(int R, int W, int S, const int32_t* poses_in, const int32_t* cut,
+                              const int32_t* need, int32_t* reach, int32_t* rfound, int32_t* gate,
+                              cudaStream_t st);
+cudaError_t launch_replan_finalize(int R, int W, int S, const int32_t* c, const int32_t* cut,
+                                   const int32_t* gate, int32_t* poses, int32_t* relax,
+                                   int32_t* status, cudaStream_t st);
 cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                             const int32_t* poses, int n, int32_t* valid, cudaStream_t st);
 

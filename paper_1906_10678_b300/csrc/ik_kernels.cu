@@ -173,8 +173,6 @@ cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* 
   if (n == 0) return cudaSuccess;
   const size_t smem = tile_smem_bytes(tc, s.reach);
   if (smem > 0 && s.d_sctab) {
-    cudaFuncSetAttribute((const void*)k_edge_masks_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
     dim3 grid(tc.tiles_y * tc.tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
     k_edge_masks_tile<<<grid, 256, smem, st>>>(d, tc, s.reach, n, occ, s.d_sc_start, s.d_sctab, mask);
     return cudaGetLastError();
@@ -443,9 +441,6 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
   if (Q <= 0) return cudaSuccess;
   const size_t smem = tile_smem_bytes(tc, seg.R);
   if (smem > 0 && seg.tab) {
-    // per device and per function; cheap enough to repeat on every launch
-    cudaFuncSetAttribute(counters ? (const void*)k_propagate_tile<true> : (const void*)k_propagate_tile<false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
     if (counters)
       k_propagate_tile<true><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
@@ -595,16 +590,121 @@ cudaError_t launch_traceback(const Dims& d, const ArmDev& arm, const int32_t* ro
   return cudaGetLastError();
 }
 
+// Batched re-solve of reach poses (replan): block q handles slot q when
+// gate[q] is set, minimising (squared distance to old pose, index).
 __global__ void __launch_bounds__(256) k_traceback_nearest(Dims d, ArmDev arm, const int32_t* root,
-                                                           const uint32_t* V, const int32_t* old_pose,
-                                                           int32_t* pose, int32_t* found) {
-  traceback_block(d, arm, root[0], root[1], root[2], V, old_pose, pose, found);
+                                                           const uint32_t* V, long vs,
+                                                           const int32_t* old_pose, long ops,
+                                                           int32_t* pose, int32_t* found,
+                                                           const int32_t* gate) {
+  const int q = blockIdx.x;
+  if (gate && !gate[q]) return;
+  traceback_block(d, arm, root[0], root[1], root[2], V + q * vs, old_pose + q * ops,
+                  pose + (long)q * 3 * (arm.S + 1), found + q);
 }
 
 cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int32_t* root,
                                      const uint32_t* V, const int32_t* old_pose, int32_t* pose,
                                      int32_t* found, cudaStream_t st) {
-  k_traceback_nearest<<<1, 256, 0, st>>>(d, arm, root, V, old_pose, pose, found);
+  k_traceback_nearest<<<1, 256, 0, st>>>(d, arm, root, V, 0, old_pose, 0, pose, found, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traceback_nearest_many(const Dims& d, const ArmDev& arm, const int32_t* root,
+                                          const uint32_t* V, long vstride, const int32_t* old_pose,
+                                          long old_stride, int32_t* pose, int32_t* found,
+                                          const int32_t* gate, int Q, cudaStream_t st) {
+  if (Q <= 0) return cudaSuccess;
+  k_traceback_nearest<<<Q, 256, 0, st>>>(d, arm, root, V, vstride, old_pose, old_stride, pose, found,
+                                          gate);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------- a9: batched replan
+
+// Per slot r (c[r] in [0, W) marks a live slot): cut = some pose after c is
+// invalid now; need = cut and the reach pose itself is invalid (re-solve it
+// from its end effector, tgt[r]); the slot's relaxation record is zeroed.
+__global__ void k_replan_prepare(int W, int S, const int32_t* __restrict__ poses_in,
+                                 const int32_t* __restrict__ c, const int32_t* __restrict__ valid,
+                                 int32_t* cut, int32_t* need, int32_t* tgt, int32_t* relax) {
+  const int r = blockIdx.x;
+  const int cr = c[r];
+  const bool live = cr >= 0 && cr < W;
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) relax[(long)r * 2 * W + i] = 0;
+  if (threadIdx.x != 0) return;
+  int k = 0;
+  if (live)
+    for (int j = cr + 1; j < W; ++j)
+      if (!valid[(long)r * W + j]) k = 1;
+  const int n = k && !valid[(long)r * W + W - 1];
+  cut[r] = k;
+  need[r] = n;
+  const int32_t* end = poses_in + (((long)r * W + W - 1) * (S + 1) + S) * 3;
+  tgt[3 * r] = n ? end[0] : -1;
+  tgt[3 * r + 1] = n ? end[1] : -1;
+  tgt[3 * r + 2] = n ? end[2] : -1;
+}
+
+// Cut slots whose reach pose is still valid keep it; gate = cut and a reach
+// pose exists (re-solved or kept).
+__global__ void k_replan_fix(int W, int S, const int32_t* __restrict__ poses_in,
+                             const int32_t* __restrict__ cut, const int32_t* __restrict__ need,
+                             int32_t* reach, int32_t* rfound, int32_t* gate) {
+  const int r = blockIdx.x;
+  const long ps = 3L * (S + 1);
+  if (cut[r] && !need[r]) {
+    for (int i = threadIdx.x; i < ps; i += blockDim.x)
+      reach[r * ps + i] = poses_in[((long)r * W + W - 1) * ps + i];
+    if (threadIdx.x == 0) rfound[r] = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) gate[r] = cut[r] && (need[r] ? rfound[r] : 1);
+}
+
+// Statuses of the slots the smooth chain does not run: live and uncut =
+// kept (poses already copied); cut without a reach pose = unreachable, the
+// poses after c repeat pose c with m = -1.
+__global__ void k_replan_finalize(int W, int S, const int32_t* __restrict__ c,
+                                  const int32_t* __restrict__ cut, const int32_t* __restrict__ gate,
+                                  int32_t* poses, int32_t* relax, int32_t* status) {
+  const int r = blockIdx.x;
+  const int cr = c[r];
+  if (cr < 0 || cr >= W || gate[r]) return;
+  const long ps = 3L * (S + 1);
+  if (!cut[r]) {
+    if (threadIdx.x == 0) status[r] = IK_PATH_KEPT;
+    return;
+  }
+  for (int j = cr + 1; j < W; ++j) {
+    for (int i = threadIdx.x; i < ps; i += blockDim.x)
+      poses[((long)r * W + j) * ps + i] = poses[((long)r * W + cr) * ps + i];
+    if (threadIdx.x == 0) relax[((long)r * W + j) * 2] = -1;
+  }
+  if (threadIdx.x == 0) status[r] = IK_PATH_UNREACHABLE;
+}
+
+cudaError_t launch_replan_prepare(int R, int W, int S, const int32_t* poses_in, const int32_t* c,
+                                  const int32_t* valid, int32_t* cut, int32_t* need, int32_t* tgt,
+                                  int32_t* relax, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  k_replan_prepare<<<R, 64, 0, st>>>(W, S, poses_in, c, valid, cut, need, tgt, relax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replan_fix(int R, int W, int S, const int32_t* poses_in, const int32_t* cut,
+                              const int32_t* need, int32_t* reach, int32_t* rfound, int32_t* gate,
+                              cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  k_replan_fix<<<R, 64, 0, st>>>(W, S, poses_in, cut, need, reach, rfound, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replan_finalize(int R, int W, int S, const int32_t* c, const int32_t* cut,
+                                   const int32_t* gate, int32_t* poses, int32_t* relax,
+                                   int32_t* status, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  k_replan_finalize<<<R, 64, 0, st>>>(W, S, c, cut, gate, poses, relax, status);
   return cudaGetLastError();
 }
 
@@ -696,9 +796,10 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
                                 const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
                                 const int32_t* __restrict__ found, int W, int j_lo, int eps2,
                                 int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw,
-                                int32_t* wbox) {
+                                int32_t* wbox, const int32_t* __restrict__ c_arr) {
   const int p = blockIdx.y;
   const int j = blockIdx.x + j_lo;
+  if (c_arr && j <= c_arr[p]) return;  // replan: waypoints up to the current one stay
   const int S = arm.S;
   const int32_t* R = reach + (long)p * 3 * (S + 1);
   __shared__ int gp[3];
@@ -791,11 +892,12 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
-                                 int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st) {
+                                 int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st,
+                                 const int32_t* c_arr) {
   if (P <= 0 || W - j_lo <= 0) return cudaSuccess;
   dim3 grid(W - j_lo, P);
   k_guide_targets<<<grid, 128, 0, st>>>(d, arm, occ, F_S, reach, found, W, j_lo, eps2, eps2_max, g,
-                                        eps_used, Vw, wbox);
+                                        eps_used, Vw, wbox, c_arr);
   return cudaGetLastError();
 }
 
@@ -1068,24 +1170,26 @@ __global__ void __launch_bounds__(kChainThreads) k_smooth_chain(Dims d, ArmDev a
   uint32_t* U = R + (long)(S + 1) * d.nw;
   const long D2 = (long)(d.nx - 1) * (d.nx - 1) + (long)(d.ny - 1) * (d.ny - 1) +
                   (long)(d.nz - 1) * (d.nz - 1);
+  const int cur = a.c_arr ? a.c_arr[p] : a.c;
   if (a.found && !a.found[p]) {
+    if (a.mode == 1) return;  // replan slots without work are finished elsewhere
     for (long i = threadIdx.x; i < W * pose_sz; i += blockDim.x) poses[i] = 0;
     for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) relax[i] = -1;
     if (threadIdx.x == 0) a.status[p] = IK_PATH_UNREACHABLE;
     return;
   }
   bool relaxed = false, broken = false;
-  const int n_steps = a.mode == 0 ? W - 1 : W - 1 - a.c;
+  const int n_steps = a.mode == 0 ? W - 1 : W - 1 - cur;
   if (threadIdx.x == 0) {
     if (a.mode == 0) {
       relax[2 * (W - 1)] = 0;
       relax[2 * (W - 1) + 1] = 0;
     } else {
-      for (int j = 0; j <= a.c; ++j) relax[2 * j] = relax[2 * j + 1] = 0;
+      for (int j = 0; j <= cur; ++j) relax[2 * j] = relax[2 * j + 1] = 0;
     }
   }
   for (int s = 0; s < n_steps; ++s) {
-    const int j = a.mode == 0 ? W - 2 - s : a.c + 1 + s;
+    const int j = a.mode == 0 ? W - 2 - s : cur + 1 + s;
     const int rj = a.mode == 0 ? j + 1 : j - 1;
     const uint32_t* V = a.Vw + ((long)p * W + j) * (S + 1) * d.nw;
     int32_t* pose = poses + (long)j * pose_sz;
@@ -1159,6 +1263,21 @@ __global__ void __launch_bounds__(kChainThreads) k_smooth_chain(Dims d, ArmDev a
   }
   if (threadIdx.x == 0)
     a.status[p] = broken ? IK_PATH_BROKEN : (relaxed ? IK_PATH_RELAXED : IK_PATH_OK);
+}
+
+cudaError_t set_kernel_attributes() {
+  // opt in to large dynamic shared memory for the tiled kernels (per device;
+  // called when a grid is created, never during stream capture)
+  const int bytes = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_edge_masks_tile,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,

@@ -74,6 +74,13 @@ _sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
 _sig("ik_validate_poses", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_replan", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, ctypes.POINTER(IkPathParams), _vp,
                        _vp, ctypes.POINTER(_i)])
+_sig("ik_replan_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _vp, _i,
+                            ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _i])
+_sig("ik_batch_capture", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _i,
+                              ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp,
+                              ctypes.POINTER(_vp)])
+_sig("ik_batch_launch", _i, [_vp])
+_sig("ik_batch_destroy", _i, [_vp])
 _sig("ik_forward_sets_noalloc", _i, [_vp, _i, _i, _i, ctypes.POINTER(IkArm), _vp, _vp, _vp])
 _sig("ik_profile_enable", _i, [_vp, _i, _i])
 _sig("ik_profile_read", _i, [_vp, _vp, _vp, _vp, _i])
@@ -85,7 +92,8 @@ EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
-    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_forward_sets_noalloc",
+    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many", "ik_batch_capture",
+    "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
 ]
@@ -309,6 +317,32 @@ def ik_reach_path_many_device(g: int, arm, root, targets, n_way: int, reach, fou
                                    _dev_ptr(status), 1), "ik_reach_path_many")
 
 
+class Batch:
+    """A captured reach + path batch (``ik_batch_capture``); all arrays are
+    contiguous int32 CUDA tensors that stay alive with the batch."""
+
+    def __init__(self, g: int, arm, root, boxes, targets, n_way: int, reach, found, poses, relax,
+                 status, delta: int = 3, eps2: int = 2, eps2_max: int = 8, max_relax: int = -1):
+        self.arm = _arm(arm)
+        self.pp = path_params(n_way, delta, eps2, eps2_max, max_relax)
+        self.keep = (boxes, targets, reach, found, poses, relax, status)
+        h = _vp()
+        _check(_lib.ik_batch_capture(g, ctypes.byref(self.arm.c), _np_ptr(_i32(root)),
+                                     _dev_ptr(boxes), boxes.shape[0], _dev_ptr(targets),
+                                     targets.shape[0], ctypes.byref(self.pp), _dev_ptr(reach),
+                                     _dev_ptr(found), _dev_ptr(poses), _dev_ptr(relax),
+                                     _dev_ptr(status), ctypes.byref(h)), "ik_batch_capture")
+        self.h = h.value
+
+    def launch(self) -> None:
+        _check(_lib.ik_batch_launch(self.h), "ik_batch_launch")
+
+    def close(self) -> None:
+        if self.h:
+            _check(_lib.ik_batch_destroy(self.h), "ik_batch_destroy")
+            self.h = 0
+
+
 def ik_validate_poses(g: int, arm, poses) -> np.ndarray:
     arm = _arm(arm)
     p = _i32(poses).reshape(-1, arm.S + 1, 3)
@@ -369,6 +403,35 @@ def ik_profile_read(g: int) -> dict:
 
 def ik_profile_name(i: int) -> str:
     return _lib.ik_profile_name(i).decode()
+
+
+def ik_replan_many(g: int, arm, root, poses, current, delta: int = 3, eps2: int = 2,
+                   eps2_max: int = 8, max_relax: int = -1):
+    """Host form.  poses [n][W][S+1][3], current [n] (-1 = empty slot).
+    Returns (poses, relax [n][W][2], status [n])."""
+    arm = _arm(arm)
+    p = _i32(poses)
+    n, W = p.shape[0], p.shape[1]
+    pp = path_params(W, delta, eps2, eps2_max, max_relax)
+    out = np.zeros_like(p)
+    relax = np.zeros((n, W, 2), np.int32)
+    status = np.zeros(n, np.int32)
+    _check(_lib.ik_replan_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _np_ptr(p),
+                               _np_ptr(_i32(current)), n, ctypes.byref(pp), _np_ptr(out),
+                               _np_ptr(relax), _np_ptr(status), 0), "ik_replan_many")
+    return out, relax, status
+
+
+def ik_replan_many_device(g: int, arm, root, poses, current, poses_out, relax_out, status_out,
+                          delta: int = 3, eps2: int = 2, eps2_max: int = 8,
+                          max_relax: int = -1) -> None:
+    """Device form: every array is a contiguous int32 CUDA tensor."""
+    arm = _arm(arm)
+    pp = path_params(poses.shape[1], delta, eps2, eps2_max, max_relax)
+    _check(_lib.ik_replan_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _dev_ptr(poses),
+                               _dev_ptr(current), poses.shape[0], ctypes.byref(pp),
+                               _dev_ptr(poses_out), _dev_ptr(relax_out), _dev_ptr(status_out), 1),
+           "ik_replan_many")
 
 
 def ik_shell_offsets(length: int, tol: float = 0.5) -> Tuple[Tuple[int, int], np.ndarray]:
