@@ -355,6 +355,31 @@ def run_ours(args):
     rep_status = np.asarray(rep_status)
     cut = rep_status != ik.IK_PATH_KEPT
 
+    # served form: continuous batching with moving obstacles on the same
+    # scene, Poisson arrivals (half reach+path, half replans of live paths)
+    served = None
+    if args.serve_seconds > 0:
+        from paper_1906_10678_b300 import serve as SV
+        g.close()
+        srv = SV.Server(sc.shape, sc.root, sc.lengths, sc.boxes, G.make_moving_boxes(sc.shape, 16, 3),
+                        n_way=N_WAY, delta=DELTA, tick_s=3.0 / 36.0, slots_path=32, slots_replan=32)
+        reqs = SV.make_requests(sc, 200.0, args.serve_seconds + args.serve_warmup, 3)
+        srv.serve(reqs, args.serve_seconds + args.serve_warmup, realtime=True)
+        keep = [r for r in srv.finished if r.arrival >= args.serve_warmup and r.poses is not None]
+        tick = np.asarray(srv.tick_ms)
+        served = {
+            "seconds": args.serve_seconds, "warmup_s": args.serve_warmup, "rate_hz": 200.0,
+            "tick_ms": 1000.0 * srv.tick_s, "ticks": int(len(tick)),
+            "tick_gpu_ms_p50": round(float(np.percentile(tick, 50)), 3),
+            "tick_gpu_ms_p99": round(float(np.percentile(tick, 99)), 3),
+            "path": SV.latency_stats([r for r in keep if r.kind == "path"]),
+            "replan": SV.latency_stats([r for r in keep if r.kind == "replan"]),
+            "path_solves_per_s": round(len([r for r in keep if r.kind == "path"]) / args.serve_seconds, 2),
+            "pending_at_end": len(srv.pending),
+            "note": "latency = completion - arrival on the wall clock, incl. waiting for a tick"}
+        srv.close()
+        g = None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -377,6 +402,7 @@ def run_ours(args):
                        "requests": int(len(rep_ms)), "cut": int(cut.sum()),
                        "status_counts": {str(k): int((rep_status == k).sum()) for k in range(5)},
                        "note": "host wall time per ik_replan call (C ABI, host buffers)"},
+            "served": served,
             "found": int(found_np.sum()),
             "path_status_counts": {str(k): int((status_np == k).sum()) for k in range(5)},
             "max_relax": int(relax_np[..., 0].max()),
@@ -392,7 +418,8 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
-    g.close()
+    if g is not None:
+        g.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -410,6 +437,8 @@ def main():
                     help="grid edge; 128 is the benchmark workload, smaller only for captures")
     ap.add_argument("--targets", type=int, default=64)
     ap.add_argument("--replan-ticks", type=int, default=3)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-warmup", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
