@@ -311,6 +311,27 @@ def run_ours(args):
     h2d = sc.boxes.nbytes + targets_np.nbytes
     d2h = sum(x.nbytes for x in out)
 
+    # the same batch on a grid that keeps no edge masks (segment tests walk
+    # supercovers on the fly): identical results, different cost profile
+    nomask_ms = None
+    if not args.no_extras:
+        with ik.Grid(*sc.shape, stream=stream.cuda_stream) as g2:
+            ik.ik_set_option(g2.h, ik.IK_OPT_EDGE_MASKS, 0)
+            def step2():
+                ik.ik_set_boxes(g2.h, boxes_d)
+                ik.ik_reach_path_many_device(g2.h, arm, sc.root, targets_d, N_WAY, reach, found,
+                                             poses, relax, status, delta=DELTA)
+            step2()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                step2()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nomask_ms = e0.elapsed_time(e1) / 2
+
     # per-kernel times: one more step with the library's event profiler on
     # (events recorded on the grid's stream around each launch), then one
     # with its work counters on (slower; counts only)
@@ -403,6 +424,9 @@ def run_ours(args):
                        "status_counts": {str(k): int((rep_status == k).sum()) for k in range(5)},
                        "note": "host wall time per ik_replan call (C ABI, host buffers)"},
             "served": served,
+            "no_edge_masks": {"ms_per_step": round(nomask_ms, 3) if nomask_ms else None,
+                              "value": round(N_TARGETS / (nomask_ms / 1000.0), 3) if nomask_ms else None,
+                              "note": "same batch, supercovers walked on the fly (IK_OPT_EDGE_MASKS 0)"},
             "found": int(found_np.sum()),
             "path_status_counts": {str(k): int((status_np == k).sum()) for k in range(5)},
             "max_relax": int(relax_np[..., 0].max()),

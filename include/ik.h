@@ -116,6 +116,15 @@ IK_API const char* ik_last_error_message(void);
  * legacy default stream).  The occupancy starts all free. */
 IK_API int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out);
 IK_API int ik_destroy_grid(ik_grid g);
+/* Grid options.  IK_OPT_EDGE_MASKS (default 1): keep one edge mask per shell
+ * offset and word (the segment test becomes one 4-byte read; 4.9 GiB for the
+ * 128^3 grid and the arm {20,18,...,6}; rebuilt when the occupancy changes).
+ * With 0 every segment test walks the offset's supercover against the
+ * occupancy instead: no mask memory and no rebuild, slower tests -- the
+ * better choice for grids solved once or changing often.  Results are
+ * identical either way. */
+#define IK_OPT_EDGE_MASKS 1
+IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);
 

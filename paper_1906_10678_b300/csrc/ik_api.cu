@@ -61,6 +61,7 @@ struct ik_grid_s {
   std::vector<Rec> recs;
   unsigned long long* d_counters = nullptr;
   bool capturing = false;  // inside ik_batch_capture: no allocation, no host transfer
+  bool use_masks = true;   // store per-offset edge masks (else walk supercovers on the fly)
 };
 
 struct ik_batch_s {
@@ -293,8 +294,10 @@ int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<
     ShellDev* s = nullptr;
     rc = get_shell(g, lo2, hi2, &s);
     if (rc) return rc;
-    rc = ensure_masks(g, s);
-    if (rc) return rc;
+    if (g->use_masks) {
+      rc = ensure_masks(g, s);
+      if (rc) return rc;
+    }
     SegDev& sd = ad->seg[k];
     sd.off = s->d_off;
     sd.rows = s->d_rows;
@@ -302,7 +305,8 @@ int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<
     sd.sctab = s->d_sctab;
     sd.sc_start = s->d_sc_start;
     sd.sc = s->d_sc;
-    sd.mask = s->d_mask;
+    sd.mask = g->use_masks ? s->d_mask : nullptr;
+    sd.occ = g->d_occ;
     sd.n = (int)s->host.off.size();
     sd.lo2 = lo2;
     sd.hi2 = hi2;
@@ -842,6 +846,7 @@ static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std
   CK(launch_rasterize(d, d_boxes, n_boxes, g->d_occ, g->st));
   std::vector<std::pair<int, int>> done;
   for (const auto& k : key) {
+    if (!g->use_masks) break;
     if (std::find(done.begin(), done.end(), k) != done.end()) continue;
     done.push_back(k);
     ShellDev* sh = g->shells[k];
@@ -936,7 +941,8 @@ int ik_batch_launch(ik_batch b) {
   // the replay leaves a new occupancy with its edge masks and forward sets:
   // later calls on this stream may use them as they are
   forget_device_state(g);
-  for (const auto& k : b->key) g->shells[k]->mask_version = g->version;
+  if (g->use_masks)
+    for (const auto& k : b->key) g->shells[k]->mask_version = g->version;
   g->f_valid = true;
   g->f_version = g->version;
   g->f_key = b->key;
@@ -1139,6 +1145,22 @@ int ik_replan_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const in
     if ((rc = copy_out(g, status_out, dstatus, (size_t)4 * n, 0))) return rc;
   }
   return sync(g);
+}
+
+int ik_set_option(ik_grid g, int option, int value) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (option != IK_OPT_EDGE_MASKS) return IK_ERR_ARG;
+  if ((rc = sync(g))) return rc;
+  g->use_masks = value != 0;
+  if (!g->use_masks) {
+    for (auto& kv : g->shells) {
+      cudaFree(kv.second->d_mask);
+      kv.second->d_mask = nullptr;
+      kv.second->mask_version = ~0ull;
+    }
+  }
+  return IK_OK;
 }
 
 int ik_profile_enable(ik_grid g, int timing, int counting) {

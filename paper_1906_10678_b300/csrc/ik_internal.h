@@ -53,12 +53,14 @@ struct SegDev {
   const int32_t* rows;     // [(2R+1)^2 + 1] row starts, see ShellHost
   const int32_t* sc_start; // [n + 1]
   const int32_t* sc;       // packed supercover voxels
-  const uint32_t* mask;    // [n][nw] edge masks: bit of voxel p in row e = segment p -> p + off[e] free
+  const uint32_t* mask;    // [n][nw] edge masks: bit of voxel p in row e = segment p -> p + off[e]
+                           // free; nullptr: each test walks the supercover against occ
   int n;
   int lo2, hi2;
   int R;                   // max |component| of an offset
   const int32_t* tab;      // [n] shared-memory deltas for the tiled kernel, see TileCfg
   const int32_t* sctab;    // [sc_start[n]] shared-memory deltas of the supercover voxels
+  const uint32_t* occ;     // the grid's occupancy, for segment tests without stored masks
 };
 
 // Output tiling of the shared-memory propagation kernel: a block of 8 warps

@@ -47,6 +47,28 @@ __device__ __forceinline__ bool test_bit(const uint32_t* s, long i) {
   return (__ldg(s + (i >> 5)) >> (i & 31)) & 1u;
 }
 
+// Free bits of the segments from the 32 voxels of word (wx, y, z) along
+// offset e of the shell: the stored edge-mask word when the grid keeps edge
+// masks, else the supercover of e walked against the occupancy.
+__device__ __forceinline__ uint32_t edge_word(const Dims& d, const SegDev& sg, int e, long w, int wx,
+                                              int y, int z) {
+  if (sg.mask) return __ldg(sg.mask + (long)e * d.nw + w);
+  const int s1 = __ldg(sg.sc_start + e + 1);
+  uint32_t blocked = 0;
+  for (int i = __ldg(sg.sc_start + e); i < s1 && blocked != 0xffffffffu; ++i) {
+    const int32_t v = __ldg(sg.sc + i);
+    blocked |= ld_shifted(sg.occ, d, wx, y, z, unpack_x(v), unpack_y(v), unpack_z(v));
+  }
+  return ~blocked;
+}
+
+// The segment from voxel p (linear index pi) along offset e: free?
+__device__ __forceinline__ bool edge_bit(const Dims& d, const SegDev& sg, int e, long pi) {
+  const long w = pi >> 5;
+  const int wx = (int)(w % d.wx), y = (int)((w / d.wx) % d.ny), z = (int)(w / ((long)d.wx * d.ny));
+  return (edge_word(d, sg, e, w, wx, y, z) >> (pi & 31)) & 1u;
+}
+
 static inline int grid_for(long n, int block) { return (int)((n + block - 1) / block); }
 
 // ------------------------------------------------------- a1: rasterise boxes
@@ -253,7 +275,6 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
     const int ez0 = max(bz0 - zhi, -R), ez1 = min(bz1 - zlo, R);
     const int ey0 = max(by0 - yhi, -R), ey1 = min(by1 - ylo, R);
     const int exlo = 32 * (bx0 - wx) - 31, exhi = 32 * (bx1 - wx) + 31;
-    const uint32_t* M = seg.mask + w;
     bool live = m != 0;
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
       const int sz = z + ez;
@@ -274,7 +295,7 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
           }
           if (x & m & ~acc) {
             if (kCount) ++mloads;
-            acc |= x & __ldg(M + (long)e * d.nw);
+            acc |= x & edge_word(d, seg, e, w, wx, y, z);
           }
         }
       }
@@ -363,7 +384,6 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
     const int ey0 = max(by0 - ylast, -R), ey1 = min(by1 - y0, R);
     // lanes without a word read a harmless in-range spot
     const int base = valid ? ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1) : (R * RY + R) * P + 1;
-    const uint32_t* M = seg.mask + w;
     bool live = m != 0;
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
       const int32_t* rowp = seg.rows + (ez + R) * side + R;
@@ -395,7 +415,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
         if (any & want) {
           uint32_t mv[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) mv[i] = (xv[i] & want) ? __ldg(M + (long)(e + i) * d.nw) : 0u;
+          for (int i = 0; i < 8; ++i) mv[i] = (xv[i] & want) ? edge_word(d, seg, e + i, w, wx, y, z) : 0u;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             if (kCount) mloads += (xv[i] & want) != 0;
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
         }
         if (x & m & ~acc) {
           if (kCount) ++mloads;
-          acc |= x & __ldg(M + (long)e * d.nw);
+          acc |= x & edge_word(d, seg, e, w, wx, y, z);
         }
       }
       live = live && (acc & m) != m;
@@ -543,8 +563,6 @@ __device__ void traceback_block(const Dims& d, const ArmDev& arm, int rx, int ry
     const uint32_t* Vk = V + (long)k * d.nw;
     const int px = p[0], py = p[1], pz = p[2];
     const long pi = lin(d, px, py, pz);
-    const uint32_t* M = sg.mask + (pi >> 5);
-    const int pb = (int)(pi & 31);
     if (threadIdx.x == 0) best = ~0ull;
     __syncthreads();
     for (int e = threadIdx.x; e < sg.n; e += blockDim.x) {
@@ -553,7 +571,7 @@ __device__ void traceback_block(const Dims& d, const ArmDev& arm, int rx, int ry
       if (!inside(d, qx, qy, qz)) continue;
       const long qi = lin(d, qx, qy, qz);
       if (!test_bit(Vk, qi)) continue;
-      if (!((__ldg(M + (long)e * d.nw) >> pb) & 1u)) continue;
+      if (!edge_bit(d, sg, e, pi)) continue;
       unsigned long long key = (unsigned long long)qi;
       if (nearest) {
         const long dx = qx - nearest[3 * k], dy = qy - nearest[3 * k + 1], dz = qz - nearest[3 * k + 2];
@@ -1015,7 +1033,7 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
         const int ex = unpack_x(o);
         if (ex < exlo || ex > exhi) continue;
         const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ex, unpack_y(o), ez);
-        if (x & m & ~acc) acc |= x & __ldg(sg.mask + (long)e * d.nw + w);
+        if (x & m & ~acc) acc |= x & edge_word(d, sg, e, w, wx, y, z);
       }
     }
   }
@@ -1121,8 +1139,6 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
     const uint32_t* Xk = X + (long)k * d.nw;
     const int px = sh.cur[0], py = sh.cur[1], pz = sh.cur[2];
     const long pi = lin(d, px, py, pz);
-    const uint32_t* M = sg.mask + (pi >> 5);
-    const int pb = (int)(pi & 31);
     if (threadIdx.x == 0) sh.best = ~0ull;
     __syncthreads();
     for (int e = threadIdx.x; e < sg.n; e += blockDim.x) {
@@ -1132,7 +1148,7 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
       const long qi = lin(d, qx, qy, qz);
       const uint32_t word = kCoherent ? Xk[qi >> 5] : __ldg(Xk + (qi >> 5));
       if (!((word >> (qi & 31)) & 1u)) continue;
-      if (!((__ldg(M + (long)e * d.nw) >> pb) & 1u)) continue;
+      if (!edge_bit(d, sg, e, pi)) continue;
       atomicMin(&sh.best, (unsigned long long)qi);
     }
     __syncthreads();

@@ -29,6 +29,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 IK_OK, IK_ERR_ARG, IK_ERR_OOM, IK_ERR_CUDA, IK_ERR_TIMEOUT, IK_ERR_STATE, IK_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
 IK_PATH_OK, IK_PATH_RELAXED, IK_PATH_BROKEN, IK_PATH_UNREACHABLE, IK_PATH_KEPT = range(5)
+IK_OPT_EDGE_MASKS = 1
 IK_MAX_SEG = 16
 IK_MAX_LEN = 100
 
@@ -59,6 +60,7 @@ _sig("ik_last_error_message", ctypes.c_char_p, [])
 _sig("ik_create_grid", _i, [_i, _i, _i, _vp, ctypes.POINTER(_vp)])
 _sig("ik_destroy_grid", _i, [_vp])
 _sig("ik_grid_words", ctypes.c_size_t, [_vp])
+_sig("ik_set_option", _i, [_vp, _i, _i])
 _sig("ik_set_obstacles", _i, [_vp, _vp, ctypes.c_size_t, _i])
 _sig("ik_set_boxes", _i, [_vp, _vp, _i, _i])
 _sig("ik_get_obstacles", _i, [_vp, _vp, ctypes.c_size_t, _i])
@@ -90,7 +92,7 @@ _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 
 EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
-    "ik_grid_words", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
+    "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
     "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
@@ -187,6 +189,10 @@ def ik_destroy_grid(g: int) -> None:
 
 def ik_grid_words(g: int) -> int:
     return int(_lib.ik_grid_words(g))
+
+
+def ik_set_option(g: int, option: int, value: int) -> None:
+    _check(_lib.ik_set_option(g, option, int(value)), "ik_set_option")
 
 
 def ik_set_boxes(g: int, boxes) -> None:
