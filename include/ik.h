@@ -234,6 +234,48 @@ IK_API int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3],
 IK_API int ik_batch_launch(ik_batch b);
 IK_API int ik_batch_destroy(ik_batch b);
 
+/* ------------------------------------------------- uneven batch (a10) */
+/* One independent reach + path problem of an uneven batch: its own grid
+ * (extents as in ik_create_grid), boxes (host, [n_boxes][6], inclusive),
+ * arm, root, target and waypoint count. */
+typedef struct {
+  int32_t nx, ny, nz;
+  const int32_t* boxes;
+  int32_t n_boxes;
+  int32_t n_seg;
+  const int32_t* len;
+  float tol;
+  int32_t root[3];
+  int32_t target[3];
+  int32_t n_way;
+} ik_problem;
+
+/* Path rules shared by the batch (as in ik_path_params), and lanes: how many
+ * problems run concurrently (0: 16). */
+typedef struct {
+  int32_t delta, eps2, eps2_max, max_relax;
+  int32_t lanes;
+} ik_batch_params;
+
+/* Sizes (int32 counts) of the packed outputs of ik_solve_batch. */
+IK_API int ik_batch_output_sizes(const ik_problem* probs, int n, size_t* reach_ints,
+                                 size_t* poses_ints, size_t* relax_ints);
+
+/* Solve n uneven problems together (uses the current CUDA device; allocates
+ * and frees its own memory).  Every problem follows exactly the rules of
+ * ik_solve_reach + ik_plan_path on its own grid (segment tests walk the
+ * supercover; no edge masks).  The problems are spread over lanes (a stream
+ * and buffers sized for the largest problem each), and the whole batch is
+ * recorded as one CUDA graph and launched once.  Outputs are packed in
+ * problem order: found_out [n], status_out [n] (IK_PATH_UNREACHABLE when no
+ * reach pose), reach_out [(n_seg+1)*3 per problem], poses_out
+ * [n_way*(n_seg+1)*3 per problem], relax_out [n_way*2 per problem] (sizes
+ * from ik_batch_output_sizes).  gpu_ms_out (nullable) receives the graph's
+ * device time. */
+IK_API int ik_solve_batch(const ik_problem* probs, int n, const ik_batch_params* bp,
+                          int32_t* found_out, int32_t* reach_out, int32_t* poses_out,
+                          int32_t* relax_out, int32_t* status_out, double* gpu_ms_out);
+
 /* ------------------------------------------------------- replan (step a9) */
 /* Validity of n poses under the current occupancy: every joint inside the
  * grid, every offset in its shell, every segment obstacle-free.

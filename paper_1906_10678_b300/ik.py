@@ -47,6 +47,19 @@ class IkPathParams(ctypes.Structure):
                 ("eps2_max", ctypes.c_int32), ("max_relax", ctypes.c_int32)]
 
 
+class IkProblem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("boxes", ctypes.POINTER(ctypes.c_int32)), ("n_boxes", ctypes.c_int32),
+                ("n_seg", ctypes.c_int32), ("len", ctypes.POINTER(ctypes.c_int32)),
+                ("tol", ctypes.c_float), ("root", ctypes.c_int32 * 3),
+                ("target", ctypes.c_int32 * 3), ("n_way", ctypes.c_int32)]
+
+
+class IkBatchParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_int32), ("eps2", ctypes.c_int32), ("eps2_max", ctypes.c_int32),
+                ("max_relax", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+
+
 def _sig(name, res, args):
     f = getattr(_lib, name)
     f.restype = res
@@ -78,6 +91,8 @@ _sig("ik_replan", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, ctypes.POINTER(I
                        _vp, ctypes.POINTER(_i)])
 _sig("ik_replan_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _vp, _i,
                             ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _i])
+_sig("ik_batch_output_sizes", _i, [_vp, _i, _vp, _vp, _vp])
+_sig("ik_solve_batch", _i, [_vp, _i, ctypes.POINTER(IkBatchParams), _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("ik_batch_capture", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _i,
                               ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(_vp)])
@@ -94,7 +109,8 @@ EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
-    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many", "ik_batch_capture",
+    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many",
+    "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
@@ -347,6 +363,53 @@ class Batch:
         if self.h:
             _check(_lib.ik_batch_destroy(self.h), "ik_batch_destroy")
             self.h = 0
+
+
+def ik_solve_batch(problems, delta: int = 3, eps2: int = 2, eps2_max: int = 8, max_relax: int = -1,
+                   lanes: int = 0):
+    """problems: list of dicts with shape (nx, ny, nz), boxes [n][6], lengths,
+    root, target, n_way (tol 0.5).  Returns (list of per-problem dicts with
+    found, reach, poses, relax, status; device ms of the batch graph)."""
+    n = len(problems)
+    keep = []
+    arr = (IkProblem * max(n, 1))()
+    for i, p in enumerate(problems):
+        b = _i32(p["boxes"]).reshape(-1, 6)
+        L = _i32(p["lengths"])
+        keep += [b, L]
+        arr[i].nx, arr[i].ny, arr[i].nz = (int(v) for v in p["shape"])
+        arr[i].boxes = b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        arr[i].n_boxes = len(b)
+        arr[i].n_seg = len(L)
+        arr[i].len = L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        arr[i].tol = 0.5
+        arr[i].root[:] = [int(v) for v in p["root"]]
+        arr[i].target[:] = [int(v) for v in p["target"]]
+        arr[i].n_way = int(p["n_way"])
+    sizes = [ctypes.c_size_t() for _ in range(3)]
+    _check(_lib.ik_batch_output_sizes(ctypes.cast(arr, _vp), n, *(ctypes.byref(x) for x in sizes)),
+           "ik_batch_output_sizes")
+    found = np.zeros(n, np.int32)
+    status = np.zeros(n, np.int32)
+    reach = np.zeros(max(sizes[0].value, 1), np.int32)
+    poses = np.zeros(max(sizes[1].value, 1), np.int32)
+    relax = np.zeros(max(sizes[2].value, 1), np.int32)
+    ms = ctypes.c_double()
+    bp = IkBatchParams(delta, eps2, eps2_max, max_relax, lanes)
+    _check(_lib.ik_solve_batch(ctypes.cast(arr, _vp), n, ctypes.byref(bp), _np_ptr(found),
+                               _np_ptr(reach), _np_ptr(poses), _np_ptr(relax), _np_ptr(status),
+                               ctypes.byref(ms)), "ik_solve_batch")
+    out, r0, p0, x0 = [], 0, 0, 0
+    for i, p in enumerate(problems):
+        S, W = len(p["lengths"]), int(p["n_way"])
+        out.append({"found": int(found[i]), "status": int(status[i]),
+                    "reach": reach[r0:r0 + 3 * (S + 1)].reshape(S + 1, 3),
+                    "poses": poses[p0:p0 + 3 * (S + 1) * W].reshape(W, S + 1, 3),
+                    "relax": relax[x0:x0 + 2 * W].reshape(W, 2)})
+        r0 += 3 * (S + 1)
+        p0 += 3 * (S + 1) * W
+        x0 += 2 * W
+    return out, ms.value
 
 
 def ik_validate_poses(g: int, arm, poses) -> np.ndarray:

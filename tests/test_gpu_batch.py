@@ -90,3 +90,32 @@ def test_replan_many_matches_single_replans_and_oracle(ik):
             po, ro, so = O.replan(occ2, sc.lengths, pin[r], int(current[r]))
             assert s1 == so and (r1 == ro).all() and (p1 == po).all(), r
         assert set(sm[live].tolist()) >= {ik.IK_PATH_KEPT}
+
+
+def _as_dict(p):
+    return {"shape": p.scene.shape, "boxes": p.scene.boxes, "lengths": p.scene.lengths,
+            "root": p.scene.root, "target": p.target, "n_way": p.n_way}
+
+
+def test_uneven_batch_matches_single_problem_calls(ik):
+    import oracle as O
+    probs = G.c4_problems(12, 2)
+    out, ms = ik.ik_solve_batch([_as_dict(p) for p in probs], lanes=4)
+    assert ms > 0
+    for p, r in zip(probs, out):
+        sc = p.scene
+        with ik.Grid(*sc.shape) as g:
+            ik.ik_set_boxes(g.h, sc.boxes)
+            reach, found, poses, relax, status = ik.ik_reach_path_many(
+                g.h, sc.lengths, sc.root, np.asarray([p.target], np.int32), p.n_way)
+        assert r["found"] == found[0] and r["status"] == status[0], sc.name
+        if found[0]:
+            assert (r["reach"] == reach[0]).all()
+            assert (r["poses"] == poses[0]).all() and (r["relax"] == relax[0]).all(), sc.name
+    # one small problem against the oracle's reach
+    small = [(p, r) for p, r in zip(probs, out) if p.scene.shape[0] == 64]
+    if small:
+        p, r = small[0]
+        occ = O.rasterize(p.scene.shape, p.scene.boxes)
+        po, fo, _ = O.reach_many(occ, p.scene.lengths, p.scene.root, [p.target], threads=8)
+        assert fo[0] == r["found"] and (not fo[0] or (po[0] == r["reach"]).all())
