@@ -55,7 +55,19 @@ __device__ __forceinline__ uint32_t edge_word(const Dims& d, const SegDev& sg, i
   if (sg.mask) return __ldg(sg.mask + (long)e * d.nw + w);
   const int s1 = __ldg(sg.sc_start + e + 1);
   uint32_t blocked = 0;
-  for (int i = __ldg(sg.sc_start + e); i < s1 && blocked != 0xffffffffu; ++i) {
+  int i = __ldg(sg.sc_start + e);
+  // four independent voxel reads per pass; the all-blocked exit is checked
+  // once per pass so that the reads do not wait on each other
+  for (; i + 4 <= s1 && blocked != 0xffffffffu; i += 4) {
+    uint32_t b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int32_t v = __ldg(sg.sc + i + u);
+      b[u] = ld_shifted(sg.occ, d, wx, y, z, unpack_x(v), unpack_y(v), unpack_z(v));
+    }
+    blocked |= b[0] | b[1] | b[2] | b[3];
+  }
+  for (; i < s1; ++i) {
     const int32_t v = __ldg(sg.sc + i);
     blocked |= ld_shifted(sg.occ, d, wx, y, z, unpack_x(v), unpack_y(v), unpack_z(v));
   }
