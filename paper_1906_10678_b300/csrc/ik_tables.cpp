@@ -152,22 +152,21 @@ TileCfg make_tile_cfg(const Dims& d) {
   tc.TZ = 8;
   tc.tiles_y = (d.ny + tc.TY - 1) / tc.TY;
   tc.tiles_z = (d.nz + tc.TZ - 1) / tc.TZ;
-  // smallest pitch >= wx + 2 whose lane addresses (lo and hi words) spread
-  // over the banks with the fewest collisions
-  int best = d.wx + 2, best_conf = 1 << 30;
-  for (int P = d.wx + 2; P <= d.wx + 2 + 32; ++P) {
-    int hits[32] = {0};
-    int conf = 0;
-    for (int l = 0; l < tc.lanes; ++l) {
-      const int b = ((l / d.wx) * P + (l % d.wx)) & 31;
-      conf = std::max(conf, ++hits[b]);
-    }
-    if (conf < best_conf) {
-      best_conf = conf;
-      best = P;
-    }
-    if (conf == 1) break;
-  }
+  // Pitch of a staged row (words).  A conflict-free pitch (every lane of a
+  // warp on its own bank) is taken when one exists within about twice the
+  // row width; otherwise the smallest pitch with at most 2-way conflicts,
+  // which keeps the halo small.  At most 31, so a row fits one warp.
+  auto degree = [&](int P) {
+    int hits[32] = {0}, conf = 0;
+    for (int l = 0; l < tc.lanes; ++l) conf = std::max(conf, ++hits[((l / d.wx) * P + (l % d.wx)) & 31]);
+    return conf;
+  };
+  int best = -1;
+  for (int P = d.wx + 2; P <= std::min(31, 2 * (d.wx + 2) + 2) && best < 0; ++P)
+    if (degree(P) == 1) best = P;
+  for (int P = d.wx + 2; P <= 31 && best < 0; ++P)
+    if (degree(P) <= 2) best = P;
+  if (best < 0) best = std::min(31, d.wx + 2);
   tc.P = best;
   return tc;
 }
