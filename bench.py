@@ -264,6 +264,11 @@ def run_ours(args):
         ik.ik_reach_path_many_device(g.h, arm, sc.root, targets_d, N_WAY, reach, found, poses,
                                      relax, status, delta=DELTA)
 
+    # tile depth chosen by the autotuner (measured on this very step, cached)
+    from paper_1906_10678_b300 import tune
+    tuning = tune.tile_depth(g.h, stream, sc.shape, sc.lengths, sc.root, boxes_d, targets_d, N_WAY,
+                             (reach, found, poses, relax, status), delta=DELTA)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -423,6 +428,7 @@ def run_ours(args):
                        "requests": int(len(rep_ms)), "cut": int(cut.sum()),
                        "status_counts": {str(k): int((rep_status == k).sum()) for k in range(5)},
                        "note": "host wall time per ik_replan call (C ABI, host buffers)"},
+            "tuning": tuning,
             "served": served,
             "no_edge_masks": {"ms_per_step": round(nomask_ms, 3) if nomask_ms else None,
                               "value": round(N_TARGETS / (nomask_ms / 1000.0), 3) if nomask_ms else None,

@@ -124,6 +124,9 @@ IK_API int ik_destroy_grid(ik_grid g);
  * better choice for grids solved once or changing often.  Results are
  * identical either way. */
 #define IK_OPT_EDGE_MASKS 1
+/* IK_OPT_TILE_DEPTH: output slices per block of the propagation kernel, 8
+ * (one per warp) or 16 (two per warp, default 8).  Results are identical. */
+#define IK_OPT_TILE_DEPTH 2
 IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);

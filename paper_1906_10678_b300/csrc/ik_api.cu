@@ -1150,6 +1150,11 @@ int ik_replan_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const in
 int ik_set_option(ik_grid g, int option, int value) {
   int rc = set_device(g);
   if (rc) return rc;
+  if (option == IK_OPT_TILE_DEPTH) {
+    if (value != 8 && value != 16) return IK_ERR_ARG;
+    g->tc.depth = value;
+    return IK_OK;
+  }
   if (option != IK_OPT_EDGE_MASKS) return IK_ERR_ARG;
   if ((rc = sync(g))) return rc;
   g->use_masks = value != 0;

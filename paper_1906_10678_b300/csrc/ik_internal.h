@@ -72,6 +72,7 @@ struct SegDev {
 // shared-memory word delta and the funnel shift of offset e.
 struct TileCfg {
   int TY, TZ, P, lanes, tiles_y, tiles_z;
+  int depth = 8;  // output slices per tile of the propagation: 8 (one per warp) or 16 (two)
 };
 TileCfg make_tile_cfg(const Dims& d);
 // Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).

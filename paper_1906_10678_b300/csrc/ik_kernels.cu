@@ -465,12 +465,204 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
   if (kCount && threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
 }
 
+// The same propagation with a 16-slice tile: warp i computes the output
+// words of slices z0 + i and z0 + 8 + i, so each offset's table entry and
+// address serve two output words (two shared-memory pairs, two funnel
+// shifts).  Slices of the pair outside the z range of the box of X at a
+// given dz are masked out (their shared words are not staged).
+template <bool kCount>
+__global__ void __launch_bounds__(256, 2) k_propagate_tile2(Dims d, SegDev seg, TileCfg tc,
+                                                         const uint32_t* __restrict__ X, long xs,
+                                                         const uint32_t* __restrict__ mask, long ms,
+                                                         const uint32_t* __restrict__ occ,
+                                                         uint32_t* __restrict__ out, long os,
+                                                         const int32_t* __restrict__ xbox,
+                                                         int32_t* __restrict__ obox, long bs,
+                                                         unsigned long long* __restrict__ counters) {
+  extern __shared__ uint32_t sx[];
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr int TD = 16;
+  const int q = blockIdx.y;
+  const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * TD;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = seg.R, RY = tc.TY + 2 * R, P = tc.P;
+  const int za = z0 + warp, zb = za + 8, wx = lane % d.wx, y = y0 + lane / d.wx;
+  const bool lane_ok = lane < tc.lanes && y < d.ny;
+  const bool va = lane_ok && za < d.nz, vb = lane_ok && zb < d.nz;
+  const long wa = va ? ((long)za * d.ny + y) * d.wx + wx : 0;
+  const long wb = vb ? ((long)zb * d.ny + y) * d.wx + wx : 0;
+  const uint32_t* Xq = X + q * xs;
+  const int32_t* xb = xbox + q * bs;
+  const int bx0 = __ldg(xb + 0), by0 = __ldg(xb + 1), bz0 = __ldg(xb + 2);
+  const int bx1 = -__ldg(xb + 3), by1 = -__ldg(xb + 4), bz1 = -__ldg(xb + 5);
+  uint32_t ma = 0, mb = 0;
+  if (va) ma = (mask ? __ldg(mask + q * ms + wa) : 0xffffffffu) & ~__ldg(occ + wa);
+  if (vb) mb = (mask ? __ldg(mask + q * ms + wb) : 0xffffffffu) & ~__ldg(occ + wb);
+  const bool touches = bx0 <= bx1 && by1 >= y0 - R && by0 <= y0 + tc.TY - 1 + R &&
+                       bz1 >= z0 - R && bz0 <= z0 + TD - 1 + R;
+  if (!__syncthreads_or(touches && (ma | mb) != 0)) {
+    if (va) out[q * os + wa] = 0u;
+    if (vb) out[q * os + wb] = 0u;
+    return;
+  }
+  // stage the readable part of the source halo (as in k_propagate_tile)
+  {
+    const int sz0 = max(bz0, z0 - R), sz1 = min(bz1, z0 + TD - 1 + R);
+    const int sy0 = max(by0 - tc.TY + 1, y0 - R), sy1 = min(by1 + tc.TY - 1, y0 + tc.TY - 1 + R);
+    const int ny_rows = sy1 - sy0 + 1, n_rows = (sz1 - sz0 + 1) * ny_rows;
+    const int per_pass = 32 / P;
+    const int sub = lane / P, c = lane % P, sw = c - 1;
+    const bool col_in = sw >= bx0 && sw <= bx1;
+    if (ny_rows > 0 && sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+        const int sy = sy0 + r % ny_rows, sz = sz0 + r / ny_rows;
+        uint32_t v = 0u;
+        if (col_in && sy >= by0 && sy <= by1) v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
+        sx[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t acc_a = 0, acc_b = 0;
+  unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0;
+  if (__any_sync(kFull, (ma | mb) != 0)) {
+    const int side = 2 * R + 1;
+    const int ylast = min(y0 + tc.TY, d.ny) - 1;
+    const int ez0 = max(bz0 - zb, -R), ez1 = min(bz1 - za, R);
+    const int ey0 = max(by0 - ylast, -R), ey1 = min(by1 - y0, R);
+    const int base_a = lane_ok ? ((warp + R) * RY + (y - y0 + R)) * P + (wx + 1) : (R * RY + R) * P + 1;
+    const int slice8 = 8 * RY * P;
+    bool live_a = ma != 0, live_b = mb != 0;
+    for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
+      const bool ua = za + ez >= bz0 && za + ez <= bz1;
+      const bool ub = zb + ez >= bz0 && zb + ez <= bz1;
+      if (!ua && !ub) continue;
+      const uint32_t ka = ua ? 0xffffffffu : 0u, kb = ub ? 0xffffffffu : 0u;
+      const int32_t* rowp = seg.rows + (ez + R) * side + R;
+      const int e1 = __ldg(rowp + ey1 + 1);
+      const int za_b = base_a + ez * RY * P, zb_b = za_b + slice8;
+      int e = __ldg(rowp + ey0);
+      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - e);
+      for (; e + 8 <= e1; e += 8) {
+        uint32_t xa[8], xb_[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int32_t t = __ldg(seg.tab + e + i);
+          const int dl = t >> 5;
+          xa[i] = __funnelshift_r(sx[za_b + dl], sx[za_b + dl + 1], t) & ka;
+          xb_[i] = __funnelshift_r(sx[zb_b + dl], sx[zb_b + dl + 1], t) & kb;
+        }
+        const uint32_t want_a = ma & ~acc_a, want_b = mb & ~acc_b;
+        uint32_t any_a = 0, any_b = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          any_a |= xa[i];
+          any_b |= xb_[i];
+        }
+        if (kCount) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (live_a && ua) {
+              ++visited;
+              nonzero += xa[i] != 0;
+            }
+            if (live_b && ub) {
+              ++visited;
+              nonzero += xb_[i] != 0;
+            }
+          }
+        }
+        if (any_a & want_a) {
+          uint32_t mv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) mv[i] = (xa[i] & want_a) ? edge_word(d, seg, e + i, wa, wx, y, za) : 0u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (kCount) mloads += (xa[i] & want_a) != 0;
+            acc_a |= xa[i] & mv[i];
+          }
+        }
+        if (any_b & want_b) {
+          uint32_t mv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) mv[i] = (xb_[i] & want_b) ? edge_word(d, seg, e + i, wb, wx, y, zb) : 0u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (kCount) mloads += (xb_[i] & want_b) != 0;
+            acc_b |= xb_[i] & mv[i];
+          }
+        }
+      }
+      for (; e < e1; ++e) {
+        const int32_t t = __ldg(seg.tab + e);
+        const int dl = t >> 5;
+        const uint32_t x1 = __funnelshift_r(sx[za_b + dl], sx[za_b + dl + 1], t) & ka;
+        const uint32_t x2 = __funnelshift_r(sx[zb_b + dl], sx[zb_b + dl + 1], t) & kb;
+        if (kCount) {
+          if (live_a && ua) {
+            ++visited;
+            nonzero += x1 != 0;
+          }
+          if (live_b && ub) {
+            ++visited;
+            nonzero += x2 != 0;
+          }
+        }
+        if (x1 & ma & ~acc_a) {
+          if (kCount) ++mloads;
+          acc_a |= x1 & edge_word(d, seg, e, wa, wx, y, za);
+        }
+        if (x2 & mb & ~acc_b) {
+          if (kCount) ++mloads;
+          acc_b |= x2 & edge_word(d, seg, e, wb, wx, y, zb);
+        }
+      }
+      live_a = live_a && (acc_a & ma) != ma;
+      live_b = live_b && (acc_b & mb) != mb;
+      if (!__any_sync(kFull, live_a || live_b)) break;
+    }
+  }
+  acc_a &= ma;
+  acc_b &= mb;
+  if (va) out[q * os + wa] = acc_a;
+  if (vb) out[q * os + wb] = acc_b;
+  box_accumulate(obox + q * bs, acc_a != 0, wx, y, za);
+  box_accumulate(obox + q * bs, acc_b != 0, wx, y, zb);
+  if (kCount) {
+    if (va || vb) {
+      atomicAdd(counters + 0, visited);
+      atomicAdd(counters + 1, nonzero);
+      atomicAdd(counters + 2, mloads);
+      atomicAdd(counters + 3, (unsigned long long)(ma != 0) + (unsigned long long)(mb != 0));
+    }
+    if (lane == 0) atomicAdd(counters + 4, warp_iters);
+    if (threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
+  }
+}
+
+size_t tile2_smem_bytes(const TileCfg& tc, int R) {
+  if (R > 31 || tc.P > 31) return 0;
+  const size_t bytes = (size_t)(16 + 2 * R) * (tc.TY + 2 * R) * tc.P * 4;
+  return bytes <= 200 * 1024 ? bytes : 0;
+}
+
 cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,
                              long x_stride, const uint32_t* mask, long mask_stride,
                              const uint32_t* occ, uint32_t* out, long out_stride, int Q,
                              const int32_t* xbox, int32_t* obox, long box_stride, cudaStream_t st,
                              unsigned long long* counters) {
   if (Q <= 0) return cudaSuccess;
+  const size_t smem2 = tc.depth == 16 ? tile2_smem_bytes(tc, seg.R) : 0;
+  if (smem2 > 0 && seg.tab) {
+    dim3 grid(tc.tiles_y * ((d.nz + 15) / 16), Q);
+    if (counters)
+      k_propagate_tile2<true><<<grid, 256, smem2, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
+                                                        out, out_stride, xbox, obox, box_stride, counters);
+    else
+      k_propagate_tile2<false><<<grid, 256, smem2, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
+                                                         out, out_stride, xbox, obox, box_stride, nullptr);
+    return cudaGetLastError();
+  }
   const size_t smem = tile_smem_bytes(tc, seg.R);
   if (smem > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
@@ -1304,6 +1496,12 @@ cudaError_t set_kernel_attributes() {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile2<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile2<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
