@@ -421,7 +421,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h)},
             "plain": {"value": round(1000.0 / float(np.mean(plain_ms)), 3), "unit": UNIT,
                       "ms_per_solve": round(float(np.mean(plain_ms)), 3), "sample": len(plain_ms)},
-            "replan": {"p50_ms": round(float(np.percentile(rep_ms, 50)), 3),
+            "replan": None if len(rep_ms) == 0 else {
+                       "p50_ms": round(float(np.percentile(rep_ms, 50)), 3),
                        "p99_ms": round(float(np.percentile(rep_ms, 99)), 3),
                        "cut_p50_ms": round(float(np.percentile(rep_ms[cut], 50)), 3) if cut.any() else None,
                        "cut_p99_ms": round(float(np.percentile(rep_ms[cut], 99)), 3) if cut.any() else None,

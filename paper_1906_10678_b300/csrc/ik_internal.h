@@ -77,6 +77,10 @@ struct TileCfg {
 TileCfg make_tile_cfg(const Dims& d);
 // Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).
 size_t tile_smem_bytes(const TileCfg& tc, int R);
+// Both halos (X and occupancy) of the tiled propagation without stored edge
+// masks; 0 when they do not fit in kTileOccSmemMax bytes.
+constexpr int kTileOccSmemMax = 227 * 1024;
+size_t tile_occ_smem_bytes(const TileCfg& tc, int R);
 
 // Bounding box of a voxel set in word coordinates, kept in "min form" so
 // that every component accumulates with atomicMin: {wx0, y0, z0, -wx1, -y1,
@@ -114,8 +118,10 @@ cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* 
 // queries (mask_stride 0: one mask shared by all queries).
 // xbox / obox: boxes of X[q] and out[q] at q * box_stride ints; obox must
 // be set empty beforehand and receives the box of the output.
-// The tiled shared-memory kernel runs when tile_smem_bytes(tc, seg.R) > 0,
-// the global-load kernel otherwise.
+// The tiled shared-memory kernel runs when tile_smem_bytes(tc, seg.R) > 0
+// (for a segment without stored edge masks, when tile_occ_smem_bytes > 0:
+// its supercover walks then read an occupancy halo in shared memory), the
+// global-load kernel otherwise.
 cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,
                              long x_stride, const uint32_t* mask, long mask_stride,
                              const uint32_t* occ, uint32_t* out, long out_stride, int Q,

@@ -74,6 +74,32 @@ __device__ __forceinline__ uint32_t edge_word(const Dims& d, const SegDev& sg, i
   return ~blocked;
 }
 
+// The same free bits from an occupancy halo staged in shared memory with the
+// layout of the tiled kernels: base is the lane's own word in the halo and
+// sctab holds each supercover voxel's shared-memory delta and x shift.
+__device__ __forceinline__ uint32_t edge_word_tile(const SegDev& sg, int e, const uint32_t* so,
+                                                   int base) {
+  const int s1 = __ldg(sg.sc_start + e + 1);
+  uint32_t blocked = 0;
+  int i = __ldg(sg.sc_start + e);
+  for (; i + 4 <= s1 && blocked != 0xffffffffu; i += 4) {
+    uint32_t b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int32_t t = __ldg(sg.sctab + i + u);
+      const int a = base + (t >> 5);
+      b[u] = __funnelshift_r(so[a], so[a + 1], t);  // shift taken mod 32
+    }
+    blocked |= b[0] | b[1] | b[2] | b[3];
+  }
+  for (; i < s1; ++i) {
+    const int32_t t = __ldg(sg.sctab + i);
+    const int a = base + (t >> 5);
+    blocked |= __funnelshift_r(so[a], so[a + 1], t);
+  }
+  return ~blocked;
+}
+
 // The segment from voxel p (linear index pi) along offset e: free?
 __device__ __forceinline__ bool edge_bit(const Dims& d, const SegDev& sg, int e, long pi) {
   const long w = pi >> 5;
@@ -335,7 +361,7 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
 // walk visits, per warp (one z slice), the dz range that can reach the box
 // of X and, per dz, the one contiguous run of offsets whose dy can reach it
 // from any of the warp's rows.
-template <bool kCount>
+template <bool kCount, bool kOcc>
 __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, TileCfg tc,
                                                         const uint32_t* __restrict__ X, long xs,
                                                         const uint32_t* __restrict__ mask, long ms,
@@ -386,6 +412,27 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
       }
     }
   }
+  // Without stored edge masks the occupancy halo goes to a second region of
+  // the same layout.  A supercover voxel lies between the output voxel and
+  // its source, whose z and y lie in the box of X, so only rows between the
+  // tile and that box are staged (zero outside the grid).
+  uint32_t* so = sx + (tc.TZ + 2 * R) * RY * P;
+  if (kOcc) {
+    const int oz0 = max(z0 - R, min(z0, bz0)), oz1 = min(z0 + tc.TZ - 1 + R, max(z0 + tc.TZ - 1, bz1));
+    const int oy0 = max(y0 - R, min(y0, by0)), oy1 = min(y0 + tc.TY - 1 + R, max(y0 + tc.TY - 1, by1));
+    const int ny_rows = oy1 - oy0 + 1, n_rows = (oz1 - oz0 + 1) * ny_rows;
+    const int per_pass = 32 / P;
+    const int sub = lane / P, c = lane % P, sw = c - 1;
+    if (ny_rows > 0 && sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+        const int sy = oy0 + r % ny_rows, sz = oz0 + r / ny_rows;
+        uint32_t v = 0u;
+        if (sw >= 0 && sw < d.wx && sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz)
+          v = __ldg(seg.occ + ((long)sz * d.ny + sy) * d.wx + sw);
+        so[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
+      }
+    }
+  }
   __syncthreads();
   uint32_t acc = 0;
   unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0;
@@ -425,13 +472,25 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
           for (int i = 0; i < 8; ++i) nonzero += xv[i] != 0;
         }
         if (any & want) {
-          uint32_t mv[8];
+          if (kOcc) {
+            // supercover walks in shared memory: one at a time, each skipped
+            // once the accumulator already holds the bits it could add
 #pragma unroll
-          for (int i = 0; i < 8; ++i) mv[i] = (xv[i] & want) ? edge_word(d, seg, e + i, w, wx, y, z) : 0u;
+            for (int i = 0; i < 8; ++i) {
+              if (xv[i] & m & ~acc) {
+                if (kCount) ++mloads;
+                acc |= xv[i] & edge_word_tile(seg, e + i, so, base);
+              }
+            }
+          } else {
+            uint32_t mv[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            if (kCount) mloads += (xv[i] & want) != 0;
-            acc |= xv[i] & mv[i];
+            for (int i = 0; i < 8; ++i) mv[i] = (xv[i] & want) ? edge_word(d, seg, e + i, w, wx, y, z) : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (kCount) mloads += (xv[i] & want) != 0;
+              acc |= xv[i] & mv[i];
+            }
           }
         }
       }
@@ -445,7 +504,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
         }
         if (x & m & ~acc) {
           if (kCount) ++mloads;
-          acc |= x & edge_word(d, seg, e, w, wx, y, z);
+          acc |= x & (kOcc ? edge_word_tile(seg, e, so, base) : edge_word(d, seg, e, w, wx, y, z));
         }
       }
       live = live && (acc & m) != m;
@@ -663,15 +722,30 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
                                                          out, out_stride, xbox, obox, box_stride, nullptr);
     return cudaGetLastError();
   }
+  const size_t smem_o = (!seg.mask && seg.sctab) ? tile_occ_smem_bytes(tc, seg.R) : 0;
+  if (smem_o > 0 && seg.tab) {
+    dim3 grid(tc.tiles_y * tc.tiles_z, Q);
+    if (counters)
+      k_propagate_tile<true, true><<<grid, 256, smem_o, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+                                                              occ, out, out_stride, xbox, obox, box_stride,
+                                                              counters);
+    else
+      k_propagate_tile<false, true><<<grid, 256, smem_o, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+                                                               occ, out, out_stride, xbox, obox, box_stride,
+                                                               nullptr);
+    return cudaGetLastError();
+  }
   const size_t smem = tile_smem_bytes(tc, seg.R);
   if (smem > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
     if (counters)
-      k_propagate_tile<true><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
-                                                      out, out_stride, xbox, obox, box_stride, counters);
+      k_propagate_tile<true, false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+                                                             occ, out, out_stride, xbox, obox, box_stride,
+                                                             counters);
     else
-      k_propagate_tile<false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride, occ,
-                                                       out, out_stride, xbox, obox, box_stride, nullptr);
+      k_propagate_tile<false, false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+                                                              occ, out, out_stride, xbox, obox, box_stride,
+                                                              nullptr);
     return cudaGetLastError();
   }
   dim3 grid(grid_for(d.nw, 256), Q);
@@ -1492,11 +1566,17 @@ cudaError_t set_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute((const void*)k_edge_masks_tile,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile2<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

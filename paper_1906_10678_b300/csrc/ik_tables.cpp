@@ -178,4 +178,10 @@ size_t tile_smem_bytes(const TileCfg& tc, int R) {
   return bytes <= 200 * 1024 ? bytes : 0;
 }
 
+size_t tile_occ_smem_bytes(const TileCfg& tc, int R) {
+  if (R > 31 || tc.P > 31) return 0;
+  const size_t bytes = 2 * (size_t)(tc.TZ + 2 * R) * (tc.TY + 2 * R) * tc.P * 4;
+  return bytes <= (size_t)kTileOccSmemMax ? bytes : 0;
+}
+
 }  // namespace ikb
