@@ -1282,6 +1282,65 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
   __syncthreads();
 }
 
+// Occupancy of the box that holds every supercover voxel one level of the
+// chain can test, staged in shared memory: a segment runs from a voxel of
+// one box to a voxel of the other, so its supercover lies in the hull of the
+// two boxes (one extra word on either side in x, read by the funnel shifts
+// for bits that the result masks away).  Larger boxes (strong relaxation)
+// keep reading the occupancy in global memory.
+constexpr int kChainOccWords = 10240;
+
+struct OccBox {
+  const uint32_t* s;
+  int w0, y0, z0, nw, ny;
+  bool ok;
+};
+
+__device__ OccBox chain_stage_occ(const Dims& d, const SegDev& sg, const Box& a, const Box& b,
+                                  uint32_t* s) {
+  // with stored edge masks one mask word per test is cheaper than a walk
+  OccBox ob;
+  ob.s = s;
+  ob.w0 = (min(a.x0, b.x0) >> 5) - 1;
+  ob.y0 = min(a.y0, b.y0);
+  ob.z0 = min(a.z0, b.z0);
+  ob.nw = (max(a.x1, b.x1) >> 5) + 1 - ob.w0 + 1;
+  ob.ny = max(a.y1, b.y1) - ob.y0 + 1;
+  const int nz = max(a.z1, b.z1) - ob.z0 + 1;
+  const long total = (long)ob.nw * ob.ny * nz;
+  ob.ok = !sg.mask && total <= kChainOccWords;
+  __syncthreads();  // the previous level's readers are done with s
+  if (ob.ok) {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int ww = ob.w0 + t % ob.nw, yy = ob.y0 + (t / ob.nw) % ob.ny, zz = ob.z0 + t / (ob.nw * ob.ny);
+      s[t] = (ww >= 0 && ww < d.wx) ? __ldg(sg.occ + ((long)zz * d.ny + yy) * d.wx + ww) : 0u;
+    }
+  }
+  __syncthreads();
+  return ob;
+}
+
+// edge_word with the supercover walked against a staged occupancy box
+__device__ __forceinline__ uint32_t edge_word_box(const Dims& d, const SegDev& sg, const OccBox& ob, int e,
+                                                  long w, int wx, int y, int z) {
+  if (!ob.ok) return edge_word(d, sg, e, w, wx, y, z);
+  const int s1 = __ldg(sg.sc_start + e + 1);
+  const uint32_t* base = ob.s + ((z - ob.z0) * ob.ny + (y - ob.y0)) * ob.nw + (wx - ob.w0);
+  auto voxel = [&](int i) {
+    const int32_t v = __ldg(sg.sc + i);
+    const int vx = unpack_x(v);
+    const uint32_t* row = base + (unpack_z(v) * ob.ny + unpack_y(v)) * ob.nw + (vx >> 5);
+    return __funnelshift_r(row[0], row[1], vx);  // shift taken mod 32
+  };
+  uint32_t blocked = 0;
+  int i = __ldg(sg.sc_start + e);
+  // four independent reads per pass, the all-blocked exit checked per pass
+  for (; i + 4 <= s1 && blocked != 0xffffffffu; i += 4)
+    blocked |= voxel(i) | voxel(i + 1) | voxel(i + 2) | voxel(i + 3);
+  for (; i < s1; ++i) blocked |= voxel(i);
+  return ~blocked;
+}
+
 // One restricted propagation word: OR over the segment's offsets of the
 // source set shifted by the offset, limited to offsets whose source voxels
 // can fall in the source box, AND edge mask, within `m`.
@@ -1292,9 +1351,9 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
 // the group must call it (idle lanes pass m = 0).
 constexpr int kG = 8;
 
-__device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const uint32_t* src,
-                                                    const Box& sb, int wx, int y, int z, long w,
-                                                    uint32_t m) {
+__device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const OccBox& ob,
+                                                    const uint32_t* src, const Box& sb, int wx, int y,
+                                                    int z, long w, uint32_t m) {
   const int g = threadIdx.x % kG;
   const unsigned gmask = ((1u << kG) - 1u) << ((threadIdx.x & 31) & ~(kG - 1));
   uint32_t acc = 0;
@@ -1311,7 +1370,7 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
         const int ex = unpack_x(o);
         if (ex < exlo || ex > exhi) continue;
         const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ex, unpack_y(o), ez);
-        if (x & m & ~acc) acc |= x & edge_word(d, sg, e, w, wx, y, z);
+        if (x & m & ~acc) acc |= x & edge_word_box(d, sg, ob, e, w, wx, y, z);
       }
     }
   }
@@ -1320,7 +1379,7 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
 
 // Forward restriction: R_0 = {root}, R_k = (V_k & Ball(ref_k, delta)) & D_k(R_{k-1}).
 __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* V,
-                              uint32_t* R, int delta2) {
+                              uint32_t* R, int delta2, uint32_t* so) {
   const int S = arm.S;
   if (threadIdx.x == 0) {
     const long i = lin(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]);
@@ -1334,6 +1393,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
     const uint32_t* Vk = V + (long)k * d.nw;
     uint32_t* dst = R + (long)k * d.nw;
     const long n = box_words(b);
+    const OccBox ob = chain_stage_occ(d, sg, b, sb, so);
     int any = 0;
     // kG lanes per word; the loop bound is uniform per lane group
     for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
@@ -1346,7 +1406,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = ball_bits(wx, y, z, sh.ref[k], delta2) & __ldg(Vk + w);
       }
-      const uint32_t acc = restricted_word(d, sg, src, sb, wx, y, z, w, m);
+      const uint32_t acc = restricted_word(d, sg, ob, src, sb, wx, y, z, w, m);
       if (acc && threadIdx.x % kG == 0) {
         dst[w] = acc;
         any = 1;
@@ -1359,7 +1419,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
 
 // Backward restriction: U_S = R_S, U_k = R_k & D_{k+1}(U_{k+1}).
 __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* R,
-                               uint32_t* U) {
+                               uint32_t* U, uint32_t* so) {
   const int S = arm.S;
   {
     const Box b = sh.box[S];
@@ -1379,6 +1439,7 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
     const uint32_t* Rk = R + (long)k * d.nw;
     uint32_t* dst = U + (long)k * d.nw;
     const long n = box_words(b);
+    const OccBox ob = chain_stage_occ(d, sg, b, sb, so);
     for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
       const long t = t0 + threadIdx.x / kG;
       int wx = 0, y = 0, z = 0;
@@ -1389,7 +1450,7 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = Rk[w];
       }
-      const uint32_t acc = restricted_word(d, sg, src, sb, wx, y, z, w, m);
+      const uint32_t acc = restricted_word(d, sg, ob, src, sb, wx, y, z, w, m);
       if (acc && threadIdx.x % kG == 0) dst[w] = acc;
     }
     __syncthreads();
@@ -1401,7 +1462,7 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
 // `coherent` selects plain loads for sets written in this kernel.
 template <bool kCoherent>
 __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* X,
-                            int32_t* pose) {
+                            int32_t* pose, uint32_t* so) {
   const int S = arm.S;
   if (threadIdx.x == 0) {
     sh.cur[0] = sh.ref[0][0];
@@ -1418,7 +1479,16 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
     const int px = sh.cur[0], py = sh.cur[1], pz = sh.cur[2];
     const long pi = lin(d, px, py, pz);
     if (threadIdx.x == 0) sh.best = ~0ull;
+    // the restricted sets lie in the ball boxes: stage the hull of p and box k
+    OccBox ob;
+    ob.ok = false;
+    if (kCoherent) {
+      const Box pb{px, px, py, py, pz, pz};
+      ob = chain_stage_occ(d, sg, pb, sh.box[k], so);
+    }
     __syncthreads();
+    const int pwx = px >> 5;
+    const long pw = pi >> 5;
     for (int e = threadIdx.x; e < sg.n; e += blockDim.x) {
       const int32_t o = __ldg(sg.off + e);
       const int qx = px + unpack_x(o), qy = py + unpack_y(o), qz = pz + unpack_z(o);
@@ -1426,7 +1496,7 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
       const long qi = lin(d, qx, qy, qz);
       const uint32_t word = kCoherent ? Xk[qi >> 5] : __ldg(Xk + (qi >> 5));
       if (!((word >> (qi & 31)) & 1u)) continue;
-      if (!edge_bit(d, sg, e, pi)) continue;
+      if (!((edge_word_box(d, sg, ob, e, pw, pwx, py, pz) >> (px & 31)) & 1u)) continue;
       atomicMin(&sh.best, (unsigned long long)qi);
     }
     __syncthreads();
@@ -1446,16 +1516,9 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
   return true;
 }
 
-__device__ bool chain_feasible(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* V,
-                               uint32_t* R, uint32_t* U, int delta) {
-  chain_boxes(d, sh, arm.S, delta);
-  const bool ok = chain_forward(d, arm, sh, V, R, delta * delta);
-  chain_clear(d, sh, arm.S, R, U);
-  return ok;
-}
-
-__global__ void __launch_bounds__(kChainThreads) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
+__global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
   __shared__ ChainShared sh;
+  __shared__ uint32_t so[kChainOccWords];
   const int p = blockIdx.x, S = arm.S, W = a.W;
   const long pose_sz = 3L * (S + 1);
   int32_t* poses = a.poses + (long)p * W * pose_sz;
@@ -1473,6 +1536,7 @@ __global__ void __launch_bounds__(kChainThreads) k_smooth_chain(Dims d, ArmDev a
     return;
   }
   bool relaxed = false, broken = false;
+  int guess = 0;  // search start: the relaxation of the previous waypoint
   const int n_steps = a.mode == 0 ? W - 1 : W - 1 - cur;
   if (threadIdx.x == 0) {
     if (a.mode == 0) {
@@ -1496,55 +1560,82 @@ __global__ void __launch_bounds__(kChainThreads) k_smooth_chain(Dims d, ArmDev a
     const bool vok = inside(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]) &&
                      test_bit(V, lin(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]));
     int m_star = -1;
+    // R holds the forward restriction of the last feasibility test (boxes in
+    // sh.box) when r_for >= 0; dirty: R / U hold words that must be cleared
+    int r_for = -1;
+    bool dirty = false;
+    auto covers = [&](int m) { return (long)(a.delta + m) * (a.delta + m) >= D2; };
+    // Is there a chain inside the balls of radius delta + m?  Once the ball
+    // covers the grid ((delta + m)^2 >= D2) there is, because V is non-empty.
+    auto feasible = [&](int m) {
+      if (covers(m)) return true;
+      if (dirty) chain_clear(d, sh, S, R, U);
+      chain_boxes(d, sh, S, a.delta + m);
+      const bool ok = chain_forward(d, arm, sh, V, R, (a.delta + m) * (a.delta + m), so);
+      dirty = true;
+      r_for = ok ? m : -1;
+      return ok;
+    };
     if (vok) {
-      // smallest m with a chain inside the balls of radius delta + m; the
-      // ball covers the grid once (delta + m)^2 >= D2, and then a chain exists
-      // because V is non-empty.  Feasibility grows with m, so a doubling then
-      // bisecting search finds the same m as trying m = 0, 1, 2, ... in turn.
-      auto covers = [&](int m) { return (long)(a.delta + m) * (a.delta + m) >= D2; };
+      // Smallest m with a chain inside the balls of radius delta + m (at most
+      // max_relax when that is bounded).  Feasibility only grows with m, so
+      // any search that brackets the smallest feasible m finds the same m as
+      // trying m = 0, 1, 2, ... in turn.  The search starts next to the
+      // previous waypoint's m, which consecutive waypoints usually share:
+      // gallop down or up from there, then bisect.
+      const int cap = a.max_relax >= 0 ? a.max_relax : 0x3fffffff;
       int lo = -1, hi = -1;
-      for (int m = 0; m <= 3; ++m) {
-        if (covers(m) || chain_feasible(d, arm, sh, V, R, U, a.delta + m)) {
-          hi = m;
-          break;
-        }
-        lo = m;
+      const int g = min(guess, cap);
+      if (g > 0) {
+        if (feasible(g - 1)) hi = g - 1;
+        else lo = g - 1;
       }
       if (hi < 0) {
-        int step = 4;
-        for (;;) {
-          const int m = lo + step;
-          if (covers(m) || chain_feasible(d, arm, sh, V, R, U, a.delta + m)) {
+        for (int step = 1;; step *= 2) {
+          if (lo >= cap) break;
+          const int m = (int)min((long)lo + step, (long)cap);
+          if (feasible(m)) {
             hi = m;
             break;
           }
           lo = m;
-          step *= 2;
         }
+      } else {
+        for (int step = 1; hi > 0; step *= 2) {
+          const int m = max(hi - step, 0);
+          if (!feasible(m)) {
+            lo = m;
+            break;
+          }
+          hi = m;
+        }
+      }
+      if (hi >= 0) {
         while (hi - lo > 1) {
           const int mid = lo + (hi - lo) / 2;
-          if (covers(mid) || chain_feasible(d, arm, sh, V, R, U, a.delta + mid)) hi = mid;
+          if (feasible(mid)) hi = mid;
           else lo = mid;
         }
       }
       m_star = hi;
-      if (a.max_relax >= 0 && m_star > a.max_relax) m_star = -1;
     }
     bool done = false;
     if (m_star >= 0) {
+      guess = m_star;
       if (covers_full(D2, a.delta + m_star)) {
-        done = chain_trace<false>(d, arm, sh, V, pose);
+        if (dirty) chain_clear(d, sh, S, R, U);
+        dirty = false;
+        done = chain_trace<false>(d, arm, sh, V, pose, so);
       } else {
-        chain_boxes(d, sh, S, a.delta + m_star);
-        const int dm = a.delta + m_star;
-        const bool ok = chain_forward(d, arm, sh, V, R, dm * dm);
+        bool ok = true;
+        if (r_for != m_star) ok = feasible(m_star);  // the last test was another m
         if (ok) {
-          chain_backward(d, arm, sh, R, U);
-          done = chain_trace<true>(d, arm, sh, U, pose);
+          chain_backward(d, arm, sh, R, U, so);
+          done = chain_trace<true>(d, arm, sh, U, pose, so);
         }
-        chain_clear(d, sh, S, R, U);
       }
     }
+    if (dirty) chain_clear(d, sh, S, R, U);
     if (done) {
       if (m_star > 0) relaxed = true;
       if (threadIdx.x == 0) relax[2 * j] = m_star;
