@@ -264,10 +264,15 @@ def run_ours(args):
         ik.ik_reach_path_many_device(g.h, arm, sc.root, targets_d, N_WAY, reach, found, poses,
                                      relax, status, delta=DELTA)
 
-    # tile depth chosen by the autotuner (measured on this very step, cached)
-    from paper_1906_10678_b300 import tune
-    tuning = tune.tile_depth(g.h, stream, sc.shape, sc.lengths, sc.root, boxes_d, targets_d, N_WAY,
-                             (reach, found, poses, relax, status), delta=DELTA)
+    # tile depth chosen by the autotuner (measured on this very step, cached),
+    # or fixed by --tile-depth
+    if args.tile_depth == "auto":
+        from paper_1906_10678_b300 import tune
+        tuning = tune.tile_depth(g.h, stream, sc.shape, sc.lengths, sc.root, boxes_d, targets_d, N_WAY,
+                                 (reach, found, poses, relax, status), delta=DELTA)
+    else:
+        ik.ik_set_option(g.h, ik.IK_OPT_TILE_DEPTH, int(args.tile_depth))
+        tuning = {"depth": int(args.tile_depth), "fixed": True}
 
     for _ in range(args.warmup):
         step()
@@ -501,6 +506,8 @@ def main():
     ap.add_argument("--problems", type=int, default=1024)
     ap.add_argument("--lanes", type=int, default=16)
     ap.add_argument("--serve-warmup", type=float, default=2.0)
+    ap.add_argument("--tile-depth", default="auto", choices=["auto", "8", "16"],
+                    help="propagation tile depth; auto = the autotuner's choice")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -48,6 +48,7 @@ struct Lane {
 struct ProbInfo {
   Dims d;
   TileCfg tc;
+  TileCfg tcs[IK_MAX_SEG];  // per segment: tc, or a narrower pitch where tc's halos do not fit
   ArmDev arm;
   int S, W;
   size_t off_reach, off_poses, off_relax;  // into the packed outputs (int32 units)
@@ -185,7 +186,7 @@ int enqueue_problem(Engine& E, Lane& L, const ProbInfo& pi, int idx, const ik_ba
   CKB(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, st));
   CKB(launch_seed_points(d, root, 1, nullptr, occ, F, d.nw, nullptr, fb, 0, st));
   for (int k = 1; k <= S; ++k)
-    CKB(launch_propagate(d, pi.tc, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, occ, F + k * d.nw,
+    CKB(launch_propagate(d, pi.tcs[k - 1], ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, occ, F + k * d.nw,
                          0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, st));
   // reach
   uint32_t* V = P<uint32_t>(L.V);
@@ -194,7 +195,7 @@ int enqueue_problem(Engine& E, Lane& L, const ProbInfo& pi, int idx, const ik_ba
   CKB(launch_seed_points(d, target, 1, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr,
                          vb + 6 * S, 0, st));
   for (int k = S; k >= 1; --k)
-    CKB(launch_propagate(d, pi.tc, ad.seg[k - 1], V + (long)k * d.nw, 0, F + (long)(k - 1) * d.nw, 0,
+    CKB(launch_propagate(d, pi.tcs[k - 1], ad.seg[k - 1], V + (long)k * d.nw, 0, F + (long)(k - 1) * d.nw, 0,
                          occ, V + (long)(k - 1) * d.nw, 0, 1, vb + 6 * k, vb + 6 * (k - 1), 0, st));
   CKB(launch_traceback(d, ad, root, V, qs, 1, reach, found, st));
   // waypoint survivor sets
@@ -205,7 +206,7 @@ int enqueue_problem(Engine& E, Lane& L, const ProbInfo& pi, int idx, const ik_ba
   CKB(launch_guide_targets(d, ad, occ, F + (long)S * d.nw, reach, found, 1, W, 0, bp.eps2, bp.eps2_max,
                            P<int32_t>(L.g), P<int32_t>(L.eps), Vw, wb, st));
   for (int k = S; k >= 1; --k)
-    CKB(launch_propagate(d, pi.tc, ad.seg[k - 1], Vw + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
+    CKB(launch_propagate(d, pi.tcs[k - 1], ad.seg[k - 1], Vw + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
                          occ, Vw + (long)(k - 1) * d.nw, qs, W, wb + 6 * k, wb + 6 * (k - 1),
                          6L * (S + 1), st));
   // smooth chain
@@ -303,8 +304,18 @@ int ik_solve_batch(const ik_problem* probs, int n, const ik_batch_params* bp, in
       if (hi2 < lo2) return IK_ERR_ARG;
       BatchShell* s = nullptr;
       if ((rc = E.shell(lo2, hi2, &s))) return rc;
+      // Without edge masks the tiled kernel stages an occupancy halo beside
+      // the source halo; where both do not fit at the grid's pitch, the
+      // narrowest pitch (row width + 2 words) is taken for this segment.
+      TileCfg tck = pi.tc;
+      if (tile_occ_smem_bytes(tck, s->host.R) == 0) {
+        TileCfg narrow = pi.tc;
+        narrow.P = pi.d.wx + 2;
+        if (narrow.P <= 31 && tile_occ_smem_bytes(narrow, s->host.R) > 0) tck = narrow;
+      }
+      pi.tcs[k] = tck;
       int32_t *tab = nullptr, *sctab = nullptr;
-      if ((rc = E.tables(s, pi.tc, &tab, &sctab))) return rc;
+      if ((rc = E.tables(s, tck, &tab, &sctab))) return rc;
       SegDev& sd = pi.arm.seg[k];
       sd.off = s->off;
       sd.rows = s->rows;

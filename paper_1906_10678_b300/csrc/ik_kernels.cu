@@ -1287,8 +1287,9 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
 // one box to a voxel of the other, so its supercover lies in the hull of the
 // two boxes (one extra word on either side in x, read by the funnel shifts
 // for bits that the result masks away).  Larger boxes (strong relaxation)
-// keep reading the occupancy in global memory.
-constexpr int kChainOccWords = 10240;
+// keep reading the occupancy in global memory.  The box lives in the
+// kernel's dynamic shared memory (kChainOccWords words).
+constexpr int kChainOccWords = 45056;
 
 struct OccBox {
   const uint32_t* s;
@@ -1518,7 +1519,7 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
 
 __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
   __shared__ ChainShared sh;
-  __shared__ uint32_t so[kChainOccWords];
+  extern __shared__ uint32_t so[];
   const int p = blockIdx.x, S = arm.S, W = a.W;
   const long pose_sz = 3L * (S + 1);
   int32_t* poses = a.poses + (long)p * W * pose_sz;
@@ -1669,6 +1670,9 @@ cudaError_t set_kernel_attributes() {
     e = cudaFuncSetAttribute((const void*)k_propagate_tile<false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_smooth_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kChainOccWords * sizeof(uint32_t)));
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile2<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -1680,7 +1684,7 @@ cudaError_t set_kernel_attributes() {
 cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
                                 cudaStream_t st) {
   if (a.P <= 0) return cudaSuccess;
-  k_smooth_chain<<<a.P, kChainThreads, 0, st>>>(d, arm, a);
+  k_smooth_chain<<<a.P, kChainThreads, kChainOccWords * sizeof(uint32_t), st>>>(d, arm, a);
   return cudaGetLastError();
 }
 

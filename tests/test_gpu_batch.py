@@ -119,3 +119,25 @@ def test_uneven_batch_matches_single_problem_calls(ik):
         occ = O.rasterize(p.scene.shape, p.scene.boxes)
         po, fo, _ = O.reach_many(occ, p.scene.lengths, p.scene.root, [p.target], threads=8)
         assert fo[0] == r["found"] and (not fo[0] or (po[0] == r["reach"]).all())
+
+
+def test_uneven_batch_long_segments_narrow_pitch(ik):
+    """Segments of length 24 on 128^3 and 192^3 grids: their two halos take
+    the narrow shared-memory pitch in the batch engine (no edge masks); the
+    results equal the single-problem calls on grids with stored edge masks."""
+    probs = []
+    for n, lengths, seed in ((128, (24, 22, 12, 8, 6), 11), (192, (24, 16, 10, 6, 5), 12)):
+        sc = G.scaled_scene(n, lengths, 150, 4, 24, seed, f"long{n}")
+        t = G.draw_targets(sc, 1, seed)[0]
+        probs.append(G.Problem(sc, tuple(int(v) for v in t), 12))
+    out, _ = ik.ik_solve_batch([_as_dict(p) for p in probs], lanes=2)
+    for p, r in zip(probs, out):
+        sc = p.scene
+        with ik.Grid(*sc.shape) as g:
+            ik.ik_set_boxes(g.h, sc.boxes)
+            reach, found, poses, relax, status = ik.ik_reach_path_many(
+                g.h, sc.lengths, sc.root, np.asarray([p.target], np.int32), p.n_way)
+        assert r["found"] == found[0] and r["status"] == status[0], sc.name
+        if found[0]:
+            assert (r["reach"] == reach[0]).all()
+            assert (r["poses"] == poses[0]).all() and (r["relax"] == relax[0]).all(), sc.name
