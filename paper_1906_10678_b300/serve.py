@@ -62,11 +62,15 @@ class Server:
     ``static_boxes`` int32 [n][6]; ``moving`` a ``scenegen.MovingBoxes``
     (advanced in place, one step per tick); ``slots_path`` / ``slots_replan``
     default to what ``mem_budget`` bytes of survivor sets allow.
+    ``edge_masks`` False serves from a grid that keeps no per-offset edge
+    masks (segment tests walk supercovers against the tick's occupancy):
+    on large grids the masks of every tick would cost more than the tick.
     """
 
     def __init__(self, shape, root, lengths, static_boxes, moving, n_way: int = 32,
                  delta: int = 3, tick_s: float = 3.0 / 36.0, slots_path: Optional[int] = None,
-                 slots_replan: Optional[int] = None, mem_budget: float = 24e9, device: int = 0):
+                 slots_replan: Optional[int] = None, mem_budget: float = 24e9, device: int = 0,
+                 edge_masks: bool = True):
         import torch
         self.torch = torch
         torch.cuda.set_device(device)
@@ -88,6 +92,8 @@ class Server:
         self.slots_replan = slots_replan or min(64, cap)
         self.stream = torch.cuda.Stream(device=device)
         self.grid = ik.Grid(nx, ny, nz, stream=self.stream.cuda_stream)
+        if not edge_masks:
+            ik.ik_set_option(self.grid.h, ik.IK_OPT_EDGE_MASKS, 0)
         self.arm = ik.Arm(self.lengths)
         dev = torch.device("cuda", device)
         i32 = dict(dtype=torch.int32, device=dev)
