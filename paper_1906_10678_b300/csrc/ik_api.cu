@@ -62,6 +62,13 @@ struct ik_grid_s {
   unsigned long long* d_counters = nullptr;
   bool capturing = false;  // inside ik_batch_capture: no allocation, no host transfer
   bool use_masks = true;   // store per-offset edge masks (else walk supercovers on the fly)
+  // Captured batches hold device pointers of this grid.  A buffer replaced
+  // while any batch lives is retired (freed when the last batch goes), and
+  // every replacement or mask-layout change bumps buf_gen, so that a replay
+  // knows whether its buffers are still the grid's.
+  int live_batches = 0;
+  std::vector<void*> retired;
+  uint64_t buf_gen = 0;
 };
 
 struct ik_batch_s {
@@ -70,6 +77,8 @@ struct ik_batch_s {
   cudaGraphExec_t exec = nullptr;
   int root[3] = {0, 0, 0};
   std::vector<std::pair<int, int>> key;  // the arm's shells
+  uint64_t gen = 0;                      // the grid's buf_gen at capture
+  int32_t* d_root = nullptr;             // device copy of root, read by the graph
 };
 
 namespace {
@@ -160,13 +169,27 @@ unsigned long long* counters(ik_grid g, int id) {
 
 // Grow a device buffer to at least `bytes`; contents are not kept.  With
 // `zero`, a newly allocated buffer is cleared.
+// Gives up a device buffer: freed, or kept for the captured batches that
+// still write it.
+int release(ik_grid g, void* p) {
+  if (!p) return IK_OK;
+  ++g->buf_gen;
+  if (g->live_batches > 0) {
+    g->retired.push_back(p);
+    return IK_OK;
+  }
+  CK(cudaStreamSynchronize(g->st));
+  CK(cudaFree(p));
+  return IK_OK;
+}
+
 int ensure(ik_grid g, DevBuf& b, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return IK_OK;
   if (g->capturing) return IK_ERR_STATE;  // buffers are sized by the warm-up run
   if (b.p) {
-    CK(cudaStreamSynchronize(g->st));
-    CK(cudaFree(b.p));
+    int rc = release(g, b.p);
+    if (rc) return rc;
     b.p = nullptr;
     b.bytes = 0;
   }
@@ -262,42 +285,94 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
   return IK_OK;
 }
 
-// Edge masks of a shell for the current occupancy (recomputed when stale).
-int ensure_masks(ik_grid g, ShellDev* s) {
-  if (s->mask_version == g->version && s->d_mask) return IK_OK;
-  if (!s->d_mask) {
-    const size_t bytes = s->host.off.size() * (size_t)g->d.nw * 4;
+// Edge masks of a shell for the current occupancy over (at least) the word
+// box `need`; recomputed when stale.  Masks still valid for another box keep
+// it: the new box is the union of both.
+int ensure_masks(ik_grid g, ShellDev* s, const MaskBox& need) {
+  const bool valid = s->d_mask && s->mask_version == g->version;
+  if (valid && s->mbox.contains(need)) return IK_OK;
+  if (g->capturing) return IK_ERR_STATE;
+  MaskBox b = need;
+  if (valid) {
+    b.wx0 = std::min(b.wx0, s->mbox.wx0);
+    b.y0 = std::min(b.y0, s->mbox.y0);
+    b.z0 = std::min(b.z0, s->mbox.z0);
+    b.wx1 = std::max(b.wx1, s->mbox.wx1);
+    b.y1 = std::max(b.y1, s->mbox.y1);
+    b.z1 = std::max(b.z1, s->mbox.z1);
+  }
+  const size_t bytes = s->host.off.size() * (size_t)b.words() * 4;
+  if (bytes > s->mask_bytes) {
+    int rc = release(g, s->d_mask);
+    if (rc) return rc;
+    s->d_mask = nullptr;
+    s->mask_bytes = 0;
     cudaError_t e = cudaMalloc(&s->d_mask, bytes);
     if (e != cudaSuccess) {
       s->d_mask = nullptr;
       return fail_cuda(e);
     }
+    s->mask_bytes = bytes;
   }
+  if (memcmp(&b, &s->mbox, sizeof(b)) != 0) ++g->buf_gen;  // new layout of the mask rows
+  s->mbox = b;
   {
     ProfScope ps(g, P_MASKS);
-    CK(launch_edge_masks(g->d, g->tc, g->d_occ, *s, s->d_mask, g->st));
+    CK(launch_edge_masks(g->d, g->tc, g->d_occ, *s, b, s->d_mask, g->st));
   }
   s->mask_version = g->version;
   return IK_OK;
 }
 
-int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<int, int>>* key) {
+// Word box of the voxels within `reach` of `root` along every axis (the
+// positions a joint reached through segments of that summed reach can take),
+// clipped to the grid; the whole grid when root is outside it.
+MaskBox reach_box(const Dims& d, const int32_t* root, int reach) {
+  MaskBox b{0, 0, 0, d.wx - 1, d.ny - 1, d.nz - 1};
+  if (!root || root[0] < 0 || root[0] >= d.nx || root[1] < 0 || root[1] >= d.ny || root[2] < 0 ||
+      root[2] >= d.nz)
+    return b;
+  b.wx0 = std::max(0, root[0] - reach) >> 5;
+  b.wx1 = std::min(d.nx - 1, root[0] + reach) >> 5;
+  b.y0 = std::max(0, root[1] - reach);
+  b.y1 = std::min(d.ny - 1, root[1] + reach);
+  b.z0 = std::max(0, root[2] - reach);
+  b.z1 = std::min(d.nz - 1, root[2] + reach);
+  return b;
+}
+
+// Device tables of an arm for chains rooted at `root` (host pointer).  Every
+// edge-mask word a kernel reads for segment k lies at a joint position that
+// segments 1..k can reach from the root, so segment k's masks need only the
+// word box of the root grown by the summed reach of segments 1..k.  root
+// nullptr: the caller reads no edge masks (none are built).
+int resolve_arm(ik_grid g, const ik_arm* arm, const int32_t* root, ArmDev* ad,
+                std::vector<std::pair<int, int>>* key) {
   int rc = check_arm(arm);
   if (rc) return rc;
   memset(ad, 0, sizeof(*ad));
   ad->S = arm->n_seg;
   if (key) key->clear();
+  const bool masks = g->use_masks && root;
+  ShellDev* sh[IK_MAX_SEG];
+  int reach = 0;
   for (int k = 0; k < arm->n_seg; ++k) {
     int lo2, hi2;
     shell_bounds(arm->len[k], (double)arm->tol, &lo2, &hi2);
     if (hi2 < lo2) return IK_ERR_ARG;
-    ShellDev* s = nullptr;
-    rc = get_shell(g, lo2, hi2, &s);
+    rc = get_shell(g, lo2, hi2, &sh[k]);
     if (rc) return rc;
-    if (g->use_masks) {
-      rc = ensure_masks(g, s);
+    reach += sh[k]->reach;
+    if (masks) {
+      rc = ensure_masks(g, sh[k], reach_box(g->d, root, reach));
       if (rc) return rc;
     }
+    if (key) key->push_back(std::make_pair(lo2, hi2));
+  }
+  // filled once every mask is in place (a shell shared by two segments may
+  // have grown its box for the second)
+  for (int k = 0; k < arm->n_seg; ++k) {
+    const ShellDev* s = sh[k];
     SegDev& sd = ad->seg[k];
     sd.off = s->d_off;
     sd.rows = s->d_rows;
@@ -305,14 +380,14 @@ int resolve_arm(ik_grid g, const ik_arm* arm, ArmDev* ad, std::vector<std::pair<
     sd.sctab = s->d_sctab;
     sd.sc_start = s->d_sc_start;
     sd.sc = s->d_sc;
-    sd.mask = g->use_masks ? s->d_mask : nullptr;
+    sd.mask = masks ? s->d_mask : nullptr;
+    sd.mbox = s->mbox;
     sd.occ = g->d_occ;
     sd.n = (int)s->host.off.size();
-    sd.lo2 = lo2;
-    sd.hi2 = hi2;
+    sd.lo2 = s->host.lo2;
+    sd.hi2 = s->host.hi2;
     sd.R = s->reach;
     ad->len[k] = arm->len[k];
-    if (key) key->push_back(std::make_pair(lo2, hi2));
   }
   return IK_OK;
 }
@@ -466,6 +541,7 @@ int ik_destroy_grid(ik_grid g) {
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
                     &g->b_g, &g->b_valid, &g->b_old};
   for (DevBuf* b : bufs) cudaFree(b->p);
+  for (void* p : g->retired) cudaFree(p);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   cudaFree(g->d_counters);
   cudaFree(g->d_occ);
@@ -519,7 +595,7 @@ int ik_forward_sets(ik_grid g, const ik_arm* arm, const int32_t root[3], uint32_
   if (!root || !point_inside(g->d, root)) return IK_ERR_ARG;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
   if ((rc = ensure_forward(g, ad, key, root))) return rc;
   if ((rc = copy_out(g, fsets_out, g->F.p, (size_t)(ad.S + 1) * g->d.nw * 4, on_device))) return rc;
   return sync(g);
@@ -588,7 +664,7 @@ int ik_solve_reach_many(ik_grid g, const ik_arm* arm, const int32_t root[3], con
   }
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
   if ((rc = reach_many_impl(g, ad, key, root, targets, n, poses_out, found_out, vsets_out, on_device,
                             nullptr, nullptr)))
     return rc;
@@ -675,7 +751,7 @@ int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, in
     return IK_ERR_ARG;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, reach_pose, &ad, &key))) return rc;
   const int S = ad.S;
   for (int k = 0; k <= S; ++k)
     if (!point_inside(g->d, reach_pose + 3 * k)) return IK_ERR_ARG;
@@ -734,7 +810,7 @@ int ik_validate_poses(ik_grid g, const ik_arm* arm, const int32_t* poses, int n,
   if (n < 0 || (n > 0 && (!poses || !valid_out))) return IK_ERR_ARG;
   if (n == 0) return IK_OK;
   ArmDev ad;
-  if ((rc = resolve_arm(g, arm, &ad, nullptr))) return rc;
+  if ((rc = resolve_arm(g, arm, nullptr, &ad, nullptr))) return rc;
   const int S = ad.S;
   if ((rc = to_device(g, g->b_poses, poses, (size_t)n * 12 * (S + 1)))) return rc;
   if ((rc = ensure(g, g->b_valid, (size_t)4 * n))) return rc;
@@ -751,7 +827,7 @@ int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const 
   if ((rc = check_path_params(pp))) return rc;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, reach_pose, &ad, &key))) return rc;
   const int S = ad.S, W = pp->n_way;
   const size_t pose_bytes = (size_t)12 * (S + 1);
   // the reach pose must be a valid pose of this arm in this grid
@@ -799,7 +875,7 @@ int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], cons
       if (!point_inside(g->d, targets + 3 * i)) return IK_ERR_ARG;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
   const int S = ad.S, W = pp->n_way;
   const size_t pose_bytes = (size_t)12 * (S + 1);
   int32_t *d_reach = nullptr, *d_found = nullptr;
@@ -835,7 +911,8 @@ int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], cons
 // sized by a warm-up call): rasterise the boxes, rebuild every edge mask and
 // the forward sets, then reach, waypoint sets and smooth chains.
 static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int, int>>& key,
-                              const int32_t* d_boxes, int n_boxes, const int32_t* d_targets, int n,
+                              const int32_t* d_root, const int32_t* d_boxes, int n_boxes,
+                              const int32_t* d_targets, int n,
                               const ik_path_params* pp, int32_t* d_reach, int32_t* d_found,
                               int32_t* d_poses, int32_t* d_relax, int32_t* d_status) {
   const Dims& d = g->d;
@@ -850,12 +927,12 @@ static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std
     if (std::find(done.begin(), done.end(), k) != done.end()) continue;
     done.push_back(k);
     ShellDev* sh = g->shells[k];
-    CK(launch_edge_masks(d, g->tc, g->d_occ, *sh, sh->d_mask, g->st));
+    CK(launch_edge_masks(d, g->tc, g->d_occ, *sh, sh->mbox, sh->d_mask, g->st));
   }
   uint32_t* F = ptr<uint32_t>(g->F);
   int32_t* fb = ptr<int32_t>(g->F_box);
   CK(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, g->st));
-  CK(launch_seed_points(d, ptr<int32_t>(g->b_root), 1, nullptr, g->d_occ, F, d.nw, nullptr, fb, 0, g->st));
+  CK(launch_seed_points(d, d_root, 1, nullptr, g->d_occ, F, d.nw, nullptr, fb, 0, g->st));
   for (int k = 1; k <= S; ++k)
     CK(launch_propagate(d, g->tc, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ,
                         F + k * d.nw, 0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, g->st));
@@ -865,7 +942,7 @@ static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std
   CK(launch_seed_points(d, d_targets, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr,
                         vb + 6 * S, 6L * (S + 1), g->st));
   if ((rc = backward_sets(g, ad, V, n, P_BWD_REACH, vb))) return rc;
-  CK(launch_traceback(d, ad, ptr<int32_t>(g->b_root), V, qs, n, d_reach, d_found, g->st));
+  CK(launch_traceback(d, ad, d_root, V, qs, n, d_reach, d_found, g->st));
   if ((rc = waypoint_sets_impl(g, ad, d_reach, d_found, n, W, 0, pp->eps2, pp->eps2_max))) return rc;
   CK(cudaMemcpy2DAsync(d_poses + (long)(W - 1) * 3 * (S + 1), pose_bytes * W, d_reach, pose_bytes,
                        pose_bytes, n, cudaMemcpyDeviceToDevice, g->st));
@@ -892,16 +969,21 @@ int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const 
   if ((rc = ik_reach_path_many(g, arm, root, targets_dev, n, pp, reach_dev, found_dev, poses_dev,
                                relax_dev, status_dev, 1)))
     return rc;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
-  if ((rc = to_device(g, g->b_root, root, 12))) return rc;
-  if ((rc = sync(g))) return rc;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
+  // the root is the batch's own input: ordinary calls reuse the grid's buffer
+  int32_t* d_root = nullptr;
+  CK(cudaMalloc(&d_root, 16));
+  if (cudaMemcpy(d_root, root, 12, cudaMemcpyHostToDevice) != cudaSuccess || (rc = sync(g))) {
+    cudaFree(d_root);
+    return rc ? rc : IK_ERR_CUDA;
+  }
   const bool prof = g->prof_on, cnt = g->count_on;
   g->prof_on = g->count_on = false;
   g->capturing = true;
   cudaError_t e = cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    rc = enqueue_reach_path(g, ad, key, boxes_dev, n_boxes, targets_dev, n, pp, reach_dev, found_dev,
-                            poses_dev, relax_dev, status_dev);
+    rc = enqueue_reach_path(g, ad, key, d_root, boxes_dev, n_boxes, targets_dev, n, pp, reach_dev,
+                            found_dev, poses_dev, relax_dev, status_dev);
   } else {
     rc = fail_cuda(e);
   }
@@ -911,15 +993,16 @@ int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const 
   g->prof_on = prof;
   g->count_on = cnt;
   forget_device_state(g);
-  if (rc) {
+  if (rc || e2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
-    return rc;
+    cudaFree(d_root);
+    return rc ? rc : fail_cuda(e2);
   }
-  if (e2 != cudaSuccess) return fail_cuda(e2);
   cudaGraphExec_t exec = nullptr;
   e = cudaGraphInstantiate(&exec, graph, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(graph);
+    cudaFree(d_root);
     return fail_cuda(e);
   }
   ik_batch b = new ik_batch_s();
@@ -927,7 +1010,10 @@ int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const 
   b->graph = graph;
   b->exec = exec;
   memcpy(b->root, root, 12);
+  b->d_root = d_root;
   b->key = key;
+  b->gen = g->buf_gen;
+  ++g->live_batches;
   *out = b;
   return IK_OK;
 }
@@ -939,8 +1025,11 @@ int ik_batch_launch(ik_batch b) {
   if (rc) return rc;
   CK(cudaGraphLaunch(b->exec, g->st));
   // the replay leaves a new occupancy with its edge masks and forward sets:
-  // later calls on this stream may use them as they are
+  // later calls on this stream may use them as they are, unless the grid
+  // has replaced a buffer (or a mask layout) since the capture, in which
+  // case the replay wrote buffers of its own
   forget_device_state(g);
+  if (b->gen != g->buf_gen) return IK_OK;
   if (g->use_masks)
     for (const auto& k : b->key) g->shells[k]->mask_version = g->version;
   g->f_valid = true;
@@ -956,6 +1045,12 @@ int ik_batch_destroy(ik_batch b) {
   cudaStreamSynchronize(b->g->st);
   cudaGraphExecDestroy(b->exec);
   cudaGraphDestroy(b->graph);
+  cudaFree(b->d_root);
+  ik_grid g = b->g;
+  if (--g->live_batches == 0) {
+    for (void* p : g->retired) cudaFree(p);
+    g->retired.clear();
+  }
   delete b;
   return IK_OK;
 }
@@ -971,7 +1066,7 @@ int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int n_way, 
   if (pp->n_way != n_way) return IK_ERR_ARG;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, poses_in, &ad, &key))) return rc;
   const int S = ad.S, W = n_way, c = current_idx;
   const size_t pose_bytes = (size_t)12 * (S + 1);
   const int32_t* root = poses_in;
@@ -1109,7 +1204,7 @@ int ik_replan_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const in
   if (n == 0) return IK_OK;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
-  if ((rc = resolve_arm(g, arm, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
   const int S = ad.S, W = pp->n_way;
   const size_t path_bytes = (size_t)12 * (S + 1) * W;
   if (!on_device) {
@@ -1160,8 +1255,10 @@ int ik_set_option(ik_grid g, int option, int value) {
   g->use_masks = value != 0;
   if (!g->use_masks) {
     for (auto& kv : g->shells) {
-      cudaFree(kv.second->d_mask);
+      if ((rc = release(g, kv.second->d_mask))) return rc;
       kv.second->d_mask = nullptr;
+      kv.second->mask_bytes = 0;
+      kv.second->mbox = MaskBox{0, 0, 0, -1, -1, -1};
       kv.second->mask_version = ~0ull;
     }
   }

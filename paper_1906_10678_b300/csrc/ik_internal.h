@@ -47,14 +47,31 @@ void build_shell(int lo2, int hi2, ShellHost* out);
 // Closed supercover of 0 -> d by incremental traversal; (z, y, x) order.
 void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
 
+// A box of words {wx0..wx1} x {y0..y1} x {z0..z1} (inclusive) over which
+// edge masks are stored; a mask row holds its words in (z, y, x) order.
+struct MaskBox {
+  int wx0, y0, z0, wx1, y1, z1;
+  __host__ __device__ int nwx() const { return wx1 - wx0 + 1; }
+  __host__ __device__ int nyy() const { return y1 - y0 + 1; }
+  __host__ __device__ long words() const { return (long)nwx() * nyy() * (z1 - z0 + 1); }
+  __host__ __device__ long index(int wx, int y, int z) const {
+    return ((long)(z - z0) * nyy() + (y - y0)) * nwx() + (wx - wx0);
+  }
+  __host__ __device__ bool contains(const MaskBox& o) const {
+    return o.wx0 >= wx0 && o.wx1 <= wx1 && o.y0 >= y0 && o.y1 <= y1 && o.z0 >= z0 && o.z1 <= z1;
+  }
+};
+
 // Device view of one segment's tables.
 struct SegDev {
   const int32_t* off;      // [n] packed offsets, device order (z, y, x)
   const int32_t* rows;     // [(2R+1)^2 + 1] row starts, see ShellHost
   const int32_t* sc_start; // [n + 1]
   const int32_t* sc;       // packed supercover voxels
-  const uint32_t* mask;    // [n][nw] edge masks: bit of voxel p in row e = segment p -> p + off[e]
-                           // free; nullptr: each test walks the supercover against occ
+  const uint32_t* mask;    // [n][box words] edge masks over the word box `mbox`: bit of voxel p
+                           // in row e = segment p -> p + off[e] free; nullptr: each test walks
+                           // the supercover against occ
+  MaskBox mbox;            // words of the grid the masks cover (every word a test can read)
   int n;
   int lo2, hi2;
   int R;                   // max |component| of an offset
@@ -103,7 +120,9 @@ struct ShellDev {
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;
-  uint64_t mask_version = ~0ull;
+  size_t mask_bytes = 0;         // allocated bytes of d_mask
+  MaskBox mbox{0, 0, 0, -1, -1, -1};  // words covered by d_mask
+  uint64_t mask_version = ~0ull;  // occupancy version the masks were built for
   int reach = 0;
 };
 
@@ -111,8 +130,9 @@ struct ShellDev {
 // All launchers enqueue on `st` and return the launch error (cudaSuccess).
 cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, uint32_t* occ,
                              cudaStream_t st);
+// Edge masks of shell s over the word box b (mask rows of b.words() words).
 cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
-                              uint32_t* mask, cudaStream_t st);
+                              const MaskBox& b, uint32_t* mask, cudaStream_t st);
 // out[q] = (mask ? mask[q] : ~0) & D_seg(X[q]) for q < Q; sets are nw words
 // apart with stride `x_stride` / `out_stride` / `mask_stride` words between
 // queries (mask_stride 0: one mask shared by all queries).

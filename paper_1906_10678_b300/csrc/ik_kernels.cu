@@ -52,7 +52,7 @@ __device__ __forceinline__ bool test_bit(const uint32_t* s, long i) {
 // masks, else the supercover of e walked against the occupancy.
 __device__ __forceinline__ uint32_t edge_word(const Dims& d, const SegDev& sg, int e, long w, int wx,
                                               int y, int z) {
-  if (sg.mask) return __ldg(sg.mask + (long)e * d.nw + w);
+  if (sg.mask) return __ldg(sg.mask + (long)e * sg.mbox.words() + sg.mbox.index(wx, y, z));
   const int s1 = __ldg(sg.sc_start + e + 1);
   uint32_t blocked = 0;
   int i = __ldg(sg.sc_start + e);
@@ -152,21 +152,21 @@ cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, u
 // M_e[p] = AND over v in SC(0, e) of free(p + v): the segment p -> p + e is
 // obstacle-free.  One thread per (offset, word); the offset's supercover list
 // is uniform across the block (blockIdx.y = offset).
-__global__ void k_edge_masks(Dims d, const uint32_t* __restrict__ occ,
+__global__ void k_edge_masks(Dims d, MaskBox b, const uint32_t* __restrict__ occ,
                              const int32_t* __restrict__ sc_start, const int32_t* __restrict__ sc,
                              int n_off, uint32_t* __restrict__ mask) {
+  const long nb = b.words();
   for (int e = blockIdx.y; e < n_off; e += gridDim.y) {
     const int s0 = __ldg(sc_start + e), s1 = __ldg(sc_start + e + 1);
-    for (long w = blockIdx.x * (long)blockDim.x + threadIdx.x; w < d.nw;
-         w += (long)gridDim.x * blockDim.x) {
-      int wx, y, z;
-      word_coords(d, w, &wx, &y, &z);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nb; t += (long)gridDim.x * blockDim.x) {
+      const int wx = b.wx0 + (int)(t % b.nwx()), y = b.y0 + (int)((t / b.nwx()) % b.nyy());
+      const int z = b.z0 + (int)(t / ((long)b.nwx() * b.nyy()));
       uint32_t blocked = 0;
       for (int i = s0; i < s1 && blocked != 0xffffffffu; ++i) {
         const int32_t v = __ldg(sc + i);
         blocked |= ld_shifted(occ, d, wx, y, z, unpack_x(v), unpack_y(v), unpack_z(v));
       }
-      mask[(long)e * d.nw + w] = ~blocked;
+      mask[(long)e * nb + t] = ~blocked;
     }
   }
 }
@@ -178,13 +178,15 @@ __global__ void k_edge_masks(Dims d, const uint32_t* __restrict__ occ,
 // shared loads and a funnel shift at a precomputed delta.
 constexpr int kMaskChunk = 64;
 
-__global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, int R, int n_off,
+__global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, MaskBox b, int tiles_y,
+                                                         int R, int n_off,
                                                          const uint32_t* __restrict__ occ,
                                                          const int32_t* __restrict__ sc_start,
                                                          const int32_t* __restrict__ sctab,
                                                          uint32_t* __restrict__ mask) {
   extern __shared__ uint32_t so[];
-  const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
+  // tiles of the mask box (y and z); a tile still spans every word of its rows
+  const int y0 = b.y0 + (blockIdx.x % tiles_y) * tc.TY, z0 = b.z0 + (blockIdx.x / tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R, P = tc.P;
   {
@@ -202,8 +204,8 @@ __global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, int
   }
   __syncthreads();
   const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
-  if (warp >= tc.TZ || lane >= tc.lanes || y >= d.ny || z >= d.nz) return;
-  const long w = ((long)z * d.ny + y) * d.wx + wx;
+  if (warp >= tc.TZ || lane >= tc.lanes || y > b.y1 || z > b.z1 || wx < b.wx0 || wx > b.wx1) return;
+  const long w = b.index(wx, y, z), nb = b.words();
   const int base = ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1);
   const int e_end = min(n_off, (int)(blockIdx.y + 1) * kMaskChunk);
   for (int e = blockIdx.y * kMaskChunk; e < e_end; ++e) {
@@ -223,24 +225,26 @@ __global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, int
       const int a = base + (t >> 5);
       blocked |= __funnelshift_r(so[a], so[a + 1], t & 31);
     }
-    mask[(long)e * d.nw + w] = ~blocked;
+    mask[(long)e * nb + w] = ~blocked;
   }
 }
 
 cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
-                              uint32_t* mask, cudaStream_t st) {
+                              const MaskBox& b, uint32_t* mask, cudaStream_t st) {
   const int n = (int)s.host.off.size();
-  if (n == 0) return cudaSuccess;
+  if (n == 0 || b.words() <= 0) return cudaSuccess;
   const size_t smem = tile_smem_bytes(tc, s.reach);
   if (smem > 0 && s.d_sctab) {
-    dim3 grid(tc.tiles_y * tc.tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
-    k_edge_masks_tile<<<grid, 256, smem, st>>>(d, tc, s.reach, n, occ, s.d_sc_start, s.d_sctab, mask);
+    const int tiles_y = (b.nyy() + tc.TY - 1) / tc.TY, tiles_z = (b.z1 - b.z0 + tc.TZ) / tc.TZ;
+    dim3 grid(tiles_y * tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
+    k_edge_masks_tile<<<grid, 256, smem, st>>>(d, tc, b, tiles_y, s.reach, n, occ, s.d_sc_start,
+                                               s.d_sctab, mask);
     return cudaGetLastError();
   }
   const int block = 256;
-  const int gx = max(1, min(grid_for(d.nw, block), 64));
+  const int gx = max(1, min(grid_for(b.words(), block), 64));
   dim3 grid(gx, min(n, 65535));
-  k_edge_masks<<<grid, block, 0, st>>>(d, occ, s.d_sc_start, s.d_sc, n, mask);
+  k_edge_masks<<<grid, block, 0, st>>>(d, b, occ, s.d_sc_start, s.d_sc, n, mask);
   return cudaGetLastError();
 }
 

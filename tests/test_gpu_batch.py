@@ -141,3 +141,95 @@ def test_uneven_batch_long_segments_narrow_pitch(ik):
         if found[0]:
             assert (r["reach"] == reach[0]).all()
             assert (r["poses"] == poses[0]).all() and (r["relax"] == relax[0]).all(), sc.name
+
+
+def _scene64():
+    sc = G.scaled_scene(64, (8, 7, 6, 5), 60, 2, 8, 21, "mb64")
+    import oracle as O
+    occ = O.rasterize(sc.shape, sc.boxes)
+    # a second root away from the first (floor centre): the nearest free voxel to (14, 48, 30)
+    free = np.argwhere(occ == 0)  # (z, y, x)
+    d2 = ((free - np.array([30, 48, 14])) ** 2).sum(1)
+    z, y, x = free[np.argmin(d2)]
+    return sc, occ, (int(x), int(y), int(z))
+
+
+def _targets_near(occ, lengths, root, n, seed):
+    """n free voxels within reach of root (rejection sampling, seeded)."""
+    rng = np.random.default_rng(seed)
+    reach = sum(lengths)
+    out = []
+    while len(out) < n:
+        p = np.asarray(root) + rng.integers(-reach, reach + 1, 3)
+        if (p < 0).any() or (p >= 64).any() or occ[p[2], p[1], p[0]]:
+            continue
+        if ((p - np.asarray(root)) ** 2).sum() <= reach * reach:
+            out.append(p)
+    return np.asarray(out, np.int32)
+
+
+def test_edge_mask_boxes_for_two_roots(ik):
+    """Edge masks are stored over the box each root's chains can reach; a grid
+    used from two roots (boxes grown to their union) gives the results of
+    fresh grids, and the reach poses of the oracle."""
+    import oracle as O
+    sc, occ, root2 = _scene64()
+    t1 = _targets_near(occ, sc.lengths, sc.root, 5, 1)
+    t2 = _targets_near(occ, sc.lengths, root2, 5, 2)
+    with ik.Grid(*sc.shape) as g:
+        ik.ik_set_boxes(g.h, sc.boxes)
+        a1 = ik.ik_reach_path_many(g.h, sc.lengths, sc.root, t1, 8)
+        a2 = ik.ik_reach_path_many(g.h, sc.lengths, root2, t2, 8)
+        a1b = ik.ik_reach_path_many(g.h, sc.lengths, sc.root, t1, 8)
+    for root, t, got in ((sc.root, t1, a1), (root2, t2, a2), (sc.root, t1, a1b)):
+        with ik.Grid(*sc.shape) as g2:
+            ik.ik_set_boxes(g2.h, sc.boxes)
+            want = ik.ik_reach_path_many(g2.h, sc.lengths, root, t, 8)
+        for a, w_ in zip(got, want):
+            assert (a == w_).all()
+    po, fo, _ = O.reach_many(occ, sc.lengths, root2, t2, threads=4)
+    assert (a2[1] == fo).all() and (a2[0][fo == 1] == po[fo == 1]).all()
+
+
+def test_batch_replay_after_the_grid_replaced_its_buffers(ik):
+    """A captured batch keeps working after ordinary calls on its grid grew
+    the scratch buffers and the edge-mask boxes (the old buffers stay with the
+    batch); the grid's own later calls stay correct too."""
+    import torch
+    torch.cuda.set_device(0)
+    sc, occ, root2 = _scene64()
+    n, W, S = 4, 8, len(sc.lengths)
+    t1 = _targets_near(occ, sc.lengths, sc.root, n, 3)
+    stream = torch.cuda.Stream()
+    g = ik.Grid(*sc.shape, stream=stream.cuda_stream)
+    boxes = torch.from_numpy(sc.boxes.copy()).cuda()
+    targets = torch.from_numpy(t1.copy()).cuda()
+    outs = [torch.zeros(sz, dtype=torch.int32, device="cuda")
+            for sz in ((n, S + 1, 3), (n,), (n, W, S + 1, 3), (n, W, 2), (n,))]
+    b = ik.Batch(g.h, sc.lengths, sc.root, boxes, targets, W, *outs)
+    b.launch()
+    stream.synchronize()
+    first = [o.cpu().numpy().copy() for o in outs]
+    # ordinary calls that need larger buffers and a larger mask box
+    t_many = _targets_near(occ, sc.lengths, root2, 3 * n, 4)
+    big = ik.ik_reach_path_many(g.h, sc.lengths, root2, t_many, 2 * W)
+    for o in outs:
+        o.zero_()
+    b.launch()
+    stream.synchronize()
+    again = [o.cpu().numpy() for o in outs]
+    for a, w_ in zip(again, first):
+        assert (a == w_).all()
+    after = ik.ik_reach_path_many(g.h, sc.lengths, sc.root, t1, W)
+    b.close()
+    g.close()
+    with ik.Grid(*sc.shape) as g2:
+        ik.ik_set_boxes(g2.h, sc.boxes)
+        want1 = ik.ik_reach_path_many(g2.h, sc.lengths, sc.root, t1, W)
+        want2 = ik.ik_reach_path_many(g2.h, sc.lengths, root2, t_many, 2 * W)
+    for a, w_ in zip(first, want1):
+        assert (a == w_).all()
+    for a, w_ in zip(after, want1):
+        assert (a == w_).all()
+    for a, w_ in zip(big, want2):
+        assert (a == w_).all()
