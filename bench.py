@@ -388,19 +388,19 @@ def run_ours(args):
 
     # served form: continuous batching with moving obstacles, Poisson
     # arrivals at 200 req/s (half reach+path, half replans of live paths).
-    # Default scene: 256^3, 300 static + 16 moving boxes, served from a grid
-    # without edge masks (rebuilding 40 GB of masks every tick would cost
-    # more than the tick); --serve-scene c3 serves the 128^3 scene with masks.
+    # Default scene: 256^3, 300 static + 16 moving boxes; --serve-scene c3
+    # serves the 128^3 scene.  Edge masks are rebuilt every tick over the
+    # boxes the arm can reach (about 4 GB at 256^3); --serve-no-masks serves
+    # from a grid that walks supercovers instead.
     served = None
     if args.serve_seconds > 0:
         from paper_1906_10678_b300 import serve as SV
         g.close()
         if args.serve_scene == "c5":
             ssc, smv = G.c5_scene(3)
-            masks = False
         else:
             ssc, smv = sc, G.make_moving_boxes(sc.shape, 16, 3)
-            masks = True
+        masks = not args.serve_no_masks
         srv = SV.Server(ssc.shape, ssc.root, ssc.lengths, ssc.boxes, smv, n_way=N_WAY, delta=DELTA,
                         tick_s=3.0 / 36.0, slots_path=32, slots_replan=32, edge_masks=masks)
         reqs = SV.make_requests(ssc, 200.0, args.serve_seconds + args.serve_warmup, 3)
@@ -408,9 +408,9 @@ def run_ours(args):
         keep = [r for r in srv.finished if r.arrival >= args.serve_warmup and r.poses is not None]
         tick = np.asarray(srv.tick_ms)
         served = {
-            "scene": ("C5: 256^3, 300 static + 16 moving boxes (sides 6-16, 0.5-2 voxels/tick), "
-                      "no edge masks" if args.serve_scene == "c5" else
-                      "C3 scene (128^3) + 16 moving boxes, edge masks"),
+            "scene": ("C5: 256^3, 300 static + 16 moving boxes (sides 6-16, 0.5-2 voxels/tick)"
+                      if args.serve_scene == "c5" else "C3 scene (128^3) + 16 moving boxes"),
+            "edge_masks": masks,
             "seconds": args.serve_seconds, "warmup_s": args.serve_warmup, "rate_hz": 200.0,
             "tick_ms": 1000.0 * srv.tick_s, "ticks": int(len(tick)),
             "tick_gpu_ms_p50": round(float(np.percentile(tick, 50)), 3),
@@ -520,6 +520,8 @@ def main():
     ap.add_argument("--serve-warmup", type=float, default=2.0)
     ap.add_argument("--serve-scene", default="c5", choices=["c5", "c3"],
                     help="served workload: c5 = 256^3 with moving boxes, c3 = the 128^3 scene")
+    ap.add_argument("--serve-no-masks", action="store_true",
+                    help="serve from a grid without edge masks")
     ap.add_argument("--tile-depth", default="auto", choices=["auto", "8", "16"],
                     help="propagation tile depth; auto = the autotuner's choice")
     args = ap.parse_args()
