@@ -455,6 +455,10 @@ def run_ours(args):
             "path_status_counts": {str(k): int((status_np == k).sum()) for k in range(5)},
             "max_relax": int(relax_np[..., 0].max()),
             "clocks": clk,
+            # the library's kernel launches in the timed region: the per-class
+            # launch counts of the profiled step (identical to a timed step)
+            "gpu_launches": int(args.steps * sum(v["launches"] for k, v in prof.items()
+                                                 if not k.startswith("way_k"))),
             "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
                         for k, v in prof.items() if v["launches"] and not k.startswith("way_k")},
             "waypoint_levels": {k: {"ms": round(prof[k]["ms"], 3), "warp_iters": work[k]["warp_iters"],

@@ -95,8 +95,9 @@ TileCfg make_tile_cfg(const Dims& d);
 // Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).
 size_t tile_smem_bytes(const TileCfg& tc, int R);
 // Both halos (X and occupancy) of the tiled propagation without stored edge
-// masks; 0 when they do not fit in kTileOccSmemMax bytes.
-constexpr int kTileOccSmemMax = 227 * 1024;
+// masks; 0 when they do not fit in kTileOccSmemMax bytes (the 227 KiB a block
+// may opt in to, less 1 KiB for the kernel's static shared memory).
+constexpr int kTileOccSmemMax = 226 * 1024;
 size_t tile_occ_smem_bytes(const TileCfg& tc, int R);
 
 // Bounding box of a voxel set in word coordinates, kept in "min form" so

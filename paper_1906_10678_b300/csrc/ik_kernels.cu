@@ -365,16 +365,21 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
 // walk visits, per warp (one z slice), the dz range that can reach the box
 // of X and, per dz, the one contiguous run of offsets whose dy can reach it
 // from any of the warp's rows.
+// Slices of a staged halo: TZ + 2R with R <= 31 (the tiled kernels' limit).
+constexpr int kMaxSlices = 8 + 2 * 31;
+
 template <bool kCount, bool kOcc>
-__global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, TileCfg tc,
-                                                        const uint32_t* __restrict__ X, long xs,
-                                                        const uint32_t* __restrict__ mask, long ms,
-                                                        const uint32_t* __restrict__ occ,
-                                                        uint32_t* __restrict__ out, long os,
-                                                        const int32_t* __restrict__ xbox,
-                                                        int32_t* __restrict__ obox, long bs,
-                                                        unsigned long long* __restrict__ counters) {
+__device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev& seg, const TileCfg& tc,
+                                                    const uint32_t* __restrict__ X, long xs,
+                                                    const uint32_t* __restrict__ mask, long ms,
+                                                    const uint32_t* __restrict__ occ,
+                                                    uint32_t* __restrict__ out, long os,
+                                                    const int32_t* __restrict__ xbox,
+                                                    int32_t* __restrict__ obox, long bs,
+                                                    unsigned long long* __restrict__ counters) {
   extern __shared__ uint32_t sx[];
+  // per staged slice: the rows holding a non-zero source word
+  __shared__ int s_ymin[kMaxSlices], s_ymax[kMaxSlices];
   constexpr unsigned kFull = 0xffffffffu;
   const int q = blockIdx.y;
   const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
@@ -391,6 +396,11 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
   if (valid) m = (mask ? __ldg(mask + q * ms + w) : 0xffffffffu) & ~__ldg(occ + w);
   const bool touches = bx0 <= bx1 && by1 >= y0 - R && by0 <= y0 + tc.TY - 1 + R &&
                        bz1 >= z0 - R && bz0 <= z0 + tc.TZ - 1 + R;
+  if (kOcc)
+    for (int i = threadIdx.x; i < tc.TZ + 2 * R; i += blockDim.x) {
+      s_ymin[i] = 0x7fffffff;
+      s_ymax[i] = -0x7fffffff;
+    }
   if (!__syncthreads_or(touches && m != 0)) {
     if (valid) out[q * os + w] = 0u;
     return;
@@ -413,6 +423,14 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
         uint32_t v = 0u;
         if (col_in && sy >= by0 && sy <= by1) v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
         sx[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
+        if (kOcc) {
+          // one lane per staged row records a non-zero row in its slice
+          const unsigned nzb = __ballot_sync(__activemask(), v != 0);
+          if (c == 0 && ((nzb >> (sub * P)) & ((1u << P) - 1u))) {
+            atomicMin(&s_ymin[sz - z0 + R], sy);
+            atomicMax(&s_ymax[sz - z0 + R], sy);
+          }
+        }
       }
     }
   }
@@ -449,11 +467,20 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
     const int base = valid ? ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1) : (R * RY + R) * P + 1;
     bool live = m != 0;
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
+      // without stored masks (each edge test a supercover walk), only the
+      // rows of the source slice that hold a non-zero word
+      int eya = ey0, eyb = ey1;
+      if (kOcc) {
+        const int sl = z - z0 + R + ez;
+        eya = max(ey0, s_ymin[sl] - ylast);
+        eyb = min(ey1, s_ymax[sl] - y0);
+        if (eya > eyb) continue;
+      }
       const int32_t* rowp = seg.rows + (ez + R) * side + R;
-      const int e1 = __ldg(rowp + ey1 + 1);
+      const int e1 = __ldg(rowp + eyb + 1);
       const int zb = base + ez * RY * P;
-      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + ey0));
-      int e = __ldg(rowp + ey0);
+      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + eya));
+      int e = __ldg(rowp + eya);
       // Eight offsets per pass.  The edge-mask words a pass needs are decided
       // against the accumulator as it stood when the pass began and then
       // loaded together, so their (HBM) latencies overlap instead of each
@@ -526,6 +553,33 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
   }
   if (kCount && lane == 0) atomicAdd(counters + 4, warp_iters);
   if (kCount && threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
+}
+
+// The two forms as kernels: with stored edge masks the kernel keeps to 64
+// registers (four blocks per SM where shared memory allows); without them
+// the supercover walks run better with more registers (three blocks).
+template <bool kCount>
+__global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, TileCfg tc,
+                                                        const uint32_t* __restrict__ X, long xs,
+                                                        const uint32_t* __restrict__ mask, long ms,
+                                                        const uint32_t* __restrict__ occ,
+                                                        uint32_t* __restrict__ out, long os,
+                                                        const int32_t* __restrict__ xbox,
+                                                        int32_t* __restrict__ obox, long bs,
+                                                        unsigned long long* __restrict__ counters) {
+  propagate_tile_body<kCount, false>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters);
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(256, 3) k_propagate_tile_occ(Dims d, SegDev seg, TileCfg tc,
+                                                               const uint32_t* __restrict__ X, long xs,
+                                                               const uint32_t* __restrict__ mask, long ms,
+                                                               const uint32_t* __restrict__ occ,
+                                                               uint32_t* __restrict__ out, long os,
+                                                               const int32_t* __restrict__ xbox,
+                                                               int32_t* __restrict__ obox, long bs,
+                                                               unsigned long long* __restrict__ counters) {
+  propagate_tile_body<kCount, true>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters);
 }
 
 // The same propagation with a 16-slice tile: warp i computes the output
@@ -730,11 +784,11 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
   if (smem_o > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
     if (counters)
-      k_propagate_tile<true, true><<<grid, 256, smem_o, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+      k_propagate_tile_occ<true><<<grid, 256, smem_o, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
                                                               occ, out, out_stride, xbox, obox, box_stride,
                                                               counters);
     else
-      k_propagate_tile<false, true><<<grid, 256, smem_o, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+      k_propagate_tile_occ<false><<<grid, 256, smem_o, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
                                                                occ, out, out_stride, xbox, obox, box_stride,
                                                                nullptr);
     return cudaGetLastError();
@@ -743,11 +797,11 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
   if (smem > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
     if (counters)
-      k_propagate_tile<true, false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+      k_propagate_tile<true><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
                                                              occ, out, out_stride, xbox, obox, box_stride,
                                                              counters);
     else
-      k_propagate_tile<false, false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
+      k_propagate_tile<false><<<grid, 256, smem, st>>>(d, seg, tc, X, x_stride, mask, mask_stride,
                                                               occ, out, out_stride, xbox, obox, box_stride,
                                                               nullptr);
     return cudaGetLastError();
@@ -1291,19 +1345,23 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
 // one box to a voxel of the other, so its supercover lies in the hull of the
 // two boxes (one extra word on either side in x, read by the funnel shifts
 // for bits that the result masks away).  Larger boxes (strong relaxation)
-// keep reading the occupancy in global memory.  The box lives in the
-// kernel's dynamic shared memory (kChainOccWords words).
+// keep reading the occupancy in global memory.  The level's source set,
+// which lies in its own ball box, is staged the same way (with the extra
+// word on either side).  Both live in the kernel's dynamic shared memory:
+// kChainOccWords words for the occupancy, then kChainSrcWords for the source.
 constexpr int kChainOccWords = 45056;
+constexpr int kChainSrcWords = 8192;
 
+// A box of words staged in shared memory: words w0 .. w0 + nw - 1 of rows
+// y0 .. y0 + ny - 1 of slices z0 ..; ok = false when it did not fit.
 struct OccBox {
   const uint32_t* s;
   int w0, y0, z0, nw, ny;
   bool ok;
 };
 
-__device__ OccBox chain_stage_occ(const Dims& d, const SegDev& sg, const Box& a, const Box& b,
-                                  uint32_t* s) {
-  // with stored edge masks one mask word per test is cheaper than a walk
+__device__ __forceinline__ OccBox word_box(const Box& a, const Box& b, uint32_t* s, int cap, int* nz,
+                                           long* total) {
   OccBox ob;
   ob.s = s;
   ob.w0 = (min(a.x0, b.x0) >> 5) - 1;
@@ -1311,17 +1369,43 @@ __device__ OccBox chain_stage_occ(const Dims& d, const SegDev& sg, const Box& a,
   ob.z0 = min(a.z0, b.z0);
   ob.nw = (max(a.x1, b.x1) >> 5) + 1 - ob.w0 + 1;
   ob.ny = max(a.y1, b.y1) - ob.y0 + 1;
-  const int nz = max(a.z1, b.z1) - ob.z0 + 1;
-  const long total = (long)ob.nw * ob.ny * nz;
-  ob.ok = !sg.mask && total <= kChainOccWords;
-  __syncthreads();  // the previous level's readers are done with s
-  if (ob.ok) {
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int ww = ob.w0 + t % ob.nw, yy = ob.y0 + (t / ob.nw) % ob.ny, zz = ob.z0 + t / (ob.nw * ob.ny);
+  *nz = max(a.z1, b.z1) - ob.z0 + 1;
+  *total = (long)ob.nw * ob.ny * *nz;
+  ob.ok = *total <= cap;
+  return ob;
+}
+
+// Stages, for one level, the occupancy of the hull of boxes a and b and the
+// source set `src` (written earlier in this kernel: plain loads) over box sb.
+__device__ void chain_stage(const Dims& d, const SegDev& sg, const Box& a, const Box& b, const Box& sb,
+                            const uint32_t* src, uint32_t* so, OccBox* ob, OccBox* xb) {
+  int nz_o, nz_x;
+  long tot_o, tot_x;
+  // with stored edge masks one mask word per test beats a walk: no occupancy
+  *ob = word_box(a, b, so, sg.mask ? -1 : kChainOccWords, &nz_o, &tot_o);
+  *xb = word_box(sb, sb, so + kChainOccWords, src ? kChainSrcWords : -1, &nz_x, &tot_x);
+  __syncthreads();  // the previous level's readers are done with the buffers
+  if (ob->ok) {
+    uint32_t* s = so;
+    for (int t = threadIdx.x; t < tot_o; t += blockDim.x) {
+      const int ww = ob->w0 + t % ob->nw, yy = ob->y0 + (t / ob->nw) % ob->ny, zz = ob->z0 + t / (ob->nw * ob->ny);
       s[t] = (ww >= 0 && ww < d.wx) ? __ldg(sg.occ + ((long)zz * d.ny + yy) * d.wx + ww) : 0u;
     }
   }
+  if (xb->ok) {
+    uint32_t* s = so + kChainOccWords;
+    for (int t = threadIdx.x; t < tot_x; t += blockDim.x) {
+      const int ww = xb->w0 + t % xb->nw, yy = xb->y0 + (t / xb->nw) % xb->ny, zz = xb->z0 + t / (xb->nw * xb->ny);
+      s[t] = (ww >= 0 && ww < d.wx) ? src[((long)zz * d.ny + yy) * d.wx + ww] : 0u;
+    }
+  }
   __syncthreads();
+}
+
+__device__ OccBox chain_stage_occ(const Dims& d, const SegDev& sg, const Box& a, const Box& b,
+                                  uint32_t* s) {
+  OccBox ob, xb;
+  chain_stage(d, sg, a, b, a, nullptr, s, &ob, &xb);
   return ob;
 }
 
@@ -1357,8 +1441,8 @@ __device__ __forceinline__ uint32_t edge_word_box(const Dims& d, const SegDev& s
 constexpr int kG = 8;
 
 __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const OccBox& ob,
-                                                    const uint32_t* src, const Box& sb, int wx, int y,
-                                                    int z, long w, uint32_t m) {
+                                                    const OccBox& xb, const uint32_t* src, const Box& sb,
+                                                    int wx, int y, int z, long w, uint32_t m) {
   const int g = threadIdx.x % kG;
   const unsigned gmask = ((1u << kG) - 1u) << ((threadIdx.x & 31) & ~(kG - 1));
   uint32_t acc = 0;
@@ -1367,14 +1451,38 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
     const int ez0 = max(sb.z0 - z, -R), ez1 = min(sb.z1 - z, R);
     const int ey0 = max(sb.y0 - y, -R), ey1 = min(sb.y1 - y, R);
     const int exlo = sb.x0 - 32 * wx - 31, exhi = sb.x1 - 32 * wx;
+    // the source word of an offset (0 when its voxels cannot lie in sb)
+    auto source = [&](int e, int ez) -> uint32_t {
+      const int32_t o = __ldg(sg.off + e);
+      const int ex = unpack_x(o);
+      if (ex < exlo || ex > exhi) return 0u;
+      if (xb.ok) {
+        const uint32_t* row = xb.s + ((z + ez - xb.z0) * xb.ny + (y + unpack_y(o) - xb.y0)) * xb.nw +
+                              (wx + (ex >> 5) - xb.w0);
+        return __funnelshift_r(row[0], row[1], ex);  // shift taken mod 32
+      }
+      return ld_shifted_rw(src, d, wx, y, z, ex, unpack_y(o), ez);
+    };
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
       const int32_t* rowp = sg.rows + (ez + R) * side + R;
       const int e1 = __ldg(rowp + ey1 + 1);
-      for (int e = __ldg(rowp + ey0) + g; e < e1; e += kG) {
-        const int32_t o = __ldg(sg.off + e);
-        const int ex = unpack_x(o);
-        if (ex < exlo || ex > exhi) continue;
-        const uint32_t x = ld_shifted_rw(src, d, wx, y, z, ex, unpack_y(o), ez);
+      int e = __ldg(rowp + ey0) + g;
+      // four of the lane's offsets per pass: their edge tests are decided
+      // against the accumulator as the pass began and issued together, so
+      // that the latencies of their mask reads overlap
+      for (; e + 3 * kG < e1; e += 4 * kG) {
+        uint32_t x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = source(e + u * kG, ez);
+        const uint32_t want = m & ~acc;
+        uint32_t mv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mv[u] = (x[u] & want) ? edge_word_box(d, sg, ob, e + u * kG, w, wx, y, z) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc |= x[u] & mv[u];
+      }
+      for (; e < e1; e += kG) {
+        const uint32_t x = source(e, ez);
         if (x & m & ~acc) acc |= x & edge_word_box(d, sg, ob, e, w, wx, y, z);
       }
     }
@@ -1398,7 +1506,8 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
     const uint32_t* Vk = V + (long)k * d.nw;
     uint32_t* dst = R + (long)k * d.nw;
     const long n = box_words(b);
-    const OccBox ob = chain_stage_occ(d, sg, b, sb, so);
+    OccBox ob, xb;
+    chain_stage(d, sg, b, sb, sb, src, so, &ob, &xb);
     int any = 0;
     // kG lanes per word; the loop bound is uniform per lane group
     for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
@@ -1411,7 +1520,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = ball_bits(wx, y, z, sh.ref[k], delta2) & __ldg(Vk + w);
       }
-      const uint32_t acc = restricted_word(d, sg, ob, src, sb, wx, y, z, w, m);
+      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m);
       if (acc && threadIdx.x % kG == 0) {
         dst[w] = acc;
         any = 1;
@@ -1444,7 +1553,8 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
     const uint32_t* Rk = R + (long)k * d.nw;
     uint32_t* dst = U + (long)k * d.nw;
     const long n = box_words(b);
-    const OccBox ob = chain_stage_occ(d, sg, b, sb, so);
+    OccBox ob, xb;
+    chain_stage(d, sg, b, sb, sb, src, so, &ob, &xb);
     for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
       const long t = t0 + threadIdx.x / kG;
       int wx = 0, y = 0, z = 0;
@@ -1455,7 +1565,7 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = Rk[w];
       }
-      const uint32_t acc = restricted_word(d, sg, ob, src, sb, wx, y, z, w, m);
+      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m);
       if (acc && threadIdx.x % kG == 0) dst[w] = acc;
     }
     __syncthreads();
@@ -1662,20 +1772,20 @@ cudaError_t set_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute((const void*)k_edge_masks_tile,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true, false>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false, false>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile<true, true>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_occ<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile<false, true>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_occ<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_smooth_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kChainOccWords * sizeof(uint32_t)));
+                             (int)((kChainOccWords + kChainSrcWords) * sizeof(uint32_t)));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile2<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1688,7 +1798,8 @@ cudaError_t set_kernel_attributes() {
 cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
                                 cudaStream_t st) {
   if (a.P <= 0) return cudaSuccess;
-  k_smooth_chain<<<a.P, kChainThreads, kChainOccWords * sizeof(uint32_t), st>>>(d, arm, a);
+  k_smooth_chain<<<a.P, kChainThreads, (kChainOccWords + kChainSrcWords) * sizeof(uint32_t), st>>>(d, arm,
+                                                                                                   a);
   return cudaGetLastError();
 }
 
