@@ -152,6 +152,25 @@ def reach_many(occ, lengths, root, targets, want_sets: bool = False, threads: in
     return poses, found, vs
 
 
+def reach_set(occ, lengths, root, T, cone=None, tol: float = 0.5):
+    """Reach for a target set T ([nz][ny][nx], non-zero = target) with an
+    optional approach cone (ax, ay, az, num, den) on the last segment
+    (section "The gap in gMS"; see orc_reach_set).  Returns (pose [S+1][3],
+    found, vsets [S+1][nz][ny][nx])."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    lo2, hi2 = arm_bounds(lengths, tol)
+    S = len(lengths)
+    T = _u8(np.asarray(T) != 0)
+    pose = np.zeros((S + 1, 3), np.int32)
+    found = np.zeros(1, np.int32)
+    vs = np.zeros((S + 1, nz, ny, nx), np.uint8)
+    c = None if cone is None else _i32(cone)
+    _load().orc_reach_set(nx, ny, nz, _p(occ), S, _p(lo2), _p(hi2), _p(_i32(root)), _p(T),
+                          _p(c) if c is not None else None, _p(pose), _p(vs), _p(found))
+    return pose, int(found[0]), vs
+
+
 def pose_valid(occ, lengths, pose, tol: float = 0.5) -> bool:
     occ = _u8(occ)
     nx, ny, nz = _dims(occ)

@@ -592,6 +592,61 @@ int orc_reach_many(int nx, int ny, int nz, const uint8_t* occ, int S, const int3
   return 0;
 }
 
+// Approach cone on the last segment (section "The gap in gMS": the backward
+// path from the target is the set of permissible angles of attack of the
+// last segment, a single vector or a cone of them).  cone = {ax, ay, az, num,
+// den}: the segment vector s (from joint S-1 to the end effector) is
+// admissible when it points into the half-space of the axis a and its angle
+// to a is at most theta with cos^2 theta = num / den, i.e.
+//   s.a > 0  and  den * (s.a)^2 >= num * |s|^2 * |a|^2   (exact integers).
+static bool in_cone(const V3& s, const int32_t* c) {
+  const long dot = (long)s.x * c[0] + (long)s.y * c[1] + (long)s.z * c[2];
+  if (dot <= 0) return false;
+  const long s2 = sq(s.x) + sq(s.y) + sq(s.z);
+  const long a2 = sq(c[0]) + sq(c[1]) + sq(c[2]);
+  return (long)c[4] * dot * dot >= (long)c[3] * s2 * a2;
+}
+
+// The offsets of segment s (with their supercovers) that lie in the cone.
+static Segment cone_segment(const Segment& s, const int32_t* c) {
+  Segment out;
+  out.lo2 = s.lo2;
+  out.hi2 = s.hi2;
+  for (size_t i = 0; i < s.offs.size(); ++i) {
+    if (!in_cone(s.offs[i], c)) continue;
+    out.offs.push_back(s.offs[i]);
+    out.sc.push_back(s.sc[i]);
+  }
+  return out;
+}
+
+// Reach for a target set T (bytes [nvox]; a "cloud of target points",
+// section "Dynamic Obstacles") with an optional approach cone on the last
+// segment (nullptr: any direction).  F is grown with the full shells; the
+// backward sets from T and the traceback use segment S restricted to the
+// cone, so every found chain ends in T with its last segment in the cone.
+// V_S keeps its definition F_S & T.  pose_out [S+1][3]; vsets_out
+// (nullable) [S+1][nvox]; *found_out 1 / 0.
+int orc_reach_set(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                  const int32_t* hi2, const int32_t* root, const uint8_t* T, const int32_t* cone,
+                  int32_t* pose_out, uint8_t* vsets_out, int32_t* found_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  const V3 r{root[0], root[1], root[2]};
+  std::vector<Set> F = forward_sets(P, r);
+  Problem Pc = P;
+  if (cone) Pc.seg[S - 1] = cone_segment(P.seg[S - 1], cone);
+  Set t(T, T + P.g.nvox());
+  std::vector<Set> V = intersect(F, backward_sets(Pc, t));
+  std::vector<V3> pose;
+  const bool ok = traceback_min_index(Pc, V, r, &pose);
+  *found_out = ok ? 1 : 0;
+  if (!ok) pose.assign(S + 1, V3{0, 0, 0});
+  write_pose(pose, pose_out);
+  if (vsets_out)
+    for (int k = 0; k <= S; ++k) std::memcpy(vsets_out + (size_t)k * P.g.nvox(), V[k].data(), P.g.nvox());
+  return 0;
+}
+
 // Pose validity: joints inside the grid, offsets in the shells, every
 // supercover voxel free.  Returns 1 / 0.
 int orc_pose_valid(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,

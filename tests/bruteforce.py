@@ -137,14 +137,16 @@ class Chains:
             return
         yield from rec([root], first)
 
-    def joint_sets(self, root: V, targets) -> Tuple[List[set], List[set], List[tuple]]:
+    def joint_sets(self, root: V, targets, last_offsets=None) -> Tuple[List[set], List[set], List[tuple]]:
         """(F sets, V sets, all valid chains ending in ``targets``).
 
         F_k collects p_k of every valid partial chain of k segments (dead
         ends included); V_k collects p_k of every full chain ending in a free
-        target voxel.
+        target voxel.  ``last_offsets`` (optional) limits the last segment of
+        the full chains to those offsets (F is unaffected).
         """
         targets = set(tuple(int(v) for v in t) for t in targets)
+        allowed_last = None if last_offsets is None else set(tuple(int(v) for v in d) for d in last_offsets)
         F = [set() for _ in range(self.S + 1)]
         Vs = [set() for _ in range(self.S + 1)]
         good = []
@@ -154,7 +156,8 @@ class Chains:
 
         def rec(chain, k):
             if k > self.S:
-                if chain[-1] in targets:
+                last = tuple(chain[-1][i] - chain[-2][i] for i in range(3))
+                if chain[-1] in targets and (allowed_last is None or last in allowed_last):
                     good.append(tuple(chain))
                     for j, p in enumerate(chain):
                         Vs[j].add(p)

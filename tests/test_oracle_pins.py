@@ -162,6 +162,115 @@ def test_sets_and_reach_vs_enumeration(shape, lengths, n_boxes, seed):
             assert tuple(map(tuple, poses[i].tolist())) == ch.lexmin(good), t
 
 
+CONES = [((0, 0, 1), 1, 2), ((1, 0, 0), 0, 1), ((1, 1, 1), 1, 4), ((0, -1, 2), 3, 4),
+         ((-2, 1, 1), 1, 3)]
+
+
+def _cone_offsets(lo2, hi2, cone):
+    """The shell's offsets inside the cone (vectorised over the numpy mesh):
+    positive projection on the axis and cos^2 of the angle >= num / den."""
+    (ax, ay, az), num, den = cone
+    D = BF.shell_offsets(lo2, hi2).astype(np.int64)
+    a = np.array([ax, ay, az], np.int64)
+    proj = D @ a
+    keep = (proj > 0) & (den * proj * proj >= num * (D * D).sum(1) * (a @ a))
+    return D[keep]
+
+
+@pytest.mark.parametrize("scene", range(len(TINY)))
+def test_reach_set_and_cone_vs_enumeration(scene):
+    """Target clouds with an approach cone on the last segment (section "The
+    gap in gMS"): found, pose (lexicographically smallest chain) and V_k for
+    k < S against enumeration of every chain whose last segment lies in the
+    cone; V_S = F_S & T."""
+    shape, lengths, n_boxes, seed = TINY[scene]
+    rng = np.random.default_rng(500 + seed)
+    nx, ny, nz = shape
+    root = (nx // 2, ny // 2, 0)
+    boxes = _rand_scene(rng, shape, n_boxes, 3, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    ch = BF.Chains(BF.occupancy(shape, boxes), bounds)
+    S = len(lengths)
+    for ci, cone in enumerate(CONES + [None]):
+        cloud = [tuple(int(v) for v in rng.integers(0, [nx, ny, nz])) for _ in range(4)]
+        T = np.zeros(occ.shape, np.uint8)
+        for t in cloud:
+            T[t[2], t[1], t[0]] = 1
+        last = None if cone is None else _cone_offsets(*bounds[-1], cone)
+        Fb, Vb, good = ch.joint_sets(root, cloud, last_offsets=last)
+        flat = None if cone is None else (*cone[0], cone[1], cone[2])
+        pose, found, vs = O.reach_set(occ, lengths, root, T, flat)
+        assert found == bool(good), (ci, cloud)
+        if good:
+            assert tuple(map(tuple, pose.tolist())) == ch.lexmin(good), ci
+            for j in range(1, S):
+                assert (pose[j] - pose[j - 1] != 0).any()
+            if last is not None:
+                d = tuple(int(v) for v in pose[S] - pose[S - 1])
+                assert d in set(map(tuple, last.tolist()))
+        for k in range(S):
+            assert BF.to_set(vs[k]) == Vb[k], (ci, k)
+        assert BF.to_set(vs[S]) == Fb[S] & BF.to_set(T), ci
+
+
+def test_reach_cone_exact_axis_closed_form():
+    """cos^2 = 1: the last segment is exactly L along the axis, so a chain
+    exists iff the arm without its last segment reaches t - L * axis and the
+    segment from there to t is free; the pose then ends with that point."""
+    shape, lengths = (11, 11, 11), (3, 2, 3)
+    rng = np.random.default_rng(42)
+    root = (5, 5, 0)
+    boxes = _rand_scene(rng, shape, 5, 3, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    S, L = len(lengths), lengths[-1]
+    hits = 0
+    for _ in range(30):
+        t = tuple(int(v) for v in rng.integers(0, 11, 3))
+        T = np.zeros(occ.shape, np.uint8)
+        T[t[2], t[1], t[0]] = 1
+        pose, found, _ = O.reach_set(occ, lengths, root, T, (0, 0, -1, 1, 1))
+        q = (t[0], t[1], t[2] + L)  # joint S-1 straight above t
+        want = False
+        if q[2] < 11 and not occ[t[2], t[1], t[0]]:
+            p2, f2, _ = O.reach_many(occ, lengths[:-1], root, [q])
+            seg_free = all(not occ[z, t[1], t[0]] for z in range(t[2], q[2] + 1))
+            want = bool(f2[0]) and seg_free
+        assert found == want, t
+        if found:
+            hits += 1
+            assert tuple(pose[S - 1]) == q and tuple(pose[S]) == t
+    assert hits > 0
+
+
+def test_reach_set_union_law():
+    """A cloud's solution is the better of its parts: found(T1 | T2) =
+    found(T1) or found(T2), and the chosen chain is the lexicographically
+    smaller of the two parts' chains."""
+    shape, lengths, n_boxes, seed = TINY[0]
+    rng = np.random.default_rng(77)
+    nx, ny, nz = shape
+    root = (nx // 2, ny // 2, 0)
+    boxes = _rand_scene(rng, shape, n_boxes, 3, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    key = lambda p: tuple(int((q[2] * ny + q[1]) * nx + q[0]) for q in p[1:])
+    for cone in (None, (0, 0, 1, 1, 4)):
+        for _ in range(6):
+            Ts = []
+            for _ in range(2):
+                T = np.zeros(occ.shape, np.uint8)
+                for t in rng.integers(0, [nx, ny, nz], (3, 3)):
+                    T[t[2], t[1], t[0]] = 1
+                Ts.append(T)
+            p1, f1, _ = O.reach_set(occ, lengths, root, Ts[0], cone)
+            p2, f2, _ = O.reach_set(occ, lengths, root, Ts[1], cone)
+            pu, fu, _ = O.reach_set(occ, lengths, root, Ts[0] | Ts[1], cone)
+            assert fu == (f1 or f2)
+            if fu:
+                best = min([p for p, f in ((p1, f1), (p2, f2)) if f], key=key)
+                assert (pu == best).all()
+
+
 def test_backward_sets_vs_enumeration():
     shape, lengths = (8, 7, 6), (3, 2, 2)
     rng = np.random.default_rng(11)
