@@ -131,7 +131,7 @@ IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);
 
-/* ---------------------------------------------------- obstacles (step a1) */
+/* ---------------------------------------------------------- obstacles */
 /* Replace the occupancy with a bit-packed set (1 = occupied), n_words =
  * ik_grid_words(g).  Bits of x >= nx do not exist (nx % 32 == 0). */
 IK_API int ik_set_obstacles(ik_grid g, const uint32_t* occ_words, size_t n_words, int on_device);
@@ -141,7 +141,7 @@ IK_API int ik_set_obstacles(ik_grid g, const uint32_t* occ_words, size_t n_words
 IK_API int ik_set_boxes(ik_grid g, const int32_t* boxes, int n_boxes, int on_device);
 IK_API int ik_get_obstacles(ik_grid g, uint32_t* occ_words, size_t n_words, int on_device);
 
-/* ------------------------------------------------- reach IK (steps a3-a5) */
+/* ----------------------------------------------------------- reach IK */
 /* Forward reachable sets F_0..F_S (section "The procedure for IK solution",
  * Steps 1 and 2A): F_0 = {root} if free, F_k = every voxel reachable from
  * F_{k-1} by an admissible obstacle-free segment k.  fsets_out is
@@ -169,7 +169,43 @@ IK_API int ik_solve_reach_many(ik_grid g, const ik_arm* arm, const int32_t root[
                         const int32_t* targets, int n, int32_t* poses_out, int32_t* found_out,
                         uint32_t* vsets_out, int on_device);
 
-/* -------------------------------------------------- path (steps a6 - a8) */
+/* ------------------------------------------- target cones and clouds */
+/* Approach cone on the last segment (section "The gap in gMS": the backward
+ * path from the target is the set of permissible angles of attack of the
+ * last segment, one vector or a cone of them).  The segment vector s (from
+ * joint n_seg - 1 to the end effector) is admissible when s . axis > 0 and
+ * cos2_den * (s . axis)^2 >= cos2_num * |s|^2 * |axis|^2, i.e. its angle to
+ * the axis is at most theta with cos^2 theta = cos2_num / cos2_den (exact
+ * integer test).  axis != 0 with components in [-1024, 1024];
+ * 0 <= cos2_num <= cos2_den <= 1000000, cos2_den >= 1 (else IK_ERR_ARG); a
+ * cone that keeps no offset of the last segment's shell is IK_ERR_ARG. */
+typedef struct {
+  int32_t axis[3];
+  int32_t cos2_num, cos2_den;
+} ik_cone;
+
+/* ik_solve_reach_many with the last segment restricted to `cone` (nullable:
+ * no restriction, identical to ik_solve_reach_many).  The forward sets use
+ * the whole shells; the backward sets from each target and the traceback
+ * use the cone's offsets for the last segment, so a found pose ends at the
+ * target with its last segment in the cone.  V_n_seg stays F_n_seg & {target}.
+ * Arrays and on_device as for ik_solve_reach_many. */
+IK_API int ik_solve_reach_many_cone(ik_grid g, const ik_arm* arm, const ik_cone* cone,
+                                    const int32_t root[3], const int32_t* targets, int n,
+                                    int32_t* poses_out, int32_t* found_out, uint32_t* vsets_out,
+                                    int on_device);
+
+/* Reach for a target set T (a "cloud of target points", section "Dynamic
+ * Obstacles"; host bit set of ik_grid_words(g) words, same layout as the
+ * occupancy) with an optional approach cone.  V_n_seg = F_n_seg & T; the
+ * chosen pose is the minimum-index traceback of the survivor sets, so its end
+ * effector is the smallest-index voxel of T that the chain can reach.
+ * pose_out [n_seg + 1][3]; vsets_out nullable [n_seg + 1][words]; *found. */
+IK_API int ik_solve_reach_set(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int32_t root[3],
+                              const uint32_t* target_words, int32_t* pose_out, uint32_t* vsets_out,
+                              int* found);
+
+/* --------------------------------------------------------------- path */
 /* Guide waypoints on a reach pose (section "Path Planning"): W points spaced
  * evenly in nominal arc length Lambda = sum L_k along the polyline
  * p_0 .. p_S.  Waypoint j lies on segment k with
@@ -214,7 +250,7 @@ IK_API int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3
                        int n, const ik_path_params* pp, int32_t* reach_out, int32_t* found_out,
                        int32_t* poses_out, int32_t* relax_out, int32_t* status_out, int on_device);
 
-/* --------------------------------------------- batched graph (step a10) */
+/* ------------------------------------------------------ batched graph */
 /* A reach + path batch recorded once as a CUDA graph and replayed.  The
  * graph reads n_boxes boxes from boxes_dev and n targets from targets_dev
  * (device, [n][3]) each time it runs, rasterises the occupancy, rebuilds
@@ -237,7 +273,7 @@ IK_API int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3],
 IK_API int ik_batch_launch(ik_batch b);
 IK_API int ik_batch_destroy(ik_batch b);
 
-/* ------------------------------------------------- uneven batch (a10) */
+/* ------------------------------------------------------- uneven batch */
 /* One independent reach + path problem of an uneven batch: its own grid
  * (extents as in ik_create_grid), boxes (host, [n_boxes][6], inclusive),
  * arm, root, target and waypoint count. */
@@ -279,7 +315,7 @@ IK_API int ik_solve_batch(const ik_problem* probs, int n, const ik_batch_params*
                           int32_t* found_out, int32_t* reach_out, int32_t* poses_out,
                           int32_t* relax_out, int32_t* status_out, double* gpu_ms_out);
 
-/* ------------------------------------------------------- replan (step a9) */
+/* ------------------------------------------------------------- replan */
 /* Validity of n poses under the current occupancy: every joint inside the
  * grid, every offset in its shell, every segment obstacle-free.
  * poses [n][n_seg + 1][3]; valid_out [n] (1 / 0). */

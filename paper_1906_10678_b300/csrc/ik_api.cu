@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 #include <string>
@@ -38,6 +39,8 @@ struct ik_grid_s {
   uint32_t* d_occ = nullptr;
   uint64_t version = 1;
   std::map<std::pair<int, int>, ShellDev*> shells;
+  // shells restricted to an approach cone: (lo2, hi2, ax, ay, az, num, den)
+  std::map<std::array<int, 7>, ShellDev*> cone_shells;
   // forward-set cache
   bool f_valid = false;
   int f_root[3] = {0, 0, 0};
@@ -104,6 +107,7 @@ void forget_device_state(ik_grid g) {
   ++g->version;
   g->f_valid = false;
   for (auto& kv : g->shells) kv.second->mask_version = ~0ull;
+  for (auto& kv : g->cone_shells) kv.second->mask_version = ~0ull;
 }
 
 enum ProfId {
@@ -223,16 +227,11 @@ int check_arm(const ik_arm* arm) {
   return IK_OK;
 }
 
-// Shell table for (lo2, hi2), built on the host and uploaded once.
-int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
-  auto key = std::make_pair(lo2, hi2);
-  auto it = g->shells.find(key);
-  if (it != g->shells.end()) {
-    *out = it->second;
-    return IK_OK;
-  }
+// Shell table for (lo2, hi2) (restricted to `cone` when given), built on the
+// host and uploaded.
+int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out) {
   ShellDev* s = new ShellDev();
-  build_shell(lo2, hi2, &s->host);
+  build_shell(lo2, hi2, &s->host, cone);
   const size_t n = s->host.off.size();
   if (n == 0) {
     delete s;
@@ -280,8 +279,45 @@ int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
   CK(cudaMemcpyAsync(s->d_sc_start, s->host.sc_start.data(), (n + 1) * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_sc, s->host.sc.data(), s->host.sc.size() * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaStreamSynchronize(g->st));
-  g->shells[key] = s;
   *out = s;
+  return IK_OK;
+}
+
+int get_shell(ik_grid g, int lo2, int hi2, ShellDev** out) {
+  auto key = std::make_pair(lo2, hi2);
+  auto it = g->shells.find(key);
+  if (it != g->shells.end()) {
+    *out = it->second;
+    return IK_OK;
+  }
+  int rc = make_shell(g, lo2, hi2, nullptr, out);
+  if (rc) return rc;
+  g->shells[key] = *out;
+  return IK_OK;
+}
+
+int get_cone_shell(ik_grid g, int lo2, int hi2, const ik_cone& c, ShellDev** out) {
+  const std::array<int, 7> key{lo2, hi2, c.axis[0], c.axis[1], c.axis[2], c.cos2_num, c.cos2_den};
+  auto it = g->cone_shells.find(key);
+  if (it != g->cone_shells.end()) {
+    *out = it->second;
+    return IK_OK;
+  }
+  const ConeSpec cs{c.axis[0], c.axis[1], c.axis[2], c.cos2_num, c.cos2_den};
+  int rc = make_shell(g, lo2, hi2, &cs, out);
+  if (rc) return rc;
+  g->cone_shells[key] = *out;
+  return IK_OK;
+}
+
+int check_cone(const ik_cone* c) {
+  if (!c) return IK_OK;
+  const int* a = c->axis;
+  if (a[0] == 0 && a[1] == 0 && a[2] == 0) return IK_ERR_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (a[i] < -1024 || a[i] > 1024) return IK_ERR_ARG;
+  if (c->cos2_den < 1 || c->cos2_den > 1000000 || c->cos2_num < 0 || c->cos2_num > c->cos2_den)
+    return IK_ERR_ARG;
   return IK_OK;
 }
 
@@ -525,8 +561,10 @@ int ik_destroy_grid(ik_grid g) {
   if (!g) return IK_ERR_ARG;
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->st);
-  for (auto& kv : g->shells) {
-    ShellDev* s = kv.second;
+  std::vector<ShellDev*> all;
+  for (auto& kv : g->shells) all.push_back(kv.second);
+  for (auto& kv : g->cone_shells) all.push_back(kv.second);
+  for (ShellDev* s : all) {
     cudaFree(s->d_off);
     cudaFree(s->d_tab);
     cudaFree(s->d_sctab);
@@ -602,19 +640,24 @@ int ik_forward_sets(ik_grid g, const ik_arm* arm, const int32_t root[3], uint32_
 }
 
 // Reach for n targets; every array is a device pointer when on_device.
+// Reach for n targets (or, with d_tset, for the one target set d_tset).
+// `ad` grows the forward sets; `adb` (nullable: ad) runs the backward sets
+// and the traceback, so that it may restrict the last segment to a cone.
 static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int, int>>& key,
                            const int32_t* root, const int32_t* targets, int n, int32_t* poses_out,
                            int32_t* found_out, uint32_t* vsets_out, int on_device,
-                           int32_t** d_poses, int32_t** d_found) {
+                           int32_t** d_poses, int32_t** d_found, const ArmDev* adb = nullptr,
+                           const uint32_t* d_tset = nullptr) {
   const Dims& d = g->d;
   const int S = ad.S;
+  const ArmDev& ab = adb ? *adb : ad;
   int rc = ensure_forward(g, ad, key, root);
   if (rc) return rc;
   const long qs = (long)(S + 1) * d.nw;
   if ((rc = ensure(g, g->V, (size_t)n * qs * 4))) return rc;
   uint32_t* V = ptr<uint32_t>(g->V);
   const int32_t* dt = targets;
-  if (!on_device) {
+  if (!on_device && !d_tset) {
     if ((rc = to_device(g, g->b_targets, targets, (size_t)n * 12))) return rc;
     dt = ptr<int32_t>(g->b_targets);
   }
@@ -625,10 +668,13 @@ static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::p
   const uint32_t* F = ptr<uint32_t>(g->F);
   {
     ProfScope ps(g, P_SEED);
-    CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr,
-                          vb + 6 * S, 6L * (S + 1), g->st));
+    if (d_tset)
+      CK(launch_seed_set(d, d_tset, F + (long)S * d.nw, V + (long)S * d.nw, vb + 6 * S, g->st));
+    else
+      CK(launch_seed_points(d, dt, n, F + (long)S * d.nw, nullptr, V + (long)S * d.nw, qs, nullptr,
+                            vb + 6 * S, 6L * (S + 1), g->st));
   }
-  if ((rc = backward_sets(g, ad, V, n, P_BWD_REACH, vb))) return rc;
+  if ((rc = backward_sets(g, ab, V, n, P_BWD_REACH, vb))) return rc;
   int32_t* dp = poses_out;
   int32_t* df = found_out;
   if (!on_device || !poses_out || !found_out) {
@@ -639,7 +685,7 @@ static int reach_many_impl(ik_grid g, const ArmDev& ad, const std::vector<std::p
   }
   {
     ProfScope ps(g, P_TRACE);
-    CK(launch_traceback(d, ad, ptr<int32_t>(g->b_root), V, qs, n, dp, df, g->st));
+    CK(launch_traceback(d, ab, ptr<int32_t>(g->b_root), V, qs, n, dp, df, g->st));
   }
   if (!on_device) {
     if ((rc = copy_out(g, poses_out, dp, (size_t)n * 12 * (S + 1), 0))) return rc;
@@ -669,6 +715,77 @@ int ik_solve_reach_many(ik_grid g, const ik_arm* arm, const int32_t root[3], con
                             nullptr, nullptr)))
     return rc;
   return sync(g);
+}
+
+// The arm with its last segment restricted to `cone` (tables and edge masks
+// of the cone's part of the shell, over the reachable box of the root).
+static int cone_arm(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int32_t* root,
+                    const ArmDev& ad, ArmDev* adc) {
+  *adc = ad;
+  const int S = ad.S;
+  ShellDev* s = nullptr;
+  int rc = get_cone_shell(g, ad.seg[S - 1].lo2, ad.seg[S - 1].hi2, *cone, &s);
+  if (rc) return rc;
+  int reach = 0;
+  for (int k = 0; k < S; ++k) reach += ad.seg[k].R;
+  const bool masks = g->use_masks;
+  if (masks && (rc = ensure_masks(g, s, reach_box(g->d, root, reach)))) return rc;
+  SegDev& sd = adc->seg[S - 1];
+  sd.off = s->d_off;
+  sd.rows = s->d_rows;
+  sd.tab = s->d_tab;
+  sd.sctab = s->d_sctab;
+  sd.sc_start = s->d_sc_start;
+  sd.sc = s->d_sc;
+  sd.mask = masks ? s->d_mask : nullptr;
+  sd.mbox = s->mbox;
+  sd.n = (int)s->host.off.size();
+  sd.R = s->reach;
+  (void)arm;
+  return IK_OK;
+}
+
+int ik_solve_reach_many_cone(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int32_t root[3],
+                             const int32_t* targets, int n, int32_t* poses_out, int32_t* found_out,
+                             uint32_t* vsets_out, int on_device) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!root || !point_inside(g->d, root) || n < 0 || (n > 0 && !targets)) return IK_ERR_ARG;
+  if ((rc = check_cone(cone))) return rc;
+  if (n == 0) return IK_OK;
+  if (!on_device) {
+    for (int i = 0; i < n; ++i)
+      if (!point_inside(g->d, targets + 3 * i)) return IK_ERR_ARG;
+  }
+  ArmDev ad, adc;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
+  if (cone && (rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+  if ((rc = reach_many_impl(g, ad, key, root, targets, n, poses_out, found_out, vsets_out, on_device,
+                            nullptr, nullptr, cone ? &adc : nullptr)))
+    return rc;
+  return sync(g);
+}
+
+int ik_solve_reach_set(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int32_t root[3],
+                       const uint32_t* target_words, int32_t* pose_out, uint32_t* vsets_out,
+                       int* found) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!root || !point_inside(g->d, root) || !target_words || !pose_out || !found) return IK_ERR_ARG;
+  if ((rc = check_cone(cone))) return rc;
+  ArmDev ad, adc;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
+  if (cone && (rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+  if ((rc = to_device(g, g->b_old, target_words, (size_t)g->d.nw * 4))) return rc;
+  int32_t fnd = 0;
+  if ((rc = reach_many_impl(g, ad, key, root, nullptr, 1, pose_out, &fnd, vsets_out, 0, nullptr, nullptr,
+                            cone ? &adc : nullptr, ptr<uint32_t>(g->b_old))))
+    return rc;
+  if ((rc = sync(g))) return rc;
+  *found = fnd;
+  return IK_OK;
 }
 
 int ik_solve_reach(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t target[3],
@@ -1254,12 +1371,15 @@ int ik_set_option(ik_grid g, int option, int value) {
   if ((rc = sync(g))) return rc;
   g->use_masks = value != 0;
   if (!g->use_masks) {
-    for (auto& kv : g->shells) {
-      if ((rc = release(g, kv.second->d_mask))) return rc;
-      kv.second->d_mask = nullptr;
-      kv.second->mask_bytes = 0;
-      kv.second->mbox = MaskBox{0, 0, 0, -1, -1, -1};
-      kv.second->mask_version = ~0ull;
+    std::vector<ShellDev*> all;
+    for (auto& kv : g->shells) all.push_back(kv.second);
+    for (auto& kv : g->cone_shells) all.push_back(kv.second);
+    for (ShellDev* sh : all) {
+      if ((rc = release(g, sh->d_mask))) return rc;
+      sh->d_mask = nullptr;
+      sh->mask_bytes = 0;
+      sh->mbox = MaskBox{0, 0, 0, -1, -1, -1};
+      sh->mask_version = ~0ull;
     }
   }
   return IK_OK;

@@ -43,7 +43,14 @@ struct ShellHost {
 };
 
 void shell_bounds(int len, double tol, int* lo2, int* hi2);
-void build_shell(int lo2, int hi2, ShellHost* out);
+// Approach cone on a segment: offset s is kept when s.a > 0 and
+// den * (s.a)^2 >= num * |s|^2 * |a|^2 (cos^2 of the half-angle = num / den).
+struct ConeSpec {
+  int ax, ay, az, num, den;
+};
+// The shell lo2 <= |d|^2 <= hi2, or its part inside `cone` when given (R
+// stays floor(sqrt(hi2)), the reach of the whole shell).
+void build_shell(int lo2, int hi2, ShellHost* out, const ConeSpec* cone = nullptr);
 // Closed supercover of 0 -> d by incremental traversal; (z, y, x) order.
 void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
 
@@ -215,6 +222,9 @@ cudaError_t launch_replan_fix(int R, int W, int S, const int32_t* poses_in, cons
 cudaError_t launch_replan_finalize(int R, int W, int S, const int32_t* c, const int32_t* cut,
                                    const int32_t* gate, int32_t* poses, int32_t* relax,
                                    int32_t* status, cudaStream_t st);
+// out[w] = T[w] & F[w] (a target set within reach), with its word box.
+cudaError_t launch_seed_set(const Dims& d, const uint32_t* T, const uint32_t* F, uint32_t* out,
+                            int32_t* obox, cudaStream_t st);
 cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                             const int32_t* poses, int n, int32_t* valid, cudaStream_t st);
 

@@ -109,7 +109,7 @@ __device__ __forceinline__ bool edge_bit(const Dims& d, const SegDev& sg, int e,
 
 static inline int grid_for(long n, int block) { return (int)((n + block - 1) / block); }
 
-// ------------------------------------------------------- a1: rasterise boxes
+// ----------------------------------------------------------- rasterise boxes
 
 // One thread per occupancy word: OR of the x-runs of every box that covers
 // the word's row.  Boxes are staged through shared memory in chunks.
@@ -248,7 +248,7 @@ cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* 
   return cudaGetLastError();
 }
 
-// ------------------------------------------------- a3/a4: one propagation D_k
+// ------------------------------------------------------- one propagation D_k
 
 // Warp-level accumulation of the word box of the lanes whose output word is
 // non-empty: one atomicMin per component per warp.  Every lane still active
@@ -867,7 +867,7 @@ cudaError_t launch_and(const uint32_t* a, const uint32_t* b, uint32_t* out, long
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------- a5: reach traceback
+// ----------------------------------------------------------- reach traceback
 
 // One block per query.  p_0 = root; p_k = min linear index over the offsets
 // e of segment k with q = p_{k-1} + e inside the grid, q in V_k and the
@@ -974,7 +974,7 @@ cudaError_t launch_traceback_nearest_many(const Dims& d, const ArmDev& arm, cons
   return cudaGetLastError();
 }
 
-// ----------------------------------------------------- a9: batched replan
+// --------------------------------------------------------- batched replan
 
 // Per slot r (c[r] in [0, W) marks a live slot): cut = some pose after c is
 // invalid now; need = cut and the reach pose itself is invalid (re-solve it
@@ -1062,7 +1062,7 @@ cudaError_t launch_replan_finalize(int R, int W, int S, const int32_t* c, const 
   return cudaGetLastError();
 }
 
-// ------------------------------------------------ a9: validate poses (G7)
+// ------------------------------------------------------------ validate poses
 
 // Shell index of offset (x, y, z) in device order (row (z, y), then a scan
 // of the row's x offsets); -1 when the offset is not in the shell.
@@ -1103,6 +1103,25 @@ __global__ void k_validate(Dims d, ArmDev arm, const uint32_t* __restrict__ occ,
   if (!ok) atomicAnd(valid + i, 0);
 }
 
+__global__ void k_seed_set(Dims d, const uint32_t* __restrict__ T, const uint32_t* __restrict__ F,
+                           uint32_t* __restrict__ out, int32_t* __restrict__ obox) {
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  uint32_t v = 0;
+  int wx = 0, y = 0, z = 0;
+  if (w < d.nw) {
+    word_coords(d, w, &wx, &y, &z);
+    v = __ldg(T + w) & __ldg(F + w);
+    out[w] = v;
+  }
+  box_accumulate(obox, v != 0, wx, y, z);
+}
+
+cudaError_t launch_seed_set(const Dims& d, const uint32_t* T, const uint32_t* F, uint32_t* out,
+                            int32_t* obox, cudaStream_t st) {
+  k_seed_set<<<grid_for(d.nw, 256), 256, 0, st>>>(d, T, F, out, obox);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill_i32(int32_t* p, long n, int32_t v) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -1117,7 +1136,7 @@ cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* oc
   return cudaGetLastError();
 }
 
-// -------------------------------------------- a6: guide points + targets
+// ------------------------------------------------ guide points + targets
 
 // Adds voxel (x, y, z) to a min-form word box.
 __device__ __forceinline__ void box_point(int32_t* b, int x, int y, int z) {
@@ -1255,7 +1274,7 @@ cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_
   return cudaGetLastError();
 }
 
-// ------------------------------------------------- a8: smooth chain per path
+// ----------------------------------------------------- smooth chain per path
 
 // Sets written earlier in the same kernel are read with plain loads (the
 // read-only path is not coherent with in-kernel writes).

@@ -88,7 +88,15 @@ void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out) {
   for (auto& v : vox) out->push_back(pack3(v[0], v[1], v[2]));
 }
 
-void build_shell(int lo2, int hi2, ShellHost* sh) {
+static bool cone_keeps(const ConeSpec& c, long x, long y, long z) {
+  const long proj = x * c.ax + y * c.ay + z * c.az;
+  if (proj <= 0) return false;
+  const long n2 = x * x + y * y + z * z;
+  const long a2 = (long)c.ax * c.ax + (long)c.ay * c.ay + (long)c.az * c.az;
+  return (long)c.den * proj * proj >= (long)c.num * n2 * a2;
+}
+
+void build_shell(int lo2, int hi2, ShellHost* sh, const ConeSpec* cone) {
   struct Off {
     int x, y, z, n2;
   };
@@ -104,6 +112,7 @@ void build_shell(int lo2, int hi2, ShellHost* sh) {
       for (int x = -xmax; x <= xmax; ++x) {
         int ax = x < 0 ? -x : x;
         if (ax < xmin) continue;
+        if (cone && !cone_keeps(*cone, x, y, z)) continue;
         offs.push_back({x, y, z, (int)(x * x + yz)});
       }
     }

@@ -56,6 +56,11 @@ class IkProblem(ctypes.Structure):
                 ("target", ctypes.c_int32 * 3), ("n_way", ctypes.c_int32)]
 
 
+class IkCone(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_int32 * 3), ("cos2_num", ctypes.c_int32),
+                ("cos2_den", ctypes.c_int32)]
+
+
 class IkBatchParams(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_int32), ("eps2", ctypes.c_int32), ("eps2_max", ctypes.c_int32),
                 ("max_relax", ctypes.c_int32), ("lanes", ctypes.c_int32)]
@@ -81,6 +86,10 @@ _sig("ik_get_obstacles", _i, [_vp, _vp, ctypes.c_size_t, _i])
 _sig("ik_forward_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i])
 _sig("ik_solve_reach", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _vp, _vp, ctypes.POINTER(_i)])
 _sig("ik_solve_reach_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _vp, _vp, _i])
+_sig("ik_solve_reach_many_cone", _i, [_vp, ctypes.POINTER(IkArm), ctypes.POINTER(IkCone), _vp, _vp, _i,
+                                      _vp, _vp, _vp, _i])
+_sig("ik_solve_reach_set", _i, [_vp, ctypes.POINTER(IkArm), ctypes.POINTER(IkCone), _vp, _vp, _vp, _vp,
+                                ctypes.POINTER(_i)])
 _sig("ik_guide", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_waypoint_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, _i, _vp, _vp])
 _sig("ik_plan_path", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPathParams), _vp, _vp,
@@ -109,7 +118,7 @@ _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
-    "ik_solve_reach", "ik_solve_reach_many", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
+    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
     "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
@@ -275,6 +284,58 @@ def ik_solve_reach_many_device(g: int, arm, root, targets, poses, found) -> None
     _check(_lib.ik_solve_reach_many(g, ctypes.byref(arm.c), _np_ptr(_i32(root)), _dev_ptr(targets),
                                     n, _dev_ptr(poses), _dev_ptr(found), None, 1),
            "ik_solve_reach_many")
+
+
+def cone(axis, cos2_num: int, cos2_den: int) -> IkCone:
+    """Approach cone of the last segment: angle to ``axis`` at most theta with
+    cos^2 theta = cos2_num / cos2_den."""
+    c = IkCone()
+    c.axis[:] = [int(v) for v in axis]
+    c.cos2_num, c.cos2_den = int(cos2_num), int(cos2_den)
+    return c
+
+
+def _cone_ref(c):
+    return None if c is None else ctypes.byref(c)
+
+
+def ik_solve_reach_many_cone(g: int, arm, cone_, root, targets, want_sets: bool = False):
+    """Host form of ik_solve_reach_many_cone (``cone_`` an IkCone or None).
+    Returns (poses [n][S+1][3], found [n], vsets or None)."""
+    arm = _arm(arm)
+    t = _i32(targets).reshape(-1, 3)
+    n = len(t)
+    poses = np.zeros((n, arm.S + 1, 3), np.int32)
+    found = np.zeros(n, np.int32)
+    vs = np.zeros((n, arm.S + 1, ik_grid_words(g)), np.uint32) if want_sets else None
+    _check(_lib.ik_solve_reach_many_cone(g, ctypes.byref(arm.c), _cone_ref(cone_), _np_ptr(_i32(root)),
+                                         _np_ptr(t), n, _np_ptr(poses), _np_ptr(found), _np_ptr(vs), 0),
+           "ik_solve_reach_many_cone")
+    return poses, found, vs
+
+
+def ik_solve_reach_many_cone_device(g: int, arm, cone_, root, targets, poses, found) -> None:
+    """Device form: ``targets``, ``poses`` and ``found`` are int32 CUDA tensors."""
+    arm = _arm(arm)
+    _check(_lib.ik_solve_reach_many_cone(g, ctypes.byref(arm.c), _cone_ref(cone_), _np_ptr(_i32(root)),
+                                         _dev_ptr(targets), targets.shape[0], _dev_ptr(poses),
+                                         _dev_ptr(found), None, 1), "ik_solve_reach_many_cone")
+
+
+def ik_solve_reach_set(g: int, arm, cone_, root, target_words, want_sets: bool = False):
+    """Reach for a target set (packed words, as ``pack_bits`` gives) with an
+    optional approach cone.  Returns (pose [S+1][3], found, vsets or None)."""
+    arm = _arm(arm)
+    tw = np.ascontiguousarray(target_words, dtype=np.uint32).reshape(-1)
+    if tw.size != ik_grid_words(g):
+        raise ValueError("target_words must hold ik_grid_words(g) words")
+    pose = np.zeros((arm.S + 1, 3), np.int32)
+    vs = np.zeros((arm.S + 1, ik_grid_words(g)), np.uint32) if want_sets else None
+    found = ctypes.c_int(0)
+    _check(_lib.ik_solve_reach_set(g, ctypes.byref(arm.c), _cone_ref(cone_), _np_ptr(_i32(root)),
+                                   _np_ptr(tw), _np_ptr(pose), _np_ptr(vs), ctypes.byref(found)),
+           "ik_solve_reach_set")
+    return pose, found.value, vs
 
 
 def ik_guide(g: int, arm, reach_pose, n_way: int) -> np.ndarray:

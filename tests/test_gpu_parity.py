@@ -52,7 +52,7 @@ def test_rasterize(ik, shape, n_boxes, seed):
         assert (ik.ik_get_obstacles(g.h) == want).all()
 
 
-# ------------------------------------------------------------- a3 / a4 / a5
+# ------------------------------------------- forward, survivor sets, reach
 
 @pytest.mark.parametrize("seed", range(8))
 def test_forward_sets_c1(ik, seed):
@@ -137,7 +137,7 @@ def test_edge_cases(ik):
             assert fg.tolist() == [1, 0]
 
 
-# ------------------------------------------------------------ a6 / a7 / a8
+# ------------------------------------------- guide, waypoint sets, chain
 
 def _reachable(sc, occ, n, seed):
     targets = G.draw_targets(sc, n, seed)
