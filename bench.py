@@ -15,6 +15,7 @@ each rank solves its own batch (weak scaling, replicas only).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -111,6 +112,20 @@ SMS, SCHEDULERS, LANES = 148, 4, 32
 OPS_PER_PAIR = 3  # funnel shift of the input word, AND with the edge mask, OR into the output
 
 
+# DRAM bytes (read + write) per launch of the waypoint pass on this workload
+# from one ncu capture of bench.py (profiles/dram_waypoint_pass_128.md), with
+# the SHA-256 of the kernel source it was taken on: reported only while that
+# source is unchanged.
+TRAFFIC_CAPTURE = {"bytes_per_launch": None, "kernels_sha256": None}
+
+
+def kernel_traffic():
+    src = os.path.join(ROOT, "paper_1906_10678_b300", "csrc", "ik_kernels.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return TRAFFIC_CAPTURE["bytes_per_launch"] if sha == TRAFFIC_CAPTURE["kernels_sha256"] else None
+
+
 def roofline(prof, work, sc, n_targets, clk):
     """Roofline of the dominant kernel (the batched backward propagation).
 
@@ -137,7 +152,7 @@ def roofline(prof, work, sc, n_targets, clk):
     achieved = ops / (ms / 1000.0) / 1e12
     return {"kernel": "k_propagate_tile (" + cls + ")", "bound": "alu",
             "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "Tops/s",
-            "frac": round(achieved / peak, 5), "traffic": None,
+            "frac": round(achieved / peak, 5), "traffic": kernel_traffic(),
             "alg_ops_per_launch": round(ops), "ms_per_launch": round(ms, 4),
             "pairs_visited": w["visited"], "pairs_nonzero": w["nonzero"],
             "mask_words_read": w["mask_words"], "warp_iters": w["warp_iters"],
@@ -386,6 +401,43 @@ def run_ours(args):
     rep_status = np.asarray(rep_status)
     cut = rep_status != ik.IK_PATH_KEPT
 
+    # approach cone on the last segment: the same 64 targets approached from
+    # above within 45 degrees (reach poses only; the occupancy, edge masks
+    # and forward sets are rebuilt every step), beside the unrestricted reach
+    cone_ = ik.cone((0, 0, -1), 1, 2)
+    cposes = torch.zeros((N_TARGETS, S + 1, 3), dtype=torch.int32, device=dev)
+    cfound = torch.zeros(N_TARGETS, dtype=torch.int32, device=dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def cone_step():
+        ik.ik_set_boxes(g.h, boxes_d)
+        ik.ik_solve_reach_many_cone_device(g.h, arm, cone_, sc.root, targets_d, cposes, cfound)
+
+    def reach_step():
+        ik.ik_set_boxes(g.h, boxes_d)
+        ik.ik_solve_reach_many_device(g.h, arm, sc.root, targets_d, cposes, cfound)
+
+    ms_reach = timed(reach_step)
+    found_reach = int(cfound.sum().item())
+    ms_cone = timed(cone_step)
+    cone_res = {"value": round(N_TARGETS / (ms_cone / 1000.0), 2), "unit": "reach solves/s",
+                "ms_per_batch": round(ms_cone, 3), "found": int(cfound.sum().item()),
+                "no_cone": {"value": round(N_TARGETS / (ms_reach / 1000.0), 2),
+                            "ms_per_batch": round(ms_reach, 3), "found": found_reach},
+                "cone": "axis (0,0,-1), cos^2 = 1/2 (45 degrees)",
+                "note": "64 targets of the 128^3 scene, reach pose only, occupancy rebuilt per batch"}
+
     # served form: continuous batching with moving obstacles, Poisson
     # arrivals at 200 req/s (half reach+path, half replans of live paths).
     # Default scene: 256^3, 300 static + 16 moving boxes; --serve-scene c3
@@ -447,6 +499,7 @@ def run_ours(args):
                        "status_counts": {str(k): int((rep_status == k).sum()) for k in range(5)},
                        "note": "host wall time per ik_replan call (C ABI, host buffers)"},
             "tuning": tuning,
+            "cone_reach": cone_res,
             "served": served,
             "no_edge_masks": {"ms_per_step": round(nomask_ms, 3) if nomask_ms else None,
                               "value": round(N_TARGETS / (nomask_ms / 1000.0), 3) if nomask_ms else None,

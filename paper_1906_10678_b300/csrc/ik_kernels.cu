@@ -1485,22 +1485,7 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
       const int32_t* rowp = sg.rows + (ez + R) * side + R;
       const int e1 = __ldg(rowp + ey1 + 1);
-      int e = __ldg(rowp + ey0) + g;
-      // four of the lane's offsets per pass: their edge tests are decided
-      // against the accumulator as the pass began and issued together, so
-      // that the latencies of their mask reads overlap
-      for (; e + 3 * kG < e1; e += 4 * kG) {
-        uint32_t x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = source(e + u * kG, ez);
-        const uint32_t want = m & ~acc;
-        uint32_t mv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) mv[u] = (x[u] & want) ? edge_word_box(d, sg, ob, e + u * kG, w, wx, y, z) : 0u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc |= x[u] & mv[u];
-      }
-      for (; e < e1; e += kG) {
+      for (int e = __ldg(rowp + ey0) + g; e < e1; e += kG) {
         const uint32_t x = source(e, ez);
         if (x & m & ~acc) acc |= x & edge_word_box(d, sg, ob, e, w, wx, y, z);
       }
