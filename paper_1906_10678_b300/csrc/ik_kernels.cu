@@ -1364,11 +1364,12 @@ __device__ void chain_clear(const Dims& d, ChainShared& sh, int S, uint32_t* R, 
 // one box to a voxel of the other, so its supercover lies in the hull of the
 // two boxes (one extra word on either side in x, read by the funnel shifts
 // for bits that the result masks away).  Larger boxes (strong relaxation)
-// keep reading the occupancy in global memory: staging a big hull every
-// level costs more than the L2-resident reads it replaces (measured).  The level's source set,
-// which lies in its own ball box, is staged the same way (with the extra
-// word on either side).  Both live in the kernel's dynamic shared memory:
-// kChainOccWords words for the occupancy, then kChainSrcWords for the source.
+// keep reading the occupancy in global memory: staging a big hull at every
+// level costs more than the L2-resident reads it replaces (measured).  The
+// level's source set, which lies in its own ball box, is staged the same way
+// (with the extra word on either side).  Both live in the kernel's dynamic
+// shared memory: kChainOccWords words for the occupancy, then kChainSrcWords
+// for the source.
 constexpr int kChainOccWords = 10240;
 constexpr int kChainSrcWords = 8192;
 
