@@ -152,6 +152,16 @@ def reach_many(occ, lengths, root, targets, want_sets: bool = False, threads: in
     return poses, found, vs
 
 
+def dilate(occ, r2: int) -> np.ndarray:
+    """Occupancy dilated by the ball |d|^2 <= r2 (section "Testing for
+    collisions"), uint8 [nz][ny][nx]."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    out = np.zeros_like(occ)
+    _load().orc_dilate(nx, ny, nz, _p(occ), int(r2), _p(out))
+    return out
+
+
 def reach_set(occ, lengths, root, T, cone=None, tol: float = 0.5):
     """Reach for a target set T ([nz][ny][nx], non-zero = target) with an
     optional approach cone (ax, ay, az, num, den) on the last segment

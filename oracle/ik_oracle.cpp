@@ -647,6 +647,30 @@ int orc_reach_set(int nx, int ny, int nz, const uint8_t* occ, int S, const int32
   return 0;
 }
 
+// Obstacle dilation (section "Testing for collisions": the obstacle volumes
+// are dilated when the grid is initialised, to account for the thickness of
+// the arm and a clearance margin): out[p] = 1 when some occupied voxel q has
+// |p - q|^2 <= r2.  A plain scatter over the occupied voxels and every
+// integer offset of the ball.
+int orc_dilate(int nx, int ny, int nz, const uint8_t* occ, int r2, uint8_t* out) {
+  Grid g{nx, ny, nz};
+  std::memset(out, 0, (size_t)g.nvox());
+  int r = 0;
+  while ((long)(r + 1) * (r + 1) <= r2) ++r;
+  for (long i = 0; i < g.nvox(); ++i) {
+    if (!occ[i]) continue;
+    const V3 q = at(g, i);
+    for (int dz = -r; dz <= r; ++dz)
+      for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+          if ((long)dx * dx + (long)dy * dy + (long)dz * dz > r2) continue;
+          const int x = q.x + dx, y = q.y + dy, z = q.z + dz;
+          if (g.inside(x, y, z)) out[g.index(x, y, z)] = 1;
+        }
+  }
+  return 0;
+}
+
 // Pose validity: joints inside the grid, offsets in the shells, every
 // supercover voxel free.  Returns 1 / 0.
 int orc_pose_valid(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,

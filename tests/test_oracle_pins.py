@@ -271,6 +271,49 @@ def test_reach_set_union_law():
                 assert (pu == best).all()
 
 
+@pytest.mark.parametrize("r2", [1, 2, 3, 5, 9, 14])
+def test_dilate_single_voxel_is_the_lattice_ball(r2):
+    occ = np.zeros((15, 15, 15), np.uint8)
+    occ[7, 7, 7] = 1
+    out = O.dilate(occ, r2)
+    z, y, x = np.mgrid[0:15, 0:15, 0:15]
+    ball = (x - 7) ** 2 + (y - 7) ** 2 + (z - 7) ** 2 <= r2
+    assert (out.astype(bool) == ball).all()
+
+
+def test_dilate_matches_scipy_binary_dilation():
+    """Against scipy's binary dilation with the ball as structuring element
+    (an independent library routine), on random scenes with ragged shapes."""
+    from scipy import ndimage
+    rng = np.random.default_rng(3)
+    for shape in [(32, 9, 7), (20, 21, 11), (64, 5, 6)]:
+        nx, ny, nz = shape
+        occ = (rng.random((nz, ny, nx)) < 0.03).astype(np.uint8)
+        for r2 in (0, 1, 2, 4, 6):
+            r = int(np.floor(np.sqrt(r2)))
+            k = np.arange(-r, r + 1)
+            Z, Y, X = np.meshgrid(k, k, k, indexing="ij")
+            st = (X * X + Y * Y + Z * Z) <= r2
+            want = ndimage.binary_dilation(occ.astype(bool), structure=st)
+            assert (O.dilate(occ, r2).astype(bool) == want).all(), (shape, r2)
+
+
+def test_dilate_identity_monotone_and_composition():
+    rng = np.random.default_rng(4)
+    occ = (rng.random((10, 12, 32)) < 0.02).astype(np.uint8)
+    assert (O.dilate(occ, 0) == occ).all()
+    prev = occ
+    for r2 in (1, 2, 3, 4, 5, 6, 8, 9):
+        cur = O.dilate(occ, r2)
+        assert (cur >= prev).all()
+        prev = cur
+    # the cube of half-width 1 is the ball r2 = 3; dilating twice by it is
+    # the cube of half-width 2, which lies between the balls r2 = 4 and 12
+    once = O.dilate(occ, 3)
+    twice = O.dilate(once, 3)
+    assert (twice >= O.dilate(occ, 4)).all() and (twice <= O.dilate(occ, 12)).all()
+
+
 def test_backward_sets_vs_enumeration():
     shape, lengths = (8, 7, 6), (3, 2, 2)
     rng = np.random.default_rng(11)
