@@ -117,16 +117,24 @@ IK_API const char* ik_last_error_message(void);
 IK_API int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out);
 IK_API int ik_destroy_grid(ik_grid g);
 /* Grid options.  IK_OPT_EDGE_MASKS (default 1): keep one edge mask per shell
- * offset and word (the segment test becomes one 4-byte read; 4.9 GiB for the
- * 128^3 grid and the arm {20,18,...,6}; rebuilt when the occupancy changes).
- * With 0 every segment test walks the offset's supercover against the
- * occupancy instead: no mask memory and no rebuild, slower tests -- the
- * better choice for grids solved once or changing often.  Results are
- * identical either way. */
+ * offset and word (the segment test becomes one 4-byte read), over the words
+ * the segment's joints can reach from the root (1.7 GB for the 128^3 grid
+ * and the arm {20,18,...,6}); rebuilt when the occupancy changes.  With 0
+ * every segment test walks the offset's supercover against the occupancy
+ * instead: no mask memory and no rebuild, slower tests -- the better choice
+ * for grids solved once.  Results are identical either way. */
 #define IK_OPT_EDGE_MASKS 1
 /* IK_OPT_TILE_DEPTH: output slices per block of the propagation kernel, 8
  * (one per warp) or 16 (two per warp, default 8).  Results are identical. */
 #define IK_OPT_TILE_DEPTH 2
+/* IK_OPT_DILATE_R2 (default 0 = off, at most 100): obstacles are dilated by
+ * the ball |v|^2 <= value before anything uses them (section "Testing for
+ * collisions": the obstacle volumes are dilated when the grid is set up, to
+ * account for the arm's thickness and a clearance margin).  It applies to
+ * the current occupancy at once and to every later ik_set_obstacles /
+ * ik_set_boxes and to batches captured afterwards (a batch keeps the value it
+ * was captured with); ik_get_obstacles returns the dilated occupancy. */
+#define IK_OPT_DILATE_R2 3
 IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);

@@ -36,7 +36,9 @@ struct ik_grid_s {
   Dims d{};
   TileCfg tc{};
   cudaStream_t st = nullptr;
-  uint32_t* d_occ = nullptr;
+  uint32_t* d_occ = nullptr;      // the occupancy every kernel reads (dilated when asked)
+  uint32_t* d_occ_raw = nullptr;  // the occupancy as set, before dilation
+  int dilate_r2 = 0;
   uint64_t version = 1;
   std::map<std::pair<int, int>, ShellDev*> shells;
   // shells restricted to an approach cone: (lo2, hi2, ax, ay, az, num, den)
@@ -546,10 +548,13 @@ int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out) {
   g->st = (cudaStream_t)cuda_stream;
   e = set_kernel_attributes();
   if (e == cudaSuccess) e = cudaMalloc(&g->d_occ, g->d.nw * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_occ_raw, g->d.nw * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ, 0, g->d.nw * 4, g->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ_raw, 0, g->d.nw * 4, g->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
   if (e != cudaSuccess) {
     cudaFree(g->d_occ);
+    cudaFree(g->d_occ_raw);
     delete g;
     return fail_cuda(e);
   }
@@ -583,18 +588,29 @@ int ik_destroy_grid(ik_grid g) {
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   cudaFree(g->d_counters);
   cudaFree(g->d_occ);
+  cudaFree(g->d_occ_raw);
   delete g;
   return IK_OK;
 }
 
 size_t ik_grid_words(ik_grid g) { return g ? (size_t)g->d.nw : 0; }
 
+// d_occ from d_occ_raw: dilated by the ball |v|^2 <= dilate_r2, or a copy.
+static int apply_dilation(ik_grid g) {
+  if (g->dilate_r2 > 0)
+    CK(launch_dilate(g->d, g->d_occ_raw, g->dilate_r2, g->d_occ, g->st));
+  else
+    CK(cudaMemcpyAsync(g->d_occ, g->d_occ_raw, (size_t)g->d.nw * 4, cudaMemcpyDeviceToDevice, g->st));
+  return IK_OK;
+}
+
 int ik_set_obstacles(ik_grid g, const uint32_t* occ_words, size_t n_words, int on_device) {
   int rc = set_device(g);
   if (rc) return rc;
   if (!occ_words || n_words != (size_t)g->d.nw) return IK_ERR_ARG;
-  CK(cudaMemcpyAsync(g->d_occ, occ_words, n_words * 4,
+  CK(cudaMemcpyAsync(g->d_occ_raw, occ_words, n_words * 4,
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
+  if ((rc = apply_dilation(g))) return rc;
   ++g->version;
   return sync(g);
 }
@@ -611,7 +627,8 @@ int ik_set_boxes(ik_grid g, const int32_t* boxes, int n_boxes, int on_device) {
   }
   {
     ProfScope ps(g, P_RASTER);
-    CK(launch_rasterize(g->d, db, n_boxes, g->d_occ, g->st));
+    CK(launch_rasterize(g->d, db, n_boxes, g->d_occ_raw, g->st));
+    if ((rc = apply_dilation(g))) return rc;
   }
   ++g->version;
   return sync(g);
@@ -1037,7 +1054,8 @@ static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std
   const long qs = (long)(S + 1) * d.nw;
   const size_t pose_bytes = (size_t)12 * (S + 1);
   int rc;
-  CK(launch_rasterize(d, d_boxes, n_boxes, g->d_occ, g->st));
+  CK(launch_rasterize(d, d_boxes, n_boxes, g->d_occ_raw, g->st));
+  if ((rc = apply_dilation(g))) return rc;
   std::vector<std::pair<int, int>> done;
   for (const auto& k : key) {
     if (!g->use_masks) break;
@@ -1366,6 +1384,13 @@ int ik_set_option(ik_grid g, int option, int value) {
     if (value != 8 && value != 16) return IK_ERR_ARG;
     g->tc.depth = value;
     return IK_OK;
+  }
+  if (option == IK_OPT_DILATE_R2) {
+    if (value < 0 || value > 100) return IK_ERR_ARG;
+    g->dilate_r2 = value;
+    if ((rc = apply_dilation(g))) return rc;
+    ++g->version;
+    return sync(g);
   }
   if (option != IK_OPT_EDGE_MASKS) return IK_ERR_ARG;
   if ((rc = sync(g))) return rc;

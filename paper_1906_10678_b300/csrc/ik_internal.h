@@ -138,6 +138,8 @@ struct ShellDev {
 // All launchers enqueue on `st` and return the launch error (cudaSuccess).
 cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, uint32_t* occ,
                              cudaStream_t st);
+// dst = src dilated by the ball |v|^2 <= r2 (src != dst).
+cudaError_t launch_dilate(const Dims& d, const uint32_t* src, int r2, uint32_t* dst, cudaStream_t st);
 // Edge masks of shell s over the word box b (mask rows of b.words() words).
 cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
                               const MaskBox& b, uint32_t* mask, cudaStream_t st);

@@ -141,6 +141,34 @@ __global__ void k_rasterize(Dims d, const int32_t* __restrict__ boxes, int nb, u
   if (w < d.nw) occ[w] = acc;
 }
 
+// Obstacle dilation by the ball |v|^2 <= r2: dst[p] = OR over the ball of
+// src[p + v], one thread per word (the ball is symmetric, so this gather is
+// the dilation); each (dz, dy) row of the ball is one run of dx.
+__global__ void k_dilate(Dims d, const uint32_t* __restrict__ src, int r2, uint32_t* __restrict__ dst) {
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (w >= d.nw) return;
+  int wx, y, z;
+  word_coords(d, w, &wx, &y, &z);
+  int r = 0;
+  while ((r + 1) * (r + 1) <= r2) ++r;
+  uint32_t acc = 0;
+  for (int dz = -r; dz <= r && acc != 0xffffffffu; ++dz) {
+    for (int dy = -r; dy <= r; ++dy) {
+      const int rem = r2 - dz * dz - dy * dy;
+      if (rem < 0) continue;
+      int b = 0;
+      while ((b + 1) * (b + 1) <= rem) ++b;
+      for (int dx = -b; dx <= b; ++dx) acc |= ld_shifted(src, d, wx, y, z, dx, dy, dz);
+    }
+  }
+  dst[w] = acc;
+}
+
+cudaError_t launch_dilate(const Dims& d, const uint32_t* src, int r2, uint32_t* dst, cudaStream_t st) {
+  k_dilate<<<grid_for(d.nw, 256), 256, 0, st>>>(d, src, r2, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rasterize(const Dims& d, const int32_t* boxes, int n_boxes, uint32_t* occ,
                              cudaStream_t st) {
   k_rasterize<<<grid_for(d.nw, 256), 256, 0, st>>>(d, boxes, n_boxes, occ);

@@ -31,6 +31,7 @@ IK_OK, IK_ERR_ARG, IK_ERR_OOM, IK_ERR_CUDA, IK_ERR_TIMEOUT, IK_ERR_STATE, IK_ERR
 IK_PATH_OK, IK_PATH_RELAXED, IK_PATH_BROKEN, IK_PATH_UNREACHABLE, IK_PATH_KEPT = range(5)
 IK_OPT_EDGE_MASKS = 1
 IK_OPT_TILE_DEPTH = 2
+IK_OPT_DILATE_R2 = 3
 IK_MAX_SEG = 16
 IK_MAX_LEN = 100
 
