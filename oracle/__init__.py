@@ -114,13 +114,27 @@ def _dims(occ: np.ndarray):
     return nx, ny, nz
 
 
-def forward(occ, lengths, root, tol: float = 0.5) -> np.ndarray:
+def _limits(limits, S):
+    """Per-segment direction limits: None, or a list of S entries, each None
+    or (ax, ay, az, num, den) -> int32 [S][5] (zero rows = no limit)."""
+    if limits is None:
+        return None
+    out = np.zeros((S, 5), np.int32)
+    for k, c in enumerate(limits):
+        if c is not None:
+            out[k] = c
+    return out
+
+
+def forward(occ, lengths, root, tol: float = 0.5, limits=None) -> np.ndarray:
     occ = _u8(occ)
     nx, ny, nz = _dims(occ)
     lo2, hi2 = arm_bounds(lengths, tol)
     S = len(lengths)
     F = np.zeros((S + 1, nz, ny, nx), np.uint8)
-    _load().orc_forward(nx, ny, nz, _p(occ), S, _p(lo2), _p(hi2), _p(_i32(root)), _p(F))
+    lim = _limits(limits, S)
+    _load().orc_forward(nx, ny, nz, _p(occ), S, _p(lo2), _p(hi2), _p(_i32(root)), _p(F),
+                        _p(lim) if lim is not None else None)
     return F
 
 
@@ -135,7 +149,7 @@ def backward(occ, lengths, T, tol: float = 0.5) -> np.ndarray:
 
 
 def reach_many(occ, lengths, root, targets, want_sets: bool = False, threads: int = 1,
-               tol: float = 0.5):
+               tol: float = 0.5, limits=None):
     """Returns (poses [n][S+1][3], found [n], vsets [n][S+1][nz][ny][nx] or None)."""
     occ = _u8(occ)
     nx, ny, nz = _dims(occ)
@@ -146,9 +160,10 @@ def reach_many(occ, lengths, root, targets, want_sets: bool = False, threads: in
     poses = np.zeros((n, S + 1, 3), np.int32)
     found = np.zeros(n, np.int32)
     vs = np.zeros((n, S + 1, nz, ny, nx), np.uint8) if want_sets else None
+    lim = _limits(limits, S)
     _load().orc_reach_many(nx, ny, nz, _p(occ), S, _p(lo2), _p(hi2), _p(_i32(root)), n,
                            _p(targets), _p(poses), _p(found), _p(vs) if want_sets else None,
-                           int(threads))
+                           int(threads), _p(lim) if lim is not None else None)
     return poses, found, vs
 
 
@@ -181,12 +196,13 @@ def reach_set(occ, lengths, root, T, cone=None, tol: float = 0.5):
     return pose, int(found[0]), vs
 
 
-def pose_valid(occ, lengths, pose, tol: float = 0.5) -> bool:
+def pose_valid(occ, lengths, pose, tol: float = 0.5, limits=None) -> bool:
     occ = _u8(occ)
     nx, ny, nz = _dims(occ)
     lo2, hi2 = arm_bounds(lengths, tol)
+    lim = _limits(limits, len(lengths))
     return bool(_load().orc_pose_valid(nx, ny, nz, _p(occ), len(lengths), _p(lo2), _p(hi2),
-                                       _p(_i32(pose))))
+                                       _p(_i32(pose)), _p(lim) if lim is not None else None))
 
 
 def guide(lengths, pose, W: int) -> np.ndarray:
@@ -241,7 +257,7 @@ def smooth_step(occ, lengths, vsets, ref_pose, delta: int = 3, max_relax: int = 
 
 
 def plan_path(occ, lengths, reach_pose, W: int, delta: int = 3, eps2: int = 2,
-              eps2_max: int = 8, max_relax: int = -1, tol: float = 0.5):
+              eps2_max: int = 8, max_relax: int = -1, tol: float = 0.5, limits=None):
     """Returns (poses [W][S+1][3], relax [W][2], status)."""
     occ = _u8(occ)
     nx, ny, nz = _dims(occ)
@@ -250,9 +266,11 @@ def plan_path(occ, lengths, reach_pose, W: int, delta: int = 3, eps2: int = 2,
     poses = np.zeros((W, S + 1, 3), np.int32)
     relax = np.zeros((W, 2), np.int32)
     st = ctypes.c_int32()
+    lim = _limits(limits, S)
     _load().orc_plan_path(nx, ny, nz, _p(occ), S, _p(_i32(lengths)), _p(lo2), _p(hi2),
                           _p(_i32(reach_pose)), int(W), int(delta), int(eps2), int(eps2_max),
-                          int(max_relax), _p(poses), _p(relax), ctypes.byref(st))
+                          int(max_relax), _p(poses), _p(relax), ctypes.byref(st),
+                          _p(lim) if lim is not None else None)
     return poses, relax, st.value
 
 

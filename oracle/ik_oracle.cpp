@@ -193,9 +193,12 @@ static bool edge_free(const Problem& P, const V3& p, const std::vector<V3>& sc) 
   return true;
 }
 
+// d is one of the segment's admissible offsets (its shell, or the part of it
+// that a direction limit keeps).
 static bool is_offset_in_shell(const Segment& s, const V3& d) {
-  long n2 = (long)d.x * d.x + (long)d.y * d.y + (long)d.z * d.z;
-  return n2 >= s.lo2 && n2 <= s.hi2;
+  for (const V3& o : s.offs)
+    if (o.x == d.x && o.y == d.y && o.z == d.z) return true;
+  return false;
 }
 
 static inline V3 at(const Grid& g, long i) {
@@ -472,12 +475,50 @@ static std::vector<Set> waypoint_V(const Problem& P, const std::vector<Set>& F, 
   return intersect(F, backward_sets(P, T));
 }
 
+// Approach cone on the last segment (section "The gap in gMS": the backward
+// path from the target is the set of permissible angles of attack of the
+// last segment, a single vector or a cone of them).  cone = {ax, ay, az, num,
+// den}: the segment vector s (from joint S-1 to the end effector) is
+// admissible when it points into the half-space of the axis a and its angle
+// to a is at most theta with cos^2 theta = num / den, i.e.
+//   s.a > 0  and  den * (s.a)^2 >= num * |s|^2 * |a|^2   (exact integers).
+static bool in_cone(const V3& s, const int32_t* c) {
+  const long dot = (long)s.x * c[0] + (long)s.y * c[1] + (long)s.z * c[2];
+  if (dot <= 0) return false;
+  const long s2 = sq(s.x) + sq(s.y) + sq(s.z);
+  const long a2 = sq(c[0]) + sq(c[1]) + sq(c[2]);
+  return (long)c[4] * dot * dot >= (long)c[3] * s2 * a2;
+}
+
+// The offsets of segment s (with their supercovers) that lie in the cone.
+static Segment cone_segment(const Segment& s, const int32_t* c) {
+  Segment out;
+  out.lo2 = s.lo2;
+  out.hi2 = s.hi2;
+  for (size_t i = 0; i < s.offs.size(); ++i) {
+    if (!in_cone(s.offs[i], c)) continue;
+    out.offs.push_back(s.offs[i]);
+    out.sc.push_back(s.sc[i]);
+  }
+  return out;
+}
+
+// limits (nullable) [S][5]: per-segment direction limits (section "The
+// procedure for IK solution", Step 1 (a): joint 1 angle constraints, e.g. the
+// first segment restricted to the upper hemisphere, section "The gap in
+// gMS").  Row k = {ax, ay, az, num, den} keeps the offsets of segment k+1 in
+// that cone (the same test as in_cone); an all-zero axis leaves it whole.
 static Problem make_problem(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
-                            const int32_t* hi2) {
+                            const int32_t* hi2, const int32_t* limits = nullptr) {
   Problem P;
   P.g = Grid{nx, ny, nz};
   P.occ = occ;
-  for (int k = 0; k < S; ++k) P.seg.push_back(make_segment(lo2[k], hi2[k]));
+  for (int k = 0; k < S; ++k) {
+    Segment s = make_segment(lo2[k], hi2[k]);
+    const int32_t* c = limits ? limits + 5 * k : nullptr;
+    if (c && (c[0] != 0 || c[1] != 0 || c[2] != 0)) s = cone_segment(s, c);
+    P.seg.push_back(s);
+  }
   return P;
 }
 
@@ -540,8 +581,8 @@ int orc_rasterize(int nx, int ny, int nz, const int32_t* boxes, int nbox, uint8_
 
 // F_0..F_S as bytes, [(S+1)][nvox].
 int orc_forward(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
-                const int32_t* hi2, const int32_t* root, uint8_t* fsets) {
-  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+                const int32_t* hi2, const int32_t* root, uint8_t* fsets, const int32_t* limits) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2, limits);
   std::vector<Set> F = forward_sets(P, V3{root[0], root[1], root[2]});
   for (int k = 0; k <= S; ++k) std::memcpy(fsets + (size_t)k * P.g.nvox(), F[k].data(), P.g.nvox());
   return 0;
@@ -562,8 +603,9 @@ int orc_backward(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_
 // vsets_out (nullable) [n][S+1][nvox].  Targets are split across n_threads.
 int orc_reach_many(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
                    const int32_t* hi2, const int32_t* root, int n, const int32_t* targets,
-                   int32_t* poses_out, int32_t* found_out, uint8_t* vsets_out, int n_threads) {
-  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+                   int32_t* poses_out, int32_t* found_out, uint8_t* vsets_out, int n_threads,
+                   const int32_t* limits) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2, limits);
   const V3 r{root[0], root[1], root[2]};
   std::vector<Set> F = forward_sets(P, r);
   auto work = [&](int t0, int step) {
@@ -590,34 +632,6 @@ int orc_reach_many(int nx, int ny, int nz, const uint8_t* occ, int S, const int3
     for (auto& x : th) x.join();
   }
   return 0;
-}
-
-// Approach cone on the last segment (section "The gap in gMS": the backward
-// path from the target is the set of permissible angles of attack of the
-// last segment, a single vector or a cone of them).  cone = {ax, ay, az, num,
-// den}: the segment vector s (from joint S-1 to the end effector) is
-// admissible when it points into the half-space of the axis a and its angle
-// to a is at most theta with cos^2 theta = num / den, i.e.
-//   s.a > 0  and  den * (s.a)^2 >= num * |s|^2 * |a|^2   (exact integers).
-static bool in_cone(const V3& s, const int32_t* c) {
-  const long dot = (long)s.x * c[0] + (long)s.y * c[1] + (long)s.z * c[2];
-  if (dot <= 0) return false;
-  const long s2 = sq(s.x) + sq(s.y) + sq(s.z);
-  const long a2 = sq(c[0]) + sq(c[1]) + sq(c[2]);
-  return (long)c[4] * dot * dot >= (long)c[3] * s2 * a2;
-}
-
-// The offsets of segment s (with their supercovers) that lie in the cone.
-static Segment cone_segment(const Segment& s, const int32_t* c) {
-  Segment out;
-  out.lo2 = s.lo2;
-  out.hi2 = s.hi2;
-  for (size_t i = 0; i < s.offs.size(); ++i) {
-    if (!in_cone(s.offs[i], c)) continue;
-    out.offs.push_back(s.offs[i]);
-    out.sc.push_back(s.sc[i]);
-  }
-  return out;
 }
 
 // Reach for a target set T (bytes [nvox]; a "cloud of target points",
@@ -674,8 +688,8 @@ int orc_dilate(int nx, int ny, int nz, const uint8_t* occ, int r2, uint8_t* out)
 // Pose validity: joints inside the grid, offsets in the shells, every
 // supercover voxel free.  Returns 1 / 0.
 int orc_pose_valid(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
-                   const int32_t* hi2, const int32_t* pose) {
-  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+                   const int32_t* hi2, const int32_t* pose, const int32_t* limits) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2, limits);
   return pose_valid(P, read_pose(pose, S)) ? 1 : 0;
 }
 
@@ -731,8 +745,8 @@ int orc_waypoint_sets(int nx, int ny, int nz, const uint8_t* occ, int S, const i
 int orc_plan_path(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
                   const int32_t* lo2, const int32_t* hi2, const int32_t* reach_pose, int W,
                   int delta, int eps2, int eps2_max, int max_relax, int32_t* poses_out,
-                  int32_t* relax_out, int32_t* status_out) {
-  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+                  int32_t* relax_out, int32_t* status_out, const int32_t* limits) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2, limits);
   std::vector<V3> reach = read_pose(reach_pose, S);
   if (W < 2 || !pose_valid(P, reach)) {
     *status_out = PATH_UNREACHABLE;

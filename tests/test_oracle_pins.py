@@ -314,6 +314,95 @@ def test_dilate_identity_monotone_and_composition():
     assert (twice >= O.dilate(occ, 4)).all() and (twice <= O.dilate(occ, 12)).all()
 
 
+def _limited_chains(occ_bool, bounds, limits):
+    ch = BF.Chains(occ_bool, bounds)
+    for k, c in enumerate(limits):
+        if c is not None:
+            ch.offs[k] = [tuple(int(v) for v in d) for d in _cone_offsets(*bounds[k], (c[:3], c[3], c[4]))]
+    return ch
+
+
+LIMITS = [
+    [(0, 0, 1, 0, 1), None, None],            # first segment in the upper half-space
+    [(0, 0, 1, 1, 4), (1, 0, 0, 0, 1), None],
+    [None, (0, 1, 1, 1, 3), (0, 0, -1, 0, 1)],
+]
+
+
+@pytest.mark.parametrize("scene", range(3))
+def test_segment_limits_vs_enumeration(scene):
+    """Per-segment direction limits (Step 1 (a) of "The procedure for IK
+    solution"): F, V and the reach pose against enumeration of every chain
+    whose segments lie in their cones."""
+    shape, lengths, n_boxes, seed = TINY[scene]
+    rng = np.random.default_rng(700 + seed)
+    nx, ny, nz = shape
+    root = (nx // 2, ny // 2, 0)
+    boxes = _rand_scene(rng, shape, n_boxes, 3, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    S = len(lengths)
+    for lim in LIMITS:
+        lim = lim[:S] + [None] * max(0, S - len(lim))
+        ch = _limited_chains(BF.occupancy(shape, boxes), bounds, lim)
+        F = O.forward(occ, lengths, root, limits=lim)
+        targets = [tuple(int(v) for v in rng.integers(0, [nx, ny, nz])) for _ in range(5)]
+        poses, found, vs = O.reach_many(occ, lengths, root, targets, want_sets=True, limits=lim)
+        for i, t in enumerate(targets):
+            Fb, Vb, good = ch.joint_sets(root, [t])
+            for k in range(S + 1):
+                assert BF.to_set(F[k]) == Fb[k], ("F", k)
+                assert BF.to_set(vs[i, k]) == Vb[k], ("V", t, k)
+            assert bool(found[i]) == bool(good)
+            if good:
+                assert tuple(map(tuple, poses[i].tolist())) == ch.lexmin(good)
+                assert O.pose_valid(occ, lengths, poses[i], limits=lim)
+
+
+def test_upper_half_space_closed_form():
+    """Segment 1 limited to s_z > 0: F_1 is the unlimited F_1 above the root's
+    plane, and a pose whose first segment points down is invalid."""
+    shape, lengths = (12, 12, 10), (3, 2, 2)
+    rng = np.random.default_rng(5)
+    root = (6, 6, 3)
+    boxes = _rand_scene(rng, shape, 6, 3, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    lim = [(0, 0, 1, 0, 1), None, None]
+    F = O.forward(occ, lengths, root, limits=lim)
+    F0 = O.forward(occ, lengths, root)
+    z = np.arange(shape[2])[:, None, None]
+    assert (F[1] == (F0[1] * (z > root[2]))).all()
+    assert (F[2] <= F0[2]).all() and (F[3] <= F0[3]).all()
+    poses, found, _ = O.reach_many(occ, lengths, root, [tuple(int(v) for v in np.argwhere(F0[3])[0][::-1])])
+    if found[0] and poses[0][1][2] <= root[2]:
+        assert not O.pose_valid(occ, lengths, poses[0], limits=lim)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_plan_path_with_limits_vs_enumeration(seed):
+    rng = np.random.default_rng(800 + seed)
+    shape = (10, 10, 8)
+    lengths = (3, 3, 2)
+    root = (5, 5, 0)
+    lim = [(0, 0, 1, 1, 4), None, (0, 0, -1, 0, 1)]
+    boxes = _rand_scene(rng, shape, 5, 2, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    ch = _limited_chains(BF.occupancy(shape, boxes), bounds, lim)
+    free = np.argwhere(occ == 0)[:, ::-1]
+    for _ in range(80):
+        t = tuple(int(v) for v in free[rng.integers(len(free))])
+        poses, found, _ = O.reach_many(occ, lengths, root, [t], limits=lim)
+        if found[0]:
+            break
+    assert found[0]
+    W, delta = 6, 1
+    p_o, r_o, st = O.plan_path(occ, lengths, poses[0], W, delta=delta, eps2=1, eps2_max=4, limits=lim)
+    p_b, r_b = _brute_plan(ch, lengths, poses[0], W, delta, 1, 4)
+    assert [tuple(map(tuple, p.tolist())) for p in p_o] == p_b
+    assert r_o.tolist() == r_b
+
+
 def test_backward_sets_vs_enumeration():
     shape, lengths = (8, 7, 6), (3, 2, 2)
     rng = np.random.default_rng(11)
