@@ -213,6 +213,23 @@ IK_API int ik_solve_reach_set(ik_grid g, const ik_arm* arm, const ik_cone* cone,
                               const uint32_t* target_words, int32_t* pose_out, uint32_t* vsets_out,
                               int* found);
 
+/* Per-segment direction limits (section "The procedure for IK solution",
+ * Step 1 (a): joint 1 angle constraints -- section "The gap in gMS" gives the
+ * first segment restricted to the upper hemisphere of the quiver, or less).
+ * limits[k] restricts segment k+1's vector s = p_{k+1} - p_k to the cone of
+ * ik_cone (same test and ranges as above); an all-zero axis leaves that
+ * segment free; limits = NULL clears the arm's limits.  The limits belong to
+ * the grid and to this arm (same lengths and tol) and apply to every later
+ * call with it: forward sets, reach, waypoint sets, paths, replans,
+ * validation and batches captured afterwards.  A limit that keeps no offset
+ * of its shell makes those calls fail with IK_ERR_ARG; so does an approach
+ * cone (ik_solve_reach_many_cone / ik_solve_reach_set) for an arm whose last
+ * segment is limited.  The uneven batch (ik_solve_batch) and
+ * ik_forward_sets_noalloc do not apply limits.  Only absolute directions are
+ * expressible here: a limit on the angle between consecutive segments would
+ * need the previous segment's direction in the state of the set propagation. */
+IK_API int ik_set_segment_limits(ik_grid g, const ik_arm* arm, const ik_cone* limits);
+
 /* --------------------------------------------------------------- path */
 /* Guide waypoints on a reach pose (section "Path Planning"): W points spaced
  * evenly in nominal arc length Lambda = sum L_k along the polyline

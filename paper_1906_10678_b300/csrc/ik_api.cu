@@ -43,6 +43,8 @@ struct ik_grid_s {
   std::map<std::pair<int, int>, ShellDev*> shells;
   // shells restricted to an approach cone: (lo2, hi2, ax, ay, az, num, den)
   std::map<std::array<int, 7>, ShellDev*> cone_shells;
+  // per-segment direction limits, by arm (n_seg, lengths, tol bits)
+  std::map<std::vector<int32_t>, std::vector<ik_cone>> limits;
   // forward-set cache
   bool f_valid = false;
   int f_root[3] = {0, 0, 0};
@@ -82,6 +84,7 @@ struct ik_batch_s {
   cudaGraphExec_t exec = nullptr;
   int root[3] = {0, 0, 0};
   std::vector<std::pair<int, int>> key;  // the arm's shells
+  std::vector<ShellDev*> used;           // every table whose masks the graph rebuilds
   uint64_t gen = 0;                      // the grid's buf_gen at capture
   int32_t* d_root = nullptr;             // device copy of root, read by the graph
 };
@@ -384,47 +387,87 @@ MaskBox reach_box(const Dims& d, const int32_t* root, int reach) {
 // segments 1..k can reach from the root, so segment k's masks need only the
 // word box of the root grown by the summed reach of segments 1..k.  root
 // nullptr: the caller reads no edge masks (none are built).
+std::vector<int32_t> arm_key(const ik_arm* arm) {
+  std::vector<int32_t> k(arm->len, arm->len + arm->n_seg);
+  int32_t tb;
+  memcpy(&tb, &arm->tol, 4);
+  k.push_back(tb);
+  return k;
+}
+
+const std::vector<ik_cone>* arm_limits(ik_grid g, const ik_arm* arm) {
+  auto it = g->limits.find(arm_key(arm));
+  return it == g->limits.end() ? nullptr : &it->second;
+}
+
+bool has_axis(const ik_cone& c) { return c.axis[0] != 0 || c.axis[1] != 0 || c.axis[2] != 0; }
+
+void fill_seg(const ShellDev* s, const ik_grid g, bool masks, SegDev* sd) {
+  sd->off = s->d_off;
+  sd->rows = s->d_rows;
+  sd->tab = s->d_tab;
+  sd->sctab = s->d_sctab;
+  sd->sc_start = s->d_sc_start;
+  sd->sc = s->d_sc;
+  sd->mask = masks ? s->d_mask : nullptr;
+  sd->mbox = s->mbox;
+  sd->occ = g->d_occ;
+  sd->n = (int)s->host.off.size();
+  sd->lo2 = s->host.lo2;
+  sd->hi2 = s->host.hi2;
+  sd->R = s->reach;
+}
+
+// Device tables of an arm for chains rooted at `root` (host pointer).  Every
+// edge-mask word a kernel reads for segment k lies at a joint position that
+// segments 1..k can reach from the root, so segment k's masks need only the
+// word box of the root grown by the summed reach of segments 1..k.  root
+// nullptr: the caller reads no edge masks (none are built).  A segment with
+// a direction limit (ik_set_segment_limits) gets the cone's part of its
+// shell, and the mirrored cone for the forward gathers.  used (nullable)
+// receives every table whose edge masks the arm reads.
 int resolve_arm(ik_grid g, const ik_arm* arm, const int32_t* root, ArmDev* ad,
-                std::vector<std::pair<int, int>>* key) {
+                std::vector<std::pair<int, int>>* key, std::vector<ShellDev*>* used = nullptr) {
   int rc = check_arm(arm);
   if (rc) return rc;
   memset(ad, 0, sizeof(*ad));
   ad->S = arm->n_seg;
   if (key) key->clear();
+  if (used) used->clear();
   const bool masks = g->use_masks && root;
-  ShellDev* sh[IK_MAX_SEG];
+  const std::vector<ik_cone>* lim = arm_limits(g, arm);
+  ShellDev *sa[IK_MAX_SEG], *sf[IK_MAX_SEG];
   int reach = 0;
   for (int k = 0; k < arm->n_seg; ++k) {
     int lo2, hi2;
     shell_bounds(arm->len[k], (double)arm->tol, &lo2, &hi2);
     if (hi2 < lo2) return IK_ERR_ARG;
-    rc = get_shell(g, lo2, hi2, &sh[k]);
+    ShellDev* whole = nullptr;
+    rc = get_shell(g, lo2, hi2, &whole);
     if (rc) return rc;
-    reach += sh[k]->reach;
-    if (masks) {
-      rc = ensure_masks(g, sh[k], reach_box(g->d, root, reach));
-      if (rc) return rc;
+    reach += whole->reach;
+    sa[k] = sf[k] = whole;
+    if (lim && has_axis((*lim)[k])) {
+      ik_cone neg = (*lim)[k];
+      for (int i = 0; i < 3; ++i) neg.axis[i] = -neg.axis[i];
+      if ((rc = get_cone_shell(g, lo2, hi2, (*lim)[k], &sa[k]))) return rc;
+      if ((rc = get_cone_shell(g, lo2, hi2, neg, &sf[k]))) return rc;
     }
     if (key) key->push_back(std::make_pair(lo2, hi2));
   }
-  // filled once every mask is in place (a shell shared by two segments may
-  // have grown its box for the second)
+  // masks once every table is known (a table shared by two segments may
+  // grow its box for the second), then the device views
+  reach = 0;
   for (int k = 0; k < arm->n_seg; ++k) {
-    const ShellDev* s = sh[k];
-    SegDev& sd = ad->seg[k];
-    sd.off = s->d_off;
-    sd.rows = s->d_rows;
-    sd.tab = s->d_tab;
-    sd.sctab = s->d_sctab;
-    sd.sc_start = s->d_sc_start;
-    sd.sc = s->d_sc;
-    sd.mask = masks ? s->d_mask : nullptr;
-    sd.mbox = s->mbox;
-    sd.occ = g->d_occ;
-    sd.n = (int)s->host.off.size();
-    sd.lo2 = s->host.lo2;
-    sd.hi2 = s->host.hi2;
-    sd.R = s->reach;
+    reach += sa[k]->reach;
+    for (ShellDev* s : {sa[k], sf[k]}) {
+      if (masks && (rc = ensure_masks(g, s, reach_box(g->d, root, reach)))) return rc;
+      if (used && std::find(used->begin(), used->end(), s) == used->end()) used->push_back(s);
+    }
+  }
+  for (int k = 0; k < arm->n_seg; ++k) {
+    fill_seg(sa[k], g, masks, &ad->seg[k]);
+    fill_seg(sf[k], g, masks, &ad->segf[k]);
     ad->len[k] = arm->len[k];
   }
   return IK_OK;
@@ -458,7 +501,7 @@ int ensure_forward(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int,
   }
   for (int k = 1; k <= S; ++k) {
     ProfScope ps(g, P_FWD);
-    CK(launch_propagate(d, g->tc, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
+    CK(launch_propagate(d, g->tc, ad.segf[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ, F + k * d.nw,
                         0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, g->st, counters(g, P_FWD)));
   }
   g->f_valid = true;
@@ -740,6 +783,10 @@ static int cone_arm(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int
                     const ArmDev& ad, ArmDev* adc) {
   *adc = ad;
   const int S = ad.S;
+  // an approach cone replaces the last segment's table: with a direction
+  // limit on that segment as well the two would have to be intersected
+  const std::vector<ik_cone>* lim = arm_limits(g, arm);
+  if (lim && has_axis((*lim)[S - 1])) return IK_ERR_ARG;
   ShellDev* s = nullptr;
   int rc = get_cone_shell(g, ad.seg[S - 1].lo2, ad.seg[S - 1].hi2, *cone, &s);
   if (rc) return rc;
@@ -758,7 +805,27 @@ static int cone_arm(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int
   sd.mbox = s->mbox;
   sd.n = (int)s->host.off.size();
   sd.R = s->reach;
-  (void)arm;
+  return IK_OK;
+}
+
+int ik_set_segment_limits(ik_grid g, const ik_arm* arm, const ik_cone* limits) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if ((rc = check_arm(arm))) return rc;
+  const std::vector<int32_t> key = arm_key(arm);
+  bool any = false;
+  if (limits) {
+    for (int k = 0; k < arm->n_seg; ++k) {
+      if (!has_axis(limits[k])) continue;
+      if ((rc = check_cone(&limits[k]))) return rc;
+      any = true;
+    }
+  }
+  if (any)
+    g->limits[key] = std::vector<ik_cone>(limits, limits + arm->n_seg);
+  else
+    g->limits.erase(key);
+  g->f_valid = false;  // cached forward sets may be of the old limits
   return IK_OK;
 }
 
@@ -1044,7 +1111,7 @@ int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], cons
 // with no host transfer, allocation or synchronisation (every buffer was
 // sized by a warm-up call): rasterise the boxes, rebuild every edge mask and
 // the forward sets, then reach, waypoint sets and smooth chains.
-static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std::pair<int, int>>& key,
+static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<ShellDev*>& used,
                               const int32_t* d_root, const int32_t* d_boxes, int n_boxes,
                               const int32_t* d_targets, int n,
                               const ik_path_params* pp, int32_t* d_reach, int32_t* d_found,
@@ -1056,20 +1123,14 @@ static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<std
   int rc;
   CK(launch_rasterize(d, d_boxes, n_boxes, g->d_occ_raw, g->st));
   if ((rc = apply_dilation(g))) return rc;
-  std::vector<std::pair<int, int>> done;
-  for (const auto& k : key) {
-    if (!g->use_masks) break;
-    if (std::find(done.begin(), done.end(), k) != done.end()) continue;
-    done.push_back(k);
-    ShellDev* sh = g->shells[k];
-    CK(launch_edge_masks(d, g->tc, g->d_occ, *sh, sh->mbox, sh->d_mask, g->st));
-  }
+  if (g->use_masks)
+    for (ShellDev* sh : used) CK(launch_edge_masks(d, g->tc, g->d_occ, *sh, sh->mbox, sh->d_mask, g->st));
   uint32_t* F = ptr<uint32_t>(g->F);
   int32_t* fb = ptr<int32_t>(g->F_box);
   CK(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, g->st));
   CK(launch_seed_points(d, d_root, 1, nullptr, g->d_occ, F, d.nw, nullptr, fb, 0, g->st));
   for (int k = 1; k <= S; ++k)
-    CK(launch_propagate(d, g->tc, ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ,
+    CK(launch_propagate(d, g->tc, ad.segf[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, g->d_occ,
                         F + k * d.nw, 0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, g->st));
   uint32_t* V = ptr<uint32_t>(g->V);
   int32_t* vb = ptr<int32_t>(g->V_box);
@@ -1099,12 +1160,13 @@ int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const 
   *out = nullptr;
   ArmDev ad;
   std::vector<std::pair<int, int>> key;
+  std::vector<ShellDev*> used;
   // warm-up: size every buffer and build every table with one ordinary run
   if ((rc = ik_set_boxes(g, boxes_dev, n_boxes, 1))) return rc;
   if ((rc = ik_reach_path_many(g, arm, root, targets_dev, n, pp, reach_dev, found_dev, poses_dev,
                                relax_dev, status_dev, 1)))
     return rc;
-  if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
+  if ((rc = resolve_arm(g, arm, root, &ad, &key, &used))) return rc;
   // the root is the batch's own input: ordinary calls reuse the grid's buffer
   int32_t* d_root = nullptr;
   CK(cudaMalloc(&d_root, 16));
@@ -1117,7 +1179,7 @@ int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const 
   g->capturing = true;
   cudaError_t e = cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    rc = enqueue_reach_path(g, ad, key, d_root, boxes_dev, n_boxes, targets_dev, n, pp, reach_dev,
+    rc = enqueue_reach_path(g, ad, used, d_root, boxes_dev, n_boxes, targets_dev, n, pp, reach_dev,
                             found_dev, poses_dev, relax_dev, status_dev);
   } else {
     rc = fail_cuda(e);
@@ -1147,6 +1209,7 @@ int ik_batch_capture(ik_grid g, const ik_arm* arm, const int32_t root[3], const 
   memcpy(b->root, root, 12);
   b->d_root = d_root;
   b->key = key;
+  b->used = used;
   b->gen = g->buf_gen;
   ++g->live_batches;
   *out = b;
@@ -1166,7 +1229,7 @@ int ik_batch_launch(ik_batch b) {
   forget_device_state(g);
   if (b->gen != g->buf_gen) return IK_OK;
   if (g->use_masks)
-    for (const auto& k : b->key) g->shells[k]->mask_version = g->version;
+    for (ShellDev* sh : b->used) sh->mask_version = g->version;
   g->f_valid = true;
   g->f_version = g->version;
   g->f_key = b->key;

@@ -171,7 +171,10 @@ int enqueue_problem(Engine& E, Lane& L, const ProbInfo& pi, int idx, const ik_ba
   cudaStream_t st = L.st;
   uint32_t* occ = P<uint32_t>(L.occ);
   ArmDev ad = pi.arm;
-  for (int k = 0; k < S; ++k) ad.seg[k].occ = occ;
+  for (int k = 0; k < S; ++k) {
+    ad.seg[k].occ = occ;
+    ad.segf[k] = ad.seg[k];  // whole shells: symmetric
+  }
   const int32_t* root = P<int32_t>(E.roots) + 3 * idx;
   const int32_t* target = P<int32_t>(E.targets) + 3 * idx;
   int32_t* reach = P<int32_t>(E.out_reach) + pi.off_reach;
@@ -186,7 +189,7 @@ int enqueue_problem(Engine& E, Lane& L, const ProbInfo& pi, int idx, const ik_ba
   CKB(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, st));
   CKB(launch_seed_points(d, root, 1, nullptr, occ, F, d.nw, nullptr, fb, 0, st));
   for (int k = 1; k <= S; ++k)
-    CKB(launch_propagate(d, pi.tcs[k - 1], ad.seg[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, occ, F + k * d.nw,
+    CKB(launch_propagate(d, pi.tcs[k - 1], ad.segf[k - 1], F + (k - 1) * d.nw, 0, nullptr, 0, occ, F + k * d.nw,
                          0, 1, fb + 6 * (k - 1), fb + 6 * k, 0, st));
   // reach
   uint32_t* V = P<uint32_t>(L.V);

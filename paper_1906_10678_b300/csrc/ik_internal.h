@@ -112,8 +112,14 @@ size_t tile_occ_smem_bytes(const TileCfg& tc, int R);
 // -z1}.  A box whose bytes are all 0x7f is empty (wx0 > wx1).
 constexpr int kBoxEmptyByte = 0x7f;
 
+// seg[k]: segment k+1's offsets as segment vectors s = p_{k+1} - p_k (the
+// backward sets, tracebacks and validation read them so); segf[k]: the same
+// segment mirrored, -s (the forward gathers read it so: joint k+1 at p takes
+// its source at p - s).  A whole shell is symmetric, so both are the same
+// table; a direction limit (a cone) makes them two.
 struct ArmDev {
   SegDev seg[IK_MAX_SEG];
+  SegDev segf[IK_MAX_SEG];
   int S;
   int len[IK_MAX_SEG];
 };

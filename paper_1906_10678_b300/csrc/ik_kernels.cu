@@ -1535,7 +1535,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
   __syncthreads();
   for (int k = 1; k <= S; ++k) {
     const Box b = sh.box[k], sb = sh.box[k - 1];
-    const SegDev& sg = arm.seg[k - 1];
+    const SegDev& sg = arm.segf[k - 1];  // the forward gather reads the mirrored offsets
     const uint32_t* src = R + (long)(k - 1) * d.nw;
     const uint32_t* Vk = V + (long)k * d.nw;
     uint32_t* dst = R + (long)k * d.nw;

@@ -91,6 +91,7 @@ _sig("ik_solve_reach_many_cone", _i, [_vp, ctypes.POINTER(IkArm), ctypes.POINTER
                                       _vp, _vp, _vp, _i])
 _sig("ik_solve_reach_set", _i, [_vp, ctypes.POINTER(IkArm), ctypes.POINTER(IkCone), _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(_i)])
+_sig("ik_set_segment_limits", _i, [_vp, ctypes.POINTER(IkArm), _vp])
 _sig("ik_guide", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_waypoint_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, _i, _vp, _vp])
 _sig("ik_plan_path", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPathParams), _vp, _vp,
@@ -119,7 +120,7 @@ _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
-    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
+    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
     "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
@@ -337,6 +338,24 @@ def ik_solve_reach_set(g: int, arm, cone_, root, target_words, want_sets: bool =
                                    _np_ptr(tw), _np_ptr(pose), _np_ptr(vs), ctypes.byref(found)),
            "ik_solve_reach_set")
     return pose, found.value, vs
+
+
+def ik_set_segment_limits(g: int, arm, limits) -> None:
+    """Per-segment direction limits for this arm on this grid: ``limits`` is
+    None (clear) or a list of n_seg entries, each None (free) or an IkCone /
+    (axis, cos2_num, cos2_den)."""
+    arm = _arm(arm)
+    if limits is None:
+        _check(_lib.ik_set_segment_limits(g, ctypes.byref(arm.c), None), "ik_set_segment_limits")
+        return
+    arr = (IkCone * arm.S)()
+    for k, c in enumerate(limits):
+        if c is None:
+            continue
+        if not isinstance(c, IkCone):
+            c = cone(*c)
+        arr[k] = c
+    _check(_lib.ik_set_segment_limits(g, ctypes.byref(arm.c), arr), "ik_set_segment_limits")
 
 
 def ik_guide(g: int, arm, reach_pose, n_way: int) -> np.ndarray:
