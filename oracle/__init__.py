@@ -167,6 +167,27 @@ def reach_many(occ, lengths, root, targets, want_sets: bool = False, threads: in
     return poses, found, vs
 
 
+def plan_between(occ, lengths, start_pose, guide_lengths, target, W: int, delta: int = 3,
+                 eps2: int = 2, eps2_max: int = 8, max_relax: int = -1, tol: float = 0.5):
+    """Path between arbitrary poses (section "Path between Arbitrary Poses";
+    see orc_plan_between).  Returns (poses [W][S+1][3], relax [W][2], status,
+    guide pose [Sv+1][3])."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    lo2, hi2 = arm_bounds(lengths, tol)
+    vlo2, vhi2 = arm_bounds(guide_lengths, tol)
+    S, Sv = len(lengths), len(guide_lengths)
+    poses = np.zeros((W, S + 1, 3), np.int32)
+    relax = np.zeros((W, 2), np.int32)
+    vpose = np.zeros((Sv + 1, 3), np.int32)
+    st = ctypes.c_int32()
+    _load().orc_plan_between(nx, ny, nz, _p(occ), S, _p(lo2), _p(hi2), _p(_i32(start_pose)), Sv,
+                             _p(_i32(guide_lengths)), _p(vlo2), _p(vhi2), _p(_i32(target)), int(W),
+                             int(delta), int(eps2), int(eps2_max), int(max_relax), _p(poses),
+                             _p(relax), ctypes.byref(st), _p(vpose))
+    return poses, relax, st.value, vpose
+
+
 def dilate(occ, r2: int) -> np.ndarray:
     """Occupancy dilated by the ball |d|^2 <= r2 (section "Testing for
     collisions"), uint8 [nz][ny][nx]."""

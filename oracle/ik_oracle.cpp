@@ -661,6 +661,77 @@ int orc_reach_set(int nx, int ny, int nz, const uint8_t* occ, int S, const int32
   return 0;
 }
 
+// Path between arbitrary poses (section "Path between Arbitrary Poses"): a
+// virtual arm (Sv segments, shells vlo2/vhi2, nominal lengths vlens) rooted
+// at the end effector of the start pose reaches for the target with the
+// reach search (F, B, V = F & B, minimum-index traceback); its pose is the
+// guide polyline of the end effector (guide points by the nominal-arc rule of
+// the virtual arm, g_0 = the start's end effector, g_{W-1} = the target).
+// The actual arm's pose^(0) is the start pose and poses 1..W-1 are chained
+// forward, each the smooth step around the previous pose with its
+// relaxation ladder, waypoint targets as for any path (T_{W-1} = {target}).
+// No valid start pose, target outside the grid or no virtual reach:
+// PATH_UNREACHABLE, every pose the start pose, relax m = -1 for j >= 1.
+// poses_out [W][S+1][3], relax_out [W][2], vpose_out (nullable) [Sv+1][3].
+int orc_plan_between(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lo2,
+                     const int32_t* hi2, const int32_t* start_pose, int Sv, const int32_t* vlens,
+                     const int32_t* vlo2, const int32_t* vhi2, const int32_t* target, int W, int delta,
+                     int eps2, int eps2_max, int max_relax, int32_t* poses_out, int32_t* relax_out,
+                     int32_t* status_out, int32_t* vpose_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  Problem Pv = make_problem(nx, ny, nz, occ, Sv, vlo2, vhi2);
+  const std::vector<V3> start = read_pose(start_pose, S);
+  std::vector<std::vector<V3>> poses(W, start);
+  for (int j = 0; j < W; ++j) relax_out[2 * j] = relax_out[2 * j + 1] = 0;
+  const V3 t{target[0], target[1], target[2]};
+  auto unreachable = [&]() {
+    for (int j = 1; j < W; ++j) relax_out[2 * j] = -1;
+    for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
+    *status_out = PATH_UNREACHABLE;
+    return 0;
+  };
+  if (W < 2 || !pose_valid(P, start) || !P.g.inside(t.x, t.y, t.z)) return unreachable();
+  // the virtual arm's reach from the start's end effector
+  const V3 vroot = start[S];
+  Set T(P.g.nvox(), 0);
+  T[P.g.index(t.x, t.y, t.z)] = 1;
+  std::vector<Set> Vv = intersect(forward_sets(Pv, vroot), backward_sets(Pv, T));
+  std::vector<V3> vpose;
+  if (!traceback_min_index(Pv, Vv, vroot, &vpose)) return unreachable();
+  if (vpose_out) write_pose(vpose, vpose_out);
+  std::vector<int> Lv(vlens, vlens + Sv);
+  const std::vector<V3> g = guide_points(Lv, vpose, W);
+  // the actual arm, chained forward from the start pose
+  std::vector<Set> F = forward_sets(P, start[0]);
+  bool relaxed = false, broken = false;
+  for (int j = 1; j < W; ++j) {
+    int used = 0;
+    Set Tj;
+    if (j == W - 1) {
+      Tj = T;
+    } else {
+      Tj = waypoint_target(P, g[j], eps2, eps2_max, &used);
+      if (used != eps2) relaxed = true;
+    }
+    std::vector<Set> V = waypoint_V(P, F, Tj);
+    std::vector<V3> pose;
+    const int m = smooth_ladder(P, V, poses[j - 1], delta, max_relax, &pose);
+    relax_out[2 * j + 1] = used;
+    if (m < 0) {
+      broken = true;
+      poses[j] = poses[j - 1];
+      relax_out[2 * j] = -1;
+    } else {
+      if (m > 0) relaxed = true;
+      poses[j] = pose;
+      relax_out[2 * j] = m;
+    }
+  }
+  for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
+  *status_out = broken ? PATH_BROKEN : (relaxed ? PATH_RELAXED : PATH_OK);
+  return 0;
+}
+
 // Obstacle dilation (section "Testing for collisions": the obstacle volumes
 // are dilated when the grid is initialised, to account for the thickness of
 // the arm and a clearance margin): out[p] = 1 when some occupied voxel q has

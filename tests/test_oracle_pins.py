@@ -786,3 +786,100 @@ def test_scene_shapes():
     for p in t:
         assert not sc.point_occupied(tuple(p))
         assert int(((p - np.asarray(sc.root)) ** 2).sum()) <= reach * reach
+
+
+def _brute_between(ch, chv, lengths, vlengths, start, target, W, delta, eps2, eps2_max):
+    """Path between arbitrary poses by enumeration: the virtual arm's
+    lexicographically smallest chain from the start's end effector to the
+    target, guide points by the rational rule, then each pose the smallest
+    chain inside the balls around the previous pose."""
+    S = len(lengths)
+    vroot = tuple(int(v) for v in start[S])
+    _, _, vgood = chv.joint_sets(vroot, [target])
+    if not vgood:
+        return None
+    vpose = chv.lexmin(vgood)
+    g = _guide_fraction(vlengths, np.asarray(vpose), W)
+    poses = [tuple(map(tuple, np.asarray(start).tolist()))] + [None] * (W - 1)
+    relax = [[0, 0] for _ in range(W)]
+    root = poses[0][0]
+    diag2 = (ch.nx - 1) ** 2 + (ch.ny - 1) ** 2 + (ch.nz - 1) ** 2
+    for j in range(1, W):
+        if j == W - 1:
+            T, used = {tuple(target)}, 0
+        else:
+            T, used = set(), -1
+            for e2 in range(eps2, max(eps2, eps2_max) + 1):
+                T = {(x, y, z) for z in range(ch.nz) for y in range(ch.ny) for x in range(ch.nx)
+                     if (x - g[j][0]) ** 2 + (y - g[j][1]) ** 2 + (z - g[j][2]) ** 2 <= e2
+                     and ch.free((x, y, z))}
+                if T:
+                    used = e2
+                    break
+        relax[j][1] = used
+        ref = poses[j - 1]
+        m = 0
+        while True:
+            d = delta + m
+            good = _ball_chains(ch, root, ref, d, T)
+            if good:
+                poses[j] = ch.lexmin(good)
+                relax[j][0] = m
+                break
+            if d * d >= diag2:
+                poses[j] = ref
+                relax[j][0] = -1
+                break
+            m += 1
+    return poses, relax, vpose
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_plan_between_vs_enumeration(seed):
+    """Path between arbitrary poses (section "Path between Arbitrary Poses")
+    against enumeration: the virtual arm's pose, the guide, every pose and
+    relaxation record."""
+    rng = np.random.default_rng(900 + seed)
+    shape = (10, 10, 8)
+    lengths, vlengths = (3, 3, 2), (2, 2)
+    root = (5, 5, 0)
+    boxes = _rand_scene(rng, shape, 4, 2, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    ch = BF.Chains(BF.occupancy(shape, boxes), [O.shell_bounds(L) for L in lengths])
+    chv = BF.Chains(BF.occupancy(shape, boxes), [O.shell_bounds(L) for L in vlengths])
+    free = np.argwhere(occ == 0)[:, ::-1]
+    # a valid start pose: the reach pose of some target
+    for _ in range(50):
+        t0 = tuple(int(v) for v in free[rng.integers(len(free))])
+        p0, f0, _ = O.reach_many(occ, lengths, root, [t0])
+        if f0[0]:
+            break
+    assert f0[0]
+    start = p0[0]
+    W, delta = 5, 1
+    checked = 0
+    for _ in range(12):
+        target = tuple(int(v) for v in free[rng.integers(len(free))])
+        poses, relax, st, vpose = O.plan_between(occ, lengths, start, vlengths, target, W,
+                                                 delta=delta, eps2=1, eps2_max=4)
+        want = _brute_between(ch, chv, lengths, vlengths, start, target, W, delta, 1, 4)
+        if want is None:
+            assert st == O.PATH_UNREACHABLE
+            assert all((p == start).all() for p in poses)
+            continue
+        checked += 1
+        p_b, r_b, v_b = want
+        assert tuple(map(tuple, vpose.tolist())) == v_b
+        assert [tuple(map(tuple, p.tolist())) for p in poses] == p_b
+        assert relax.tolist() == r_b
+        assert (poses[0] == start).all()
+    assert checked > 0
+
+
+def test_plan_between_invalid_start():
+    shape, lengths = (10, 10, 8), (3, 3, 2)
+    occ = np.zeros((8, 10, 10), np.uint8)
+    bad = np.array([[5, 5, 0], [5, 5, 1], [5, 5, 4], [5, 5, 6]], np.int32)  # |s_1| = 1: not a shell offset
+    poses, relax, st, _ = O.plan_between(occ, lengths, bad, (2, 2), (3, 3, 3), 4)
+    assert st == O.PATH_UNREACHABLE and (relax[1:, 0] == -1).all()
+    assert all((p == bad).all() for p in poses)
