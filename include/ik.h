@@ -263,6 +263,23 @@ IK_API int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_p
 IK_API int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const ik_path_params* pp,
                  int32_t* poses_out, int32_t* relax_out, int* status);
 
+/* Path between arbitrary poses (section "Path between Arbitrary Poses"): a
+ * virtual arm guide_arm, rooted at the end effector of start_pose, reaches
+ * for the target with the reach search of ik_solve_reach; its pose is the
+ * polyline the end effector follows (guide points by the nominal-arc rule
+ * of guide_arm: g_0 = the start's end effector, g_{n_way-1} = target).
+ * pose^(0) = start_pose and poses 1 .. n_way-1 are chained forward, each the
+ * smooth step around the previous pose with the relaxation ladder (as in
+ * ik_plan_path; T_{n_way-1} = {target}).  start_pose [n_seg+1][3] must lie in
+ * the grid (else IK_ERR_ARG); poses_out [n_way][n_seg+1][3]; relax_out
+ * [n_way][2]; guide_pose_out nullable [guide n_seg+1][3]; *status =
+ * IK_PATH_OK / RELAXED / BROKEN, or UNREACHABLE (every pose the start, m = -1
+ * for j >= 1) when the start is not a valid pose of this arm or the virtual
+ * arm cannot reach the target. */
+IK_API int ik_plan_between(ik_grid g, const ik_arm* arm, const int32_t* start_pose, const ik_arm* guide_arm,
+                           const int32_t target[3], const ik_path_params* pp, int32_t* poses_out,
+                           int32_t* relax_out, int32_t* guide_pose_out, int* status);
+
 /* Reach + path for n targets sharing one root, all in batched launches with
  * no host round trip between steps: reach survivor sets and poses for all
  * targets, then the survivor sets of all n * n_way waypoints in one batched

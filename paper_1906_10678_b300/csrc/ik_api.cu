@@ -844,7 +844,13 @@ int ik_solve_reach_many_cone(ik_grid g, const ik_arm* arm, const ik_cone* cone, 
   ArmDev ad, adc;
   std::vector<std::pair<int, int>> key;
   if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
-  if (cone && (rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+  if (cone) {
+    // the cone's table may be one of the arm's (a segment limit with the
+    // same cone): resolve the arm again once its masks are in place
+    if ((rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+    if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
+    if ((rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+  }
   if ((rc = reach_many_impl(g, ad, key, root, targets, n, poses_out, found_out, vsets_out, on_device,
                             nullptr, nullptr, cone ? &adc : nullptr)))
     return rc;
@@ -861,7 +867,11 @@ int ik_solve_reach_set(ik_grid g, const ik_arm* arm, const ik_cone* cone, const 
   ArmDev ad, adc;
   std::vector<std::pair<int, int>> key;
   if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
-  if (cone && (rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+  if (cone) {
+    if ((rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+    if ((rc = resolve_arm(g, arm, root, &ad, &key))) return rc;
+    if ((rc = cone_arm(g, arm, cone, root, ad, &adc))) return rc;
+  }
   if ((rc = to_device(g, g->b_old, target_words, (size_t)g->d.nw * 4))) return rc;
   int32_t fnd = 0;
   if ((rc = reach_many_impl(g, ad, key, root, nullptr, 1, pose_out, &fnd, vsets_out, 0, nullptr, nullptr,
@@ -905,7 +915,8 @@ int ik_guide(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way,
 // poses are on the device (d_reach [P][S+1][3], d_found nullable).
 static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reach,
                               const int32_t* d_found, int P, int W, int j_lo, int eps2,
-                              int eps2_max, const int32_t* c_arr = nullptr) {
+                              int eps2_max, const int32_t* c_arr = nullptr,
+                              const GuideArm* ga = nullptr) {
   const Dims& d = g->d;
   const int S = ad.S;
   const long qs = (long)(S + 1) * d.nw;
@@ -924,7 +935,7 @@ static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reac
     ProfScope ps(g, P_GUIDE);
     CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
                             eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, wb, g->st,
-                            c_arr));
+                            c_arr, ga));
   }
   if (j_lo == 0) return backward_sets(g, ad, Vw, P * W, P_BWD_WAY, wb);
   // only waypoints j >= j_lo (P == 1 in that case)
@@ -1061,6 +1072,84 @@ int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const 
   if ((rc = sync(g))) return rc;
   *status = st;
   return IK_OK;
+}
+
+int ik_plan_between(ik_grid g, const ik_arm* arm, const int32_t* start_pose, const ik_arm* guide_arm,
+                    const int32_t target[3], const ik_path_params* pp, int32_t* poses_out,
+                    int32_t* relax_out, int32_t* guide_pose_out, int* status) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!start_pose || !target || !poses_out || !relax_out || !status) return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  if ((rc = check_arm(guide_arm))) return rc;
+  ArmDev ad, av;
+  std::vector<std::pair<int, int>> key, keyv;
+  if ((rc = resolve_arm(g, arm, start_pose, &ad, &key))) return rc;
+  const int S = ad.S, Sv = guide_arm->n_seg, W = pp->n_way;
+  const size_t pose_bytes = (size_t)12 * (S + 1);
+  for (int k = 0; k <= S; ++k)
+    if (!point_inside(g->d, start_pose + 3 * k)) return IK_ERR_ARG;
+  if (!point_inside(g->d, target)) return IK_ERR_ARG;
+  auto unreachable = [&]() {
+    for (int j = 0; j < W; ++j) {
+      memcpy(poses_out + (size_t)j * 3 * (S + 1), start_pose, pose_bytes);
+      relax_out[2 * j] = j == 0 ? 0 : -1;
+      relax_out[2 * j + 1] = 0;
+    }
+    *status = IK_PATH_UNREACHABLE;
+    return sync(g);
+  };
+  // the start must be a valid pose of this arm in this grid
+  if ((rc = to_device(g, g->b_old, start_pose, pose_bytes))) return rc;
+  if ((rc = ensure(g, g->b_valid, 4))) return rc;
+  if ((rc = validate_impl(g, ad, ptr<int32_t>(g->b_old), 1, ptr<int32_t>(g->b_valid)))) return rc;
+  int32_t valid = 0;
+  if ((rc = copy_out(g, &valid, g->b_valid.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  if (!valid) return unreachable();
+  // the virtual arm reaches from the start's end effector for the target
+  const int32_t* vroot = start_pose + 3 * S;
+  if ((rc = resolve_arm(g, guide_arm, vroot, &av, &keyv))) return rc;
+  int32_t *d_vpose = nullptr, *d_vfound = nullptr;
+  if ((rc = reach_many_impl(g, av, keyv, vroot, target, 1, nullptr, nullptr, nullptr, 0, &d_vpose,
+                            &d_vfound)))
+    return rc;
+  int32_t vfound = 0;
+  std::vector<int32_t> vpose((size_t)3 * (Sv + 1));
+  if ((rc = copy_out(g, &vfound, d_vfound, 4, 0))) return rc;
+  if ((rc = copy_out(g, vpose.data(), d_vpose, (size_t)12 * (Sv + 1), 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  if (!vfound) return unreachable();
+  if (guide_pose_out) memcpy(guide_pose_out, vpose.data(), (size_t)12 * (Sv + 1));
+  // the guide pose in a buffer that the actual arm's steps do not use
+  if ((rc = to_device(g, g->b_targets, vpose.data(), (size_t)12 * (Sv + 1)))) return rc;
+  const int32_t* d_guide = ptr<int32_t>(g->b_targets);
+  // the actual arm: forward sets from its root, waypoint sets j >= 1 along the
+  // guide, the forward chain from the start pose.  Its tables are resolved
+  // again: the virtual arm's shells may be the same tables, whose edge-mask
+  // boxes (and buffers) grew for the virtual root.
+  if ((rc = resolve_arm(g, arm, start_pose, &ad, &key))) return rc;
+  if ((rc = ensure_forward(g, ad, key, start_pose))) return rc;
+  GuideArm ga;
+  ga.S = Sv;
+  for (int k = 0; k < Sv; ++k) ga.len[k] = guide_arm->len[k];
+  if ((rc = ensure(g, g->b_found, 4))) return rc;
+  CK(cudaMemcpyAsync(ptr<int32_t>(g->b_found), &vfound, 4, cudaMemcpyHostToDevice, g->st));
+  if ((rc = waypoint_sets_impl(g, ad, d_guide, ptr<int32_t>(g->b_found), 1, W, 1, pp->eps2, pp->eps2_max,
+                               nullptr, &ga)))
+    return rc;
+  if ((rc = ensure(g, g->b_poses, pose_bytes * W))) return rc;
+  if ((rc = ensure(g, g->b_relax, (size_t)8 * W))) return rc;
+  if ((rc = ensure(g, g->b_status, 4))) return rc;
+  int32_t* dposes = ptr<int32_t>(g->b_poses);
+  CK(cudaMemcpyAsync(dposes, start_pose, pose_bytes, cudaMemcpyHostToDevice, g->st));
+  if ((rc = chain_impl(g, ad, pp, 1, 1, 0, ptr<int32_t>(g->b_found), dposes, ptr<int32_t>(g->b_relax),
+                       ptr<int32_t>(g->b_status))))
+    return rc;
+  if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W, 0))) return rc;
+  if ((rc = copy_out(g, relax_out, g->b_relax.p, (size_t)8 * W, 0))) return rc;
+  if ((rc = copy_out(g, status, g->b_status.p, 4, 0))) return rc;
+  return sync(g);
 }
 
 int ik_reach_path_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* targets,

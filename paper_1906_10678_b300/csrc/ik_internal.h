@@ -191,11 +191,19 @@ cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int
 // Vw + ((p*W + j) * (S+1) + S) * nw.  Waypoints j < j_lo are skipped.
 // wbox: boxes [P][W][S+1][6]; the box of each seeded set (index S) is
 // accumulated (set empty beforehand).
+// The polyline the guide points follow: `reach` holds, per path, the S + 1
+// joints of a pose of this arm (segment count and nominal lengths).
+struct GuideArm {
+  int S;
+  int len[IK_MAX_SEG];
+};
+// Guide points and waypoint targets.  The guide follows `reach` with the
+// arm `ga` (nullptr: the path's own arm); the targets are laid out for `arm`.
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
                                  int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st,
-                                 const int32_t* c_arr = nullptr);
+                                 const int32_t* c_arr = nullptr, const GuideArm* ga = nullptr);
 // Smooth chains for P paths (one block each).  mode 0 = plan (backward from
 // the reach pose), mode 1 = forward from pose c (replan).  scratch: per path
 // 2 * (S+1) * nw zeroed words.

@@ -1193,7 +1193,7 @@ __device__ __forceinline__ int isqrt_dev(int v) {  // floor(sqrt(v)), v >= 0
 // the waypoint target set T_j (free voxels within squared distance eps2,
 // grown to eps2_max when empty; T_{W-1} = {end effector}) intersected with
 // F_S, OR-ed into the (pre-zeroed) last survivor set of the waypoint.
-__global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__ occ,
+__global__ void k_guide_targets(Dims d, ArmDev arm, GuideArm ga, const uint32_t* __restrict__ occ,
                                 const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
                                 const int32_t* __restrict__ found, int W, int j_lo, int eps2,
                                 int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw,
@@ -1201,20 +1201,21 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
   const int p = blockIdx.y;
   const int j = blockIdx.x + j_lo;
   if (c_arr && j <= c_arr[p]) return;  // replan: waypoints up to the current one stay
-  const int S = arm.S;
-  const int32_t* R = reach + (long)p * 3 * (S + 1);
+  const int S = arm.S;    // layout of the waypoint sets
+  const int GS = ga.S;    // the guide polyline's segments
+  const int32_t* R = reach + (long)p * 3 * (GS + 1);
   __shared__ int gp[3];
   __shared__ int used;
   const bool ok = !found || found[p];
   if (threadIdx.x == 0) {
     long lam = 0;
-    for (int k = 0; k < S; ++k) lam += arm.len[k];
+    for (int k = 0; k < GS; ++k) lam += ga.len[k];
     const long num = (long)j * lam;
     long Cprev = 0;
-    int k = S;
+    int k = GS;
     long c0 = 0;
-    for (int kk = 1; kk <= S; ++kk) {
-      const long c1 = Cprev + arm.len[kk - 1];
+    for (int kk = 1; kk <= GS; ++kk) {
+      const long c1 = Cprev + ga.len[kk - 1];
       if (Cprev * (W - 1) <= num && num < c1 * (W - 1)) {
         k = kk;
         c0 = Cprev;
@@ -1222,9 +1223,9 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
       }
       Cprev = c1;
     }
-    if (k == S) c0 = lam - arm.len[S - 1];
+    if (k == GS) c0 = lam - ga.len[GS - 1];
     const long r = num - c0 * (W - 1);
-    const long den = (long)arm.len[k - 1] * (W - 1);
+    const long den = (long)ga.len[k - 1] * (W - 1);
     for (int i = 0; i < 3; ++i) {
       const long a = ok ? R[3 * (k - 1) + i] : 0, b = ok ? R[3 * k + i] : 0;
       gp[i] = (int)(a + floor_div(2 * r * (b - a) + den, 2 * den));
@@ -1242,7 +1243,7 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, const uint32_t* __restrict__
   }
   if (j == W - 1) {
     if (threadIdx.x == 0) {
-      const int tx = R[3 * S], ty = R[3 * S + 1], tz = R[3 * S + 2];
+      const int tx = R[3 * GS], ty = R[3 * GS + 1], tz = R[3 * GS + 2];
       if (inside(d, tx, ty, tz)) {
         const long i = lin(d, tx, ty, tz);
         if (test_bit(F_S, i)) {
@@ -1294,10 +1295,16 @@ cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
                                  int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st,
-                                 const int32_t* c_arr) {
+                                 const int32_t* c_arr, const GuideArm* ga) {
   if (P <= 0 || W - j_lo <= 0) return cudaSuccess;
+  GuideArm own;
+  if (!ga) {
+    own.S = arm.S;
+    for (int k = 0; k < arm.S; ++k) own.len[k] = arm.len[k];
+    ga = &own;
+  }
   dim3 grid(W - j_lo, P);
-  k_guide_targets<<<grid, 128, 0, st>>>(d, arm, occ, F_S, reach, found, W, j_lo, eps2, eps2_max, g,
+  k_guide_targets<<<grid, 128, 0, st>>>(d, arm, *ga, occ, F_S, reach, found, W, j_lo, eps2, eps2_max, g,
                                         eps_used, Vw, wbox, c_arr);
   return cudaGetLastError();
 }

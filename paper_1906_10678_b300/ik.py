@@ -98,6 +98,8 @@ _sig("ik_plan_path", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPath
                           ctypes.POINTER(_i)])
 _sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
                                 ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp, _i])
+_sig("ik_plan_between", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkArm), _vp,
+                             ctypes.POINTER(IkPathParams), _vp, _vp, _vp, ctypes.POINTER(_i)])
 _sig("ik_validate_poses", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_replan", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, ctypes.POINTER(IkPathParams), _vp,
                        _vp, ctypes.POINTER(_i)])
@@ -121,7 +123,7 @@ EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
-    "ik_reach_path_many", "ik_validate_poses", "ik_replan", "ik_replan_many",
+    "ik_reach_path_many", "ik_plan_between", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
@@ -492,6 +494,23 @@ def ik_solve_batch(problems, delta: int = 3, eps2: int = 2, eps2_max: int = 8, m
         p0 += 3 * (S + 1) * W
         x0 += 2 * W
     return out, ms.value
+
+
+def ik_plan_between(g: int, arm, start_pose, guide_arm, target, n_way: int, delta: int = 3,
+                    eps2: int = 2, eps2_max: int = 8, max_relax: int = -1):
+    """Path between arbitrary poses.  Returns (poses [W][S+1][3], relax [W][2],
+    status, guide pose [Sv+1][3])."""
+    arm = _arm(arm)
+    garm = _arm(guide_arm)
+    pp = path_params(n_way, delta, eps2, eps2_max, max_relax)
+    poses = np.zeros((n_way, arm.S + 1, 3), np.int32)
+    relax = np.zeros((n_way, 2), np.int32)
+    gpose = np.zeros((garm.S + 1, 3), np.int32)
+    st = ctypes.c_int(0)
+    _check(_lib.ik_plan_between(g, ctypes.byref(arm.c), _np_ptr(_i32(start_pose)), ctypes.byref(garm.c),
+                                _np_ptr(_i32(target)), ctypes.byref(pp), _np_ptr(poses), _np_ptr(relax),
+                                _np_ptr(gpose), ctypes.byref(st)), "ik_plan_between")
+    return poses, relax, st.value, gpose
 
 
 def ik_validate_poses(g: int, arm, poses) -> np.ndarray:
