@@ -422,6 +422,10 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
   const int bx1 = -__ldg(xb + 3), by1 = -__ldg(xb + 4), bz1 = -__ldg(xb + 5);
   uint32_t m = 0;
   if (valid) m = (mask ? __ldg(mask + q * ms + w) : 0xffffffffu) & ~__ldg(occ + w);
+  // the lane's row of stored edge masks (one word per offset, mstr apart):
+  // one address per offset instead of the box index each time
+  const uint32_t* mrow = (!kOcc && seg.mask && valid) ? seg.mask + seg.mbox.index(wx, y, z) : nullptr;
+  const long mstr = seg.mbox.words();
   const bool touches = bx0 <= bx1 && by1 >= y0 - R && by0 <= y0 + tc.TY - 1 + R &&
                        bz1 >= z0 - R && bz0 <= z0 + tc.TZ - 1 + R;
   if (kOcc)
@@ -544,7 +548,9 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
           } else {
             uint32_t mv[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) mv[i] = (xv[i] & want) ? edge_word(d, seg, e + i, w, wx, y, z) : 0u;
+            for (int i = 0; i < 8; ++i)
+              mv[i] = (xv[i] & want) ? (mrow ? __ldg(mrow + (long)(e + i) * mstr) : edge_word(d, seg, e + i, w, wx, y, z))
+                                     : 0u;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               if (kCount) mloads += (xv[i] & want) != 0;
@@ -563,7 +569,8 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
         }
         if (x & m & ~acc) {
           if (kCount) ++mloads;
-          acc |= x & (kOcc ? edge_word_tile(seg, e, so, base) : edge_word(d, seg, e, w, wx, y, z));
+          acc |= x & (kOcc ? edge_word_tile(seg, e, so, base)
+                           : (mrow ? __ldg(mrow + (long)e * mstr) : edge_word(d, seg, e, w, wx, y, z)));
         }
       }
       live = live && (acc & m) != m;
