@@ -114,16 +114,22 @@ OPS_PER_PAIR = 3  # funnel shift of the input word, AND with the edge mask, OR i
 
 # DRAM bytes (read + write) per launch of the waypoint pass on this workload
 # from one ncu capture of bench.py (profiles/dram_waypoint_pass_128.md), with
-# the SHA-256 of the kernel source it was taken on: reported only while that
-# source is unchanged.
-TRAFFIC_CAPTURE = {"bytes_per_launch": 1183171040,
-                   "kernels_sha256": "72fe96dc6ef484808d3a0cf934a509c9ceecd440006643fb6ad5fe64c8384f6f"}
+# the SHA-256 of the kernel and tiling sources it was taken on: reported only
+# while those sources are unchanged.
+TRAFFIC_CAPTURE = {"bytes_per_launch": 1183002272,
+                   "kernels_sha256": "d7c4c80f7cd05253536ee7bf0f498c102b2b2439a2ea937f693d1194432aecfc"}
+
+
+def kernel_sources_sha256() -> str:
+    h = hashlib.sha256()
+    for name in ("ik_kernels.cu", "ik_tables.cpp"):
+        with open(os.path.join(ROOT, "paper_1906_10678_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def kernel_traffic():
-    src = os.path.join(ROOT, "paper_1906_10678_b300", "csrc", "ik_kernels.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
+    sha = kernel_sources_sha256()
     return TRAFFIC_CAPTURE["bytes_per_launch"] if sha == TRAFFIC_CAPTURE["kernels_sha256"] else None
 
 

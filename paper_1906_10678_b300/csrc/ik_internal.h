@@ -91,8 +91,8 @@ struct SegDev {
 // covers all wx words of TY rows in each of TZ = 8 z slices (warp i = slice
 // z0 + i, lane = (word lane % wx, row lane / wx)); its source halo of reach R
 // is staged in shared memory as (TZ + 2R) x (TY + 2R) rows of P words (word
-// -1 .. wx, zero-padded), P chosen so that a warp's 32 row-word addresses hit
-// distinct banks.  tab[e] = ((dy * P + (dx >> 5)) << 5) | (dx & 31): the
+// -1 .. wx, zero-padded), P the narrowest pitch with at most 2-way bank
+// conflicts among a warp's row-word addresses.  tab[e] = ((dy * P + (dx >> 5)) << 5) | (dx & 31): the
 // shared-memory word delta and the funnel shift of offset e.
 struct TileCfg {
   int TY, TZ, P, lanes, tiles_y, tiles_z;

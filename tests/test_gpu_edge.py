@@ -91,3 +91,22 @@ def test_longest_segment(ik):
     Fb = ik.unpack_bits(F, shape)
     assert (Fb[1] == want).all() and Fb[0].sum() == 1 and Fb[0][10, 64, 64]
     assert fg.all() and (pg[:, 1] == targets).all() and (pg[:, 0] == root).all()
+
+
+@pytest.mark.parametrize("masks", [1, 0])
+def test_widest_rows(ik, masks):
+    """Rows of 32 words (nx = 1024, the largest): the tiled kernels cannot
+    stage a row plus its halo in one warp's pitch and stand aside; reach and
+    survivor sets exact against the oracle on a thin 1024 x 6 x 5 grid."""
+    sc = G.make_scene(1024, 6, 5, (512, 3, 0), (3, 2), 30, 1, 3, 13, "wide")
+    occ = O.rasterize(sc.shape, sc.boxes)
+    targets = G.draw_targets(sc, 6, 14)
+    with ik.Grid(*sc.shape) as g:
+        ik.ik_set_option(g.h, ik.IK_OPT_EDGE_MASKS, masks)
+        ik.ik_set_boxes(g.h, sc.boxes)
+        F = ik.ik_forward_sets(g.h, sc.lengths, sc.root)
+        pg, fg, vg = ik.ik_solve_reach_many(g.h, sc.lengths, sc.root, targets, want_sets=True)
+    assert (ik.unpack_bits(F, sc.shape) == O.forward(occ, sc.lengths, sc.root).astype(bool)).all()
+    po, fo, vo = O.reach_many(occ, sc.lengths, sc.root, targets, want_sets=True, threads=4)
+    assert (fg == fo).all() and (pg[fo == 1] == po[fo == 1]).all()
+    assert (ik.unpack_bits(vg.reshape(-1), sc.shape).reshape(vo.shape) == vo.astype(bool)).all()
