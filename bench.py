@@ -577,11 +577,12 @@ def main():
                     help="grid edge; 128 is the benchmark workload, smaller only for captures")
     ap.add_argument("--targets", type=int, default=64)
     ap.add_argument("--replan-ticks", type=int, default=3)
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="served run after the warm-up (0 skips the served section)")
     ap.add_argument("--workload", default="c3", choices=["c3", "c4"])
     ap.add_argument("--problems", type=int, default=1024)
     ap.add_argument("--lanes", type=int, default=16)
-    ap.add_argument("--serve-warmup", type=float, default=2.0)
+    ap.add_argument("--serve-warmup", type=float, default=5.0)
     ap.add_argument("--serve-scene", default="c5", choices=["c5", "c3"],
                     help="served workload: c5 = 256^3 with moving boxes, c3 = the 128^3 scene")
     ap.add_argument("--serve-no-masks", action="store_true",
