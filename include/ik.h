@@ -135,6 +135,13 @@ IK_API int ik_destroy_grid(ik_grid g);
  * ik_set_boxes and to batches captured afterwards (a batch keeps the value it
  * was captured with); ik_get_obstacles returns the dilated occupancy. */
 #define IK_OPT_DILATE_R2 3
+/* IK_OPT_WORK_LIST: how a batched backward pass (16 or more queries) visits
+ * the tiles of each level.  1 (default): a work list of the tiles a level's
+ * bounding boxes reach, walked by a grid of resident blocks, on the levels
+ * where a bound from the arm's reaches leaves at most an eighth of the tiles,
+ * and one block per (tile, query) elsewhere; 0: one block per (tile, query)
+ * on every level; 2: the work list on every level.  Results are identical. */
+#define IK_OPT_WORK_LIST 4
 IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);

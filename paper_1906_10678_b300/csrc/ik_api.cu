@@ -39,6 +39,7 @@ struct ik_grid_s {
   uint32_t* d_occ = nullptr;      // the occupancy every kernel reads (dilated when asked)
   uint32_t* d_occ_raw = nullptr;  // the occupancy as set, before dilation
   int dilate_r2 = 0;
+  int work_list = 1;              // IK_OPT_WORK_LIST
   uint64_t version = 1;
   std::map<std::pair<int, int>, ShellDev*> shells;
   // shells restricted to an approach cone: (lo2, hi2, ax, ay, az, num, den)
@@ -57,6 +58,8 @@ struct ik_grid_s {
   DevBuf b_root, b_targets, b_reach, b_found, b_poses, b_relax, b_status, b_eps, b_g, b_valid;
   DevBuf b_old;
   DevBuf b_rp, b_rin, b_rc;  // batched replan: bookkeeping, host-form inputs
+  DevBuf b_list;             // work list of the batched propagations
+  int num_sms = 148;
   // per-kernel profiling: events recorded on st around each launch
   bool prof_on = false, count_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -126,6 +129,7 @@ enum ProfId {
   P_GUIDE,
   P_CHAIN,
   P_VALIDATE,
+  P_TILE_LIST,
   P_WAY_K1,  // waypoint backward pass per segment level k = 1 .. IK_MAX_SEG
   P_N = P_WAY_K1 + IK_MAX_SEG
 };
@@ -139,6 +143,7 @@ const char* kProfNames[P_N] = {"rasterize",
                                "guide_targets",
                                "smooth_chain",
                                "validate",
+                               "tile_list",
                                "way_k1", "way_k2", "way_k3", "way_k4", "way_k5", "way_k6",
                                "way_k7", "way_k8", "way_k9", "way_k10", "way_k11", "way_k12",
                                "way_k13", "way_k14", "way_k15", "way_k16"};
@@ -518,14 +523,59 @@ int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id, 
   const int S = ad.S;
   const long qs = (long)(S + 1) * d.nw;
   const uint32_t* F = ptr<uint32_t>(g->F);
+  const int32_t* fb = ptr<int32_t>(g->F_box);
+  // work list scratch: every (query, tile) pair at most, and the count
+  WorkList wl{};
+  const WorkList* wlp = nullptr;
+  if (Q >= kListMinQueries && g->work_list > 0) {
+    const long cap = (long)Q * g->tc.tiles_y * g->tc.tiles_z;
+    int rc = ensure(g, g->b_list, (size_t)cap * sizeof(int2) + 16);
+    if (rc) return rc;
+    wl.items = ptr<int2>(g->b_list);
+    wl.count = reinterpret_cast<int*>(wl.items + cap);
+    wl.cap = cap;
+    wl.blocks = g->num_sms * 4;  // about as many as stay resident
+    wlp = &wl;
+  }
+  // R_1 + ... + R_k for the bound of each level's output below
+  int rsum[IK_MAX_SEG + 1] = {0};
+  for (int k = 1; k <= S; ++k) rsum[k] = rsum[k - 1] + ad.seg[k - 1].R;
   for (int k = S; k >= 1; --k) {
+    // V_{k-1} lies within R_1 + ... + R_{k-1} of the root (it is inside
+    // F_{k-1}) and, for a point target, within R_k + ... + R_S of it. The
+    // work list pays where that bound leaves at most an eighth of the tiles
+    // (the levels next to either end of the arm); on the others the plain
+    // grid of every (tile, query) was measured faster. Either form gives the
+    // same sets.
+    const WorkList* wk = nullptr;
+    if (wlp && g->work_list == 2) {
+      wk = wlp;
+    } else if (wlp) {
+      const TileCfg& tc = g->tc;
+      const int rf = rsum[k - 1], rt = rsum[S] - rsum[k - 1];
+      auto span = [&](int c, int n) {
+        const int lo = std::max(0, c - rf), hi = std::min(n - 1, c + rf);
+        return std::max(0, std::min(hi - lo + 1, 2 * rt + 1));
+      };
+      const long ty = std::min(tc.tiles_y, (span(g->f_root[1], d.ny) + tc.TY - 1) / tc.TY + 1);
+      const long tz = std::min(tc.tiles_z, (span(g->f_root[2], d.nz) + tc.TZ - 1) / tc.TZ + 1);
+      if (8 * ty * tz <= (long)tc.tiles_y * tc.tiles_z) wk = wlp;
+    }
+    const SegDev& seg = ad.seg[k - 1];
+    if (propagate_listed(g->tc, seg, Q, qs, wk)) {
+      ProfScope pt(g, P_TILE_LIST);
+      CK(launch_tile_list(d, g->tc, seg.R, Q, box + 6 * k, 6L * (S + 1), fb + 6 * (k - 1),
+                          V + (long)(k - 1) * d.nw, qs, *wk, g->st));
+    } else {
+      wk = nullptr;
+    }
     ProfScope ps(g, prof_id);
     // the waypoint pass is also recorded per level (work counters go there)
     ProfScope pl(g, prof_id == P_BWD_WAY ? P_WAY_K1 + k - 1 : -1);
     unsigned long long* cnt = counters(g, prof_id == P_BWD_WAY ? P_WAY_K1 + k - 1 : prof_id);
-    CK(launch_propagate(d, g->tc, ad.seg[k - 1], V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0,
-                        g->d_occ, V + (long)(k - 1) * d.nw, qs, Q, box + 6 * k, box + 6 * (k - 1),
-                        6L * (S + 1), g->st, cnt));
+    CK(launch_propagate(d, g->tc, seg, V + (long)k * d.nw, qs, F + (long)(k - 1) * d.nw, 0, g->d_occ,
+                        V + (long)(k - 1) * d.nw, qs, Q, box + 6 * k, box + 6 * (k - 1), 6L * (S + 1),
+                        g->st, cnt, wk));
   }
   return IK_OK;
 }
@@ -589,6 +639,11 @@ int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out) {
   g->d.nw = (long)g->d.wx * ny * nz;
   g->tc = make_tile_cfg(g->d);
   g->st = (cudaStream_t)cuda_stream;
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) == cudaSuccess && sms > 0)
+      g->num_sms = sms;
+  }
   e = set_kernel_attributes();
   if (e == cudaSuccess) e = cudaMalloc(&g->d_occ, g->d.nw * 4);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_occ_raw, g->d.nw * 4);
@@ -625,7 +680,7 @@ int ik_destroy_grid(ik_grid g) {
   DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->F_box, &g->V_box, &g->Vw_box,
                     &g->b_rp, &g->b_rin, &g->b_rc, &g->b_root, &g->b_targets,
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
-                    &g->b_g, &g->b_valid, &g->b_old};
+                    &g->b_g, &g->b_valid, &g->b_old, &g->b_list};
   for (DevBuf* b : bufs) cudaFree(b->p);
   for (void* p : g->retired) cudaFree(p);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
@@ -1535,6 +1590,11 @@ int ik_set_option(ik_grid g, int option, int value) {
   if (option == IK_OPT_TILE_DEPTH) {
     if (value != 8 && value != 16) return IK_ERR_ARG;
     g->tc.depth = value;
+    return IK_OK;
+  }
+  if (option == IK_OPT_WORK_LIST) {
+    if (value < 0 || value > 2) return IK_ERR_ARG;
+    g->work_list = value;
     return IK_OK;
   }
   if (option == IK_OPT_DILATE_R2) {

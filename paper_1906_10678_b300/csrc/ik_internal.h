@@ -158,11 +158,32 @@ cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* 
 // (for a segment without stored edge masks, when tile_occ_smem_bytes > 0:
 // its supercover walks then read an occupancy halo in shared memory), the
 // global-load kernel otherwise.
+// Device scratch for the work list of a batched propagation: items {query,
+// tile} (cap entries, at least Q x tiles), count[0] = items, count[1] = the
+// next item to take; blocks = the grid of resident blocks that walks the
+// list.
+struct WorkList {
+  int2* items;
+  int* count;
+  long cap;
+  int blocks;
+};
+// Whether launch_propagate walks the work list wl (Q >= kListMinQueries on
+// the tiled kernels of depth 8); when it does, launch_tile_list must have
+// built the list on the same stream just before.
+constexpr int kListMinQueries = 16;
+bool propagate_listed(const TileCfg& tc, const SegDev& seg, int Q, long out_stride, const WorkList* wl);
+// Zeroes the Q outputs and lists the (query, tile) pairs within reach R of
+// X[q]'s box (xbox) and inside the output mask's box (mbox, one min-form box
+// for all queries, nullable); only those are computed.
+cudaError_t launch_tile_list(const Dims& d, const TileCfg& tc, int R, int Q, const int32_t* xbox,
+                             long box_stride, const int32_t* mbox, uint32_t* out, long out_stride,
+                             const WorkList& wl, cudaStream_t st);
 cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,
                              long x_stride, const uint32_t* mask, long mask_stride,
                              const uint32_t* occ, uint32_t* out, long out_stride, int Q,
                              const int32_t* xbox, int32_t* obox, long box_stride, cudaStream_t st,
-                             unsigned long long* counters = nullptr);
+                             unsigned long long* counters = nullptr, const WorkList* wl = nullptr);
 // counters (nullable, 4 x u64, accumulated): offset-word pairs visited,
 // pairs whose shifted input word is non-zero, edge-mask words read, output
 // words with a non-empty mask.

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ik_internal.h"
 
 namespace ikb {
@@ -404,13 +406,13 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
                                                     uint32_t* __restrict__ out, long os,
                                                     const int32_t* __restrict__ xbox,
                                                     int32_t* __restrict__ obox, long bs,
-                                                    unsigned long long* __restrict__ counters) {
+                                                    unsigned long long* __restrict__ counters, int q,
+                                                    int tile) {
   extern __shared__ uint32_t sx[];
   // per staged slice: the rows holding a non-zero source word
   __shared__ int s_ymin[kMaxSlices], s_ymax[kMaxSlices];
   constexpr unsigned kFull = 0xffffffffu;
-  const int q = blockIdx.y;
-  const int y0 = (blockIdx.x % tc.tiles_y) * tc.TY, z0 = (blockIdx.x / tc.tiles_y) * tc.TZ;
+  const int y0 = (tile % tc.tiles_y) * tc.TY, z0 = (tile / tc.tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int R = seg.R, RY = tc.TY + 2 * R, P = tc.P;
   const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
@@ -602,7 +604,8 @@ __global__ void __launch_bounds__(256) k_propagate_tile(Dims d, SegDev seg, Tile
                                                         const int32_t* __restrict__ xbox,
                                                         int32_t* __restrict__ obox, long bs,
                                                         unsigned long long* __restrict__ counters) {
-  propagate_tile_body<kCount, false>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters);
+  propagate_tile_body<kCount, false>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters,
+                                     blockIdx.y, blockIdx.x);
 }
 
 template <bool kCount>
@@ -614,7 +617,137 @@ __global__ void __launch_bounds__(256, 3) k_propagate_tile_occ(Dims d, SegDev se
                                                                const int32_t* __restrict__ xbox,
                                                                int32_t* __restrict__ obox, long bs,
                                                                unsigned long long* __restrict__ counters) {
-  propagate_tile_body<kCount, true>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters);
+  propagate_tile_body<kCount, true>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters,
+                                    blockIdx.y, blockIdx.x);
+}
+
+// The same kernels over a work list of (query, tile) pairs that can hold
+// output (built by k_tile_list): a grid of resident blocks walks the list,
+// instead of one block per tile of every query -- most of which would find
+// nothing to do after staging their masks.
+template <bool kCount, bool kOccT>
+__device__ __forceinline__ void propagate_list(const Dims& d, const SegDev& seg, const TileCfg& tc,
+                                               const uint32_t* X, long xs, const uint32_t* mask, long ms,
+                                               const uint32_t* occ, uint32_t* out, long os,
+                                               const int32_t* xbox, int32_t* obox, long bs,
+                                               unsigned long long* counters, const int2* items,
+                                               int* count) {
+  // count[0]: items in the list; count[1]: the next item to take (items
+  // differ a lot in cost, so blocks take them one at a time)
+  __shared__ int s_it;
+  const int n = count[0];
+  for (;;) {
+    __syncthreads();  // the previous item's readers are done with shared memory
+    if (threadIdx.x == 0) s_it = atomicAdd(count + 1, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= n) break;
+    const int2 t = items[it];
+    propagate_tile_body<kCount, kOccT>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters,
+                                       t.x, t.y);
+  }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(256) k_propagate_tile_list(Dims d, SegDev seg, TileCfg tc,
+                                                             const uint32_t* __restrict__ X, long xs,
+                                                             const uint32_t* __restrict__ mask, long ms,
+                                                             const uint32_t* __restrict__ occ,
+                                                             uint32_t* __restrict__ out, long os,
+                                                             const int32_t* __restrict__ xbox,
+                                                             int32_t* __restrict__ obox, long bs,
+                                                             unsigned long long* __restrict__ counters,
+                                                             const int2* __restrict__ items,
+                                                             int* __restrict__ count) {
+  propagate_list<kCount, false>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters, items,
+                                count);
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(256, 3) k_propagate_tile_occ_list(Dims d, SegDev seg, TileCfg tc,
+                                                                    const uint32_t* __restrict__ X, long xs,
+                                                                    const uint32_t* __restrict__ mask,
+                                                                    long ms, const uint32_t* __restrict__ occ,
+                                                                    uint32_t* __restrict__ out, long os,
+                                                                    const int32_t* __restrict__ xbox,
+                                                                    int32_t* __restrict__ obox, long bs,
+                                                                    unsigned long long* __restrict__ counters,
+                                                                    const int2* __restrict__ items,
+                                                                    int* __restrict__ count) {
+  propagate_list<kCount, true>(d, seg, tc, X, xs, mask, ms, occ, out, os, xbox, obox, bs, counters, items,
+                               count);
+}
+
+// The work list of one propagation: for every query q, the tiles whose
+// output words can take bits -- those within reach R (in y and z) of the
+// word box of X[q], and inside the box of the output mask when one is given
+// (one box for all queries).  One block; items {q, tile} in query order.
+__global__ void k_tile_list(Dims d, TileCfg tc, int R, int Q, const int32_t* __restrict__ xbox, long bs,
+                            const int32_t* __restrict__ mbox, int2* __restrict__ items, long cap,
+                            int* __restrict__ count) {
+  __shared__ int warp_sum[32];
+  __shared__ long base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int q0 = 0; q0 < Q; q0 += blockDim.x) {
+    const int q = q0 + threadIdx.x;
+    int ty0 = 0, ty1 = -1, tz0 = 0, tz1 = -1;
+    if (q < Q) {
+      const int32_t* b = xbox + q * bs;
+      const int bx0 = b[0], by0 = b[1], bz0 = b[2], bx1 = -b[3], by1 = -b[4], bz1 = -b[5];
+      if (bx0 <= bx1) {
+        int ylo = max(0, by0 - R), yhi = min(d.ny - 1, by1 + R);
+        int zlo = max(0, bz0 - R), zhi = min(d.nz - 1, bz1 + R);
+        if (mbox) {
+          if (mbox[0] > -mbox[3]) {
+            yhi = -1;  // empty output mask
+          } else {
+            ylo = max(ylo, mbox[1]);
+            yhi = min(yhi, -mbox[4]);
+            zlo = max(zlo, mbox[2]);
+            zhi = min(zhi, -mbox[5]);
+          }
+        }
+        if (ylo <= yhi && zlo <= zhi) {
+          ty0 = ylo / tc.TY;
+          ty1 = yhi / tc.TY;
+          tz0 = zlo / tc.TZ;
+          tz1 = zhi / tc.TZ;
+        }
+      }
+    }
+    const int c = max(0, ty1 - ty0 + 1) * max(0, tz1 - tz0 + 1);
+    // exclusive prefix sum of c over the block
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int v = lane < nwarp ? warp_sum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (lane < nwarp) warp_sum[lane] = v;  // inclusive sums of the warps
+    }
+    __syncthreads();
+    const long off = base + (warp > 0 ? warp_sum[warp - 1] : 0) + (incl - c);
+    long k = 0;
+    for (int tz = tz0; tz <= tz1; ++tz)
+      for (int ty = ty0; ty <= ty1; ++ty, ++k)
+        if (off + k < cap) items[off + k] = make_int2(q, tz * tc.tiles_y + ty);
+    __syncthreads();
+    if (threadIdx.x == 0) base += warp_sum[nwarp - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    count[0] = (int)min(base, cap);
+    count[1] = 0;  // the next item to take
+  }
 }
 
 // The same propagation with a 16-slice tile: warp i computes the output
@@ -798,12 +931,33 @@ size_t tile2_smem_bytes(const TileCfg& tc, int R) {
   return bytes <= 200 * 1024 ? bytes : 0;
 }
 
+bool propagate_listed(const TileCfg& tc, const SegDev& seg, int Q, long out_stride, const WorkList* wl) {
+  if (!wl || Q < kListMinQueries || out_stride <= 0 || tc.depth == 16 || !seg.tab) return false;
+  if (wl->cap < (long)Q * tc.tiles_y * tc.tiles_z) return false;
+  const size_t smem_o = (!seg.mask && seg.sctab) ? tile_occ_smem_bytes(tc, seg.R) : 0;
+  return smem_o > 0 || tile_smem_bytes(tc, seg.R) > 0;
+}
+
+cudaError_t launch_tile_list(const Dims& d, const TileCfg& tc, int R, int Q, const int32_t* xbox,
+                             long box_stride, const int32_t* mbox, uint32_t* out, long out_stride,
+                             const WorkList& wl, cudaStream_t st) {
+  // the blocks write only the listed tiles: the rest of every output is zero
+  cudaError_t e = cudaMemset2DAsync(out, (size_t)out_stride * 4, 0, (size_t)d.nw * 4, (size_t)Q, st);
+  if (e != cudaSuccess) return e;
+  k_tile_list<<<1, 1024, 0, st>>>(d, tc, R, Q, xbox, box_stride, mbox, wl.items, (long)Q * tc.tiles_y * tc.tiles_z,
+                                  wl.count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X,
                              long x_stride, const uint32_t* mask, long mask_stride,
                              const uint32_t* occ, uint32_t* out, long out_stride, int Q,
                              const int32_t* xbox, int32_t* obox, long box_stride, cudaStream_t st,
-                             unsigned long long* counters) {
+                             unsigned long long* counters, const WorkList* wl) {
   if (Q <= 0) return cudaSuccess;
+  // the batched form over a work list that launch_tile_list has built
+  const bool listed = propagate_listed(tc, seg, Q, out_stride, wl);
+  const int list_grid = (int)std::min<long>((long)Q * tc.tiles_y * tc.tiles_z, wl ? wl->blocks : 1);
   const size_t smem2 = tc.depth == 16 ? tile2_smem_bytes(tc, seg.R) : 0;
   if (smem2 > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * ((d.nz + 15) / 16), Q);
@@ -816,6 +970,17 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
     return cudaGetLastError();
   }
   const size_t smem_o = (!seg.mask && seg.sctab) ? tile_occ_smem_bytes(tc, seg.R) : 0;
+  if (smem_o > 0 && seg.tab && listed) {
+    if (counters)
+      k_propagate_tile_occ_list<true><<<list_grid, 256, smem_o, st>>>(
+          d, seg, tc, X, x_stride, mask, mask_stride, occ, out, out_stride, xbox, obox, box_stride, counters,
+          wl->items, wl->count);
+    else
+      k_propagate_tile_occ_list<false><<<list_grid, 256, smem_o, st>>>(
+          d, seg, tc, X, x_stride, mask, mask_stride, occ, out, out_stride, xbox, obox, box_stride, nullptr,
+          wl->items, wl->count);
+    return cudaGetLastError();
+  }
   if (smem_o > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
     if (counters)
@@ -829,6 +994,17 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
     return cudaGetLastError();
   }
   const size_t smem = tile_smem_bytes(tc, seg.R);
+  if (smem > 0 && seg.tab && listed) {
+    if (counters)
+      k_propagate_tile_list<true><<<list_grid, 256, smem, st>>>(
+          d, seg, tc, X, x_stride, mask, mask_stride, occ, out, out_stride, xbox, obox, box_stride, counters,
+          wl->items, wl->count);
+    else
+      k_propagate_tile_list<false><<<list_grid, 256, smem, st>>>(
+          d, seg, tc, X, x_stride, mask, mask_stride, occ, out, out_stride, xbox, obox, box_stride, nullptr,
+          wl->items, wl->count);
+    return cudaGetLastError();
+  }
   if (smem > 0 && seg.tab) {
     dim3 grid(tc.tiles_y * tc.tiles_z, Q);
     if (counters)
@@ -1825,6 +2001,18 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_list<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_list<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_occ_list<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_occ_list<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile_occ<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);

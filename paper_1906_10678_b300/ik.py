@@ -32,6 +32,7 @@ IK_PATH_OK, IK_PATH_RELAXED, IK_PATH_BROKEN, IK_PATH_UNREACHABLE, IK_PATH_KEPT =
 IK_OPT_EDGE_MASKS = 1
 IK_OPT_TILE_DEPTH = 2
 IK_OPT_DILATE_R2 = 3
+IK_OPT_WORK_LIST = 4
 IK_MAX_SEG = 16
 IK_MAX_LEN = 100
 
