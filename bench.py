@@ -534,7 +534,8 @@ def run_ours(args):
                         for k, v in prof.items() if v["launches"] and not k.startswith("way_k")},
             "waypoint_levels": {k: {"ms": round(prof[k]["ms"], 3), "warp_iters": work[k]["warp_iters"],
                                     "visited": work[k]["visited"], "nonzero": work[k]["nonzero"],
-                                    "blocks": work[k]["blocks"], "live_words": work[k]["out_words"]}
+                                    "blocks": work[k]["blocks"], "live_words": work[k]["out_words"],
+                                    "walk_warps": work[k]["walk_warps"], "walk_lanes": work[k]["walk_lanes"]}
                                 for k in prof if k.startswith("way_k") and prof[k]["launches"]},
         }
         line["roofline"] = roofline(prof, work, sc, N_TARGETS, clk)

@@ -422,7 +422,9 @@ IK_API int ik_profile_enable(ik_grid g, int timing, int counting);
  * event time, launches_out[i] number of launches, counters_out[8*i + 0..7]
  * = (offset-word pairs visited, pairs with a non-zero shifted input word,
  * edge-mask words read, output words with a non-empty mask, warp-level
- * offset iterations, blocks that did work, 0, 0); any output may be NULL.
+ * offset iterations, blocks that did work, warps of the tiled kernels that
+ * walked the offsets, the lanes of those warps with a non-empty mask); any
+ * output may be NULL.
  * Returns the number of kernel classes, or a negative error. */
 IK_API int ik_profile_read(ik_grid g, double* ms_out, int64_t* launches_out, uint64_t* counters_out,
                            int cap);

@@ -492,6 +492,14 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
   __syncthreads();
   uint32_t acc = 0;
   unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0;
+  if (kCount) {
+    // warps that walk the offsets, and their lanes with a non-empty mask
+    const unsigned live_lanes = __ballot_sync(kFull, m != 0);
+    if (lane == 0 && live_lanes) {
+      atomicAdd(counters + 6, 1ull);
+      atomicAdd(counters + 7, (unsigned long long)__popc(live_lanes));
+    }
+  }
   if (__any_sync(kFull, m != 0)) {
     const int side = 2 * R + 1;
     const int ylast = min(y0 + tc.TY, d.ny) - 1;

@@ -568,7 +568,8 @@ def ik_profile_read(g: int) -> dict:
         out[_lib.ik_profile_name(i).decode()] = {
             "ms": float(ms[i]), "launches": int(n[i]), "visited": int(c[i, 0]),
             "nonzero": int(c[i, 1]), "mask_words": int(c[i, 2]), "out_words": int(c[i, 3]),
-            "warp_iters": int(c[i, 4]), "blocks": int(c[i, 5])}
+            "warp_iters": int(c[i, 4]), "blocks": int(c[i, 5]), "walk_warps": int(c[i, 6]),
+            "walk_lanes": int(c[i, 7])}
     return out
 
 
