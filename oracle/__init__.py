@@ -295,6 +295,34 @@ def plan_path(occ, lengths, reach_pose, W: int, delta: int = 3, eps2: int = 2,
     return poses, relax, st.value
 
 
+def plan_path_follow(occ, lengths, reach_pose, n: int, fold: bool, rad, eps2: int = 2,
+                     eps2_max: int = 8, max_relax: int = -1, tol: float = 0.5):
+    """The paper's follower and filter: the follower is joint S - fold, n
+    guide points per segment of the reach polyline up to it, joint k moving
+    at most rad[k-1] voxels per waypoint (-1: not filtered), the last
+    segment folded along the path when fold.  Returns (poses [W][S+1][3],
+    relax [W][2], status) with W = (S - fold) n + 1, or (None, None,
+    status) when the reach pose is not valid."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    lo2, hi2 = arm_bounds(lengths, tol)
+    S = len(lengths)
+    F = S - (1 if fold else 0)
+    W = F * int(n) + 1
+    rad = _i32(list(rad))
+    assert rad.shape == (F,)
+    poses = np.zeros((W, S + 1, 3), np.int32)
+    relax = np.zeros((W, 2), np.int32)
+    st = ctypes.c_int32()
+    w = _load().orc_plan_path_follow(nx, ny, nz, _p(occ), S, _p(_i32(lengths)), _p(lo2), _p(hi2),
+                                     _p(_i32(reach_pose)), int(n), int(bool(fold)), _p(rad),
+                                     int(eps2), int(eps2_max), int(max_relax), _p(poses), _p(relax),
+                                     ctypes.byref(st))
+    if w < 0:
+        return None, None, st.value
+    return poses, relax, st.value
+
+
 def replan(occ, lengths, poses_in, current: int, delta: int = 3, eps2: int = 2,
            eps2_max: int = 8, max_relax: int = -1, tol: float = 0.5):
     """Returns (poses [W][S+1][3], relax [W][2], status)."""

@@ -347,6 +347,84 @@ static std::vector<V3> guide_points(const std::vector<int>& L, const std::vector
   return g;
 }
 
+// Guide points of a follower on joint F (section "Path Planning": the n
+// collision sample points along each segment double as the waypoints): n
+// points per segment of the reach polyline p_0 .. p_F, the i-th point of
+// segment k at p_{k-1} + (i/n)(p_k - p_{k-1}) rounded half up per
+// component, i = 0 .. n-1, and a last point p_F.  W = F n + 1.
+static std::vector<V3> guide_points_per_segment(const std::vector<V3>& pose, int F, int n) {
+  std::vector<V3> g(F * n + 1);
+  for (int k = 1; k <= F; ++k) {
+    const V3& a = pose[k - 1];
+    const V3& b = pose[k];
+    const long D[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
+    for (int i = 0; i < n; ++i) {
+      long o[3];
+      for (int c = 0; c < 3; ++c) o[c] = floor_div(2L * i * D[c] + n, 2L * n);
+      g[(k - 1) * n + i] = V3{a.x + (int)o[0], a.y + (int)o[1], a.z + (int)o[2]};
+    }
+  }
+  g[F * n] = pose[F];
+  return g;
+}
+
+// Where the folded last segment points at waypoint j (section "Path
+// Planning": the segment beyond the follower is kept out of harm's way by
+// laying it along the path the reach pose defines).  Guide point j sits at
+// nominal arc length s_j = C_{k-1} + (i/n) L_k on the polyline p_0 .. p_S
+// (C_k = L_1 + ... + L_k); the point aimed at is the one at arc length
+// s_j + L_S, on the segment k' with C_{k'-1} <= s_j + L_S < C_{k'} (the last
+// segment when s_j + L_S = C_S), as the exact rational A / den.
+static void fold_point(const std::vector<int>& L, const std::vector<V3>& pose, int F, int n, int j,
+                       long A[3], long* den) {
+  int k = j / n + 1, i = j - (k - 1) * n;
+  if (k > F) {
+    k = F;
+    i = n;
+  }
+  const int S = F + 1;
+  std::vector<long> C(S + 1, 0);
+  for (int q = 1; q <= S; ++q) C[q] = C[q - 1] + L[q - 1];
+  const long T = (long)n * C[k - 1] + (long)i * L[k - 1] + (long)n * L[S - 1];  // n (s_j + L_S)
+  int kk = S;
+  for (int q = 1; q <= S; ++q)
+    if ((long)n * C[q - 1] <= T && T < (long)n * C[q]) {
+      kk = q;
+      break;
+    }
+  *den = (long)n * L[kk - 1];
+  const long num = T - (long)n * C[kk - 1];
+  const V3& a = pose[kk - 1];
+  const V3& b = pose[kk];
+  A[0] = *den * a.x + num * (b.x - a.x);
+  A[1] = *den * a.y + num * (b.y - a.y);
+  A[2] = *den * a.z + num * (b.z - a.z);
+}
+
+// The folded last segment from the follower f: among the admissible,
+// obstacle-free segments S from f that end inside the grid, the end
+// nearest to A / den (squared distance), then the smallest linear index.
+static bool fold_end(const Problem& P, const V3& f, const long A[3], long den, V3* out) {
+  const Grid& g = P.g;
+  const Segment& s = P.seg[P.S() - 1];
+  bool found = false;
+  long best = 0, best_i = 0;
+  for (size_t e = 0; e < s.offs.size(); ++e) {
+    const V3 q{f.x + s.offs[e].x, f.y + s.offs[e].y, f.z + s.offs[e].z};
+    if (!g.inside(q.x, q.y, q.z)) continue;
+    if (!edge_free(P, f, s.sc[e])) continue;
+    const long key = sq(den * q.x - A[0]) + sq(den * q.y - A[1]) + sq(den * q.z - A[2]);
+    const long qi = g.index(q.x, q.y, q.z);
+    if (!found || key < best || (key == best && qi < best_i)) {
+      found = true;
+      best = key;
+      best_i = qi;
+      *out = q;
+    }
+  }
+  return found;
+}
+
 // Waypoint target set: free voxels within squared distance eps2 of g.  When
 // it is empty the radius grows one unit of eps2 at a time up to eps2_max.
 static Set waypoint_target(const Problem& P, const V3& gpt, int eps2, int eps2_max, int* used) {
@@ -376,16 +454,16 @@ static Set waypoint_target(const Problem& P, const V3& gpt, int eps2, int eps2_m
 }
 
 // One smooth-chain step ("closest in configuration to the previously found
-// one" + "Filtering for smoothness"): with every joint k restricted to
-// C_k = V_k & Ball(ref_k, delta), find the chains root -> ... -> end in V_S,
-// by forward restriction then backward restriction, and take the
+// one" + "Filtering for smoothness"): with joint k restricted to
+// C_k = V_k & Ball(ref_k, r_k) (r2[k] = r_k^2; r2[k] < 0: joint k is not
+// filtered, C_k = V_k), find the chains root -> ... -> end in V_S, by
+// forward restriction then backward restriction, and take the
 // minimum-linear-index traceback.  Returns false when no chain fits.
-static bool smooth_step(const Problem& P, const std::vector<Set>& V, const std::vector<V3>& ref,
-                        long delta, std::vector<V3>* pose) {
+static bool smooth_step_radii(const Problem& P, const std::vector<Set>& V, const std::vector<V3>& ref,
+                              const std::vector<long>& r2, std::vector<V3>* pose) {
   const Grid& g = P.g;
   const int S = P.S();
-  const long d2 = delta * delta;
-  auto in_ball = [&](int k, long i) { return dist2(at(g, i), ref[k]) <= d2; };
+  auto in_ball = [&](int k, long i) { return r2[k] < 0 || dist2(at(g, i), ref[k]) <= r2[k]; };
   const V3 root = ref[0];
   long root_i = g.index(root.x, root.y, root.z);
   if (!V[0][root_i]) return false;
@@ -431,6 +509,12 @@ static bool smooth_step(const Problem& P, const std::vector<Set>& V, const std::
   return traceback_min_index(P, U, root, pose);
 }
 
+// Every joint within delta of its reference.
+static bool smooth_step(const Problem& P, const std::vector<Set>& V, const std::vector<V3>& ref,
+                        long delta, std::vector<V3>* pose) {
+  return smooth_step_radii(P, V, ref, std::vector<long>(P.S() + 1, delta * delta), pose);
+}
+
 static bool pose_valid(const Problem& P, const std::vector<V3>& pose) {
   const Grid& g = P.g;
   for (int k = 0; k <= P.S(); ++k)
@@ -462,6 +546,30 @@ static int smooth_ladder(const Problem& P, const std::vector<Set>& V, const std:
     long d = (long)delta + m;
     if (smooth_step(P, V, ref, d, pose)) return m;
     if (d * d >= D2) return -1;
+  }
+}
+
+// The same ladder with a radius per joint (rad[k] for joint k = 1..S, -1:
+// joint k is not filtered): try rad[k] + m for m = 0, 1, ... until a chain
+// is found, or every filtered joint's ball covers the grid, or max_relax
+// increments have been tried.
+static int smooth_ladder_radii(const Problem& P, const std::vector<Set>& V, const std::vector<V3>& ref,
+                               const std::vector<int>& rad, int max_relax, std::vector<V3>* pose) {
+  if (!any(V[0])) return -1;
+  const long D2 = diag2(P.g);
+  const int S = P.S();
+  for (int m = 0;; ++m) {
+    if (max_relax >= 0 && m > max_relax) return -1;
+    std::vector<long> r2(S + 1, -1);
+    bool covered = true;
+    for (int k = 1; k <= S; ++k) {
+      if (rad[k] < 0) continue;
+      const long r = (long)rad[k] + m;
+      r2[k] = r * r;
+      if (r * r < D2) covered = false;
+    }
+    if (smooth_step_radii(P, V, ref, r2, pose)) return m;
+    if (covered) return -1;
   }
 }
 
@@ -852,6 +960,84 @@ int orc_plan_path(int nx, int ny, int nz, const uint8_t* occ, int S, const int32
   for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
   *status_out = broken ? PATH_BROKEN : (relaxed ? PATH_RELAXED : PATH_OK);
   return 0;
+}
+
+// Path with the paper's follower and filter (sections "Path Planning" and
+// "Filtering for smoothness"): the follower is joint F = S - fold (fold = 1:
+// the distal end of segment S-1, the last segment folded along the path;
+// fold = 0: the end effector); it visits n guide points per segment of the
+// reach polyline p_0 .. p_F, each waypoint an IK solution of the arm's first
+// F segments with the follower within squared distance eps2 of the guide
+// point (growing to eps2_max when no free voxel is that close; the last
+// waypoint is p_F itself).  Backward from the reach pose, the pose at
+// waypoint j is the smooth step around pose^(j+1) in which joint k
+// (1..F) moves at most rad[k-1] voxels (rad[k-1] < 0: joint k is not
+// filtered), every radius growing by one voxel at a time on failure.  With
+// fold = 1 each pose's last joint is then fold_end from its follower
+// towards fold_point; a pose whose last segment finds no free end keeps
+// the follower's position there, records -1 and breaks the path.  A
+// waypoint with no chain repeats pose^(j+1) and records -1.
+// poses_out [W][S+1][3], relax_out [W][2] = {radius increments or -1, eps2
+// used}; returns W = F n + 1, or -1 when the reach pose is not valid.
+int orc_plan_path_follow(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
+                         const int32_t* lo2, const int32_t* hi2, const int32_t* reach_pose, int n,
+                         int fold, const int32_t* rad, int eps2, int eps2_max, int max_relax,
+                         int32_t* poses_out, int32_t* relax_out, int32_t* status_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<V3> reach = read_pose(reach_pose, S);
+  const int F = S - (fold ? 1 : 0);
+  if (n < 1 || F < 1 || !pose_valid(P, reach)) {
+    *status_out = PATH_UNREACHABLE;
+    return -1;
+  }
+  Problem PF = make_problem(nx, ny, nz, occ, F, lo2, hi2);
+  std::vector<int> L(lens, lens + S);
+  std::vector<int> radk(F + 1, -1);
+  for (int k = 1; k <= F; ++k) radk[k] = rad[k - 1];
+  const int W = F * n + 1;
+  std::vector<V3> g = guide_points_per_segment(reach, F, n);
+  std::vector<Set> Fs = forward_sets(PF, reach[0]);
+  std::vector<std::vector<V3>> tp(W);  // joints 0 .. F
+  tp[W - 1] = std::vector<V3>(reach.begin(), reach.begin() + F + 1);
+  relax_out[2 * (W - 1)] = 0;
+  relax_out[2 * (W - 1) + 1] = 0;
+  bool relaxed = false, broken = false;
+  for (int j = W - 2; j >= 0; --j) {
+    int used = -1;
+    Set T = waypoint_target(PF, g[j], eps2, eps2_max, &used);
+    if (used != eps2) relaxed = true;
+    std::vector<Set> V = waypoint_V(PF, Fs, T);
+    std::vector<V3> pose;
+    const int m = smooth_ladder_radii(PF, V, tp[j + 1], radk, max_relax, &pose);
+    relax_out[2 * j + 1] = used;
+    if (m < 0) {
+      broken = true;
+      tp[j] = tp[j + 1];
+      relax_out[2 * j] = -1;
+    } else {
+      if (m > 0) relaxed = true;
+      tp[j] = pose;
+      relax_out[2 * j] = m;
+    }
+  }
+  for (int j = 0; j < W; ++j) {
+    std::vector<V3> full = tp[j];
+    if (fold) {
+      long A[3], den;
+      fold_point(L, reach, F, n, j, A, &den);
+      V3 q;
+      if (fold_end(P, tp[j][F], A, den, &q)) {
+        full.push_back(q);
+      } else {
+        full.push_back(tp[j][F]);
+        relax_out[2 * j] = -1;
+        broken = true;
+      }
+    }
+    write_pose(full, poses_out + (size_t)j * 3 * (S + 1));
+  }
+  *status_out = broken ? PATH_BROKEN : (relaxed ? PATH_RELAXED : PATH_OK);
+  return W;
 }
 
 // Midcourse replan ("Dynamic Obstacles"), given the current occupancy:

@@ -729,6 +729,203 @@ def test_plan_path_invariants_c1():
                 assert (np.sum(step * step, axis=1) <= d * d).all()
 
 
+# ------------------------------------------ follower path (the paper's form)
+
+def _guide_follow_fraction(pose, F, n):
+    """n guide points per segment up to joint F, exact, rounding half up."""
+    out = []
+    for k in range(1, F + 1):
+        a, b = pose[k - 1], pose[k]
+        for i in range(n):
+            out.append(tuple(int(a[c]) + floor(Fraction(i, n) * int(b[c] - a[c]) + Fraction(1, 2))
+                             for c in range(3)))
+    out.append(tuple(int(v) for v in pose[F]))
+    return out
+
+
+def _fold_target(lengths, pose, F, n, j):
+    """The point L_S further along the reach polyline than guide point j
+    (nominal arc lengths), as exact fractions."""
+    S = len(lengths)
+    C = [0]
+    for L in lengths:
+        C.append(C[-1] + L)
+    k, i = j // n + 1, j % n
+    if k > F:
+        k, i = F, n
+    s = C[k - 1] + Fraction(i * lengths[k - 1], n) + lengths[S - 1]
+    kk = S
+    for q in range(1, S + 1):
+        if C[q - 1] <= s < C[q]:
+            kk = q
+            break
+    f = (s - C[kk - 1]) / lengths[kk - 1]
+    a, b = pose[kk - 1], pose[kk]
+    return tuple(int(a[c]) + f * int(b[c] - a[c]) for c in range(3))
+
+
+def _radius_chains(ch, root, ref, r2, targets):
+    """All valid chains with joint k within sqrt(r2[k]) of ref[k] (r2[k] < 0:
+    anywhere), ending in targets."""
+    out = []
+
+    def rec(chain, k):
+        if k > ch.S:
+            if chain[-1] in targets:
+                out.append(tuple(chain))
+            return
+        p = chain[-1]
+        for d in ch.offs[k - 1]:
+            q = (p[0] + d[0], p[1] + d[1], p[2] + d[2])
+            if not ch.inside(q):
+                continue
+            if r2[k] >= 0 and sum((q[i] - ref[k][i]) ** 2 for i in range(3)) > r2[k]:
+                continue
+            if ch.edge(p, q):
+                chain.append(q)
+                rec(chain, k + 1)
+                chain.pop()
+
+    rec([root], 1)
+    return out
+
+
+def _brute_follow(ch, chF, lengths, reach, n, fold, rad, eps2, eps2_max):
+    """The follower rule with each smooth step solved by enumeration and the
+    folded segment by a scan of its shell."""
+    S = len(lengths)
+    F = S - (1 if fold else 0)
+    W = F * n + 1
+    g = _guide_follow_fraction(reach, F, n)
+    rt = tuple(tuple(int(v) for v in p) for p in np.asarray(reach).tolist())
+    root = rt[0]
+    tp = [None] * W
+    relax = [[0, 0] for _ in range(W)]
+    tp[W - 1] = rt[:F + 1]
+    diag2 = (ch.nx - 1) ** 2 + (ch.ny - 1) ** 2 + (ch.nz - 1) ** 2
+    for j in range(W - 2, -1, -1):
+        T, used = set(), -1
+        for e2 in range(eps2, max(eps2, eps2_max) + 1):
+            T = {(x, y, z) for z in range(ch.nz) for y in range(ch.ny) for x in range(ch.nx)
+                 if (x - g[j][0]) ** 2 + (y - g[j][1]) ** 2 + (z - g[j][2]) ** 2 <= e2
+                 and ch.free((x, y, z))}
+            if T:
+                used = e2
+                break
+        relax[j][1] = used
+        ref = tp[j + 1]
+        m = 0
+        while True:
+            r2 = [None] + [-1 if r < 0 else (r + m) ** 2 for r in rad]
+            good = _radius_chains(chF, root, ref, r2, T)
+            if good:
+                tp[j] = chF.lexmin(good)
+                relax[j][0] = m
+                break
+            if all(r < 0 or (r + m) ** 2 >= diag2 for r in rad):
+                tp[j] = ref
+                relax[j][0] = -1
+                break
+            m += 1
+    full = []
+    for j in range(W):
+        pose = list(tp[j])
+        if fold:
+            a = _fold_target(lengths, reach, F, n, j)
+            f = pose[F]
+            best = None
+            for d in ch.offs[S - 1]:
+                q = (f[0] + d[0], f[1] + d[1], f[2] + d[2])
+                if not ch.inside(q) or not ch.edge(f, q):
+                    continue
+                key = (sum((q[c] - a[c]) ** 2 for c in range(3)), ch.index(q))
+                if best is None or key < best[0]:
+                    best = (key, q)
+            if best is None:
+                pose.append(f)
+                relax[j][0] = -1
+            else:
+                pose.append(best[1])
+        full.append(tuple(pose))
+    return full, relax
+
+
+def test_guide_follow_straight_arm():
+    # segments along x of lengths 4, 3, 5: two points per segment up to joint 2
+    lengths = [4, 3, 5]
+    pose = np.array([[0, 0, 0], [4, 0, 0], [7, 0, 0], [12, 0, 0]])
+    assert _guide_follow_fraction(pose, 2, 2) == [(0, 0, 0), (2, 0, 0), (4, 0, 0), (6, 0, 0), (7, 0, 0)]
+    # the fold target of the last waypoint is the end effector; of the first,
+    # the point 5 voxels along the polyline from the root
+    assert _fold_target(lengths, pose, 2, 2, 4) == (12, 0, 0)
+    assert _fold_target(lengths, pose, 2, 2, 0) == (5, 0, 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("fold", [True, False])
+def test_plan_path_follow_vs_enumeration(seed, fold):
+    rng = np.random.default_rng(900 + seed)
+    shape = (10, 10, 8)
+    lengths = (3, 3, 2, 2)
+    root = (5, 5, 0)
+    boxes = _rand_scene(rng, shape, 5, 2, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    bounds = [O.shell_bounds(L) for L in lengths]
+    F = len(lengths) - (1 if fold else 0)
+    ch = BF.Chains(BF.occupancy(shape, boxes), bounds)
+    chF = BF.Chains(BF.occupancy(shape, boxes), bounds[:F])
+    free = np.argwhere(occ == 0)[:, ::-1]
+    for _ in range(50):
+        t = tuple(int(v) for v in free[rng.integers(len(free))])
+        poses, found, _ = O.reach_many(occ, lengths, root, [t])
+        if found[0]:
+            break
+    assert found[0]
+    reach = poses[0]
+    n = 2
+    rad = [1, 2] + [-1] * (F - 2)
+    p_o, r_o, st = O.plan_path_follow(occ, lengths, reach, n, fold, rad, eps2=1, eps2_max=4)
+    p_b, r_b = _brute_follow(ch, chF, lengths, reach, n, fold, rad, 1, 4)
+    assert [tuple(map(tuple, p.tolist())) for p in p_o] == p_b
+    assert r_o.tolist() == r_b
+    want = (O.PATH_BROKEN if any(r[0] < 0 for r in r_b) else
+            O.PATH_RELAXED if any(r[0] > 0 or (r[1] != 1) for r in r_b[:-1]) else O.PATH_OK)
+    assert st == want
+    assert (p_o[-1] == reach).all()
+
+
+def test_plan_path_follow_invariants_c1():
+    sc = G.c1_scene(1)
+    occ = O.rasterize(sc.shape, sc.boxes)
+    targets = G.draw_targets(sc, 3, 2)
+    poses, found, _ = O.reach_many(occ, sc.lengths, sc.root, targets)
+    S = len(sc.lengths)
+    n, rad = 4, [2, 3, -1]
+    for i in np.nonzero(found)[0]:
+        path, relax, st = O.plan_path_follow(occ, sc.lengths, poses[i], n, True, rad)
+        g = _guide_follow_fraction(poses[i], S - 1, n)
+        assert len(path) == (S - 1) * n + 1 and (path[-1] == poses[i]).all()
+        for j in range(len(path)):
+            if relax[j][0] < 0:
+                continue
+            assert O.pose_valid(occ, sc.lengths, path[j])
+            e = path[j][S - 1] - np.array(g[j])
+            assert int(e @ e) <= max(relax[j][1], 0)
+            if j < len(path) - 1:
+                step = path[j] - path[j + 1]
+                for k in (1, 2):
+                    d = rad[k - 1] + relax[j][0]
+                    assert int(step[k] @ step[k]) <= d * d
+
+
+def test_plan_path_follow_rejects_invalid_reach():
+    sc = G.c1_scene(1)
+    occ = O.rasterize(sc.shape, sc.boxes)
+    bad = np.zeros((len(sc.lengths) + 1, 3), np.int32)
+    path, relax, st = O.plan_path_follow(occ, sc.lengths, bad, 2, True, [2, 3, -1])
+    assert path is None and st == O.PATH_UNREACHABLE
+
+
 # -------------------------------------------------------------------- replan
 
 def test_replan_keeps_valid_path_and_fixes_cut():
