@@ -270,6 +270,41 @@ IK_API int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_p
 IK_API int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const ik_path_params* pp,
                  int32_t* poses_out, int32_t* relax_out, int* status);
 
+/* The path in the paper's form (sections "Path Planning" and "Filtering for
+ * smoothness").  The follower is joint F = n_seg - fold: with fold = 1 the
+ * distal end of segment n_seg-1, whose waypoint poses are IK solutions of
+ * the arm's first F segments, the last segment being folded along the path;
+ * with fold = 0 the end effector.  Its guide points are n_per_seg points per
+ * segment of the reach polyline p_0 .. p_F (the i-th point of segment k at
+ * p_{k-1} + (i/n)(p_k - p_{k-1}) rounded half up per component, i = 0 ..
+ * n-1, then p_F), so n_way = F n_per_seg + 1; the follower lands within
+ * squared distance eps2 of its guide point (growing to eps2_max as in
+ * ik_plan_path; the last waypoint is p_F itself).  Backward from the reach
+ * pose, the pose at waypoint j is the smooth step around pose^(j+1) in which
+ * joint k = 1..F moves at most radius[k-1] voxels (-1: joint k is not
+ * filtered; the paper filters joints 1 and 2, about half and one waypoint
+ * spacing plus slack), all radii growing by one voxel at a time on failure
+ * (max_relax as in ik_path_params).  With fold = 1 the last joint of every
+ * pose is then the end of an admissible, obstacle-free segment n_seg from the
+ * follower, inside the grid, nearest to the point at nominal arc length
+ * len[n_seg-1] beyond the guide point along p_0 .. p_n_seg (then the smallest
+ * linear index); when none exists the end stays at the follower, the
+ * waypoint records -1 and the path is IK_PATH_BROKEN.  reach_pose
+ * [n_seg+1][3]; poses_out [n_way][n_seg+1][3]; relax_out [n_way][2] = {radius
+ * increments or -1, eps2 used}; *status as for ik_plan_path.  An arm with
+ * direction limits (ik_set_segment_limits) is refused with
+ * IK_ERR_UNSUPPORTED; unfiltered joints are searched over their whole
+ * survivor sets, which is slow on large grids. */
+typedef struct {
+  int32_t n_per_seg;          /* 1..64 */
+  int32_t fold;               /* 0 or 1 */
+  int32_t radius[IK_MAX_SEG]; /* radius[k-1] for joint k = 1..F: >= 0, or -1 */
+  int32_t eps2, eps2_max, max_relax;
+} ik_follow_params;
+IK_API int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reach_pose,
+                               const ik_follow_params* fp, int32_t* poses_out, int32_t* relax_out,
+                               int* status);
+
 /* Path between arbitrary poses (section "Path between Arbitrary Poses"): a
  * virtual arm guide_arm, rooted at the end effector of start_pose, reaches
  * for the target with the reach search of ik_solve_reach; its pose is the

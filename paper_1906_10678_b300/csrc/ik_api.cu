@@ -59,6 +59,7 @@ struct ik_grid_s {
   DevBuf b_old;
   DevBuf b_rp, b_rin, b_rc;  // batched replan: bookkeeping, host-form inputs
   DevBuf b_list;             // work list of the batched propagations
+  DevBuf b_tposes, b_fold;   // follower path: poses of the follower's joints, fold points
   int num_sms = 148;
   // per-kernel profiling: events recorded on st around each launch
   bool prof_on = false, count_on = false;
@@ -680,7 +681,7 @@ int ik_destroy_grid(ik_grid g) {
   DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->F_box, &g->V_box, &g->Vw_box,
                     &g->b_rp, &g->b_rin, &g->b_rc, &g->b_root, &g->b_targets,
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
-                    &g->b_g, &g->b_valid, &g->b_old, &g->b_list};
+                    &g->b_g, &g->b_valid, &g->b_old, &g->b_list, &g->b_tposes, &g->b_fold};
   for (DevBuf* b : bufs) cudaFree(b->p);
   for (void* p : g->retired) cudaFree(p);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
@@ -971,7 +972,7 @@ int ik_guide(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, int n_way,
 static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reach,
                               const int32_t* d_found, int P, int W, int j_lo, int eps2,
                               int eps2_max, const int32_t* c_arr = nullptr,
-                              const GuideArm* ga = nullptr) {
+                              const GuideArm* ga = nullptr, int32_t* fold_at = nullptr) {
   const Dims& d = g->d;
   const int S = ad.S;
   const long qs = (long)(S + 1) * d.nw;
@@ -990,7 +991,7 @@ static int waypoint_sets_impl(ik_grid g, const ArmDev& ad, const int32_t* d_reac
     ProfScope ps(g, P_GUIDE);
     CK(launch_guide_targets(d, ad, g->d_occ, F + (long)S * d.nw, d_reach, d_found, P, W, j_lo, eps2,
                             eps2_max, ptr<int32_t>(g->b_g), ptr<int32_t>(g->b_eps), Vw, wb, g->st,
-                            c_arr, ga));
+                            c_arr, ga, fold_at));
   }
   if (j_lo == 0) return backward_sets(g, ad, Vw, P * W, P_BWD_WAY, wb);
   // only waypoints j >= j_lo (P == 1 in that case)
@@ -1035,7 +1036,7 @@ int ik_waypoint_sets(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, in
 // whose preset poses are in d_poses.
 static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int P, int mode, int c,
                       const int32_t* d_found, int32_t* d_poses, int32_t* d_relax, int32_t* d_status,
-                      const int32_t* c_arr = nullptr) {
+                      const int32_t* c_arr = nullptr, const int32_t* rad = nullptr) {
   const Dims& d = g->d;
   const int S = ad.S;
   int rc = ensure(g, g->chain, (size_t)P * 2 * (S + 1) * d.nw * 4, true);
@@ -1056,6 +1057,11 @@ static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int
   a.scratch = ptr<uint32_t>(g->chain);
   a.relaxed_eps_base = pp->eps2;
   a.c_arr = c_arr;
+  // the given radius per joint, or delta for every joint
+  a.per_joint = rad != nullptr;
+  a.rad[0] = -1;
+  for (int k = 1; k <= IK_MAX_SEG; ++k) a.rad[k] = (rad && k <= S) ? rad[k - 1] : pp->delta;
+  a.vbox = ptr<int32_t>(g->Vw_box);
   {
     ProfScope ps(g, P_CHAIN);
     CK(launch_smooth_chain(d, ad, a, g->st));
@@ -1120,6 +1126,80 @@ int ik_plan_path(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const 
   if ((rc = chain_impl(g, ad, pp, 1, 0, 0, nullptr, dposes, ptr<int32_t>(g->b_relax),
                        ptr<int32_t>(g->b_status))))
     return rc;
+  int32_t st = 0;
+  if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W, 0))) return rc;
+  if ((rc = copy_out(g, relax_out, g->b_relax.p, (size_t)8 * W, 0))) return rc;
+  if ((rc = copy_out(g, &st, g->b_status.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  *status = st;
+  return IK_OK;
+}
+
+int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const ik_follow_params* fp,
+                        int32_t* poses_out, int32_t* relax_out, int* status) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!reach_pose || !poses_out || !relax_out || !status || !fp) return IK_ERR_ARG;
+  if ((rc = check_arm(arm))) return rc;
+  const int S = arm->n_seg, fold = fp->fold;
+  const int F = S - (fold ? 1 : 0), n = fp->n_per_seg;
+  if ((fold != 0 && fold != 1) || F < 1 || n < 1 || n > 64 || fp->eps2 < 0 || fp->eps2 > 4096 ||
+      fp->eps2_max < 0 || fp->eps2_max > 4096 || fp->max_relax < -1)
+    return IK_ERR_ARG;
+  for (int k = 0; k < F; ++k)
+    if (fp->radius[k] < -1 || fp->radius[k] > 4096) return IK_ERR_ARG;
+  const int W = F * n + 1;
+  if (W > 4096) return IK_ERR_ARG;
+  // the paper's form has no direction limits: an arm with limits is refused
+  if (arm_limits(g, arm)) return IK_ERR_UNSUPPORTED;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, reach_pose, &ad, &key))) return rc;
+  const size_t pose_bytes = (size_t)12 * (S + 1), tpose_bytes = (size_t)12 * (F + 1);
+  // the reach pose must be a valid pose of this arm in this grid
+  if ((rc = to_device(g, g->b_reach, reach_pose, pose_bytes))) return rc;
+  if ((rc = ensure(g, g->b_valid, 4))) return rc;
+  if ((rc = validate_impl(g, ad, ptr<int32_t>(g->b_reach), 1, ptr<int32_t>(g->b_valid)))) return rc;
+  int32_t valid = 0;
+  if ((rc = copy_out(g, &valid, g->b_valid.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  if (!valid) {
+    *status = IK_PATH_UNREACHABLE;
+    return IK_OK;
+  }
+  // the follower's arm: the first F segments (their device tables as resolved)
+  ArmDev af = ad;
+  af.S = F;
+  std::vector<std::pair<int, int>> keyF(key.begin(), key.begin() + F);
+  if ((rc = ensure_forward(g, af, keyF, reach_pose))) return rc;
+  GuideArm ga;
+  ga.S = F;
+  for (int k = 0; k < S; ++k) ga.len[k] = arm->len[k];
+  ga.n_per_seg = n;
+  ga.pose_joints = S + 1;
+  ga.fold_len = fold ? arm->len[S - 1] : 0;
+  if ((rc = ensure(g, g->b_fold, (size_t)16 * W))) return rc;
+  if ((rc = waypoint_sets_impl(g, af, ptr<int32_t>(g->b_reach), nullptr, 1, W, 0, fp->eps2, fp->eps2_max,
+                               nullptr, &ga, fold ? ptr<int32_t>(g->b_fold) : nullptr)))
+    return rc;
+  if ((rc = ensure(g, g->b_tposes, tpose_bytes * W))) return rc;
+  if ((rc = ensure(g, g->b_poses, pose_bytes * W))) return rc;
+  if ((rc = ensure(g, g->b_relax, (size_t)8 * W))) return rc;
+  if ((rc = ensure(g, g->b_status, 4))) return rc;
+  int32_t* tposes = ptr<int32_t>(g->b_tposes);
+  // the last waypoint's follower pose: the reach pose's joints 0 .. F
+  CK(cudaMemcpyAsync(tposes + (long)(W - 1) * 3 * (F + 1), g->b_reach.p, tpose_bytes,
+                     cudaMemcpyDeviceToDevice, g->st));
+  ik_path_params pp{W, 0, fp->eps2, fp->eps2_max, fp->max_relax};
+  if ((rc = chain_impl(g, af, &pp, 1, 0, 0, nullptr, tposes, ptr<int32_t>(g->b_relax),
+                       ptr<int32_t>(g->b_status), nullptr, fp->radius)))
+    return rc;
+  int32_t* dposes = fold ? ptr<int32_t>(g->b_poses) : tposes;
+  if (fold) {
+    ProfScope ps(g, P_CHAIN);
+    CK(launch_fold_last(g->d, ad.seg[S - 1], S, 1, W, tposes, ptr<int32_t>(g->b_fold), dposes,
+                        ptr<int32_t>(g->b_relax), ptr<int32_t>(g->b_status), g->st));
+  }
   int32_t st = 0;
   if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W, 0))) return rc;
   if ((rc = copy_out(g, relax_out, g->b_relax.p, (size_t)8 * W, 0))) return rc;

@@ -215,16 +215,24 @@ cudaError_t launch_traceback_nearest(const Dims& d, const ArmDev& arm, const int
 // The polyline the guide points follow: `reach` holds, per path, the S + 1
 // joints of a pose of this arm (segment count and nominal lengths).
 struct GuideArm {
-  int S;
-  int len[IK_MAX_SEG];
+  int S;                // segments of the guide polyline (joints 0 .. S of `reach`)
+  int len[IK_MAX_SEG];  // their nominal lengths; len[S]: the folded segment's (fold_len > 0)
+  int n_per_seg = 0;    // 0: W points by the nominal arc rule; n: n points per segment (W = S n + 1)
+  int pose_joints = 0;  // joints per pose record of `reach` (0: S + 1)
+  int fold_len = 0;     // > 0: also the fold points, for a last segment of this length
 };
 // Guide points and waypoint targets.  The guide follows `reach` with the
 // arm `ga` (nullptr: the path's own arm); the targets are laid out for `arm`.
+// fold_at (nullable, [P][W][4]): for ga->fold_len > 0, the point the folded
+// last segment aims at from waypoint j, as {A_x, A_y, A_z, den} = A / den:
+// nominal arc length fold_len beyond the guide point on the polyline of
+// `reach` (joints 0 .. S + 1).
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
                                  int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st,
-                                 const int32_t* c_arr = nullptr, const GuideArm* ga = nullptr);
+                                 const int32_t* c_arr = nullptr, const GuideArm* ga = nullptr,
+                                 int32_t* fold_at = nullptr);
 // Smooth chains for P paths (one block each).  mode 0 = plan (backward from
 // the reach pose), mode 1 = forward from pose c (replan).  scratch: per path
 // 2 * (S+1) * nw zeroed words.
@@ -240,9 +248,24 @@ struct ChainArgs {
   uint32_t* scratch;
   int relaxed_eps_base;     // eps2 requested (to flag eps growth)
   const int32_t* c_arr = nullptr;  // replan: per-path current waypoint (else c)
+  // per_joint: joint k = 1..S moves at most rad[k] + m voxels at relaxation
+  // m (rad[0] unused; -1: joint k is not filtered -- it stays in its
+  // survivor set, searched over that set's box from vbox); otherwise every
+  // joint moves at most delta + m
+  bool per_joint = false;
+  int rad[IK_MAX_SEG + 1];
+  const int32_t* vbox = nullptr;  // [P][W][S+1][6] min-form word boxes of the survivor sets
 };
 cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
                                 cudaStream_t st);
+// Poses [P][W][S+1][3] of a path whose follower is joint S - 1: joints
+// 0 .. S-1 from tposes [P][W][S][3], the last segment folded towards the
+// fold points [P][W][4] (see launch_guide_targets) with segment S's tables
+// sg; a pose whose last segment has no free end records -1 in relax [P][W][2]
+// and sets status [P] to IK_PATH_BROKEN.
+cudaError_t launch_fold_last(const Dims& d, const SegDev& sg, int S, int P, int W, const int32_t* tposes,
+                             const int32_t* fold_at, int32_t* poses, int32_t* relax, int32_t* status,
+                             cudaStream_t st);
 // Opt-in to large dynamic shared memory for the tiled kernels (current device).
 cudaError_t set_kernel_attributes();
 cudaError_t launch_traceback_nearest_many(const Dims& d, const ArmDev& arm, const int32_t* root,

@@ -1388,17 +1388,66 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, GuideArm ga, const uint32_t*
                                 const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
                                 const int32_t* __restrict__ found, int W, int j_lo, int eps2,
                                 int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw,
-                                int32_t* wbox, const int32_t* __restrict__ c_arr) {
+                                int32_t* wbox, const int32_t* __restrict__ c_arr,
+                                int32_t* __restrict__ fold_at) {
   const int p = blockIdx.y;
   const int j = blockIdx.x + j_lo;
   if (c_arr && j <= c_arr[p]) return;  // replan: waypoints up to the current one stay
   const int S = arm.S;    // layout of the waypoint sets
   const int GS = ga.S;    // the guide polyline's segments
-  const int32_t* R = reach + (long)p * 3 * (GS + 1);
+  const int32_t* R = reach + (long)p * 3 * (ga.pose_joints > 0 ? ga.pose_joints : GS + 1);
   __shared__ int gp[3];
   __shared__ int used;
   const bool ok = !found || found[p];
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && ga.n_per_seg > 0) {
+    // n points per segment: the i-th of segment k at p_{k-1} + (i/n)(p_k -
+    // p_{k-1}), rounded half up, and the last one at p_GS
+    const int n = ga.n_per_seg;
+    int k = j / n + 1, i = j - (k - 1) * n;
+    if (k > GS) {
+      k = GS;
+      i = n;
+    }
+    for (int c = 0; c < 3; ++c) {
+      const long a = ok ? R[3 * (k - 1) + c] : 0, b = ok ? R[3 * k + c] : 0;
+      gp[c] = (int)(a + floor_div(2L * i * (b - a) + n, 2L * n));
+      g[((long)p * W + j) * 3 + c] = gp[c];
+    }
+    if (fold_at && ga.fold_len > 0) {
+      // n times the arc length fold_len beyond this guide point, and the
+      // segment of the polyline (the fold segment GS + 1 included) it lands on
+      long C = 0;
+      for (int q = 0; q < k - 1; ++q) C += ga.len[q];
+      const long T = (long)n * C + (long)i * ga.len[k - 1] + (long)n * ga.fold_len;
+      // segment kk with n C_{kk-1} <= T < n C_kk; the fold segment when T
+      // is its far end
+      int kk = GS + 1;
+      long c0 = 0, run = 0;
+      for (int q = 1; q <= GS + 1; ++q) {
+        const long lq = q <= GS ? ga.len[q - 1] : ga.fold_len;
+        if ((long)n * run <= T && T < (long)n * (run + lq)) {
+          kk = q;
+          break;
+        }
+        run += lq;
+      }
+      if (kk == GS + 1) {
+        c0 = 0;
+        for (int q = 0; q < GS; ++q) c0 += ga.len[q];
+      } else {
+        c0 = run;
+      }
+      const long lk = kk <= GS ? ga.len[kk - 1] : ga.fold_len;
+      const long den = (long)n * lk, num = T - (long)n * c0;
+      int32_t* fa = fold_at + ((long)p * W + j) * 4;
+      for (int c = 0; c < 3; ++c) {
+        const long a = ok ? R[3 * (kk - 1) + c] : 0, b = ok ? R[3 * kk + c] : 0;
+        fa[c] = (int32_t)(den * a + num * (b - a));
+      }
+      fa[3] = (int32_t)den;
+    }
+    used = -1;
+  } else if (threadIdx.x == 0) {
     long lam = 0;
     for (int k = 0; k < GS; ++k) lam += ga.len[k];
     const long num = (long)j * lam;
@@ -1486,7 +1535,7 @@ cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_
                                  const uint32_t* F_S, const int32_t* reach, const int32_t* found,
                                  int P, int W, int j_lo, int eps2, int eps2_max, int32_t* g,
                                  int32_t* eps_used, uint32_t* Vw, int32_t* wbox, cudaStream_t st,
-                                 const int32_t* c_arr, const GuideArm* ga) {
+                                 const int32_t* c_arr, const GuideArm* ga, int32_t* fold_at) {
   if (P <= 0 || W - j_lo <= 0) return cudaSuccess;
   GuideArm own;
   if (!ga) {
@@ -1496,7 +1545,7 @@ cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_
   }
   dim3 grid(W - j_lo, P);
   k_guide_targets<<<grid, 128, 0, st>>>(d, arm, *ga, occ, F_S, reach, found, W, j_lo, eps2, eps2_max, g,
-                                        eps_used, Vw, wbox, c_arr);
+                                        eps_used, Vw, wbox, c_arr, fold_at);
   return cudaGetLastError();
 }
 
@@ -1535,25 +1584,50 @@ struct Box {
 
 constexpr int kChainThreads = 512;
 
-__device__ __forceinline__ bool covers_full(long D2, int delta) { return (long)delta * delta >= D2; }
 
 struct ChainShared {
   int ref[IK_MAX_SEG + 1][3];
   Box box[IK_MAX_SEG + 1];
+  int r2[IK_MAX_SEG + 1];  // squared ball radius of joint k, -1: no ball
+  int empty;               // some joint's search box is empty
   unsigned long long best;
   int cur[3];
 };
 
-__device__ void chain_boxes(const Dims& d, ChainShared& sh, int S, int delta) {
+// Search boxes of one feasibility test at relaxation m: the root voxel for
+// joint 0; for a filtered joint k the box of Ball(ref_k, rad[k] + m); for an
+// unfiltered one the box of its survivor set (vb: the S + 1 min-form word
+// boxes of this waypoint's sets).
+__device__ void chain_boxes(const Dims& d, ChainShared& sh, int S, int m, const int* rad,
+                            const int32_t* vb) {
+  if (threadIdx.x == 0) sh.empty = 0;
+  __syncthreads();
   if (threadIdx.x <= S) {
     const int k = threadIdx.x;
     Box b;
-    b.x0 = max(0, sh.ref[k][0] - delta);
-    b.x1 = min(d.nx - 1, sh.ref[k][0] + delta);
-    b.y0 = max(0, sh.ref[k][1] - delta);
-    b.y1 = min(d.ny - 1, sh.ref[k][1] + delta);
-    b.z0 = max(0, sh.ref[k][2] - delta);
-    b.z1 = min(d.nz - 1, sh.ref[k][2] + delta);
+    if (k == 0) {
+      b = Box{sh.ref[0][0], sh.ref[0][0], sh.ref[0][1], sh.ref[0][1], sh.ref[0][2], sh.ref[0][2]};
+      sh.r2[0] = -1;
+    } else if (rad[k] >= 0) {
+      const int r = rad[k] + m;
+      b.x0 = max(0, sh.ref[k][0] - r);
+      b.x1 = min(d.nx - 1, sh.ref[k][0] + r);
+      b.y0 = max(0, sh.ref[k][1] - r);
+      b.y1 = min(d.ny - 1, sh.ref[k][1] + r);
+      b.z0 = max(0, sh.ref[k][2] - r);
+      b.z1 = min(d.nz - 1, sh.ref[k][2] + r);
+      sh.r2[k] = r * r;
+    } else {
+      const int32_t* v = vb + 6 * k;
+      const int wx0 = v[0], wx1 = -v[3];
+      if (wx0 > wx1) {
+        b = Box{0, -1, 0, -1, 0, -1};
+        sh.empty = 1;
+      } else {
+        b = Box{32 * wx0, min(d.nx - 1, 32 * wx1 + 31), v[1], -v[4], v[2], -v[5]};
+      }
+      sh.r2[k] = -1;
+    }
     sh.box[k] = b;
   }
   __syncthreads();
@@ -1722,9 +1796,10 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
   return __reduce_or_sync(gmask, acc) & m;
 }
 
-// Forward restriction: R_0 = {root}, R_k = (V_k & Ball(ref_k, delta)) & D_k(R_{k-1}).
+// Forward restriction: R_0 = {root}, R_k = (V_k & Ball(ref_k, r_k)) & D_k(R_{k-1})
+// (no ball for an unfiltered joint).
 __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh, const uint32_t* V,
-                              uint32_t* R, int delta2, uint32_t* so) {
+                              uint32_t* R, uint32_t* so) {
   const int S = arm.S;
   if (threadIdx.x == 0) {
     const long i = lin(d, sh.ref[0][0], sh.ref[0][1], sh.ref[0][2]);
@@ -1750,7 +1825,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
       if (t < n) {
         box_word(b, t, &wx, &y, &z);
         w = ((long)z * d.ny + y) * d.wx + wx;
-        m = ball_bits(wx, y, z, sh.ref[k], delta2) & __ldg(Vk + w);
+        m = (sh.r2[k] >= 0 ? ball_bits(wx, y, z, sh.ref[k], sh.r2[k]) : 0xffffffffu) & __ldg(Vk + w);
       }
       const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m);
       if (acc && threadIdx.x % kG == 0) {
@@ -1865,8 +1940,11 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
 
 __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
   __shared__ ChainShared sh;
+  __shared__ int rad[IK_MAX_SEG + 1];  // filter radius of each joint (-1: none)
   extern __shared__ uint32_t so[];
   const int p = blockIdx.x, S = arm.S, W = a.W;
+  if (threadIdx.x <= IK_MAX_SEG) rad[threadIdx.x] = a.per_joint ? a.rad[threadIdx.x] : a.delta;
+  __syncthreads();
   const long pose_sz = 3L * (S + 1);
   int32_t* poses = a.poses + (long)p * W * pose_sz;
   int32_t* relax = a.relax + (long)p * W * 2;
@@ -1911,15 +1989,25 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDe
     // sh.box) when r_for >= 0; dirty: R / U hold words that must be cleared
     int r_for = -1;
     bool dirty = false;
-    auto covers = [&](int m) { return (long)(a.delta + m) * (a.delta + m) >= D2; };
-    // Is there a chain inside the balls of radius delta + m?  Once the ball
-    // covers the grid ((delta + m)^2 >= D2) there is, because V is non-empty.
+    const int32_t* vb = a.vbox ? a.vbox + ((long)p * W + j) * (S + 1) * 6 : nullptr;
+    // every filtered joint's ball covers the grid ((rad + m)^2 >= D2)
+    auto covers = [&](int m) {
+      for (int k = 1; k <= S; ++k)
+        if (rad[k] >= 0 && (long)(rad[k] + m) * (rad[k] + m) < D2) return false;
+      return true;
+    };
+    // Is there a chain inside the balls of radius rad + m?  Once the balls
+    // cover the grid there is, because V is non-empty.
     auto feasible = [&](int m) {
       if (covers(m)) return true;
       if (dirty) chain_clear(d, sh, S, R, U);
-      chain_boxes(d, sh, S, a.delta + m);
-      const bool ok = chain_forward(d, arm, sh, V, R, (a.delta + m) * (a.delta + m), so);
+      chain_boxes(d, sh, S, m, rad, vb);
       dirty = true;
+      if (sh.empty) {
+        r_for = -1;
+        return false;
+      }
+      const bool ok = chain_forward(d, arm, sh, V, R, so);
       r_for = ok ? m : -1;
       return ok;
     };
@@ -1969,7 +2057,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDe
     bool done = false;
     if (m_star >= 0) {
       guess = m_star;
-      if (covers_full(D2, a.delta + m_star)) {
+      if (covers(m_star)) {
         if (dirty) chain_clear(d, sh, S, R, U);
         dirty = false;
         done = chain_trace<false>(d, arm, sh, V, pose, so);
@@ -1995,6 +2083,72 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDe
   }
   if (threadIdx.x == 0)
     a.status[p] = broken ? IK_PATH_BROKEN : (relaxed ? IK_PATH_RELAXED : IK_PATH_OK);
+}
+
+// ------------------------------------------------- folded last segment
+
+// One block per (path, waypoint): the pose's joints 0 .. F come from the
+// follower chain (tposes); joint F + 1 = S is the end of the last segment
+// from the follower f: among the admissible, obstacle-free offsets of
+// segment S that end inside the grid, the end q nearest to the fold point
+// A / den (|den q - A|^2), then the smallest linear index.  Without one the
+// end stays at f, the waypoint records -1 and the path is broken.
+__global__ void k_fold_last(Dims d, SegDev sg, int S, int W, const int32_t* __restrict__ tposes,
+                            const int32_t* __restrict__ fold_at, int32_t* __restrict__ poses,
+                            int32_t* __restrict__ relax, int32_t* __restrict__ status) {
+  const int j = blockIdx.x, p = blockIdx.y, F = S - 1;
+  const int32_t* tp = tposes + ((long)p * W + j) * 3 * (F + 1);
+  int32_t* out = poses + ((long)p * W + j) * 3 * (S + 1);
+  const int32_t* fa = fold_at + ((long)p * W + j) * 4;
+  __shared__ unsigned long long best_key, best_idx;
+  if (threadIdx.x == 0) {
+    best_key = ~0ull;
+    best_idx = ~0ull;
+  }
+  for (int i = threadIdx.x; i < 3 * (F + 1); i += blockDim.x) out[i] = tp[i];
+  __syncthreads();
+  const int fx = tp[3 * F], fy = tp[3 * F + 1], fz = tp[3 * F + 2];
+  const long fi = lin(d, fx, fy, fz);
+  const long den = fa[3];
+  // pass 1: the smallest distance key; pass 2: the smallest index at that key
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = threadIdx.x; e < sg.n; e += blockDim.x) {
+      const int32_t o = __ldg(sg.off + e);
+      const int qx = fx + unpack_x(o), qy = fy + unpack_y(o), qz = fz + unpack_z(o);
+      if (!inside(d, qx, qy, qz)) continue;
+      const long ex = den * qx - fa[0], ey = den * qy - fa[1], ez = den * qz - fa[2];
+      const unsigned long long key = (unsigned long long)(ex * ex + ey * ey + ez * ez);
+      if (pass == 0 ? key >= best_key : key != best_key) continue;
+      if (!edge_bit(d, sg, e, fi)) continue;
+      if (pass == 0)
+        atomicMin(&best_key, key);
+      else
+        atomicMin(&best_idx, (unsigned long long)lin(d, qx, qy, qz));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (best_idx == ~0ull) {
+      out[3 * S] = fx;
+      out[3 * S + 1] = fy;
+      out[3 * S + 2] = fz;
+      relax[((long)p * W + j) * 2] = -1;
+      status[p] = IK_PATH_BROKEN;  // every writer stores the same value
+    } else {
+      const long qi = (long)best_idx;
+      out[3 * S] = (int)(qi % d.nx);
+      out[3 * S + 1] = (int)((qi / d.nx) % d.ny);
+      out[3 * S + 2] = (int)(qi / ((long)d.nx * d.ny));
+    }
+  }
+}
+
+cudaError_t launch_fold_last(const Dims& d, const SegDev& sg, int S, int P, int W, const int32_t* tposes,
+                             const int32_t* fold_at, int32_t* poses, int32_t* relax, int32_t* status,
+                             cudaStream_t st) {
+  if (P <= 0 || W <= 0) return cudaSuccess;
+  k_fold_last<<<dim3(W, P), 256, 0, st>>>(d, sg, S, W, tposes, fold_at, poses, relax, status);
+  return cudaGetLastError();
 }
 
 cudaError_t set_kernel_attributes() {

@@ -50,6 +50,12 @@ class IkPathParams(ctypes.Structure):
                 ("eps2_max", ctypes.c_int32), ("max_relax", ctypes.c_int32)]
 
 
+class IkFollowParams(ctypes.Structure):
+    _fields_ = [("n_per_seg", ctypes.c_int32), ("fold", ctypes.c_int32),
+                ("radius", ctypes.c_int32 * IK_MAX_SEG), ("eps2", ctypes.c_int32),
+                ("eps2_max", ctypes.c_int32), ("max_relax", ctypes.c_int32)]
+
+
 class IkProblem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("boxes", ctypes.POINTER(ctypes.c_int32)), ("n_boxes", ctypes.c_int32),
@@ -97,6 +103,8 @@ _sig("ik_guide", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_waypoint_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, _i, _vp, _vp])
 _sig("ik_plan_path", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPathParams), _vp, _vp,
                           ctypes.POINTER(_i)])
+_sig("ik_plan_path_follow", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkFollowParams), _vp,
+                                 _vp, ctypes.POINTER(_i)])
 _sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
                                 ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp, _i])
 _sig("ik_plan_between", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkArm), _vp,
@@ -123,7 +131,7 @@ _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
-    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path",
+    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path", "ik_plan_path_follow",
     "ik_reach_path_many", "ik_plan_between", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
@@ -391,6 +399,48 @@ def ik_plan_path(g: int, arm, reach_pose, n_way: int, delta: int = 3, eps2: int 
     _check(_lib.ik_plan_path(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), ctypes.byref(pp),
                              _np_ptr(poses), _np_ptr(relax), ctypes.byref(st)), "ik_plan_path")
     return poses, relax, st.value
+
+
+def ik_plan_path_follow(g: int, arm, reach_pose, n_per_seg: int, fold: bool, radius, eps2: int = 2,
+                        eps2_max: int = 8, max_relax: int = -1):
+    """The paper's follower path: follower joint S - fold, n_per_seg guide
+    points per segment, joint k filtered to radius[k-1] voxels (-1: not
+    filtered), the last segment folded along the path when fold.  Returns
+    (poses [W][S+1][3], relax [W][2], status), W = (S - fold) n_per_seg + 1."""
+    arm = _arm(arm)
+    F = arm.S - (1 if fold else 0)
+    radius = [int(r) for r in radius]
+    if len(radius) != F:
+        raise ValueError(f"radius needs {F} entries (joints 1..{F})")
+    fp = IkFollowParams()
+    fp.n_per_seg = int(n_per_seg)
+    fp.fold = 1 if fold else 0
+    for k in range(IK_MAX_SEG):
+        fp.radius[k] = radius[k] if k < F else -1
+    fp.eps2, fp.eps2_max, fp.max_relax = int(eps2), int(eps2_max), int(max_relax)
+    W = F * int(n_per_seg) + 1
+    poses = np.zeros((W, arm.S + 1, 3), np.int32)
+    relax = np.zeros((W, 2), np.int32)
+    st = _i()
+    _check(_lib.ik_plan_path_follow(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), ctypes.byref(fp),
+                                    _np_ptr(poses), _np_ptr(relax), ctypes.byref(st)),
+           "ik_plan_path_follow")
+    return poses, relax, st.value
+
+
+def paper_filter_radii(arm_lengths, n_per_seg: int, fold: bool = True, slack: int = 1):
+    """The filter of section "Filtering for smoothness": joint 1 moves about
+    half a waypoint spacing, joint 2 about one, plus slack; the other joints
+    are not filtered.  The spacing is the longest follower segment over
+    n_per_seg, rounded up."""
+    F = len(arm_lengths) - (1 if fold else 0)
+    spacing = -(-max(int(v) for v in arm_lengths[:F]) // int(n_per_seg))
+    rad = [-1] * F
+    if F >= 1:
+        rad[0] = -(-spacing // 2) + slack
+    if F >= 2:
+        rad[1] = spacing + slack
+    return rad
 
 
 def ik_reach_path_many(g: int, arm, root, targets, n_way: int, delta: int = 3, eps2: int = 2,
