@@ -295,6 +295,31 @@ def plan_path(occ, lengths, reach_pose, W: int, delta: int = 3, eps2: int = 2,
     return poses, relax, st.value
 
 
+def plan_short(occ, lengths, reach_pose, W: int, delta: int = 3, eps2: int = 2, eps2_max: int = 8,
+               max_relax: int = -1, kmax: int = 2, tol: float = 0.5):
+    """Short reaches: the guide is the pose of the shortest virtual arm
+    (L_1 .. L_{k-1}, l for k <= kmax) that reaches the target, else the reach
+    pose.  Returns (poses [W][S+1][3], relax [W][2], status, (k, l), shortcut
+    pose [k+1][3] or None); poses None when the reach pose is not valid."""
+    occ = _u8(occ)
+    nx, ny, nz = _dims(occ)
+    lo2, hi2 = arm_bounds(lengths, tol)
+    S = len(lengths)
+    poses = np.zeros((W, S + 1, 3), np.int32)
+    relax = np.zeros((W, 2), np.int32)
+    st = ctypes.c_int32()
+    sc = np.zeros(2, np.int32)
+    vpose = np.zeros((S + 1, 3), np.int32)
+    rc = _load().orc_plan_short(nx, ny, nz, _p(occ), S, _p(_i32(lengths)), _p(lo2), _p(hi2),
+                                ctypes.c_double(tol), _p(_i32(reach_pose)), int(W), int(delta), int(eps2),
+                                int(eps2_max), int(max_relax), int(kmax), _p(poses), _p(relax),
+                                ctypes.byref(st), _p(sc), _p(vpose))
+    if rc < 0:
+        return None, None, st.value, (0, 0), None
+    k, l = int(sc[0]), int(sc[1])
+    return poses, relax, st.value, (k, l), (vpose[:k + 1].copy() if k else None)
+
+
 def plan_path_follow(occ, lengths, reach_pose, n: int, fold: bool, rad, eps2: int = 2,
                      eps2_max: int = 8, max_relax: int = -1, tol: float = 0.5):
     """The paper's follower and filter: the follower is joint S - fold, n

@@ -921,6 +921,10 @@ int orc_waypoint_sets(int nx, int ny, int nz, const uint8_t* occ, int S, const i
 // pose^(j+1) with the relaxation ladder.  A waypoint whose survivor set is
 // empty is skipped (its pose repeats pose^(j+1), record -1).
 // relax_out [W][2] = {delta increments or -1, eps2 used}.
+static void plan_backward(const Problem& P, const std::vector<V3>& reach, const std::vector<V3>& g, int W,
+                          int delta, int eps2, int eps2_max, int max_relax, int32_t* poses_out,
+                          int32_t* relax_out, int32_t* status_out);
+
 int orc_plan_path(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
                   const int32_t* lo2, const int32_t* hi2, const int32_t* reach_pose, int W,
                   int delta, int eps2, int eps2_max, int max_relax, int32_t* poses_out,
@@ -932,7 +936,71 @@ int orc_plan_path(int nx, int ny, int nz, const uint8_t* occ, int S, const int32
     return -1;
   }
   std::vector<int> L(lens, lens + S);
-  std::vector<V3> g = guide_points(L, reach, W);
+  plan_backward(P, reach, guide_points(L, reach, W), W, delta, eps2, eps2_max, max_relax, poses_out,
+                relax_out, status_out);
+  return 0;
+}
+
+// Short reaches (section "Short Reaches": a near encounter of an early
+// segment hypothesis with the target makes a shorter path than the reach
+// pose's polyline).  For k = 1 .. kmax and, within k, l = 1 .. L_k, a virtual
+// arm of the segments L_1 .. L_{k-1} and one of length l (its shell from l
+// and tol, as for any segment: the shell tolerance is the encounter
+// tolerance) is rooted at the root and reaches for the target with the
+// reach search; the first virtual arm that reaches it has the smallest
+// nominal length L_1 + ... + L_{k-1} + l, and its pose is the guide
+// polyline (guide points by the nominal arc rule of its lengths).  Without
+// one the reach pose's polyline is the guide.  The poses then follow
+// orc_plan_path (backward from the reach pose).  shortcut_out [2] = {k, l}
+// ({0, 0}: no shortcut); vpose_out (nullable) [k+1][3], the shortcut's pose.
+int orc_plan_short(int nx, int ny, int nz, const uint8_t* occ, int S, const int32_t* lens,
+                   const int32_t* lo2, const int32_t* hi2, double tol, const int32_t* reach_pose, int W,
+                   int delta, int eps2, int eps2_max, int max_relax, int kmax, int32_t* poses_out,
+                   int32_t* relax_out, int32_t* status_out, int32_t* shortcut_out, int32_t* vpose_out) {
+  Problem P = make_problem(nx, ny, nz, occ, S, lo2, hi2);
+  std::vector<V3> reach = read_pose(reach_pose, S);
+  shortcut_out[0] = shortcut_out[1] = 0;
+  if (W < 2 || !pose_valid(P, reach)) {
+    *status_out = PATH_UNREACHABLE;
+    return -1;
+  }
+  std::vector<int> L(lens, lens + S);
+  const V3 root = reach[0], t = reach[S];
+  Set T(P.g.nvox(), 0);
+  T[P.g.index(t.x, t.y, t.z)] = 1;
+  std::vector<int> glen = L;
+  std::vector<V3> gpose = reach;
+  bool found = false;
+  for (int k = 1; k <= std::min(kmax, S) && !found; ++k) {
+    for (int l = 1; l <= L[k - 1] && !found; ++l) {
+      std::vector<int> vl(L.begin(), L.begin() + k), vlo(k), vhi(k);
+      vl[k - 1] = l;
+      for (int q = 0; q < k; ++q) shell_bounds(vl[q], tol, &vlo[q], &vhi[q]);
+      Problem Pv = make_problem(nx, ny, nz, occ, k, vlo.data(), vhi.data());
+      std::vector<Set> V = intersect(forward_sets(Pv, root), backward_sets(Pv, T));
+      std::vector<V3> vpose;
+      if (traceback_min_index(Pv, V, root, &vpose)) {
+        found = true;
+        glen = vl;
+        gpose = vpose;
+        shortcut_out[0] = k;
+        shortcut_out[1] = l;
+        if (vpose_out) write_pose(vpose, vpose_out);
+      }
+    }
+  }
+  plan_backward(P, reach, guide_points(glen, gpose, W), W, delta, eps2, eps2_max, max_relax, poses_out,
+                relax_out, status_out);
+  return 0;
+}
+
+// pose^(W-1) = reach pose; for j = W-2 .. 0 the pose at waypoint j is the
+// smooth step around pose^(j+1) with the relaxation ladder, the end effector
+// near guide point g[j].
+static void plan_backward(const Problem& P, const std::vector<V3>& reach, const std::vector<V3>& g, int W,
+                          int delta, int eps2, int eps2_max, int max_relax, int32_t* poses_out,
+                          int32_t* relax_out, int32_t* status_out) {
+  const int S = P.S();
   std::vector<Set> F = forward_sets(P, reach[0]);
   std::vector<std::vector<V3>> poses(W);
   poses[W - 1] = reach;
@@ -959,7 +1027,6 @@ int orc_plan_path(int nx, int ny, int nz, const uint8_t* occ, int S, const int32
   }
   for (int j = 0; j < W; ++j) write_pose(poses[j], poses_out + (size_t)j * 3 * (S + 1));
   *status_out = broken ? PATH_BROKEN : (relaxed ? PATH_RELAXED : PATH_OK);
-  return 0;
 }
 
 // Path with the paper's follower and filter (sections "Path Planning" and

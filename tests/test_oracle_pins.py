@@ -641,10 +641,11 @@ def _ball_chains(ch, root, ref, delta, targets):
     return out
 
 
-def _brute_plan(ch, lengths, reach, W, delta, eps2, eps2_max):
-    """The planning rule with each smooth step solved by enumeration."""
+def _brute_plan(ch, lengths, reach, W, delta, eps2, eps2_max, guide=None):
+    """The planning rule with each smooth step solved by enumeration (guide:
+    the guide points, else those of the reach pose)."""
     S = len(lengths)
-    g = _guide_fraction(lengths, reach, W)
+    g = _guide_fraction(lengths, reach, W) if guide is None else guide
     poses = [None] * W
     relax = [[0, 0] for _ in range(W)]
     poses[W - 1] = tuple(map(tuple, np.asarray(reach).tolist()))
@@ -727,6 +728,76 @@ def test_plan_path_invariants_c1():
                 step = path[j] - path[j + 1]
                 d = 3 + relax[j][0]
                 assert (np.sum(step * step, axis=1) <= d * d).all()
+
+
+# ------------------------------------------------------------- short reaches
+
+def _brute_short(shape, boxes, lengths, reach, kmax):
+    """The first virtual arm (L_1 .. L_{k-1}, l) in the order k, then l, whose
+    chains from the root reach the target, by enumeration; (k, l, lengths,
+    lexicographically smallest chain) or None."""
+    occb = BF.occupancy(shape, boxes)
+    root = tuple(int(v) for v in reach[0])
+    t = tuple(int(v) for v in reach[-1])
+    for k in range(1, min(kmax, len(lengths)) + 1):
+        for l in range(1, lengths[k - 1] + 1):
+            vl = list(lengths[:k])
+            vl[-1] = l
+            ch = BF.Chains(occb, [O.shell_bounds(v) for v in vl])
+            _, _, good = ch.joint_sets(root, [t])
+            if good:
+                return k, l, vl, ch.lexmin(good)
+    return None
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_plan_short_vs_enumeration(seed):
+    rng = np.random.default_rng(1200 + seed)
+    shape = (10, 10, 8)
+    lengths = (3, 3, 2)
+    root = (5, 5, 0)
+    boxes = _rand_scene(rng, shape, 5, 2, keep=[root])
+    occ = O.rasterize(shape, boxes)
+    ch = BF.Chains(BF.occupancy(shape, boxes), [O.shell_bounds(L) for L in lengths])
+    free = np.argwhere(occ == 0)[:, ::-1]
+    n_short = 0
+    for _ in range(40):
+        t = tuple(int(v) for v in free[rng.integers(len(free))])
+        poses, found, _ = O.reach_many(occ, lengths, root, [t])
+        if not found[0]:
+            continue
+        reach = poses[0]
+        W, delta = 5, 1
+        p_o, r_o, st, kl, vpose = O.plan_short(occ, lengths, reach, W, delta=delta, eps2=1, eps2_max=4)
+        want = _brute_short(shape, boxes, lengths, reach, 2)
+        if want is None:
+            assert kl == (0, 0) and vpose is None
+            guide = None
+        else:
+            k, l, vl, vchain = want
+            assert kl == (k, l)
+            assert [tuple(v) for v in vpose.tolist()] == list(vchain)
+            guide = _guide_fraction(vl, np.array(vchain), W)
+            n_short += 1
+        p_b, r_b = _brute_plan(ch, lengths, reach, W, delta, 1, 4, guide=guide)
+        assert [tuple(map(tuple, p.tolist())) for p in p_o] == p_b
+        assert r_o.tolist() == r_b
+        if n_short >= 2:
+            break
+    assert n_short >= 1
+
+
+def test_plan_short_falls_back_to_the_reach_polyline():
+    # the root itself as target: no virtual arm of length >= 1 ends there
+    sc = G.c1_scene(0)
+    occ = O.rasterize(sc.shape, sc.boxes)
+    poses, found, _ = O.reach_many(occ, sc.lengths, sc.root, [sc.root])
+    if not found[0]:
+        pytest.skip("no pose ends at the root in this scene")
+    p_s, r_s, st_s, kl, vpose = O.plan_short(occ, sc.lengths, poses[0], 6)
+    p_p, r_p, st_p = O.plan_path(occ, sc.lengths, poses[0], 6)
+    assert kl == (0, 0) and vpose is None
+    assert (p_s == p_p).all() and (r_s == r_p).all() and st_s == st_p
 
 
 # ------------------------------------------ follower path (the paper's form)
