@@ -305,6 +305,25 @@ IK_API int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reac
                                const ik_follow_params* fp, int32_t* poses_out, int32_t* relax_out,
                                int* status);
 
+/* Short reaches (section "Short Reaches"): ik_plan_path with a shorter guide
+ * where an early segment meets the target.  For k = 1 .. k_max and, within
+ * k, l = 1 .. len[k-1], the virtual arm of the segments len[0] .. len[k-2]
+ * and one of length l (its shell from l and arm->tol, so the shell tolerance
+ * is the encounter tolerance) is rooted at the root and reaches for the
+ * reach pose's end with the reach search of ik_solve_reach; the first one
+ * that reaches it (the smallest nominal length) gives the guide polyline
+ * (its pose, guide points by the nominal arc rule of its lengths); with none
+ * the reach pose is the guide, exactly as in ik_plan_path.  The poses then
+ * follow ik_plan_path: pose^(n_way-1) = reach_pose and the smooth steps
+ * backward.  shortcut_out [2] = {k, l} ({0, 0}: no shortcut);
+ * guide_pose_out nullable [k_max+1][3] (the first k+1 rows are the
+ * shortcut's pose when there is one).  k_max in [1, n_seg] (the paper tries
+ * segments 1 and 2).  An arm with direction limits is refused with
+ * IK_ERR_UNSUPPORTED.  Other arguments and outputs as for ik_plan_path. */
+IK_API int ik_plan_path_short(ik_grid g, const ik_arm* arm, const int32_t* reach_pose,
+                              const ik_path_params* pp, int k_max, int32_t* poses_out, int32_t* relax_out,
+                              int* status, int32_t* shortcut_out, int32_t* guide_pose_out);
+
 /* Path between arbitrary poses (section "Path between Arbitrary Poses"): a
  * virtual arm guide_arm, rooted at the end effector of start_pose, reaches
  * for the target with the reach search of ik_solve_reach; its pose is the

@@ -1209,6 +1209,99 @@ int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reach_pose,
   return IK_OK;
 }
 
+int ik_plan_path_short(ik_grid g, const ik_arm* arm, const int32_t* reach_pose, const ik_path_params* pp,
+                       int k_max, int32_t* poses_out, int32_t* relax_out, int* status, int32_t* shortcut_out,
+                       int32_t* guide_pose_out) {
+  int rc = set_device(g);
+  if (rc) return rc;
+  if (!reach_pose || !poses_out || !relax_out || !status || !shortcut_out) return IK_ERR_ARG;
+  if ((rc = check_path_params(pp))) return rc;
+  if ((rc = check_arm(arm))) return rc;
+  const int S = arm->n_seg, W = pp->n_way;
+  if (k_max < 1 || k_max > S) return IK_ERR_ARG;
+  if (arm_limits(g, arm)) return IK_ERR_UNSUPPORTED;
+  ArmDev ad;
+  std::vector<std::pair<int, int>> key;
+  if ((rc = resolve_arm(g, arm, reach_pose, &ad, &key))) return rc;
+  const size_t pose_bytes = (size_t)12 * (S + 1);
+  shortcut_out[0] = shortcut_out[1] = 0;
+  // the reach pose must be a valid pose of this arm in this grid
+  if ((rc = to_device(g, g->b_reach, reach_pose, pose_bytes))) return rc;
+  if ((rc = ensure(g, g->b_valid, 4))) return rc;
+  if ((rc = validate_impl(g, ad, ptr<int32_t>(g->b_reach), 1, ptr<int32_t>(g->b_valid)))) return rc;
+  int32_t valid = 0;
+  if ((rc = copy_out(g, &valid, g->b_valid.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  if (!valid) {
+    *status = IK_PATH_UNREACHABLE;
+    return IK_OK;
+  }
+  // the shortcut: the first virtual arm L_1 .. L_{k-1}, l (k = 1 .. k_max, then
+  // l = 1 .. L_k) whose reach search from the root finds the target
+  const int32_t* root = reach_pose;
+  const int32_t* target = reach_pose + 3 * S;
+  GuideArm ga;
+  ga.S = S;
+  for (int k = 0; k < S; ++k) ga.len[k] = arm->len[k];
+  std::vector<int32_t> gpose(reach_pose, reach_pose + 3 * (S + 1));
+  bool found = false;
+  for (int k = 1; k <= k_max && !found; ++k) {
+    for (int l = 1; l <= arm->len[k - 1] && !found; ++l) {
+      int32_t vlen[IK_MAX_SEG];
+      for (int q = 0; q < k; ++q) vlen[q] = arm->len[q];
+      vlen[k - 1] = l;
+      const ik_arm va{k, vlen, arm->tol};
+      ArmDev av;
+      std::vector<std::pair<int, int>> keyv;
+      if ((rc = resolve_arm(g, &va, root, &av, &keyv))) return rc;
+      int32_t *d_vpose = nullptr, *d_vfound = nullptr;
+      if ((rc = reach_many_impl(g, av, keyv, root, target, 1, nullptr, nullptr, nullptr, 0, &d_vpose,
+                                &d_vfound)))
+        return rc;
+      int32_t vfound = 0;
+      std::vector<int32_t> vpose((size_t)3 * (k + 1));
+      if ((rc = copy_out(g, &vfound, d_vfound, 4, 0))) return rc;
+      if ((rc = copy_out(g, vpose.data(), d_vpose, (size_t)12 * (k + 1), 0))) return rc;
+      if ((rc = sync(g))) return rc;
+      if (vfound) {
+        found = true;
+        shortcut_out[0] = k;
+        shortcut_out[1] = l;
+        ga.S = k;
+        for (int q = 0; q < k; ++q) ga.len[q] = vlen[q];
+        gpose = vpose;
+      }
+    }
+  }
+  if (found && guide_pose_out) memcpy(guide_pose_out, gpose.data(), gpose.size() * 4);
+  // the guide pose in a buffer that the actual arm's steps do not use; the
+  // actual arm's tables are resolved again (the virtual arms may share its
+  // shells, whose edge-mask boxes can have grown)
+  if ((rc = to_device(g, g->b_targets, gpose.data(), gpose.size() * 4))) return rc;
+  if ((rc = resolve_arm(g, arm, reach_pose, &ad, &key))) return rc;
+  if ((rc = ensure_forward(g, ad, key, reach_pose))) return rc;
+  if ((rc = to_device(g, g->b_reach, reach_pose, pose_bytes))) return rc;
+  if ((rc = waypoint_sets_impl(g, ad, ptr<int32_t>(g->b_targets), nullptr, 1, W, 0, pp->eps2, pp->eps2_max,
+                               nullptr, &ga)))
+    return rc;
+  if ((rc = ensure(g, g->b_poses, pose_bytes * W))) return rc;
+  if ((rc = ensure(g, g->b_relax, (size_t)8 * W))) return rc;
+  if ((rc = ensure(g, g->b_status, 4))) return rc;
+  int32_t* dposes = ptr<int32_t>(g->b_poses);
+  CK(cudaMemcpyAsync(dposes + (long)(W - 1) * 3 * (S + 1), g->b_reach.p, pose_bytes,
+                     cudaMemcpyDeviceToDevice, g->st));
+  if ((rc = chain_impl(g, ad, pp, 1, 0, 0, nullptr, dposes, ptr<int32_t>(g->b_relax),
+                       ptr<int32_t>(g->b_status))))
+    return rc;
+  int32_t st = 0;
+  if ((rc = copy_out(g, poses_out, dposes, pose_bytes * W, 0))) return rc;
+  if ((rc = copy_out(g, relax_out, g->b_relax.p, (size_t)8 * W, 0))) return rc;
+  if ((rc = copy_out(g, &st, g->b_status.p, 4, 0))) return rc;
+  if ((rc = sync(g))) return rc;
+  *status = st;
+  return IK_OK;
+}
+
 int ik_plan_between(ik_grid g, const ik_arm* arm, const int32_t* start_pose, const ik_arm* guide_arm,
                     const int32_t target[3], const ik_path_params* pp, int32_t* poses_out,
                     int32_t* relax_out, int32_t* guide_pose_out, int* status) {

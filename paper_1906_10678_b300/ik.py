@@ -103,6 +103,8 @@ _sig("ik_guide", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _vp])
 _sig("ik_waypoint_sets", _i, [_vp, ctypes.POINTER(IkArm), _vp, _i, _i, _i, _vp, _vp])
 _sig("ik_plan_path", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPathParams), _vp, _vp,
                           ctypes.POINTER(_i)])
+_sig("ik_plan_path_short", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkPathParams), _i, _vp,
+                                _vp, ctypes.POINTER(_i), _vp, _vp])
 _sig("ik_plan_path_follow", _i, [_vp, ctypes.POINTER(IkArm), _vp, ctypes.POINTER(IkFollowParams), _vp,
                                  _vp, ctypes.POINTER(_i)])
 _sig("ik_reach_path_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i,
@@ -131,7 +133,7 @@ _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
-    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path", "ik_plan_path_follow",
+    "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path", "ik_plan_path_follow", "ik_plan_path_short",
     "ik_reach_path_many", "ik_plan_between", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
@@ -399,6 +401,24 @@ def ik_plan_path(g: int, arm, reach_pose, n_way: int, delta: int = 3, eps2: int 
     _check(_lib.ik_plan_path(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), ctypes.byref(pp),
                              _np_ptr(poses), _np_ptr(relax), ctypes.byref(st)), "ik_plan_path")
     return poses, relax, st.value
+
+
+def ik_plan_path_short(g: int, arm, reach_pose, n_way: int, delta: int = 3, eps2: int = 2,
+                       eps2_max: int = 8, max_relax: int = -1, k_max: int = 2):
+    """Short reaches.  Returns (poses [W][S+1][3], relax [W][2], status,
+    (k, l), shortcut pose [k+1][3] or None)."""
+    arm = _arm(arm)
+    pp = path_params(n_way, delta, eps2, eps2_max, max_relax)
+    poses = np.zeros((n_way, arm.S + 1, 3), np.int32)
+    relax = np.zeros((n_way, 2), np.int32)
+    sc = np.zeros(2, np.int32)
+    gp = np.zeros((int(k_max) + 1, 3), np.int32)
+    st = _i()
+    _check(_lib.ik_plan_path_short(g, ctypes.byref(arm.c), _np_ptr(_i32(reach_pose)), ctypes.byref(pp),
+                                   int(k_max), _np_ptr(poses), _np_ptr(relax), ctypes.byref(st),
+                                   _np_ptr(sc), _np_ptr(gp)), "ik_plan_path_short")
+    k, l = int(sc[0]), int(sc[1])
+    return poses, relax, st.value, (k, l), (gp[:k + 1].copy() if k else None)
 
 
 def ik_plan_path_follow(g: int, arm, reach_pose, n_per_seg: int, fold: bool, radius, eps2: int = 2,
