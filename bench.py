@@ -40,6 +40,30 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+# ------------------------------------------- replicas (one process per GPU)
+
+def rank_targets(sc, n: int, rank: int):
+    """Each rank solves its own seeded batch of n targets: queries are
+    independent given the replicated grid, so no data moves between ranks."""
+    import scenegen as G
+    return G.draw_targets(sc, n, 1 + 1000 * rank)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time: the slowest rank's (a no-op for one rank)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_targets: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank's targets over the slowest rank's step."""
+    return n_targets * world / (ms_per_step / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -283,7 +307,7 @@ def run_ours(args):
     N_TARGETS = args.targets
     sc = workload(args.grid)
     # each rank solves its own batch of targets (replicas, no collective)
-    targets_np = G.draw_targets(sc, N_TARGETS, 1 + 1000 * rank)
+    targets_np = rank_targets(sc, N_TARGETS, rank)
     S = len(sc.lengths)
     stream = torch.cuda.Stream(device=dev)
     g = ik.Grid(*sc.shape, stream=stream.cuda_stream)
@@ -330,12 +354,10 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         dist.barrier()
     ms_per_step = ms / args.steps
-    value = N_TARGETS * world / (ms_per_step / 1000.0)
+    value = job_value(N_TARGETS, world, ms_per_step)
     found_np = found.cpu().numpy()
     status_np = status.cpu().numpy()
     relax_np = relax.cpu().numpy()
