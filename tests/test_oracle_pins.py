@@ -972,6 +972,7 @@ def test_plan_path_follow_invariants_c1():
     poses, found, _ = O.reach_many(occ, sc.lengths, sc.root, targets)
     S = len(sc.lengths)
     n, rad = 4, [2, 3, -1]
+    ch = BF.Chains(BF.occupancy(sc.shape, sc.boxes), [O.shell_bounds(L) for L in sc.lengths])
     for i in np.nonzero(found)[0]:
         path, relax, st = O.plan_path_follow(occ, sc.lengths, poses[i], n, True, rad)
         g = _guide_follow_fraction(poses[i], S - 1, n)
@@ -987,6 +988,16 @@ def test_plan_path_follow_invariants_c1():
                 for k in (1, 2):
                     d = rad[k - 1] + relax[j][0]
                     assert int(step[k] @ step[k]) <= d * d
+            # the folded end: nearest free shell end to the fold target
+            a = _fold_target(sc.lengths, poses[i], S - 1, n, j)
+            f = tuple(int(v) for v in path[j][S - 1])
+            best = None
+            for d in ch.offs[S - 1]:
+                q = (f[0] + d[0], f[1] + d[1], f[2] + d[2])
+                if ch.inside(q) and ch.edge(f, q):
+                    key = (sum((q[c] - a[c]) ** 2 for c in range(3)), ch.index(q))
+                    best = key if best is None or key < best else best
+            assert best is not None and ch.index(tuple(int(v) for v in path[j][S])) == best[1]
 
 
 def test_plan_path_follow_rejects_invalid_reach():
