@@ -91,7 +91,7 @@ typedef struct {
  *   n_way      number of waypoints W >= 2; waypoint 0 is the root, W-1 the target;
  *   delta      each joint moves at most delta voxels (Euclidean) between
  *              consecutive poses; on failure at a waypoint the bound grows by
- *              one voxel at a time ("best done adaptively");
+ *              one voxel at a time, only after a failure;
  *   eps2       the end effector lands within squared distance eps2 of the
  *              waypoint ("a greater epsilon"); if no free voxel is that close
  *              the radius grows by one unit of eps2 up to eps2_max;
@@ -210,7 +210,7 @@ IK_API int ik_solve_reach_many_cone(ik_grid g, const ik_arm* arm, const ik_cone*
                                     int32_t* poses_out, int32_t* found_out, uint32_t* vsets_out,
                                     int on_device);
 
-/* Reach for a target set T (a "cloud of target points", section "Dynamic
+/* Reach for a target set T (a cloud of targets, section "Dynamic
  * Obstacles"; host bit set of ik_grid_words(g) words, same layout as the
  * occupancy) with an optional approach cone.  V_n_seg = F_n_seg & T; the
  * chosen pose is the minimum-index traceback of the survivor sets, so its end

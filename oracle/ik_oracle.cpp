@@ -18,7 +18,8 @@
 //   * Step 1 / Step 2A of "The procedure for IK solution" become forward
 //     reachable sets F_k grown from the root, the backward (cone) mapping from
 //     the target becomes backward sets B_k, the gap test becomes V_k = F_k & B_k,
-//     and Step 3's "one is chosen" becomes a minimum-linear-index traceback.
+//     and Step 3's choice of one surviving chain becomes a minimum-linear-index
+//     traceback.
 //
 // Every set is a byte per voxel (no bit packing), every segment test walks
 // its supercover voxel by voxel, and every step follows the definitions in
@@ -269,7 +270,7 @@ static std::vector<Set> intersect(const std::vector<Set>& F, const std::vector<S
   return V;
 }
 
-// Reach traceback ("one is chosen"): p_0 = root; for k = 1..S, p_k is the
+// Reach traceback (Step 3 picks one surviving chain): p_0 = root; for k = 1..S, p_k is the
 // voxel of V_k with the smallest linear index among those reachable from
 // p_{k-1} by an admissible, obstacle-free segment k.  Returns false when
 // V_0 is empty.
@@ -369,7 +370,7 @@ static std::vector<V3> guide_points_per_segment(const std::vector<V3>& pose, int
 }
 
 // Where the folded last segment points at waypoint j (section "Path
-// Planning": the segment beyond the follower is kept out of harm's way by
+// Planning": the segment beyond the follower is kept clear of obstacles by
 // laying it along the path the reach pose defines).  Guide point j sits at
 // nominal arc length s_j = C_{k-1} + (i/n) L_k on the polyline p_0 .. p_S
 // (C_k = L_1 + ... + L_k); the point aimed at is the one at arc length
@@ -453,8 +454,9 @@ static Set waypoint_target(const Problem& P, const V3& gpt, int eps2, int eps2_m
   return T;
 }
 
-// One smooth-chain step ("closest in configuration to the previously found
-// one" + "Filtering for smoothness"): with joint k restricted to
+// One smooth-chain step (section "Smooth sequence computation": the pose
+// nearest in configuration to the previous one; section "Filtering for
+// smoothness"): with joint k restricted to
 // C_k = V_k & Ball(ref_k, r_k) (r2[k] = r_k^2; r2[k] < 0: joint k is not
 // filtered, C_k = V_k), find the chains root -> ... -> end in V_S, by
 // forward restriction then backward restriction, and take the
@@ -532,8 +534,8 @@ static long diag2(const Grid& g) {
   return sq(g.nx - 1) + sq(g.ny - 1) + sq(g.nz - 1);
 }
 
-// Relaxation ladder ("best done adaptively", section "Filtering for
-// smoothness"): delta, delta+1, ... until a chain is found or the ball
+// Relaxation ladder (section "Filtering for smoothness": the filter is
+// relaxed only after a waypoint fails): delta, delta+1, ... until a chain is found or the ball
 // covers the whole grid (delta^2 >= squared grid diagonal), or max_relax
 // increments have been tried (max_relax < 0: no cap).  Returns the number
 // of increments used, or -1.
@@ -742,7 +744,7 @@ int orc_reach_many(int nx, int ny, int nz, const uint8_t* occ, int S, const int3
   return 0;
 }
 
-// Reach for a target set T (bytes [nvox]; a "cloud of target points",
+// Reach for a target set T (bytes [nvox]; a cloud of targets,
 // section "Dynamic Obstacles") with an optional approach cone on the last
 // segment (nullptr: any direction).  F is grown with the full shells; the
 // backward sets from T and the traceback use segment S restricted to the
