@@ -93,7 +93,7 @@ typedef struct {
  *              consecutive poses; on failure at a waypoint the bound grows by
  *              one voxel at a time, only after a failure;
  *   eps2       the end effector lands within squared distance eps2 of the
- *              waypoint ("a greater epsilon"); if no free voxel is that close
+ *              waypoint (a looser tolerance than the reach's); if no free voxel is that close
  *              the radius grows by one unit of eps2 up to eps2_max;
  *   max_relax  cap on the number of delta increments, -1 = until the ball
  *              covers the grid. */
@@ -186,8 +186,8 @@ IK_API int ik_solve_reach_many(ik_grid g, const ik_arm* arm, const int32_t root[
 
 /* ------------------------------------------- target cones and clouds */
 /* Approach cone on the last segment (section "The gap in gMS": the backward
- * path from the target is the set of permissible angles of attack of the
- * last segment, one vector or a cone of them).  The segment vector s (from
+ * search from the target starts from the directions the last segment may
+ * arrive along, one vector or a cone of them).  The segment vector s (from
  * joint n_seg - 1 to the end effector) is admissible when s . axis > 0 and
  * cos2_den * (s . axis)^2 >= cos2_num * |s|^2 * |axis|^2, i.e. its angle to
  * the axis is at most theta with cos^2 theta = cos2_num / cos2_den (exact

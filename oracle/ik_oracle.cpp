@@ -586,8 +586,8 @@ static std::vector<Set> waypoint_V(const Problem& P, const std::vector<Set>& F, 
 }
 
 // Approach cone on the last segment (section "The gap in gMS": the backward
-// path from the target is the set of permissible angles of attack of the
-// last segment, a single vector or a cone of them).  cone = {ax, ay, az, num,
+// search from the target starts from the directions the last segment may
+// arrive along, one vector or a cone of them).  cone = {ax, ay, az, num,
 // den}: the segment vector s (from joint S-1 to the end effector) is
 // admissible when it points into the half-space of the axis a and its angle
 // to a is at most theta with cos^2 theta = num / den, i.e.

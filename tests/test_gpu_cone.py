@@ -1,6 +1,6 @@
 """Approach cones on the last segment and target clouds (section "The gap in
-gMS": the backward path starts from the permissible angles of attack of the
-last segment; section "Dynamic Obstacles": a cloud of targets) against
+gMS": the backward search starts from the directions the last segment may
+arrive along; section "Dynamic Obstacles": a cloud of targets) against
 the oracle, through the C ABI."""
 import numpy as np
 import pytest
