@@ -46,3 +46,19 @@ def test_latency_summary():
     assert st["p50_ms"] == float(np.percentile(np.arange(1, 101), 50))
     assert st["p99_ms"] == round(float(np.percentile(np.arange(1, 101), 99)), 3)
     assert serve.latency_stats([]) == {"n": 0}
+
+
+def test_tuner_cache_keys_and_missing_file(tmp_path):
+    from paper_1906_10678_b300 import build
+    build.build()
+    from paper_1906_10678_b300 import tune
+    assert tune.load(str(tmp_path / "absent.json")) == {}
+    bad = tmp_path / "bad.json"
+    bad.write_text("{not json")
+    assert tune.load(str(bad)) == {}
+    k1 = tune._key((128, 128, 128), [20, 18], 64, 32)
+    assert k1 == "128x128x128|20,18|64|32"
+    assert k1 != tune._key((128, 128, 128), [20, 18], 64, 16)
+    good = tmp_path / "good.json"
+    good.write_text('{"%s": {"depth": 8, "ms": {"8": 1.0, "16": 2.0}}}' % k1)
+    assert tune.load(str(good))[k1]["depth"] == 8
