@@ -17,7 +17,12 @@ Parity status per function (details in the C++ header comment):
   the worked supercover examples).
 * ``waypoint_sets``, ``plan_path``, ``replan``: rules stated only in words by
   the paper; pinned by brute force over restricted balls on tiny grids and by
-  invariants.  The paper prints no worked example for them.
+  invariants.  ``replan`` is pinned on every branch (kept path, forward chain
+  from the current pose, the reach pose re-solved by the nearest-joint rule
+  as a lexicographic minimum over all enumerated chains, unreachable
+  target), and copies of it with a planted mistake fail that pin.  The paper
+  prints no worked example for them.
+* ``count_pairs``: pinned against a numpy shift-and-pack count.
 
 Arrays: occupancy is uint8 ``[nz][ny][nx]`` (1 = occupied); poses are int32
 ``[S+1][3]`` in (x, y, z) order; sets are uint8 ``[..][nz][ny][nx]``.

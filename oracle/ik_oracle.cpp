@@ -31,8 +31,10 @@
 // (tests/test_oracle_pins.py).  The path planner and replanner follow
 // rules that the paper states only in words (sections "Smooth sequence
 // computation", "Filtering for smoothness", "Dynamic Obstacles"); they are
-// pinned by brute force over restricted balls on tiny grids and by
-// invariants, not by any number printed in the paper.
+// pinned by brute force over restricted balls on tiny grids (the replanner
+// on every branch, its reach re-solve against a lexicographic minimum over
+// all enumerated chains) and by invariants, not by any number printed in
+// the paper.  The word-pair count is pinned by a numpy shift-and-pack count.
 
 #include <algorithm>
 #include <cmath>

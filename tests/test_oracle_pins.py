@@ -4,7 +4,8 @@ Each test checks the oracle against a worked example, a closed form, an
 invariant, or brute-force enumeration on a tiny grid (``bruteforce.py``,
 which shares no code with the oracle).  The tests are chosen so that a
 dropped term, a wrong sign, a wrong index or a transposed operand in the
-oracle fails at least one of them (see ``test_planted_mistakes``).
+oracle fails at least one of them (``test_planted_mistakes_fail_replan_pin``
+compiles copies of the oracle with such mistakes and checks that they fail).
 """
 import os
 from fractions import Fraction
@@ -1035,6 +1036,237 @@ def test_replan_keeps_valid_path_and_fixes_cut():
             step = new[jj] - new[jj - 1]
             d = 3 + relax2[jj][0]
             assert (np.sum(step * step, axis=1) <= d * d).all()
+
+
+def _brute_valid(ch, pose):
+    """A pose is valid when every segment is a shell offset of its length
+    with an obstacle-free closed supercover inside the grid (enumeration's
+    own edge test)."""
+    for k in range(1, len(pose)):
+        p, q = tuple(pose[k - 1]), tuple(pose[k])
+        d2 = sum((q[i] - p[i]) ** 2 for i in range(3))
+        lo, hi = ch.bounds[k - 1]
+        if not (lo <= d2 <= hi and ch.edge(p, q)):
+            return False
+    return True
+
+
+def _brute_replan(ch, lengths, old, c, delta, eps2, eps2_max):
+    """The replan rule (section "Dynamic Obstacles") by enumeration: keep the
+    path when every pose after c is still valid; else keep the reach pose if
+    valid, or take among ALL valid chains from the root to the old target the
+    one whose joints are nearest the old reach pose's, compared joint by joint
+    from the root (squared distance, then linear index) -- a lexicographic
+    minimum over the enumerated chains, not a greedy walk over sets; then
+    chain poses c+1 .. W-1 forward from pose c, each the smallest chain inside
+    the balls around the previous pose, with T_{W-1} the reach pose's end."""
+    S, W = len(lengths), len(old)
+    old = [tuple(tuple(int(v) for v in p) for p in pose) for pose in old]
+    relax = [[0, 0] for _ in range(W)]
+    if all(_brute_valid(ch, old[j]) for j in range(c + 1, W)):
+        return old, relax, O.PATH_KEPT, None
+    root = old[0][0]
+    reach = old[W - 1]
+    resolved = None
+    if not _brute_valid(ch, reach):
+        _, _, good = ch.joint_sets(root, [old[W - 1][S]])
+        if not good:
+            poses = old[:c + 1] + [old[c]] * (W - c - 1)
+            for j in range(c + 1, W):
+                relax[j][0] = -1
+            return poses, relax, O.PATH_UNREACHABLE, None
+
+        def key(chain):
+            return tuple(v for k in range(1, S + 1)
+                         for v in (sum((chain[k][i] - old[W - 1][k][i]) ** 2 for i in range(3)),
+                                   ch.index(chain[k])))
+        reach = min(good, key=key)
+        resolved = (reach, ch.lexmin(good))
+    g = _guide_fraction(lengths, np.asarray(reach), W)
+    poses = list(old[:c + 1]) + [None] * (W - c - 1)
+    diag2 = (ch.nx - 1) ** 2 + (ch.ny - 1) ** 2 + (ch.nz - 1) ** 2
+    relaxed = broken = False
+    for j in range(c + 1, W):
+        if j == W - 1:
+            T, used = {reach[S]}, 0
+        else:
+            T, used = set(), -1
+            for e2 in range(eps2, max(eps2, eps2_max) + 1):
+                T = {(x, y, z) for z in range(ch.nz) for y in range(ch.ny) for x in range(ch.nx)
+                     if (x - g[j][0]) ** 2 + (y - g[j][1]) ** 2 + (z - g[j][2]) ** 2 <= e2
+                     and ch.free((x, y, z))}
+                if T:
+                    used = e2
+                    break
+            relaxed |= used != eps2
+        relax[j][1] = used
+        ref = poses[j - 1]
+        m = 0
+        while True:
+            d = delta + m
+            good = _ball_chains(ch, root, ref, d, T)
+            if good:
+                poses[j] = ch.lexmin(good)
+                relax[j][0] = m
+                relaxed |= m > 0
+                break
+            if d * d >= diag2:
+                poses[j] = ref
+                relax[j][0] = -1
+                broken = True
+                break
+            m += 1
+    st = O.PATH_BROKEN if broken else (O.PATH_RELAXED if relaxed else O.PATH_OK)
+    return poses, relax, st, resolved
+
+
+def _replan_cases():
+    """Tiny scenes, each with a planned path and the cuts that exercise every
+    branch of the replan rule: nothing cut; a later pose cut but the reach
+    pose kept; a joint of the reach pose (or a voxel of its segment) cut, so
+    that the reach pose is re-solved; the target itself occupied."""
+    cases = []
+    for seed in range(4):
+        rng = np.random.default_rng(1200 + seed)
+        shape = (10, 10, 8)
+        lengths = (3, 3, 2)
+        root = (5, 5, 0)
+        boxes = _rand_scene(rng, shape, 4, 2, keep=[root])
+        occ = O.rasterize(shape, boxes)
+        free = np.argwhere(occ == 0)[:, ::-1]
+        for _ in range(80):
+            t = tuple(int(v) for v in free[rng.integers(len(free))])
+            poses, found, _ = O.reach_many(occ, lengths, root, [t])
+            if found[0]:
+                break
+        assert found[0]
+        W = 6
+        path, _, _ = O.plan_path(occ, lengths, poses[0], W, delta=1, eps2=1, eps2_max=4)
+        reach = path[W - 1]
+        cuts = [("none", None)]
+        j = W - 3
+        cuts.append(("mid pose", tuple(int(v) for v in path[j][2])))
+        cuts.append(("reach joint 1", tuple(int(v) for v in reach[1])))
+        cuts.append(("reach joint 2", tuple(int(v) for v in reach[2])))
+        r2, r3 = (tuple(int(v) for v in reach[k]) for k in (2, 3))
+        sc_mid = [tuple(int(v) for v in p) for p in BF.supercover(r2, r3) if tuple(p) not in (r2, r3)]
+        if sc_mid:
+            cuts.append(("reach segment 3", sc_mid[len(sc_mid) // 2]))
+        cuts.append(("target", tuple(int(v) for v in reach[3])))
+        for name, v in cuts:
+            if v is not None and v == root:
+                continue
+            b = boxes if v is None else np.concatenate(
+                [boxes, np.asarray([[*v, *v]], np.int32)])
+            for c in (1, 2):
+                cases.append((f"seed {seed}, cut {name}, c={c}", shape, lengths, b, path, c))
+    return cases
+
+
+def _replan_mismatches(cases, delta=1, eps2=1, eps2_max=4, first=False):
+    bad, counts, differs = [], {}, 0
+    for name, shape, lengths, boxes, path, c in cases:
+        occ = O.rasterize(shape, boxes)
+        ch = BF.Chains(BF.occupancy(shape, boxes), [O.shell_bounds(L) for L in lengths])
+        p_o, r_o, st = O.replan(occ, lengths, path, c, delta=delta, eps2=eps2, eps2_max=eps2_max)
+        p_b, r_b, st_b, resolved = _brute_replan(ch, lengths, path, c, delta, eps2, eps2_max)
+        counts[st_b] = counts.get(st_b, 0) + 1
+        if resolved is not None and resolved[0] != resolved[1]:
+            differs += 1
+        same = (st == st_b and r_o.tolist() == r_b
+                and [tuple(map(tuple, p.tolist())) for p in p_o] == [tuple(p) for p in p_b])
+        if not same:
+            bad.append(name)
+            if first:
+                break
+    return bad, counts, differs
+
+
+def test_replan_vs_enumeration():
+    """orc_replan against enumeration on every branch: kept, forward chain
+    from pose c with the reach pose kept, the reach pose re-solved (its
+    nearest-joint rule checked as a lexicographic minimum over all valid
+    chains), and an unreachable target."""
+    bad, counts, differs = _replan_mismatches(_replan_cases())
+    assert not bad, bad
+    # every branch ran, and the re-solve's nearest rule picked a chain other
+    # than the plain minimum-index one at least once (so it is discriminated)
+    assert counts.get(O.PATH_KEPT, 0) > 0 and counts.get(O.PATH_UNREACHABLE, 0) > 0
+    assert counts.get(O.PATH_OK, 0) + counts.get(O.PATH_RELAXED, 0) > 0
+    assert differs > 0, counts
+
+
+# A mistake planted in a copy of the oracle source must fail the replan pin.
+_PLANTS = {
+    "nearest tie-break by largest index": ("(dd == best_d && qi < best)", "(dd == best_d && qi > best)"),
+    "reach re-solve by index only": ("if (best < 0 || dd < best_d ||", "if (best < 0 || false ||"),
+    "chain from c + 1": ("int m = smooth_ladder(P, V, poses[j - 1],",
+                         "int m = smooth_ladder(P, V, poses[std::max(j - 2, 0)],"),
+    "ball target at the last waypoint": ("    if (j == W - 1) {\n      T.assign(P.g.nvox(), 0);\n"
+                                         "      T[P.g.index(reach[S].x",
+                                         "    if (j == W) {\n      T.assign(P.g.nvox(), 0);\n"
+                                         "      T[P.g.index(reach[S].x"),
+}
+
+
+def _oracle_variant(tmp_path, old, new):
+    """Build a copy of the oracle with one substitution inside orc_replan."""
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(O.__file__), "ik_oracle.cpp")).read()
+    a = src.index("int orc_replan(")
+    b = src.index("\n}\n", a)
+    body = src[a:b]
+    assert body.count(old) == 1, old
+    path = tmp_path / "ik_oracle_planted.cpp"
+    path.write_text(src[:a] + body.replace(old, new) + src[b:])
+    lib = tmp_path / "libik_oracle_planted.so"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", str(path),
+                           "-o", str(lib)])
+    return ctypes.CDLL(str(lib))
+
+
+@pytest.mark.parametrize("plant", sorted(_PLANTS))
+def test_planted_mistakes_fail_replan_pin(tmp_path, plant):
+    cases = _replan_cases()
+    lib = _oracle_variant(tmp_path, *_PLANTS[plant])
+    O._load()
+    saved = O._lib
+    O._lib = lib
+    try:
+        bad, _, _ = _replan_mismatches(cases, first=True)
+    finally:
+        O._lib = saved
+    assert bad, plant
+
+
+def test_count_pairs_vs_numpy_shift():
+    """orc_count_pairs (the word-pair count of one propagation, section
+    "Implementation Performance" cost model restated for bitsets) against a
+    numpy formulation: shift the voxel set by each offset, pack 32 voxels of
+    a row per word, count the non-zero words; supercover sizes from the
+    Chebyshev-distance supercover."""
+    rng = np.random.default_rng(77)
+    nx, ny, nz = 64, 7, 6
+    for L, dens in ((2, 0.02), (3, 0.005), (3, 0.0)):
+        X = (rng.random((nz, ny, nx)) < dens).astype(np.uint8)
+        if dens > 0:
+            X[3, 3, 40] = 1
+        lo2, hi2 = O.shell_bounds(L)
+        pairs, terms = O.count_pairs(lo2, hi2, X)
+        bp = bt = 0
+        pad = 4
+        Xp = np.zeros((nz + 2 * pad, ny + 2 * pad, nx + 2 * pad), bool)
+        Xp[pad:pad + nz, pad:pad + ny, pad:pad + nx] = X.astype(bool)
+        for d in BF.shell_offsets(lo2, hi2):
+            dx, dy, dz = (int(v) for v in d)
+            sh = Xp[pad + dz:pad + dz + nz, pad + dy:pad + dy + ny, pad + dx:pad + dx + nx]
+            n = int(sh.reshape(nz, ny, nx // 32, 32).any(axis=3).sum())
+            bp += n
+            bt += n * len(BF.supercover_from_origin((dx, dy, dz)))
+        assert (pairs, terms) == (bp, bt), L
+        if dens == 0.0:
+            assert pairs == 0
 
 
 # ---------------------------------------------------------------- generators
