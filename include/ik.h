@@ -459,9 +459,12 @@ IK_API int ik_replan(ik_grid g, const ik_arm* arm, const int32_t* poses_in, int 
  * The first call on a device looks up the array's device address (with
  * that device current) and should come before any stream capture.  Every
  * call shares the array and overwrites the part it uses; calls whose work
- * overlaps on the GPU (other streams, other threads) race on it.  The call
- * is synchronous on cuda_stream (NULL: the legacy default stream).  Returns
- * IK_OK, IK_ERR_ARG, IK_ERR_UNSUPPORTED or IK_ERR_CUDA. */
+ * overlaps on the GPU (other streams, other threads) race on it.  Host
+ * threads are serialised by a lock while the tables are built and copied,
+ * but the kernels of two calls still race if their streams overlap.  The
+ * call is synchronous on cuda_stream (NULL: the legacy default stream).
+ * Returns IK_OK, IK_ERR_ARG, IK_ERR_UNSUPPORTED, IK_ERR_OOM (a CUDA call
+ * reported cudaErrorMemoryAllocation) or IK_ERR_CUDA. */
 IK_API int ik_forward_sets_noalloc(const uint32_t* occ_words, int nx, int ny, int nz,
                                    const ik_arm* arm, const int32_t root[3], uint32_t* fsets_out,
                                    void* cuda_stream);
@@ -495,6 +498,22 @@ IK_API const char* ik_profile_name(int i);
 IK_API int ik_replan_many(ik_grid g, const ik_arm* arm, const int32_t root[3], const int32_t* poses_in,
                           const int32_t* current, int n, const ik_path_params* pp,
                           int32_t* poses_out, int32_t* relax_out, int32_t* status_out, int on_device);
+
+/* ------------------------------------------------------- peak probes */
+/* Measured peaks for the rooflines of the boolean propagation (the paper
+ * gives no hardware figures for its GPU; section "Implementation
+ * Performance" only reports times).  Runs one throughput probe on the
+ * current device, enqueued on cuda_stream (NULL: legacy default stream) and
+ * waited for: kind 0 = 3-input logic ops (lop3.b32), kind 1 = funnel shifts
+ * (shf.r.wrap.b32), kind 2 = conflict-free 32-bit shared-memory word loads.
+ * blocks_per_sm (1..8) blocks of 256 threads per SM run iters (1..2^24)
+ * iterations of 128 (kinds 0, 1) or 32 (kind 2) ops per thread.  Outputs
+ * (nullable): ops_per_s_out = counted ops / event time; ms_out = event time;
+ * sm_mhz_out = the SM clock the first block saw (clock64 ticks per
+ * %globaltimer microsecond).  Allocates a few bytes of device memory per
+ * call.  Returns IK_OK, IK_ERR_ARG or IK_ERR_CUDA. */
+IK_API int ik_probe_peak(int kind, int blocks_per_sm, int iters, void* cuda_stream, double* ops_per_s_out,
+                         double* ms_out, double* sm_mhz_out);
 
 /* ------------------------------------------------------- host utilities */
 /* Shell bounds and offsets of one segment length, as the library builds

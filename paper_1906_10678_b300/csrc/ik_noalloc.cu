@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "ik_internal.h"
 
@@ -35,7 +36,11 @@ static __device__ __align__(256) int32_t g_na_scratch[kNaWords];
 // Device addresses of g_na_scratch, one per device, fetched on first use.
 int32_t* g_na_addr[kNaMaxDevices] = {nullptr};
 
-// Host staging of the tables (fixed size; no heap).
+// Host staging of the tables (fixed size; no heap).  g_na_mutex (which
+// allocates nothing) serialises host threads from the first use of g_na_addr
+// through the last copy out of these tables; a pageable-source
+// cudaMemcpyAsync has consumed its source when it returns.
+std::mutex g_na_mutex;
 int32_t h_na_off[kNaMaxOff];
 int32_t h_na_start[kNaMaxOff + IK_MAX_SEG];
 int32_t h_na_sc[kNaMaxSc];
@@ -219,6 +224,7 @@ int ik_forward_sets_noalloc(const uint32_t* occ_words, int nx, int ny, int nz, c
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(e);
   if (dev < 0 || dev >= kNaMaxDevices) return IK_ERR_UNSUPPORTED;
+  std::unique_lock<std::mutex> lock(g_na_mutex);
   if (!g_na_addr[dev]) {
     // once per device, with that device current: the host-side symbol is a
     // stand-in, the kernels need the device address
@@ -241,6 +247,7 @@ int ik_forward_sets_noalloc(const uint32_t* occ_words, int nx, int ny, int nz, c
     e = cudaMemcpyAsync(scratch + 2 * kNaMaxOff + IK_MAX_SEG, h_na_sc, (size_t)n_sc * 4,
                         cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return na_fail(e);
+  lock.unlock();  // the host tables are consumed; the kernels read the device scratch
   ikb::Dims d;
   d.nx = nx;
   d.ny = ny;

@@ -129,6 +129,7 @@ _sig("ik_profile_read", _i, [_vp, _vp, _vp, _vp, _i])
 _sig("ik_profile_name", ctypes.c_char_p, [_i])
 _sig("ik_shell_offsets", _i, [_i, ctypes.c_float, _vp, _vp, _i])
 _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
+_sig("ik_probe_peak", _i, [_i, _i, _i, _vp, _vp, _vp, _vp])
 
 EXPORTED = [
     "ik_version", "ik_strerror", "ik_last_error_message", "ik_create_grid", "ik_destroy_grid",
@@ -139,6 +140,7 @@ EXPORTED = [
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
+    "ik_probe_peak",
 ]
 
 
@@ -618,6 +620,18 @@ def ik_forward_sets_noalloc(occ_words, shape, arm, root, fsets_out, stream: int 
                                         _np_ptr(_i32(root)), _dev_ptr(fsets_out),
                                         _vp(stream) if stream else None),
            "ik_forward_sets_noalloc")
+
+
+PROBE_LOP3, PROBE_SHF, PROBE_LDS = 0, 1, 2
+
+
+def ik_probe_peak(kind: int, blocks_per_sm: int = 8, iters: int = 20000, stream: int = 0) -> dict:
+    """One throughput probe on the current device: {"ops_per_s", "ms", "sm_mhz"}."""
+    r = np.zeros(3, np.float64)
+    p = r.ctypes.data
+    _check(_lib.ik_probe_peak(int(kind), int(blocks_per_sm), int(iters), _vp(stream) if stream else None,
+                              _vp(p), _vp(p + 8), _vp(p + 16)), "ik_probe_peak")
+    return {"ops_per_s": float(r[0]), "ms": float(r[1]), "sm_mhz": float(r[2])}
 
 
 def ik_profile_enable(g: int, timing: bool = True, counting: bool = False) -> None:

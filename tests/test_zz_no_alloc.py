@@ -46,11 +46,16 @@ def test_noalloc_forward_sets_match_regular_entry_point(ik):
         ik.ik_forward_sets_noalloc(occ_d, scene.shape, scene.lengths, root, out)
         got = out.cpu().numpy().view(np.uint32).reshape(S + 1, -1)
         assert (got == want).all(), scene.name
-    # the same first case again, after the scratch held the other arms
+    # the same first case again, after the scratch held the other arms; this
+    # call must not change the device's free memory or torch's allocations
     scene, root = cases[0]
     occ_d, want = _case(ik, torch, scene, root)
     out = torch.zeros((want.size,), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
     ik.ik_forward_sets_noalloc(occ_d, scene.shape, scene.lengths, root, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
     assert (out.cpu().numpy().view(np.uint32).reshape(len(scene.lengths) + 1, -1) == want).all()
 
 
