@@ -130,10 +130,27 @@ def measured_peaks():
         return {}
 
 
-# Integer issue peak of the B300: 148 SMs x 4 schedulers x 32 lanes, one
-# warp instruction per scheduler per clock, at the maximum SM clock.
-SMS, SCHEDULERS, LANES = 148, 4, 32
-OPS_PER_PAIR = 3  # funnel shift of the input word, AND with the edge mask, OR into the output
+# Algorithmic work per non-zero (offset, output word) pair of a propagation
+# (SURVEY-style W_alg with the supercover terms paid by the edge-mask
+# kernel): one AND with the edge-mask word and one OR into the output word;
+# and two words read: the shifted source word (staged in shared memory) and
+# the edge-mask word.
+OPS_PER_PAIR = 2
+WORDS_PER_PAIR = 2
+
+
+def probe_peaks(ik, stream) -> dict:
+    """The library's own throughput probes (ik_probe_peak), best of three:
+    3-input logic ops (the integer roofline) and conflict-free 32-bit
+    shared-memory word loads (the bitset-traffic roofline), with the SM clock
+    each probe saw."""
+    out = {}
+    for kind, name, bps in ((ik.PROBE_LOP3, "lop3", 8), (ik.PROBE_SHF, "shf", 8), (ik.PROBE_LDS, "lds", 4)):
+        ik.ik_probe_peak(kind, bps, 2000, stream)
+        best = max((ik.ik_probe_peak(kind, bps, 20000, stream) for _ in range(3)),
+                   key=lambda r: r["ops_per_s"])
+        out[name] = {"per_s": best["ops_per_s"], "sm_mhz": best["sm_mhz"]}
+    return out
 
 
 # DRAM bytes (read + write) per launch of the waypoint pass on this workload
@@ -157,42 +174,81 @@ def kernel_traffic():
     return TRAFFIC_CAPTURE["bytes_per_launch"] if sha == TRAFFIC_CAPTURE["kernels_sha256"] else None
 
 
-def roofline(prof, work, sc, n_targets, clk):
-    """Roofline of the dominant kernel (the batched backward propagation).
+def _kernel_roof(name, ms, launches, ops, words, peaks, clk_mhz):
+    """Fractions of one kernel class against the probed peaks, scaled to the
+    SM clock sampled during the timed region."""
+    def at_clk(p):
+        return p["per_s"] * (clk_mhz / p["sm_mhz"]) if clk_mhz and p["sm_mhz"] else p["per_s"]
+    int_peak = at_clk(peaks["lop3"]) / 1e12
+    lds_peak = at_clk(peaks["lds"]) / 1e12
+    launches = max(1, launches)
+    t = ms / launches / 1000.0
+    ach_ops = ops / launches / t / 1e12 if t > 0 else 0.0
+    ach_words = words / launches / t / 1e12 if t > 0 else 0.0
+    return {"kernel": name, "ms_per_launch": round(ms / launches, 4), "launches": launches,
+            "alg_ops_per_launch": round(ops / launches), "alg_words_per_launch": round(words / launches),
+            "int": {"achieved": round(ach_ops, 4), "peak": round(int_peak, 3), "unit": "Tops/s",
+                    "frac": round(ach_ops / int_peak, 5)},
+            "bitset_traffic": {"achieved": round(ach_words, 4), "peak": round(lds_peak, 3),
+                               "unit": "Twords/s", "frac": round(ach_words / lds_peak, 5)}}
 
-    The propagation is integer work on on-chip data (its only HBM traffic is
-    the edge-mask words, a few percent of HBM bandwidth), so it is measured
-    against the integer issue rate.  Algorithmic work of a launch = every
-    (offset, output word) pair whose shifted input word is non-zero and
-    whose output word may still take bits, times 3 word operations; the pair
-    count comes from the kernel's own counters on an identical step.
+
+def roofline(prof, work, peaks, clk):
+    """Rooflines per kernel class (every class above 1 % of the step), and
+    the line's roofline object for the dominant one (the batched backward
+    propagation of the waypoint pass).
+
+    The work is boolean and on-chip: its rooflines are the integer issue
+    rate (3-input logic ops) and the shared-memory word-load rate, both
+    measured by the library's probes, not HBM (the pass moves well under
+    2 % of HBM bandwidth).  Algorithmic work per launch: for a propagation,
+    2 word-ops and 2 word loads per non-zero (offset, output word) pair that
+    the kernel's counters record on an identical step; for the edge masks,
+    one OR and one word load per supercover voxel term (|SC(e)| per (offset,
+    word) pair); for the smooth chain, as for a propagation, its restricted
+    propagations' non-zero pairs.  The binding roofline is the one with the
+    larger fraction.
     """
-    cls = max((k for k in prof if k.startswith("propagate")), key=lambda k: prof[k]["ms"])
-    p = prof[cls]
-    if cls == "propagate_backward_waypoints":
-        # the waypoint pass keeps its work counters per segment level
-        w = {f: sum(v[f] for k, v in work.items() if k.startswith("way_k"))
-             for f in ("visited", "nonzero", "mask_words", "out_words", "warp_iters", "blocks")}
-    else:
-        w = work[cls]
-    launches = max(1, p["launches"])
-    ops = OPS_PER_PAIR * w["nonzero"] / launches
-    ms = p["ms"] / launches
-    peak_mhz = measured_peaks().get("sm_max_mhz", 2032.0)
-    peak = SMS * SCHEDULERS * LANES * peak_mhz * 1e6 / 1e12
-    achieved = ops / (ms / 1000.0) / 1e12
-    # the dense levels run k_propagate_tile, the sparse ones its work-list
-    # form k_propagate_tile_list (same body)
-    return {"kernel": "k_propagate_tile[_list] (" + cls + ")", "bound": "alu",
-            "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "Tops/s",
-            "frac": round(achieved / peak, 5), "traffic": kernel_traffic(),
-            "alg_ops_per_launch": round(ops), "ms_per_launch": round(ms, 4),
-            "pairs_visited": w["visited"], "pairs_nonzero": w["nonzero"],
-            "mask_words_read": w["mask_words"], "warp_iters": w["warp_iters"],
-            "active_blocks": w["blocks"],
-            "mask_gbs": round(4.0 * w["mask_words"] / launches / (ms / 1000.0) / 1e9, 1),
-            "peak_source": "148 SMs x 4 schedulers x 32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
-            "sm_mhz_under_load": clk.get("sm_mhz")}
+    clk_mhz = clk.get("sm_mhz")
+    total = sum(v["ms"] for k, v in prof.items() if not k.startswith("way_k"))
+    per = {}
+    for cls in ("propagate_backward_waypoints", "propagate_forward", "propagate_backward_reach",
+                "edge_masks", "smooth_chain"):
+        p = prof.get(cls)
+        if not p or not p["launches"] or p["ms"] < 0.01 * total:
+            continue
+        if cls == "propagate_backward_waypoints":
+            w = {f: sum(v[f] for k, v in work.items() if k.startswith("way_k"))
+                 for f in ("visited", "nonzero", "mask_words")}
+        else:
+            w = work[cls]
+        if cls == "edge_masks":
+            ops, words = w["nonzero"], w["nonzero"]  # supercover terms (one OR, one word each)
+        else:
+            ops, words = OPS_PER_PAIR * w["nonzero"], WORDS_PER_PAIR * w["nonzero"]
+        r = _kernel_roof(cls, p["ms"], p["launches"], ops, words, peaks, clk_mhz)
+        r["share_of_step"] = round(p["ms"] / total, 4)
+        if cls.startswith("propagate"):
+            r["pairs_visited"], r["pairs_nonzero"] = w["visited"], w["nonzero"]
+            r["mask_words_read"] = w["mask_words"]
+        elif cls == "edge_masks":
+            r["pairs"], r["supercover_terms"] = w["visited"], w["nonzero"]
+        else:
+            r["pairs_visited"], r["pairs_nonzero"] = w["visited"], w["nonzero"]
+        per[cls] = r
+    top = per["propagate_backward_waypoints"]
+    binding = "bitset_traffic" if top["bitset_traffic"]["frac"] >= top["int"]["frac"] else "int"
+    return {"kernel": "k_propagate_tile[_list] (propagate_backward_waypoints)", "bound": "alu",
+            "achieved": top["int"]["achieved"], "peak": top["int"]["peak"], "unit": "Tops/s",
+            "frac": top["int"]["frac"], "traffic": kernel_traffic(),
+            "bitset_traffic": top["bitset_traffic"], "binding": binding,
+            "alg_ops_per_launch": top["alg_ops_per_launch"], "ms_per_launch": top["ms_per_launch"],
+            "pairs_visited": top["pairs_visited"], "pairs_nonzero": top["pairs_nonzero"],
+            "peak_source": "ik_probe_peak (lop3.b32 / ld.shared.b32 throughput probes, best of 3, "
+                           "run in this process), scaled to the SM clock sampled in the timed region",
+            "peaks_measured": {k: {"per_s": round(v["per_s"] / 1e12, 3), "unit": "T/s",
+                                   "sm_mhz": round(v["sm_mhz"], 1)} for k, v in peaks.items()},
+            "sm_mhz_under_load": clk_mhz, "per_kernel": per}
 
 
 def oracle_sample(threads: int):
@@ -228,14 +284,32 @@ def oracle_sample(threads: int):
     return passes_per_s / 32.0, wall
 
 
+def physical_cores() -> int:
+    try:
+        import psutil
+        return psutil.cpu_count(logical=False) or os.cpu_count() or 1
+    except ImportError:
+        return os.cpu_count() or 1
+
+
+LOWER_BOUND_NOTE = ("a lower bound on the oracle's cost (an upper bound on its solves/s): per "
+                    "reach+path only its 32 backward passes are counted, not the forward sets "
+                    "(shared by a batch) nor the smooth steps")
+
+
 def cpu_baseline():
+    """The oracle on all host threads, and single-threaded (the canonical
+    figure): each thread runs one backward pass of the 128^3 scene."""
     cores = os.cpu_count() or 1
     value, wall = oracle_sample(cores)
+    one, wall1 = oracle_sample(1)
     return {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{cores} unmasked backward passes (one per host thread) from seeded "
                       f"target voxels of the 128^3 scene, {wall:.1f} s wall; solves/s = passes/s "
-                      f"/ 32 (1 reach + 31 waypoint passes per reach+path; forward sets and "
-                      f"smooth steps not included)"}
+                      f"/ 32 (1 reach + 31 waypoint passes per reach+path)",
+            "single_thread": {"value": round(one, 6), "unit": UNIT, "cores": 1,
+                              "sample": f"1 backward pass, {wall1:.1f} s"},
+            "note": LOWER_BOUND_NOTE}
 
 
 def bench_config(world: int) -> dict:
@@ -253,9 +327,9 @@ def run_reference(args):
         return
     cores = os.cpu_count() or 1
     # one oracle backward pass at 128^3 takes tens of seconds of CPU: a step
-    # runs a quarter of the cores' worth of passes in parallel, so that the
-    # default --steps 5 run ends within a few minutes
-    per_step = max(1, cores // 4)
+    # runs one pass per physical core in parallel (the hyperthreads add
+    # little to the oracle's throughput and double each step's wall time)
+    per_step = physical_cores()
     # warm-up steps: load and touch the oracle library (no oracle state to warm)
     import oracle as O
     for _ in range(args.warmup):
@@ -275,8 +349,9 @@ def run_reference(args):
         "config": bench_config(world),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": per_step, "kind": "oracle",
                          "sample": f"per step {per_step} unmasked backward passes of the 128^3 scene "
-                                   f"(one per host thread, {cores} cores on the host); "
-                                   f"solves/s = passes/s / 32"},
+                                   f"(one per physical core; {cores} logical CPUs on the host); "
+                                   f"solves/s = passes/s / 32",
+                         "note": LOWER_BOUND_NOTE},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }))
@@ -411,6 +486,7 @@ def run_ours(args):
     step()
     work = ik.ik_profile_read(g.h)
     ik.ik_profile_enable(g.h, timing=False, counting=False)
+    peaks = probe_peaks(ik, stream.cuda_stream)
 
     # plain single-query form on a sample of targets
     plain_ms = []
@@ -560,7 +636,7 @@ def run_ours(args):
                                     "walk_warps": work[k]["walk_warps"], "walk_lanes": work[k]["walk_lanes"]}
                                 for k in prof if k.startswith("way_k") and prof[k]["launches"]},
         }
-        line["roofline"] = roofline(prof, work, sc, N_TARGETS, clk)
+        line["roofline"] = roofline(prof, work, peaks, clk)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

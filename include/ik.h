@@ -300,6 +300,12 @@ typedef struct {
   int32_t fold;               /* 0 or 1 */
   int32_t radius[IK_MAX_SEG]; /* radius[k-1] for joint k = 1..F: >= 0, or -1 */
   int32_t eps2, eps2_max, max_relax;
+  /* 1: ignore radius[] and take the paper's filter (section "Filtering for
+   * smoothness": joint 1 moves about half a waypoint spacing, joint 2 about
+   * one, plus one voxel of slack; the other joints unfiltered): with the
+   * spacing s = ceil(max_{k <= F} len[k-1] / n_per_seg), radius 1 =
+   * ceil(s / 2) + 1, radius 2 = s + 1, the rest -1.  0: radius[] as given. */
+  int32_t paper_radii;
 } ik_follow_params;
 IK_API int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reach_pose,
                                const ik_follow_params* fp, int32_t* poses_out, int32_t* relax_out,

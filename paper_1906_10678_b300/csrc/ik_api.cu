@@ -71,6 +71,7 @@ struct ik_grid_s {
   };
   std::vector<Rec> recs;
   unsigned long long* d_counters = nullptr;
+  std::vector<unsigned long long> h_counters;  // counts known on the host at launch time
   bool capturing = false;  // inside ik_batch_capture: no allocation, no host transfer
   bool use_masks = true;   // store per-offset edge masks (else walk supercovers on the fly)
   // Captured batches hold device pointers of this grid.  A buffer replaced
@@ -366,6 +367,12 @@ int ensure_masks(ik_grid g, ShellDev* s, const MaskBox& need) {
   {
     ProfScope ps(g, P_MASKS);
     CK(launch_edge_masks(g->d, g->tc, g->d_occ, *s, b, s->d_mask, g->st));
+  }
+  if (g->count_on) {
+    // (offset, word) pairs, and the supercover voxel terms they OR together
+    const unsigned long long words = (unsigned long long)b.words();
+    g->h_counters[kCounters * P_MASKS + 0] += (unsigned long long)s->host.off.size() * words;
+    g->h_counters[kCounters * P_MASKS + 1] += (unsigned long long)s->host.sc.size() * words;
   }
   s->mask_version = g->version;
   return IK_OK;
@@ -1062,6 +1069,7 @@ static int chain_impl(ik_grid g, const ArmDev& ad, const ik_path_params* pp, int
   a.rad[0] = -1;
   for (int k = 1; k <= IK_MAX_SEG; ++k) a.rad[k] = (rad && k <= S) ? rad[k - 1] : pp->delta;
   a.vbox = ptr<int32_t>(g->Vw_box);
+  a.counters = counters(g, P_CHAIN);
   {
     ProfScope ps(g, P_CHAIN);
     CK(launch_smooth_chain(d, ad, a, g->st));
@@ -1146,8 +1154,21 @@ int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reach_pose,
   if ((fold != 0 && fold != 1) || F < 1 || n < 1 || n > 64 || fp->eps2 < 0 || fp->eps2 > 4096 ||
       fp->eps2_max < 0 || fp->eps2_max > 4096 || fp->max_relax < -1)
     return IK_ERR_ARG;
+  if (fp->paper_radii != 0 && fp->paper_radii != 1) return IK_ERR_ARG;
+  int32_t rad[IK_MAX_SEG];
+  if (fp->paper_radii) {
+    // the paper's filter on joints 1 and 2 from the waypoint spacing
+    int lmax = 0;
+    for (int k = 0; k < F; ++k) lmax = std::max(lmax, (int)arm->len[k]);
+    const int spacing = (lmax + n - 1) / n;
+    for (int k = 0; k < IK_MAX_SEG; ++k) rad[k] = -1;
+    rad[0] = (spacing + 1) / 2 + 1;
+    if (F >= 2) rad[1] = spacing + 1;
+  } else {
+    for (int k = 0; k < IK_MAX_SEG; ++k) rad[k] = fp->radius[k];
+  }
   for (int k = 0; k < F; ++k)
-    if (fp->radius[k] < -1 || fp->radius[k] > 4096) return IK_ERR_ARG;
+    if (rad[k] < -1 || rad[k] > 4096) return IK_ERR_ARG;
   const int W = F * n + 1;
   if (W > 4096) return IK_ERR_ARG;
   // the paper's form has no direction limits: an arm with limits is refused
@@ -1192,7 +1213,7 @@ int ik_plan_path_follow(ik_grid g, const ik_arm* arm, const int32_t* reach_pose,
                      cudaMemcpyDeviceToDevice, g->st));
   ik_path_params pp{W, 0, fp->eps2, fp->eps2_max, fp->max_relax};
   if ((rc = chain_impl(g, af, &pp, 1, 0, 0, nullptr, tposes, ptr<int32_t>(g->b_relax),
-                       ptr<int32_t>(g->b_status), nullptr, fp->radius)))
+                       ptr<int32_t>(g->b_status), nullptr, rad)))
     return rc;
   int32_t* dposes = fold ? ptr<int32_t>(g->b_poses) : tposes;
   if (fold) {
@@ -1804,6 +1825,7 @@ int ik_profile_enable(ik_grid g, int timing, int counting) {
   }
   g->prof_on = timing != 0;
   g->count_on = counting != 0;
+  g->h_counters.assign(kCounters * P_N, 0ull);
   return sync(g);
 }
 
@@ -1828,6 +1850,11 @@ int ik_profile_read(ik_grid g, double* ms_out, int64_t* launches_out, uint64_t* 
                   cudaMemcpyDeviceToHost));
     CK(cudaMemset(g->d_counters, 0, sizeof(unsigned long long) * kCounters * P_N));
   }
+  if (g->h_counters.size() == cnt.size())
+    for (size_t i = 0; i < cnt.size(); ++i) {
+      cnt[i] += g->h_counters[i];
+      g->h_counters[i] = 0;
+    }
   for (int i = 0; i < P_N && i < cap; ++i) {
     if (ms_out) ms_out[i] = ms[i];
     if (launches_out) launches_out[i] = n[i];

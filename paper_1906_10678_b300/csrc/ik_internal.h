@@ -255,6 +255,9 @@ struct ChainArgs {
   bool per_joint = false;
   int rad[IK_MAX_SEG + 1];
   const int32_t* vbox = nullptr;  // [P][W][S+1][6] min-form word boxes of the survivor sets
+  // nullable, accumulated: [0] (offset, word) pairs the restricted
+  // propagations visited, [1] those whose shifted source word was non-zero
+  unsigned long long* counters = nullptr;
 };
 cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArgs& a,
                                 cudaStream_t st);

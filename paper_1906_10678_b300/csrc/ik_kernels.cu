@@ -1592,6 +1592,7 @@ struct ChainShared {
   int empty;               // some joint's search box is empty
   unsigned long long best;
   int cur[3];
+  unsigned long long* cnt;  // work counters (ChainArgs::counters), nullable
 };
 
 // Search boxes of one feasibility test at relaxation m: the root voxel for
@@ -1763,10 +1764,12 @@ constexpr int kG = 8;
 
 __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const OccBox& ob,
                                                     const OccBox& xb, const uint32_t* src, const Box& sb,
-                                                    int wx, int y, int z, long w, uint32_t m) {
+                                                    int wx, int y, int z, long w, uint32_t m,
+                                                    unsigned long long* cnt) {
   const int g = threadIdx.x % kG;
   const unsigned gmask = ((1u << kG) - 1u) << ((threadIdx.x & 31) & ~(kG - 1));
   uint32_t acc = 0;
+  unsigned long long visited = 0, nonzero = 0;
   if (m) {
     const int R = sg.R, side = 2 * R + 1;
     const int ez0 = max(sb.z0 - z, -R), ez1 = min(sb.z1 - z, R);
@@ -1789,9 +1792,17 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
       const int e1 = __ldg(rowp + ey1 + 1);
       for (int e = __ldg(rowp + ey0) + g; e < e1; e += kG) {
         const uint32_t x = source(e, ez);
+        if (cnt) {
+          ++visited;
+          nonzero += x != 0u;
+        }
         if (x & m & ~acc) acc |= x & edge_word_box(d, sg, ob, e, w, wx, y, z);
       }
     }
+  }
+  if (cnt && visited) {
+    atomicAdd(cnt + 0, visited);
+    atomicAdd(cnt + 1, nonzero);
   }
   return __reduce_or_sync(gmask, acc) & m;
 }
@@ -1827,7 +1838,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = (sh.r2[k] >= 0 ? ball_bits(wx, y, z, sh.ref[k], sh.r2[k]) : 0xffffffffu) & __ldg(Vk + w);
       }
-      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m);
+      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m, sh.cnt);
       if (acc && threadIdx.x % kG == 0) {
         dst[w] = acc;
         any = 1;
@@ -1872,7 +1883,7 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = Rk[w];
       }
-      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m);
+      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m, sh.cnt);
       if (acc && threadIdx.x % kG == 0) dst[w] = acc;
     }
     __syncthreads();
@@ -1944,6 +1955,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDe
   extern __shared__ uint32_t so[];
   const int p = blockIdx.x, S = arm.S, W = a.W;
   if (threadIdx.x <= IK_MAX_SEG) rad[threadIdx.x] = a.per_joint ? a.rad[threadIdx.x] : a.delta;
+  if (threadIdx.x == 0) sh.cnt = a.counters;
   __syncthreads();
   const long pose_sz = 3L * (S + 1);
   int32_t* poses = a.poses + (long)p * W * pose_sz;

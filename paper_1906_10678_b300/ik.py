@@ -53,7 +53,8 @@ class IkPathParams(ctypes.Structure):
 class IkFollowParams(ctypes.Structure):
     _fields_ = [("n_per_seg", ctypes.c_int32), ("fold", ctypes.c_int32),
                 ("radius", ctypes.c_int32 * IK_MAX_SEG), ("eps2", ctypes.c_int32),
-                ("eps2_max", ctypes.c_int32), ("max_relax", ctypes.c_int32)]
+                ("eps2_max", ctypes.c_int32), ("max_relax", ctypes.c_int32),
+                ("paper_radii", ctypes.c_int32)]
 
 
 class IkProblem(ctypes.Structure):
@@ -423,22 +424,29 @@ def ik_plan_path_short(g: int, arm, reach_pose, n_way: int, delta: int = 3, eps2
     return poses, relax, st.value, (k, l), (gp[:k + 1].copy() if k else None)
 
 
-def ik_plan_path_follow(g: int, arm, reach_pose, n_per_seg: int, fold: bool, radius, eps2: int = 2,
+def ik_plan_path_follow(g: int, arm, reach_pose, n_per_seg: int, fold: bool, radius=None, eps2: int = 2,
                         eps2_max: int = 8, max_relax: int = -1):
     """The paper's follower path: follower joint S - fold, n_per_seg guide
     points per segment, joint k filtered to radius[k-1] voxels (-1: not
-    filtered), the last segment folded along the path when fold.  Returns
+    filtered; radius None: the library applies the paper's filter on joints
+    1 and 2), the last segment folded along the path when fold.  Returns
     (poses [W][S+1][3], relax [W][2], status), W = (S - fold) n_per_seg + 1."""
     arm = _arm(arm)
     F = arm.S - (1 if fold else 0)
-    radius = [int(r) for r in radius]
-    if len(radius) != F:
-        raise ValueError(f"radius needs {F} entries (joints 1..{F})")
     fp = IkFollowParams()
     fp.n_per_seg = int(n_per_seg)
     fp.fold = 1 if fold else 0
-    for k in range(IK_MAX_SEG):
-        fp.radius[k] = radius[k] if k < F else -1
+    if radius is None:
+        fp.paper_radii = 1
+        for k in range(IK_MAX_SEG):
+            fp.radius[k] = -1
+    else:
+        radius = [int(r) for r in radius]
+        if len(radius) != F:
+            raise ValueError(f"radius needs {F} entries (joints 1..{F})")
+        fp.paper_radii = 0
+        for k in range(IK_MAX_SEG):
+            fp.radius[k] = radius[k] if k < F else -1
     fp.eps2, fp.eps2_max, fp.max_relax = int(eps2), int(eps2_max), int(max_relax)
     W = F * int(n_per_seg) + 1
     poses = np.zeros((W, arm.S + 1, 3), np.int32)
@@ -448,21 +456,6 @@ def ik_plan_path_follow(g: int, arm, reach_pose, n_per_seg: int, fold: bool, rad
                                     _np_ptr(poses), _np_ptr(relax), ctypes.byref(st)),
            "ik_plan_path_follow")
     return poses, relax, st.value
-
-
-def paper_filter_radii(arm_lengths, n_per_seg: int, fold: bool = True, slack: int = 1):
-    """The filter of section "Filtering for smoothness": joint 1 moves about
-    half a waypoint spacing, joint 2 about one, plus slack; the other joints
-    are not filtered.  The spacing is the longest follower segment over
-    n_per_seg, rounded up."""
-    F = len(arm_lengths) - (1 if fold else 0)
-    spacing = -(-max(int(v) for v in arm_lengths[:F]) // int(n_per_seg))
-    rad = [-1] * F
-    if F >= 1:
-        rad[0] = -(-spacing // 2) + slack
-    if F >= 2:
-        rad[1] = spacing + slack
-    return rad
 
 
 def ik_reach_path_many(g: int, arm, root, targets, n_way: int, delta: int = 3, eps2: int = 2,

@@ -25,6 +25,20 @@ def _grid(ik, sc, masks):
     return g
 
 
+def _paper_radii(lengths, n, fold):
+    """The paper's filter (section "Filtering for smoothness"), stated here
+    for the oracle's input: joint 1 about half a waypoint spacing and joint 2
+    about one, plus a voxel of slack; spacing = longest follower segment / n,
+    rounded up."""
+    F = len(lengths) - (1 if fold else 0)
+    s = -(-max(lengths[:F]) // n)
+    rad = [-1] * F
+    rad[0] = -(-s // 2) + 1
+    if F >= 2:
+        rad[1] = s + 1
+    return rad
+
+
 @pytest.mark.parametrize("masks", [1, 0])
 @pytest.mark.parametrize("seed", range(3))
 def test_follow_matches_oracle_c1(ik, seed, masks):
@@ -32,7 +46,7 @@ def test_follow_matches_oracle_c1(ik, seed, masks):
     occ = O.rasterize(sc.shape, sc.boxes)
     targets = G.draw_targets(sc, 4, 60 + seed)
     poses, found, _ = O.reach_many(occ, sc.lengths, sc.root, targets, threads=4)
-    cases = [(4, True, ik.paper_filter_radii(sc.lengths, 4)),   # the paper's filter (joints 1, 2)
+    cases = [(4, True, None),                                   # the paper's filter (joints 1, 2)
              (3, True, [1, 2, 3]),                               # every follower joint filtered
              (2, False, [2, 3, -1, -1])]                         # the end effector as follower
     n_done = 0
@@ -40,7 +54,8 @@ def test_follow_matches_oracle_c1(ik, seed, masks):
         for i in np.nonzero(found)[0][:2]:
             for n, fold, rad in cases:
                 pg, rg, sg = ik.ik_plan_path_follow(g.h, sc.lengths, poses[i], n, fold, rad)
-                po, ro, so = O.plan_path_follow(occ, sc.lengths, poses[i], n, fold, rad)
+                po, ro, so = O.plan_path_follow(occ, sc.lengths, poses[i], n, fold,
+                                                _paper_radii(sc.lengths, n, fold) if rad is None else rad)
                 assert sg == so
                 assert (rg == ro).all()
                 assert (pg == po).all()
