@@ -398,28 +398,64 @@ typedef struct {
   int32_t n_way;
 } ik_problem;
 
-/* Path rules shared by the batch (as in ik_path_params), and lanes: how many
- * problems run concurrently (0: 16). */
+/* Path rules shared by the batch (as in ik_path_params); blocks_per_sm: the
+ * persistent kernel's resident blocks per SM (0 or 1: one). */
 typedef struct {
   int32_t delta, eps2, eps2_max, max_relax;
-  int32_t lanes;
+  int32_t blocks_per_sm;
 } ik_batch_params;
 
 /* Sizes (int32 counts) of the packed outputs of ik_solve_batch. */
 IK_API int ik_batch_output_sizes(const ik_problem* probs, int n, size_t* reach_ints,
                                  size_t* poses_ints, size_t* relax_ints);
 
-/* Solve n uneven problems together (uses the current CUDA device; allocates
- * and frees its own memory).  Every problem follows exactly the rules of
- * ik_solve_reach + ik_plan_path on its own grid (segment tests walk the
- * supercover; no edge masks).  The problems are spread over lanes (a stream
- * and buffers sized for the largest problem each), and the whole batch is
- * recorded as one CUDA graph and launched once.  Outputs are packed in
- * problem order: found_out [n], status_out [n] (IK_PATH_UNREACHABLE when no
- * reach pose), reach_out [(n_seg+1)*3 per problem], poses_out
- * [n_way*(n_seg+1)*3 per problem], relax_out [n_way*2 per problem] (sizes
- * from ik_batch_output_sizes).  gpu_ms_out (nullable) receives the graph's
- * device time. */
+/* An engine for uneven batches on the current device: it keeps the shell
+ * tables, the device pool, the work queue and the pinned staging between
+ * calls (allocated when a call first needs them, reused afterwards).  Not
+ * thread-safe across concurrent calls on one engine beyond an internal lock.
+ * Destroying an engine waits for the device. */
+typedef struct ik_batch_engine_s* ik_batch_engine;
+IK_API int ik_batch_engine_create(ik_batch_engine* out);
+IK_API int ik_batch_engine_destroy(ik_batch_engine e);
+/* Pool bytes one launch may use (0: 70 % of the device's free memory at the
+ * first call); a batch that needs more runs as several launches in problem
+ * order. */
+IK_API int ik_batch_engine_set_budget(ik_batch_engine e, size_t pool_bytes);
+/* How long (ns, at least 1000; default 20 s) a launch waits with no work
+ * item completing anywhere before it gives up: its blocks then stop taking
+ * items and the unfinished problems report IK_ERR_TIMEOUT in job_rc. */
+IK_API int ik_batch_engine_set_timeout(ik_batch_engine e, int64_t ns);
+
+/* Solve n uneven problems (the systems pattern of batching, no paper
+ * counterpart; every problem follows exactly the rules of ik_solve_reach +
+ * ik_plan_path on its own grid, sections "The procedure for IK solution",
+ * "Smooth sequence computation" and "Filtering for smoothness"; segment
+ * tests walk the supercover, no edge masks are stored).  Asynchronous on
+ * cuda_stream (NULL: the legacy default stream): the call copies the host
+ * inputs (probs and their boxes and lengths) to pinned staging and device
+ * memory in stream order, clears the engine's pool, and launches ONE
+ * persistent kernel whose resident blocks take work items (rasterise slabs,
+ * seeds, propagation tiles of every level of every problem, tracebacks,
+ * guide points, smooth chains) from a device queue; the block that finishes
+ * a stage of a problem queues that problem's next stage.  Outputs are device
+ * pointers, packed in problem order: found [n], status [n] (an IK_PATH_*
+ * code), reach [(n_seg+1)*3 per problem], poses [n_way*(n_seg+1)*3 per
+ * problem], relax [n_way*2 per problem] (sizes from ik_batch_output_sizes),
+ * and job_rc [n]: IK_OK when the problem finished, IK_ERR_TIMEOUT when the
+ * launch gave up (ik_batch_engine_set_timeout).  Every segment length must
+ * keep the shell's reach within 31 voxels (else IK_ERR_UNSUPPORTED), and at
+ * most 8192 boxes per problem.  Returns IK_ERR_ARG / IK_ERR_OOM /
+ * IK_ERR_CUDA when enqueueing fails. */
+IK_API int ik_solve_batch_async(ik_batch_engine e, const ik_problem* probs, int n, const ik_batch_params* bp,
+                                int32_t* found_dev, int32_t* reach_dev, int32_t* poses_dev,
+                                int32_t* relax_dev, int32_t* status_dev, int32_t* job_rc_dev,
+                                void* cuda_stream);
+
+/* The same, synchronous, with host outputs, on a per-device engine that the
+ * library keeps for the process (its memory grows to the largest batch and
+ * is reused).  gpu_ms_out (nullable) receives the device time from the
+ * first upload to the end of the last launch.  Returns the first job's
+ * error (IK_ERR_TIMEOUT) if any problem did not finish. */
 IK_API int ik_solve_batch(const ik_problem* probs, int n, const ik_batch_params* bp,
                           int32_t* found_out, int32_t* reach_out, int32_t* poses_out,
                           int32_t* relax_out, int32_t* status_out, double* gpu_ms_out);

@@ -269,6 +269,8 @@ cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArg
 cudaError_t launch_fold_last(const Dims& d, const SegDev& sg, int S, int P, int W, const int32_t* tposes,
                              const int32_t* fold_at, int32_t* poses, int32_t* relax, int32_t* status,
                              cudaStream_t st);
+// p[0 .. n) = v.
+cudaError_t launch_fill_i32(int32_t* p, long n, int32_t v, cudaStream_t st);
 // Opt-in to large dynamic shared memory for the tiled kernels (current device).
 cudaError_t set_kernel_attributes();
 cudaError_t launch_traceback_nearest_many(const Dims& d, const ArmDev& arm, const int32_t* root,
@@ -290,5 +292,53 @@ cudaError_t launch_seed_set(const Dims& d, const uint32_t* T, const uint32_t* F,
                             int32_t* obox, cudaStream_t st);
 cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                             const int32_t* poses, int n, int32_t* valid, cudaStream_t st);
+
+// ------------------------------------------------ persistent uneven batch
+// One resident-block launch solves a whole batch of independent reach +
+// path problems (each with its own grid, arm, root, target and waypoint
+// count).  A problem moves through stages -- rasterise (slabs of 16 z
+// slices), forward seed, forward levels 1..S, reach seed, reach levels S..1,
+// traceback, guide points (one item per waypoint), waypoint levels S..1
+// (items per (tile, waypoint)), smooth chain -- and the block that finishes
+// the last item of a stage pushes the next stage's items onto one device
+// queue (the tiles within reach of the source sets' boxes), so no item waits
+// on another.  Blocks wait only for a queue slot to be published, with a
+// time limit after which the launch gives up and the unfinished problems
+// report IK_ERR_TIMEOUT.
+constexpr int kBatchThreads = 512;  // 16 warps: 16-slice tiles, and the chain's block size
+constexpr int kBatchTZ = 16;
+constexpr int kBatchSlab = 16;      // z slices per rasterise item
+
+struct BatchProb {
+  Dims d;
+  TileCfg tcs[IK_MAX_SEG];  // tiling of the propagation of segment k+1
+  ArmDev arm;
+  int S, W, n_boxes, n_slabs;
+  int root[3], target[3];
+  const int32_t* boxes;  // [n_boxes][6], inclusive
+  // the problem's own buffers (each 128-byte aligned, written before read)
+  uint32_t *occ, *F, *V, *Vw, *chain;
+  int32_t *Fbox, *Vbox, *Vwbox, *reach, *found, *g, *eps, *poses, *relax, *status;
+  // the caller's packed outputs for this problem
+  int32_t *o_found, *o_reach, *o_poses, *o_relax, *o_status, *o_rc;
+};
+
+struct BatchQueue {
+  int4* items;  // {problem + 1 (0: slot not yet published), stage, a, b}
+  long long cap;
+  unsigned long long* ctl;  // [0] next slot to take, [1] slots reserved, [2] problems done,
+                            // [3] items completed (progress), [4] error (1: timeout, 2: overflow)
+  int2* state;              // per problem: {stage, items of the stage still pending}
+};
+
+struct BatchRules {
+  int delta, eps2, eps2_max, max_relax;
+};
+
+// Dynamic shared memory the persistent kernel needs besides its tile halos.
+size_t batch_chain_smem_bytes();
+cudaError_t batch_set_smem(size_t bytes);
+cudaError_t launch_batch_persistent(const BatchProb* probs, int n, const BatchQueue& q, const BatchRules& r,
+                                    int blocks, size_t smem, long long timeout_ns, cudaStream_t st);
 
 }  // namespace ikb

@@ -395,10 +395,21 @@ __global__ void __launch_bounds__(256) k_propagate(Dims d, SegDev seg, const uin
 // walk visits, per warp (one z slice), the dz range that can reach the box
 // of X and, per dz, the one contiguous run of offsets whose dy can reach it
 // from any of the warp's rows.
-// Slices of a staged halo: TZ + 2R with R <= 31 (the tiled kernels' limit).
-constexpr int kMaxSlices = 8 + 2 * 31;
+// Slices of a staged halo: TZ + 2R with TZ <= 16 and R <= 31 (the tiled
+// kernels' limits).
+constexpr int kMaxSlices = 16 + 2 * 31;
 
-template <bool kCount, bool kOcc>
+// Loads of sets that a persistent launch writes while it runs (kCoh): the
+// L2-coherent path instead of the read-only one.
+template <bool kCoh>
+__device__ __forceinline__ int32_t ld_box(const int32_t* p) {
+  return kCoh ? __ldcg(p) : __ldg(p);
+}
+
+// The block has blockDim.x / 32 warps (8 for the grid API's kernels, 16 for
+// the persistent batch kernel); warp i computes slice z0 + i of the tile
+// (warps at or beyond tc.TZ only stage).
+template <bool kCount, bool kOcc, bool kCoh = false>
 __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev& seg, const TileCfg& tc,
                                                     const uint32_t* __restrict__ X, long xs,
                                                     const uint32_t* __restrict__ mask, long ms,
@@ -420,8 +431,9 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
   const long w = valid ? ((long)z * d.ny + y) * d.wx + wx : 0;
   const uint32_t* Xq = X + q * xs;
   const int32_t* xb = xbox + q * bs;
-  const int bx0 = __ldg(xb + 0), by0 = __ldg(xb + 1), bz0 = __ldg(xb + 2);
-  const int bx1 = -__ldg(xb + 3), by1 = -__ldg(xb + 4), bz1 = -__ldg(xb + 5);
+  const int bx0 = ld_box<kCoh>(xb + 0), by0 = ld_box<kCoh>(xb + 1), bz0 = ld_box<kCoh>(xb + 2);
+  const int bx1 = -ld_box<kCoh>(xb + 3), by1 = -ld_box<kCoh>(xb + 4), bz1 = -ld_box<kCoh>(xb + 5);
+  const int nwarps = blockDim.x >> 5;
   uint32_t m = 0;
   if (valid) m = (mask ? __ldg(mask + q * ms + w) : 0xffffffffu) & ~__ldg(occ + w);
   // the lane's row of stored edge masks (one word per offset, mstr apart):
@@ -452,7 +464,7 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
     const int sub = lane / P, c = lane % P, sw = c - 1;
     const bool col_in = sw >= bx0 && sw <= bx1;
     if (ny_rows > 0 && sub < per_pass) {
-      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += nwarps * per_pass) {
         const int sy = sy0 + r % ny_rows, sz = sz0 + r / ny_rows;
         uint32_t v = 0u;
         if (col_in && sy >= by0 && sy <= by1) v = __ldg(Xq + ((long)sz * d.ny + sy) * d.wx + sw);
@@ -480,7 +492,7 @@ __device__ __forceinline__ void propagate_tile_body(const Dims& d, const SegDev&
     const int per_pass = 32 / P;
     const int sub = lane / P, c = lane % P, sw = c - 1;
     if (ny_rows > 0 && sub < per_pass) {
-      for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += nwarps * per_pass) {
         const int sy = oy0 + r % ny_rows, sz = oz0 + r / ny_rows;
         uint32_t v = 0u;
         if (sw >= 0 && sw < d.wx && sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz)
@@ -1346,6 +1358,12 @@ __global__ void k_fill_i32(int32_t* p, long n, int32_t v) {
   if (i < n) p[i] = v;
 }
 
+cudaError_t launch_fill_i32(int32_t* p, long n, int32_t v, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_i32<<<grid_for(n, 256), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_validate(const Dims& d, const ArmDev& arm, const uint32_t* occ,
                             const int32_t* poses, int n, int32_t* valid, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -1384,14 +1402,13 @@ __device__ __forceinline__ int isqrt_dev(int v) {  // floor(sqrt(v)), v >= 0
 // the waypoint target set T_j (free voxels within squared distance eps2,
 // grown to eps2_max when empty; T_{W-1} = {end effector}) intersected with
 // F_S, OR-ed into the (pre-zeroed) last survivor set of the waypoint.
-__global__ void k_guide_targets(Dims d, ArmDev arm, GuideArm ga, const uint32_t* __restrict__ occ,
-                                const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
-                                const int32_t* __restrict__ found, int W, int j_lo, int eps2,
-                                int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw,
-                                int32_t* wbox, const int32_t* __restrict__ c_arr,
-                                int32_t* __restrict__ fold_at) {
-  const int p = blockIdx.y;
-  const int j = blockIdx.x + j_lo;
+// Guide point and waypoint target of waypoint j of path p (one block).
+__device__ void guide_targets_block(const Dims& d, const ArmDev& arm, const GuideArm& ga,
+                                    const uint32_t* __restrict__ occ, const uint32_t* __restrict__ F_S,
+                                    const int32_t* __restrict__ reach, const int32_t* __restrict__ found,
+                                    int W, int eps2, int eps2_max, int32_t* g, int32_t* eps_used,
+                                    uint32_t* Vw, int32_t* wbox, const int32_t* __restrict__ c_arr,
+                                    int32_t* __restrict__ fold_at, int p, int j) {
   if (c_arr && j <= c_arr[p]) return;  // replan: waypoints up to the current one stay
   const int S = arm.S;    // layout of the waypoint sets
   const int GS = ga.S;    // the guide polyline's segments
@@ -1529,6 +1546,16 @@ __global__ void k_guide_targets(Dims d, ArmDev arm, GuideArm ga, const uint32_t*
       box_point(vb, x, y, z);
     }
   }
+}
+
+__global__ void k_guide_targets(Dims d, ArmDev arm, GuideArm ga, const uint32_t* __restrict__ occ,
+                                const uint32_t* __restrict__ F_S, const int32_t* __restrict__ reach,
+                                const int32_t* __restrict__ found, int W, int j_lo, int eps2,
+                                int eps2_max, int32_t* g, int32_t* eps_used, uint32_t* Vw,
+                                int32_t* wbox, const int32_t* __restrict__ c_arr,
+                                int32_t* __restrict__ fold_at) {
+  guide_targets_block(d, arm, ga, occ, F_S, reach, found, W, eps2, eps2_max, g, eps_used, Vw, wbox, c_arr,
+                      fold_at, blockIdx.y, blockIdx.x + j_lo);
 }
 
 cudaError_t launch_guide_targets(const Dims& d, const ArmDev& arm, const uint32_t* occ,
@@ -1949,11 +1976,11 @@ __device__ bool chain_trace(const Dims& d, const ArmDev& arm, ChainShared& sh, c
   return true;
 }
 
-__global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
-  __shared__ ChainShared sh;
-  __shared__ int rad[IK_MAX_SEG + 1];  // filter radius of each joint (-1: none)
-  extern __shared__ uint32_t so[];
-  const int p = blockIdx.x, S = arm.S, W = a.W;
+// The smooth chain of path p (one block; sh, rad and the dynamic shared
+// buffer so of (kChainOccWords + kChainSrcWords) words belong to the caller).
+__device__ void smooth_chain_block(const Dims& d, const ArmDev& arm, const ChainArgs& a, int p,
+                                   ChainShared& sh, int* rad, uint32_t* so) {
+  const int S = arm.S, W = a.W;
   if (threadIdx.x <= IK_MAX_SEG) rad[threadIdx.x] = a.per_joint ? a.rad[threadIdx.x] : a.delta;
   if (threadIdx.x == 0) sh.cnt = a.counters;
   __syncthreads();
@@ -2097,6 +2124,13 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDe
     a.status[p] = broken ? IK_PATH_BROKEN : (relaxed ? IK_PATH_RELAXED : IK_PATH_OK);
 }
 
+__global__ void __launch_bounds__(kChainThreads, 1) k_smooth_chain(Dims d, ArmDev arm, ChainArgs a) {
+  __shared__ ChainShared sh;
+  __shared__ int rad[IK_MAX_SEG + 1];  // filter radius of each joint (-1: none)
+  extern __shared__ uint32_t so[];
+  smooth_chain_block(d, arm, a, blockIdx.x, sh, rad, so);
+}
+
 // ------------------------------------------------- folded last segment
 
 // One block per (path, waypoint): the pose's joints 0 .. F come from the
@@ -2212,5 +2246,8 @@ cudaError_t launch_smooth_chain(const Dims& d, const ArmDev& arm, const ChainArg
                                                                                                    a);
   return cudaGetLastError();
 }
+
+// The persistent uneven-batch kernel uses the block bodies above.
+#include "ik_batch_kernel.cuh"
 
 }  // namespace ikb

@@ -72,7 +72,7 @@ class IkCone(ctypes.Structure):
 
 class IkBatchParams(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_int32), ("eps2", ctypes.c_int32), ("eps2_max", ctypes.c_int32),
-                ("max_relax", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+                ("max_relax", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 def _sig(name, res, args):
@@ -119,6 +119,12 @@ _sig("ik_replan_many", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _vp, _i,
                             ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _i])
 _sig("ik_batch_output_sizes", _i, [_vp, _i, _vp, _vp, _vp])
 _sig("ik_solve_batch", _i, [_vp, _i, ctypes.POINTER(IkBatchParams), _vp, _vp, _vp, _vp, _vp, _vp])
+_sig("ik_batch_engine_create", _i, [ctypes.POINTER(_vp)])
+_sig("ik_batch_engine_destroy", _i, [_vp])
+_sig("ik_batch_engine_set_budget", _i, [_vp, ctypes.c_size_t])
+_sig("ik_batch_engine_set_timeout", _i, [_vp, ctypes.c_int64])
+_sig("ik_solve_batch_async", _i, [_vp, _vp, _i, ctypes.POINTER(IkBatchParams), _vp, _vp, _vp, _vp, _vp, _vp,
+                                  _vp])
 _sig("ik_batch_capture", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _i,
                               ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(_vp)])
@@ -137,7 +143,8 @@ EXPORTED = [
     "ik_grid_words", "ik_set_option", "ik_set_obstacles", "ik_set_boxes", "ik_get_obstacles", "ik_forward_sets",
     "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path", "ik_plan_path_follow", "ik_plan_path_short",
     "ik_reach_path_many", "ik_plan_between", "ik_validate_poses", "ik_replan", "ik_replan_many",
-    "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_capture",
+    "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_engine_create", "ik_batch_engine_destroy",
+    "ik_batch_engine_set_budget", "ik_batch_engine_set_timeout", "ik_solve_batch_async", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
@@ -515,11 +522,9 @@ class Batch:
             self.h = 0
 
 
-def ik_solve_batch(problems, delta: int = 3, eps2: int = 2, eps2_max: int = 8, max_relax: int = -1,
-                   lanes: int = 0):
-    """problems: list of dicts with shape (nx, ny, nz), boxes [n][6], lengths,
-    root, target, n_way (tol 0.5).  Returns (list of per-problem dicts with
-    found, reach, poses, relax, status; device ms of the batch graph)."""
+def _problem_array(problems):
+    """ik_problem structs of a list of dicts (shape, boxes, lengths, root,
+    target, n_way; tol 0.5), with the arrays they point at kept alive."""
     n = len(problems)
     keep = []
     arr = (IkProblem * max(n, 1))()
@@ -536,19 +541,20 @@ def ik_solve_batch(problems, delta: int = 3, eps2: int = 2, eps2_max: int = 8, m
         arr[i].root[:] = [int(v) for v in p["root"]]
         arr[i].target[:] = [int(v) for v in p["target"]]
         arr[i].n_way = int(p["n_way"])
+    return arr, keep
+
+
+def ik_batch_output_sizes(problems):
+    """(reach ints, poses ints, relax ints) of the packed outputs."""
+    arr, keep = _problem_array(problems)
     sizes = [ctypes.c_size_t() for _ in range(3)]
-    _check(_lib.ik_batch_output_sizes(ctypes.cast(arr, _vp), n, *(ctypes.byref(x) for x in sizes)),
+    _check(_lib.ik_batch_output_sizes(ctypes.cast(arr, _vp), len(problems), *(ctypes.byref(x) for x in sizes)),
            "ik_batch_output_sizes")
-    found = np.zeros(n, np.int32)
-    status = np.zeros(n, np.int32)
-    reach = np.zeros(max(sizes[0].value, 1), np.int32)
-    poses = np.zeros(max(sizes[1].value, 1), np.int32)
-    relax = np.zeros(max(sizes[2].value, 1), np.int32)
-    ms = ctypes.c_double()
-    bp = IkBatchParams(delta, eps2, eps2_max, max_relax, lanes)
-    _check(_lib.ik_solve_batch(ctypes.cast(arr, _vp), n, ctypes.byref(bp), _np_ptr(found),
-                               _np_ptr(reach), _np_ptr(poses), _np_ptr(relax), _np_ptr(status),
-                               ctypes.byref(ms)), "ik_solve_batch")
+    return tuple(x.value for x in sizes)
+
+
+def unpack_batch(problems, found, reach, poses, relax, status):
+    """Per-problem dicts of the packed outputs (numpy arrays)."""
     out, r0, p0, x0 = [], 0, 0, 0
     for i, p in enumerate(problems):
         S, W = len(p["lengths"]), int(p["n_way"])
@@ -559,7 +565,72 @@ def ik_solve_batch(problems, delta: int = 3, eps2: int = 2, eps2_max: int = 8, m
         r0 += 3 * (S + 1)
         p0 += 3 * (S + 1) * W
         x0 += 2 * W
-    return out, ms.value
+    return out
+
+
+def ik_solve_batch(problems, delta: int = 3, eps2: int = 2, eps2_max: int = 8, max_relax: int = -1,
+                   blocks_per_sm: int = 0):
+    """problems: list of dicts with shape (nx, ny, nz), boxes [n][6], lengths,
+    root, target, n_way (tol 0.5).  Returns (list of per-problem dicts with
+    found, reach, poses, relax, status; device ms of the batch)."""
+    n = len(problems)
+    arr, keep = _problem_array(problems)
+    r_n, p_n, x_n = ik_batch_output_sizes(problems)
+    found = np.zeros(n, np.int32)
+    status = np.zeros(n, np.int32)
+    reach = np.zeros(max(r_n, 1), np.int32)
+    poses = np.zeros(max(p_n, 1), np.int32)
+    relax = np.zeros(max(x_n, 1), np.int32)
+    ms = ctypes.c_double()
+    bp = IkBatchParams(delta, eps2, eps2_max, max_relax, blocks_per_sm)
+    _check(_lib.ik_solve_batch(ctypes.cast(arr, _vp), n, ctypes.byref(bp), _np_ptr(found),
+                               _np_ptr(reach), _np_ptr(poses), _np_ptr(relax), _np_ptr(status),
+                               ctypes.byref(ms)), "ik_solve_batch")
+    return unpack_batch(problems, found, reach, poses, relax, status), ms.value
+
+
+class BatchEngine:
+    """Owning wrapper of an ``ik_batch_engine`` (current device)."""
+
+    def __init__(self):
+        h = _vp()
+        _check(_lib.ik_batch_engine_create(ctypes.byref(h)), "ik_batch_engine_create")
+        self.h = h.value
+
+    def set_budget(self, pool_bytes: int) -> None:
+        _check(_lib.ik_batch_engine_set_budget(self.h, int(pool_bytes)), "ik_batch_engine_set_budget")
+
+    def set_timeout(self, ns: int) -> None:
+        _check(_lib.ik_batch_engine_set_timeout(self.h, int(ns)), "ik_batch_engine_set_timeout")
+
+    def solve_async(self, problems, found, reach, poses, relax, status, job_rc, stream: int = 0,
+                    delta: int = 3, eps2: int = 2, eps2_max: int = 8, max_relax: int = -1,
+                    blocks_per_sm: int = 0) -> None:
+        """Enqueue the batch on ``stream``; outputs are int32 CUDA tensors of
+        the packed sizes (ik_batch_output_sizes) and job_rc [n]."""
+        arr, keep = _problem_array(problems)
+        bp = IkBatchParams(delta, eps2, eps2_max, max_relax, blocks_per_sm)
+        _check(_lib.ik_solve_batch_async(self.h, ctypes.cast(arr, _vp), len(problems), ctypes.byref(bp),
+                                         _dev_ptr(found), _dev_ptr(reach), _dev_ptr(poses), _dev_ptr(relax),
+                                         _dev_ptr(status), _dev_ptr(job_rc), _vp(stream) if stream else None),
+               "ik_solve_batch_async")
+
+    def close(self) -> None:
+        if self.h:
+            _lib.ik_batch_engine_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ik_plan_between(g: int, arm, start_pose, guide_arm, target, n_way: int, delta: int = 3,

@@ -100,7 +100,7 @@ def _as_dict(p):
 def test_uneven_batch_matches_single_problem_calls(ik):
     import oracle as O
     probs = G.c4_problems(12, 2)
-    out, ms = ik.ik_solve_batch([_as_dict(p) for p in probs], lanes=4)
+    out, ms = ik.ik_solve_batch([_as_dict(p) for p in probs])
     assert ms > 0
     for p, r in zip(probs, out):
         sc = p.scene
@@ -130,7 +130,7 @@ def test_uneven_batch_long_segments_narrow_pitch(ik):
         sc = G.scaled_scene(n, lengths, 150, 4, 24, seed, f"long{n}")
         t = G.draw_targets(sc, 1, seed)[0]
         probs.append(G.Problem(sc, tuple(int(v) for v in t), 12))
-    out, _ = ik.ik_solve_batch([_as_dict(p) for p in probs], lanes=2)
+    out, _ = ik.ik_solve_batch([_as_dict(p) for p in probs])
     for p, r in zip(probs, out):
         sc = p.scene
         with ik.Grid(*sc.shape) as g:
@@ -233,3 +233,77 @@ def test_batch_replay_after_the_grid_replaced_its_buffers(ik):
         assert (a == w_).all()
     for a, w_ in zip(big, want2):
         assert (a == w_).all()
+
+
+def _packed_outputs(ik, torch, dicts):
+    r_n, p_n, x_n = ik.ik_batch_output_sizes(dicts)
+    i32 = dict(dtype=torch.int32, device="cuda")
+    n = len(dicts)
+    return [torch.full((n,), -7, **i32), torch.full((r_n,), -7, **i32), torch.full((p_n,), -7, **i32),
+            torch.full((x_n,), -7, **i32), torch.full((n,), -7, **i32), torch.full((n,), -7, **i32)]
+
+
+def test_uneven_batch_async_on_a_stream_equals_sync(ik):
+    """ik_solve_batch_async (device outputs, a caller stream, a status per
+    job) gives exactly what the synchronous form gives, twice in a row on one
+    engine (the second call reuses the engine's memory)."""
+    import torch
+    probs = [_as_dict(p) for p in G.c4_problems(10, 5)]
+    want, _ = ik.ik_solve_batch(probs)
+    stream = torch.cuda.Stream()
+    with ik.BatchEngine() as eng:
+        for _ in range(2):
+            found, reach, poses, relax, status, rc = _packed_outputs(ik, torch, probs)
+            eng.solve_async(probs, found, reach, poses, relax, status, rc, stream=stream.cuda_stream)
+            stream.synchronize()
+            assert (rc.cpu().numpy() == ik.IK_OK).all()
+            got = ik.unpack_batch(probs, found.cpu().numpy(), reach.cpu().numpy(), poses.cpu().numpy(),
+                                  relax.cpu().numpy(), status.cpu().numpy())
+            for a, b in zip(got, want):
+                assert a["found"] == b["found"] and a["status"] == b["status"]
+                assert (a["reach"] == b["reach"]).all() and (a["poses"] == b["poses"]).all()
+                assert (a["relax"] == b["relax"]).all()
+
+
+def test_uneven_batch_waves_equal_one_launch(ik):
+    """A pool budget that fits one problem at a time (one launch per problem)
+    gives the same results as the whole batch in one launch."""
+    import torch
+    probs = [_as_dict(p) for p in G.c4_problems(6, 6)]
+    want, _ = ik.ik_solve_batch(probs)
+    with ik.BatchEngine() as eng:
+        eng.set_budget(1)
+        found, reach, poses, relax, status, rc = _packed_outputs(ik, torch, probs)
+        eng.solve_async(probs, found, reach, poses, relax, status, rc)
+        torch.cuda.synchronize()
+        assert (rc.cpu().numpy() == ik.IK_OK).all()
+        got = ik.unpack_batch(probs, found.cpu().numpy(), reach.cpu().numpy(), poses.cpu().numpy(),
+                              relax.cpu().numpy(), status.cpu().numpy())
+    for a, b in zip(got, want):
+        assert a["status"] == b["status"] and (a["poses"] == b["poses"]).all()
+
+
+def test_uneven_batch_timeout_is_reported_and_the_context_stays_usable(ik):
+    """With a wait limit too short for any work (1 microsecond) the
+    persistent launch gives up on its own: unfinished problems report
+    IK_ERR_TIMEOUT in their job status (no fault, no hang), and the next call
+    with the default limit on the same engine is exact."""
+    import torch
+    probs = [_as_dict(p) for p in G.c4_problems(4, 7)]
+    want, _ = ik.ik_solve_batch(probs)
+    with ik.BatchEngine() as eng:
+        eng.set_timeout(1000)
+        found, reach, poses, relax, status, rc = _packed_outputs(ik, torch, probs)
+        eng.solve_async(probs, found, reach, poses, relax, status, rc)
+        torch.cuda.synchronize()
+        codes = set(rc.cpu().numpy().tolist())
+        assert ik.IK_ERR_TIMEOUT in codes and codes <= {ik.IK_OK, ik.IK_ERR_TIMEOUT}
+        eng.set_timeout(20 * 10 ** 9)
+        found, reach, poses, relax, status, rc = _packed_outputs(ik, torch, probs)
+        eng.solve_async(probs, found, reach, poses, relax, status, rc)
+        torch.cuda.synchronize()
+        assert (rc.cpu().numpy() == ik.IK_OK).all()
+        got = ik.unpack_batch(probs, found.cpu().numpy(), reach.cpu().numpy(), poses.cpu().numpy(),
+                              relax.cpu().numpy(), status.cpu().numpy())
+    for a, b in zip(got, want):
+        assert a["status"] == b["status"] and (a["poses"] == b["poses"]).all()
