@@ -351,6 +351,7 @@ int run_wave(ik_batch_engine_s* E, const ik_problem* probs, const std::vector<Pr
   if ((rc = grow(E->ctl, 8 * sizeof(unsigned long long)))) return rc;
   if ((rc = grow(E->state, (size_t)n * sizeof(int2)))) return rc;
   if ((rc = grow(E->boxes, std::max<size_t>(box_words, 1) * 4))) return rc;
+  if (smem > batch_smem_limit()) return IK_ERR_UNSUPPORTED;
   if (smem > E->smem_set) {
     CKB(batch_set_smem(smem));
     E->smem_set = smem;

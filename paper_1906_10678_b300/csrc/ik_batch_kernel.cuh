@@ -418,6 +418,18 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_persistent(const Bat
 
 size_t batch_chain_smem_bytes() { return (size_t)(kChainOccWords + kChainSrcWords) * sizeof(uint32_t); }
 
+size_t batch_smem_limit() {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, (const void*)k_batch_persistent) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+}
+
 cudaError_t batch_set_smem(size_t bytes) {
   return cudaFuncSetAttribute((const void*)k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)bytes);

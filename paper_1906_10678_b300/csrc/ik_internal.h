@@ -338,6 +338,8 @@ struct BatchRules {
 // Dynamic shared memory the persistent kernel needs besides its tile halos.
 size_t batch_chain_smem_bytes();
 cudaError_t batch_set_smem(size_t bytes);
+// The dynamic shared memory one block of the persistent kernel may take.
+size_t batch_smem_limit();
 cudaError_t launch_batch_persistent(const BatchProb* probs, int n, const BatchQueue& q, const BatchRules& r,
                                     int blocks, size_t smem, long long timeout_ns, cudaStream_t st);
 
