@@ -142,6 +142,11 @@ IK_API int ik_destroy_grid(ik_grid g);
  * and one block per (tile, query) elsewhere; 0: one block per (tile, query)
  * on every level; 2: the work list on every level.  Results are identical. */
 #define IK_OPT_WORK_LIST 4
+/* IK_OPT_QUERY_PAIRS: 1 (default): on the levels of a batched backward pass
+ * that run one block per tile (not the work list), with stored edge masks,
+ * a block carries two queries, which share the output mask and the
+ * edge-mask words; 0: one query per block.  Results are identical. */
+#define IK_OPT_QUERY_PAIRS 5
 IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);

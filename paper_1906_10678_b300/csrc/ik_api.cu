@@ -1786,6 +1786,11 @@ int ik_set_option(ik_grid g, int option, int value) {
     g->tc.depth = value;
     return IK_OK;
   }
+  if (option == IK_OPT_QUERY_PAIRS) {
+    if (value != 0 && value != 1) return IK_ERR_ARG;
+    g->tc.pair = value;
+    return IK_OK;
+  }
   if (option == IK_OPT_WORK_LIST) {
     if (value < 0 || value > 2) return IK_ERR_ARG;
     g->work_list = value;

@@ -97,6 +97,7 @@ struct SegDev {
 struct TileCfg {
   int TY, TZ, P, lanes, tiles_y, tiles_z;
   int depth = 8;  // output slices per tile of the propagation: 8 (one per warp) or 16 (two)
+  int pair = 1;   // two queries per block on the dense levels of a batched pass (IK_OPT_QUERY_PAIRS)
 };
 TileCfg make_tile_cfg(const Dims& d);
 // Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).

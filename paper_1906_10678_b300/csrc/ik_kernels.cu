@@ -698,6 +698,183 @@ __global__ void __launch_bounds__(256, 3) k_propagate_tile_occ_list(Dims d, SegD
                                count);
 }
 
+// Two queries per block.  The queries of a batched backward pass share the
+// output mask (F_{k-1} & ~Occ) and every edge-mask word M_e[p]: a block that
+// carries queries q0 = 2 blockIdx.y and q1 = q0 + 1 over one tile stages both
+// source halos interleaved (one 64-bit shared word per position), decodes
+// each offset once, fetches both queries' source words with one 64-bit load
+// per word, and loads an edge-mask word once when either query can still
+// take bits from it.  The walk covers the union of the two queries' ranges
+// (a query's staged words outside its own box are zero).  Stored edge masks
+// only; results equal two one-query blocks.
+template <bool kCount>
+__global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg, TileCfg tc,
+                                                             const uint32_t* __restrict__ X, long xs,
+                                                             const uint32_t* __restrict__ mask,
+                                                             const uint32_t* __restrict__ occ,
+                                                             uint32_t* __restrict__ out, long os, int Q,
+                                                             const int32_t* __restrict__ xbox,
+                                                             int32_t* __restrict__ obox, long bs,
+                                                             unsigned long long* __restrict__ counters) {
+  extern __shared__ uint2 s2[];
+  constexpr unsigned kFull = 0xffffffffu;
+  const int tile = blockIdx.x;
+  const int q0 = 2 * blockIdx.y, q1 = q0 + 1;
+  const bool has1 = q1 < Q;
+  const int y0 = (tile % tc.tiles_y) * tc.TY, z0 = (tile / tc.tiles_y) * tc.TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = seg.R, RY = tc.TY + 2 * R, P = tc.P;
+  const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
+  const bool valid = warp < tc.TZ && lane < tc.lanes && y < d.ny && z < d.nz;
+  const long w = valid ? ((long)z * d.ny + y) * d.wx + wx : 0;
+  // the boxes of both sources (an empty box for a missing second query)
+  int b0[6], b1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    b0[i] = __ldg(xbox + q0 * bs + i);
+    b1[i] = has1 ? __ldg(xbox + q1 * bs + i) : 0x7f7f7f7f;
+  }
+  const int ax0 = b0[0], ay0 = b0[1], az0 = b0[2], ax1 = -b0[3], ay1 = -b0[4], az1 = -b0[5];
+  const int cx0 = b1[0], cy0 = b1[1], cz0 = b1[2], cx1 = -b1[3], cy1 = -b1[4], cz1 = -b1[5];
+  auto touches = [&](int x0_, int y0_, int z0_, int x1_, int y1_, int z1_) {
+    return x0_ <= x1_ && y1_ >= y0 - R && y0_ <= y0 + tc.TY - 1 + R && z1_ >= z0 - R && z0_ <= z0 + tc.TZ - 1 + R;
+  };
+  const bool t0 = touches(ax0, ay0, az0, ax1, ay1, az1), t1 = touches(cx0, cy0, cz0, cx1, cy1, cz1);
+  uint32_t m = 0;
+  if (valid) m = (mask ? __ldg(mask + w) : 0xffffffffu) & ~__ldg(occ + w);
+  const uint32_t* mrow = valid ? seg.mask + seg.mbox.index(wx, y, z) : nullptr;
+  const long mstr = seg.mbox.words();
+  if (!__syncthreads_or((t0 || t1) && m != 0)) {
+    if (valid) {
+      out[q0 * os + w] = 0u;
+      if (has1) out[q1 * os + w] = 0u;
+    }
+    return;
+  }
+  // the union of the two boxes (an empty box contributes nothing)
+  const bool e0 = ax0 > ax1, e1b = cx0 > cx1;
+  const int uy0 = e0 ? cy0 : (e1b ? ay0 : min(ay0, cy0)), uy1 = e0 ? cy1 : (e1b ? ay1 : max(ay1, cy1));
+  const int uz0 = e0 ? cz0 : (e1b ? az0 : min(az0, cz0)), uz1 = e0 ? cz1 : (e1b ? az1 : max(az1, cz1));
+  // stage both halos, interleaved: the rows the walk can read (as in the
+  // one-query form, over the union of the boxes), box words copied, the rest zero
+  {
+    const int sz0 = max(uz0, z0 - R), sz1 = min(uz1, z0 + tc.TZ - 1 + R);
+    const int sy0 = max(uy0 - tc.TY + 1, y0 - R), sy1 = min(uy1 + tc.TY - 1, y0 + tc.TY - 1 + R);
+    const int ny_rows = sy1 - sy0 + 1, n_rows = (sz1 - sz0 + 1) * ny_rows;
+    const int per_pass = 32 / P, nwarps = blockDim.x >> 5;
+    const int sub = lane / P, c = lane % P, sw = c - 1;
+    if (ny_rows > 0 && sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += nwarps * per_pass) {
+        const int sy = sy0 + r % ny_rows, sz = sz0 + r / ny_rows;
+        const long row = ((long)sz * d.ny + sy) * d.wx + sw;
+        uint2 v = make_uint2(0u, 0u);
+        if (sw >= ax0 && sw <= ax1 && sy >= ay0 && sy <= ay1 && sz >= az0 && sz <= az1)
+          v.x = __ldg(X + q0 * xs + row);
+        if (sw >= cx0 && sw <= cx1 && sy >= cy0 && sy <= cy1 && sz >= cz0 && sz <= cz1)
+          v.y = __ldg(X + q1 * xs + row);
+        s2[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t acc0 = 0, acc1 = 0;
+  unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0;
+  if (__any_sync(kFull, m != 0)) {
+    const int side = 2 * R + 1;
+    const int ylast = min(y0 + tc.TY, d.ny) - 1;
+    const int ez0 = max(uz0 - z, -R), ez1 = min(uz1 - z, R);
+    const int ey0 = max(uy0 - ylast, -R), ey1 = min(uy1 - y0, R);
+    const int base = valid ? ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1) : (R * RY + R) * P + 1;
+    bool live0 = m != 0, live1 = has1 && m != 0;
+    for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
+      const int32_t* rowp = seg.rows + (ez + R) * side + R;
+      const int e1 = __ldg(rowp + ey1 + 1);
+      const int zb = base + ez * RY * P;
+      if (kCount && lane == 0) warp_iters += (unsigned long long)max(0, e1 - __ldg(rowp + ey0));
+      int e = __ldg(rowp + ey0);
+      for (; e + 8 <= e1; e += 8) {
+        uint32_t xa[8], xb[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int32_t t = __ldg(seg.tab + e + i);
+          const int a = zb + (t >> 5);
+          const uint2 lo = s2[a], hi = s2[a + 1];
+          xa[i] = __funnelshift_r(lo.x, hi.x, t);  // shift taken mod 32
+          xb[i] = __funnelshift_r(lo.y, hi.y, t);
+        }
+        const uint32_t want0 = m & ~acc0, want1 = m & ~acc1;
+        uint32_t any = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) any |= (xa[i] & want0) | (xb[i] & want1);
+        if (kCount) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (live0) nonzero += xa[i] != 0;
+            if (live1) nonzero += xb[i] != 0;
+          }
+          visited += 8 * ((int)live0 + (int)live1);
+        }
+        if (any) {
+          uint32_t mv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            mv[i] = ((xa[i] & want0) | (xb[i] & want1)) ? __ldg(mrow + (long)(e + i) * mstr) : 0u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (kCount) mloads += ((xa[i] & want0) | (xb[i] & want1)) != 0;
+            acc0 |= xa[i] & mv[i];
+            acc1 |= xb[i] & mv[i];
+          }
+        }
+      }
+      for (; e < e1; ++e) {
+        const int32_t t = __ldg(seg.tab + e);
+        const int a = zb + (t >> 5);
+        const uint2 lo = s2[a], hi = s2[a + 1];
+        const uint32_t x0 = __funnelshift_r(lo.x, hi.x, t), x1 = __funnelshift_r(lo.y, hi.y, t);
+        if (kCount) {
+          if (live0) {
+            ++visited;
+            nonzero += x0 != 0;
+          }
+          if (live1) {
+            ++visited;
+            nonzero += x1 != 0;
+          }
+        }
+        const uint32_t need = (x0 & m & ~acc0) | (x1 & m & ~acc1);
+        if (need) {
+          if (kCount) ++mloads;
+          const uint32_t mv = __ldg(mrow + (long)e * mstr);
+          acc0 |= x0 & mv;
+          acc1 |= x1 & mv;
+        }
+      }
+      live0 = live0 && (acc0 & m) != m;
+      live1 = live1 && (acc1 & m) != m;
+      if (!__any_sync(kFull, live0 || live1)) break;
+    }
+  }
+  acc0 &= m;
+  acc1 &= m;
+  if (valid) {
+    out[q0 * os + w] = acc0;
+    if (has1) out[q1 * os + w] = acc1;
+  }
+  box_accumulate(obox + q0 * bs, acc0 != 0, wx, y, z);
+  if (has1) box_accumulate(obox + q1 * bs, acc1 != 0, wx, y, z);
+  if (kCount) {
+    if (valid) {
+      atomicAdd(counters + 0, visited);
+      atomicAdd(counters + 1, nonzero);
+      atomicAdd(counters + 2, mloads);
+      atomicAdd(counters + 3, (unsigned long long)(m != 0) * (has1 ? 2ull : 1ull));
+    }
+    if (lane == 0) atomicAdd(counters + 4, warp_iters);
+    if (threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
+  }
+}
+
 // The work list of one propagation: for every query q, the tiles whose
 // output words can take bits -- those within reach R (in y and z) of the
 // word box of X[q], and inside the box of the output mask when one is given
@@ -1014,6 +1191,17 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
     return cudaGetLastError();
   }
   const size_t smem = tile_smem_bytes(tc, seg.R);
+  if (smem > 0 && seg.tab && seg.mask && !listed && Q >= 2 && mask_stride == 0 && tc.pair &&
+      2 * smem <= (size_t)kTileOccSmemMax) {
+    dim3 grid(tc.tiles_y * tc.tiles_z, (Q + 1) / 2);
+    if (counters)
+      k_propagate_tile_pair<true><<<grid, 256, 2 * smem, st>>>(d, seg, tc, X, x_stride, mask, occ, out, out_stride,
+                                                               Q, xbox, obox, box_stride, counters);
+    else
+      k_propagate_tile_pair<false><<<grid, 256, 2 * smem, st>>>(d, seg, tc, X, x_stride, mask, occ, out,
+                                                                out_stride, Q, xbox, obox, box_stride, nullptr);
+    return cudaGetLastError();
+  }
   if (smem > 0 && seg.tab && listed) {
     if (counters)
       k_propagate_tile_list<true><<<list_grid, 256, smem, st>>>(
@@ -2203,6 +2391,12 @@ cudaError_t set_kernel_attributes() {
   const int bytes = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute((const void*)k_edge_masks_tile,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
