@@ -13,11 +13,14 @@ have arrived are admitted into the free slots of the tick's batch (a fixed
 number of reach+path slots and of replan slots, sized by a device-memory
 budget); one captured CUDA graph rebuilds the snapshot (occupancy, edge
 masks, forward sets) and solves every admitted path slot, and the admitted
-replans run right after it on the same stream, batched.  Requests that
-arrive while a tick's work is on the GPU wait for the next tick, so the
-batch is refilled continuously.  A request's result depends only on its
-input and on the snapshot of the tick that admitted it (stamped on the
-request), so it is the same whether it is served alone or in a mix.
+replans run right after it on the same stream, batched.  For the rest of
+the tick the server keeps admitting: whenever requests have arrived and
+the GPU is free, they are solved as one more batch against the SAME
+snapshot (the grid keeps the tick's edge masks and forward sets, so such a
+batch only propagates, traces and chains), until the tick ends.  A
+request's result depends only on its input and on the snapshot of the tick
+that admitted it (stamped on the request), so it is the same whether it is
+served alone or in a mix, at a tick's start or within it.
 
 A path request becomes a live path when it completes; the arm is taken to
 advance one waypoint per tick along it.  A replan request names a live path
@@ -118,30 +121,49 @@ class Server:
         self.dead = set()
         self.pending: List[Request] = []
         self.finished: List[Request] = []
-        self.tick_ms: List[float] = []
+        self.tick_ms: List[float] = []    # GPU work of each tick's start (snapshot + admitted)
+        self.within_ms: List[float] = []  # GPU work of each batch admitted within a tick
 
     def _boxes(self) -> np.ndarray:
         return np.concatenate([self.static, self.moving.boxes()]).astype(np.int32)
 
     # ------------------------------------------------------------------ ticks
 
-    def run_tick(self, now: float) -> List[Request]:
-        """Advance the obstacles, admit what has arrived, solve; returns the
-        requests finished by this tick."""
-        torch = self.torch
-        self.moving.step()
-        self.tick += 1
+    def _admit(self, now: float):
+        """The requests that have arrived by `now` and fit the slots."""
         admitted_p = [r for r in self.pending if r.kind == "path" and r.arrival <= now]
         admitted_p = admitted_p[: self.slots_path]
         admitted_r = [r for r in self.pending if r.kind == "replan" and r.arrival <= now
                       and r.path_id in self.live]
         admitted_r = admitted_r[: self.slots_replan]
         # replans of paths that ended without a reach pose have nothing to do
-        dropped = [r for r in self.pending if r.kind == "replan" and r.path_id in self.dead]
+        dropped = [r for r in self.pending if r.kind == "replan" and r.path_id in self.dead
+                   and r.arrival <= now]
         for r in dropped:
             r.status, r.done, r.tick = ik.IK_PATH_UNREACHABLE, now, self.tick
         taken = {id(r) for r in admitted_p + admitted_r + dropped}
         self.pending = [r for r in self.pending if id(r) not in taken]
+        return admitted_p, admitted_r
+
+    def run_tick(self, now: float) -> List[Request]:
+        """Advance the obstacles, admit what has arrived, solve; returns the
+        requests finished at the tick's start."""
+        self.moving.step()
+        self.tick += 1
+        admitted_p, admitted_r = self._admit(now)
+        return self._solve(now, admitted_p, admitted_r, snapshot=True)
+
+    def run_within_tick(self, now: float) -> List[Request]:
+        """Solve what has arrived by `now` against the current tick's
+        snapshot (no rebuild); returns the finished requests (none when
+        nothing has arrived)."""
+        admitted_p, admitted_r = self._admit(now)
+        if not admitted_p and not admitted_r:
+            return []
+        return self._solve(now, admitted_p, admitted_r, snapshot=False)
+
+    def _solve(self, now: float, admitted_p, admitted_r, snapshot: bool) -> List[Request]:
+        torch = self.torch
         t0 = time.perf_counter()
         with torch.cuda.stream(self.stream):
             self.boxes_d.copy_(torch.from_numpy(self._boxes()), non_blocking=False)
@@ -161,14 +183,21 @@ class Server:
                 r.input_poses = lp.poses.copy()
             self.rp_in_d.copy_(torch.from_numpy(pin))
             self.rp_cur_d.copy_(torch.from_numpy(cur))
-        # snapshot + path slots (one graph), then the replan slots
-        self.batch.launch()
+        if snapshot:
+            # snapshot + path slots (one graph), then the replan slots
+            self.batch.launch()
+        elif admitted_p:
+            # the tick's snapshot stays: only the admitted paths are solved
+            n = len(admitted_p)
+            ik.ik_reach_path_many_device(self.grid.h, self.arm, self.root, self.targets_d[:n], self.W,
+                                         self.reach_d[:n], self.found_d[:n], self.poses_d[:n],
+                                         self.relax_d[:n], self.status_d[:n], delta=self.delta)
         if admitted_r:
             ik.ik_replan_many_device(self.grid.h, self.arm, self.root, self.rp_in_d, self.rp_cur_d,
                                      self.rp_out_d, self.rp_relax_d, self.rp_status_d,
                                      delta=self.delta)
         self.stream.synchronize()
-        self.tick_ms.append((time.perf_counter() - t0) * 1000.0)
+        (self.tick_ms if snapshot else self.within_ms).append((time.perf_counter() - t0) * 1000.0)
         done_t = now + (time.perf_counter() - t0)
         out = []
         if admitted_p:
@@ -196,11 +225,15 @@ class Server:
         self.finished.extend(out)
         return out
 
-    def serve(self, requests: List[Request], duration: float, realtime: bool = True) -> None:
-        """Run ticks for ``duration`` seconds of server clock.  With
-        ``realtime`` the clock is the wall clock (a tick waits for its
-        start time); otherwise ticks follow each other back to back and the
-        clock advances by ``tick_s`` per tick (deterministic admission)."""
+    def serve(self, requests: List[Request], duration: float, realtime: bool = True,
+              within: bool = True) -> None:
+        """Run ticks for ``duration`` seconds of server clock, admitting
+        requests within each tick as they arrive (``within``; else only at
+        tick starts).  With ``realtime`` the clock is the wall clock (a tick
+        waits for its start time, and within it the server waits for the
+        next arrival or the GPU); otherwise the clock is simulated: ticks
+        follow each other back to back and, within a tick, each arrival is
+        admitted at its own arrival time (deterministic admission)."""
         self.pending.extend(sorted(requests, key=lambda r: r.arrival))
         start = time.perf_counter()
         k = 0
@@ -208,6 +241,7 @@ class Server:
             t_tick = k * self.tick_s
             if t_tick > duration:
                 break
+            t_end = t_tick + self.tick_s
             if realtime:
                 wait = start + t_tick - time.perf_counter()
                 if wait > 0:
@@ -216,6 +250,21 @@ class Server:
             else:
                 now = t_tick
             self.run_tick(now)
+            while within:
+                if realtime:
+                    now = time.perf_counter() - start
+                if now >= t_end:
+                    break
+                if self.run_within_tick(now):
+                    continue
+                # nothing admissible now: wait for the next arrival (or the tick's end)
+                nxt = min((r.arrival for r in self.pending if r.arrival > now), default=None)
+                if realtime:
+                    time.sleep(max(0.0, min(t_end if nxt is None else nxt, t_end) - now))
+                elif nxt is None or nxt >= t_end:
+                    break
+                else:
+                    now = nxt
             k += 1
 
     def close(self) -> None:

@@ -31,17 +31,25 @@ def _fresh(r):
     return q
 
 
-def test_results_same_alone_and_in_the_mix(serve):
+@pytest.mark.parametrize("within", [False, True])
+def test_results_same_alone_and_in_the_mix(serve, within):
+    """Served at tick starts only (within=False: every tick's arrivals in one
+    batch with the snapshot rebuild) or also within ticks (within=True: each
+    arrival solved on arrival against the tick's snapshot, without a
+    rebuild), every result equals the same request served alone at its
+    tick's start, and a direct call on the tick's snapshot."""
     from paper_1906_10678_b300 import ik
     sc = G.c1_scene(0)
     reqs = serve.make_requests(sc, 120.0, 1.0, 5)
     a = _server(serve, sc)
-    a.serve(reqs, 1.0, realtime=False)
+    a.serve(reqs, 1.0, realtime=False, within=within)
     done = [r for r in a.finished if r.poses is not None]
     paths = [r for r in done if r.kind == "path"]
     replans = [r for r in done if r.kind == "replan"]
     assert len(paths) >= 6 and len(replans) >= 3
     assert max(len([r for r in done if r.tick == t]) for t in range(1, a.tick + 1)) >= 3
+    if within:
+        assert len(a.within_ms) > 0  # some requests were admitted within a tick
     a.close()
     for r in paths[:3] + replans[:3]:
         b = _server(serve, sc)
