@@ -3,6 +3,8 @@
 // host: the host builds the integer shell/supercover tables once per segment
 // length and then only enqueues kernels and copies.
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -40,6 +42,9 @@ struct ik_grid_s {
   uint32_t* d_occ_raw = nullptr;  // the occupancy as set, before dilation
   int dilate_r2 = 0;
   int work_list = 1;              // IK_OPT_WORK_LIST
+  int use_tma = 0;                // IK_OPT_TMA_MASKS (off: measured slower, see the header)
+  std::map<int, CUtensorMap> tmaps;  // TMA tensor maps over d_occ, per shell reach
+  int* d_tma_slow = nullptr;      // blocks whose TMA copy did not complete in time
   uint64_t version = 1;
   std::map<std::pair<int, int>, ShellDev*> shells;
   // shells restricted to an approach cone: (lo2, hi2, ax, ay, az, num, den)
@@ -267,9 +272,22 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     const int delta = (vz * RY + vy) * g->tc.P + (vx >> 5);
     sctab[i] = (int32_t)((uint32_t)delta << 5) | (vx & 31);
   }
+  // and for the TMA-staged brick (pitch BX, word w at column w + 4)
+  const int BX = tma_mask_pitch(g->d);
+  std::vector<int32_t> sctab_tma;
+  if (BX > 0) {
+    sctab_tma.resize(s->host.sc.size());
+    for (size_t i = 0; i < sctab_tma.size(); ++i) {
+      const int32_t v = s->host.sc[i];
+      const int vx = unpack_x(v), vy = unpack_y(v), vz = unpack_z(v);
+      const int delta = (vz * RY + vy) * BX + (vx >> 5);
+      sctab_tma[i] = (int32_t)((uint32_t)delta << 5) | (vx & 31);
+    }
+  }
   cudaError_t e = cudaMalloc(&s->d_off, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_tab, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sctab, sctab.size() * 4);
+  if (e == cudaSuccess && BX > 0) e = cudaMalloc(&s->d_sctab_tma, sctab_tma.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
@@ -277,6 +295,7 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     cudaFree(s->d_off);
     cudaFree(s->d_tab);
     cudaFree(s->d_sctab);
+    cudaFree(s->d_sctab_tma);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -285,6 +304,8 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
   }
   CK(cudaMemcpyAsync(s->d_tab, tab.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_sctab, sctab.data(), sctab.size() * 4, cudaMemcpyHostToDevice, g->st));
+  if (BX > 0)
+    CK(cudaMemcpyAsync(s->d_sctab_tma, sctab_tma.data(), sctab_tma.size() * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_off, s->host.dev_off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_rows, s->host.rows.data(), s->host.rows.size() * 4, cudaMemcpyHostToDevice,
                      g->st));
@@ -336,6 +357,54 @@ int check_cone(const ik_cone* c) {
 // Edge masks of a shell for the current occupancy over (at least) the word
 // box `need`; recomputed when stale.  Masks still valid for another box keep
 // it: the new box is the union of both.
+// cuTensorMapEncodeTiled, reached through the runtime (no link to the driver
+// library); nullptr when the driver does not offer it.
+PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
+  return fn;
+}
+
+// The tensor map over the grid's occupancy for bricks of shell reach R
+// (nullptr when the TMA form does not apply).
+const CUtensorMap* occ_tmap(ik_grid g, int R) {
+  auto it = g->tmaps.find(R);
+  if (it != g->tmaps.end()) return &it->second;
+  const int BX = tma_mask_pitch(g->d);
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tma_encode_fn();
+  if (BX <= 0 || !fn) return nullptr;
+  const Dims& d = g->d;
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)d.wx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)d.wx * 4, (cuuint64_t)d.wx * d.ny * 4};
+  cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)(g->tc.TY + 2 * R), (cuuint32_t)(g->tc.TZ + 2 * R)};
+  cuuint32_t es[3] = {1, 1, 1};
+  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void*)g->d_occ, dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return nullptr;
+  return &g->tmaps.emplace(R, m).first->second;
+}
+
+// Edge masks of shell s over box b: the TMA-staged form where it applies
+// (and IK_OPT_TMA_MASKS is on), else the per-thread staging.
+cudaError_t launch_masks(ik_grid g, const ShellDev& s, const MaskBox& b, uint32_t* mask) {
+  if (g->use_tma && s.d_sctab_tma && tma_mask_smem_bytes(g->tc, s.reach, tma_mask_pitch(g->d)) > 0) {
+    const CUtensorMap* m = occ_tmap(g, s.reach);
+    if (m) return launch_edge_masks_tma(g->d, g->tc, m, g->d_occ, s, b, mask, g->d_tma_slow, g->st);
+  }
+  return launch_edge_masks(g->d, g->tc, g->d_occ, s, b, mask, g->st);
+}
+
 int ensure_masks(ik_grid g, ShellDev* s, const MaskBox& need) {
   const bool valid = s->d_mask && s->mask_version == g->version;
   if (valid && s->mbox.contains(need)) return IK_OK;
@@ -366,7 +435,7 @@ int ensure_masks(ik_grid g, ShellDev* s, const MaskBox& need) {
   s->mbox = b;
   {
     ProfScope ps(g, P_MASKS);
-    CK(launch_edge_masks(g->d, g->tc, g->d_occ, *s, b, s->d_mask, g->st));
+    CK(launch_masks(g, *s, b, s->d_mask));
   }
   if (g->count_on) {
     // (offset, word) pairs, and the supercover voxel terms they OR together
@@ -655,6 +724,8 @@ int ik_create_grid(int nx, int ny, int nz, void* cuda_stream, ik_grid* out) {
   e = set_kernel_attributes();
   if (e == cudaSuccess) e = cudaMalloc(&g->d_occ, g->d.nw * 4);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_occ_raw, g->d.nw * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_tma_slow, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_tma_slow, 0, sizeof(int), g->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ, 0, g->d.nw * 4, g->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_occ_raw, 0, g->d.nw * 4, g->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
@@ -679,12 +750,14 @@ int ik_destroy_grid(ik_grid g) {
     cudaFree(s->d_off);
     cudaFree(s->d_tab);
     cudaFree(s->d_sctab);
+    cudaFree(s->d_sctab_tma);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
     cudaFree(s->d_mask);
     delete s;
   }
+  cudaFree(g->d_tma_slow);
   DevBuf* bufs[] = {&g->F, &g->V, &g->Vw, &g->chain, &g->boxes, &g->F_box, &g->V_box, &g->Vw_box,
                     &g->b_rp, &g->b_rin, &g->b_rc, &g->b_root, &g->b_targets,
                     &g->b_reach, &g->b_found, &g->b_poses, &g->b_relax, &g->b_status, &g->b_eps,
@@ -1462,7 +1535,7 @@ static int enqueue_reach_path(ik_grid g, const ArmDev& ad, const std::vector<She
   CK(launch_rasterize(d, d_boxes, n_boxes, g->d_occ_raw, g->st));
   if ((rc = apply_dilation(g))) return rc;
   if (g->use_masks)
-    for (ShellDev* sh : used) CK(launch_edge_masks(d, g->tc, g->d_occ, *sh, sh->mbox, sh->d_mask, g->st));
+    for (ShellDev* sh : used) CK(launch_masks(g, *sh, sh->mbox, sh->d_mask));
   uint32_t* F = ptr<uint32_t>(g->F);
   int32_t* fb = ptr<int32_t>(g->F_box);
   CK(cudaMemsetAsync(fb, kBoxEmptyByte, (size_t)(S + 1) * 24, g->st));
@@ -1789,6 +1862,11 @@ int ik_set_option(ik_grid g, int option, int value) {
   if (option == IK_OPT_QUERY_PAIRS) {
     if (value != 0 && value != 1) return IK_ERR_ARG;
     g->tc.pair = value;
+    return IK_OK;
+  }
+  if (option == IK_OPT_TMA_MASKS) {
+    if (value != 0 && value != 1) return IK_ERR_ARG;
+    g->use_tma = value;
     return IK_OK;
   }
   if (option == IK_OPT_WORK_LIST) {

@@ -132,6 +132,7 @@ struct ShellDev {
   int32_t* d_rows = nullptr;
   int32_t* d_tab = nullptr;
   int32_t* d_sctab = nullptr;  // per supercover voxel: (shared-memory delta << 5) | (dx & 31)
+  int32_t* d_sctab_tma = nullptr;  // the same for the TMA-staged brick (pitch tma_mask_pitch)
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;
@@ -150,6 +151,16 @@ cudaError_t launch_dilate(const Dims& d, const uint32_t* src, int r2, uint32_t* 
 // Edge masks of shell s over the word box b (mask rows of b.words() words).
 cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
                               const MaskBox& b, uint32_t* mask, cudaStream_t st);
+// The same with the occupancy brick of every tile staged by a TMA tensor
+// load: tmap is a CUtensorMap over occ (uint32 words, dims {wx, ny, nz}, box
+// {BX, TY + 2R, TZ + 2R}, out-of-bounds fill zero) for BX = tma_mask_pitch(d)
+// (0: the grid's rows are not 16-byte multiples, no TMA form); *slow counts
+// blocks whose copy did not complete in time (they staged with loads).
+int tma_mask_pitch(const Dims& d);
+size_t tma_mask_smem_bytes(const TileCfg& tc, int R, int BX);
+cudaError_t launch_edge_masks_tma(const Dims& d, const TileCfg& tc, const void* tmap, const uint32_t* occ,
+                                  const ShellDev& s, const MaskBox& b, uint32_t* mask, int* slow,
+                                  cudaStream_t st);
 // out[q] = (mask ? mask[q] : ~0) & D_seg(X[q]) for q < Q; sets are nw words
 // apart with stride `x_stride` / `out_stride` / `mask_stride` words between
 // queries (mask_stride 0: one mask shared by all queries).

@@ -5,6 +5,7 @@
 // at a time with one or two word loads and a funnel shift; voxels outside the
 // grid read as 0.  Everything here is exact boolean arithmetic.
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -257,6 +258,130 @@ __global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, Mas
     }
     mask[(long)e * nb + w] = ~blocked;
   }
+}
+
+// The same edge masks with the occupancy brick of a tile (its halo of reach
+// R in y and z, words -4 .. BX - 5 in x) copied into shared memory by one
+// TMA tensor load (cp.async.bulk.tensor, completion on an mbarrier) instead
+// of per-thread loads.  The copy starts at word -4 because a tiled copy's
+// innermost coordinate must be a multiple of 16 bytes; the words outside
+// the grid arrive as zeros (the tensor map's out-of-bounds fill), so word
+// w of a row sits at column w + 4 of a BX-word staged row.  sctab holds the
+// supercover deltas for that pitch.  The wait is bounded: if the copy has
+// not completed after kTmaWaitNs, the block stages the brick with plain
+// loads instead (the same values, so a late copy changes nothing) and
+// counts the event in *slow.
+constexpr long long kTmaWaitNs = 200LL * 1000 * 1000;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__global__ void __launch_bounds__(256) k_edge_masks_tma(const __grid_constant__ CUtensorMap tmap, Dims d,
+                                                        TileCfg tc, MaskBox b, int tiles_y, int R, int n_off,
+                                                        int BX, const uint32_t* __restrict__ occ,
+                                                        const int32_t* __restrict__ sc_start,
+                                                        const int32_t* __restrict__ sctab,
+                                                        uint32_t* __restrict__ mask, int* slow) {
+  extern __shared__ __align__(128) uint32_t so_raw[];
+  __shared__ __align__(8) unsigned long long bar;
+  // the copy's destination: 128-byte aligned
+  uint32_t* so = (uint32_t*)(((uintptr_t)so_raw + 127) & ~(uintptr_t)127);
+  const int y0 = b.y0 + (blockIdx.x % tiles_y) * tc.TY, z0 = b.z0 + (blockIdx.x / tiles_y) * tc.TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R;
+  const uint32_t bytes = (uint32_t)BX * RY * RZ * 4u;
+  const uint32_t bar_a = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(so)),
+        "l"((unsigned long long)&tmap), "r"(-4), "r"(y0 - R), "r"(z0 - R), "r"(bar_a)
+        : "memory");
+  }
+  __syncthreads();  // the barrier is initialised before anyone waits on it
+  uint32_t done = 0;
+  long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar_a)
+        : "memory");
+    if (done) break;
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kTmaWaitNs) break;
+  }
+  if (!__syncthreads_and(done)) {
+    // fall back to plain loads of the same brick
+    if (threadIdx.x == 0) atomicAdd(slow, 1);
+    const int n = RZ * RY * BX;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int c = i % BX, r = (i / BX) % RY, zz = i / (BX * RY);
+      const int sw = c - 4, sy = y0 - R + r, sz = z0 - R + zz;
+      uint32_t v = 0u;
+      if (sw >= 0 && sw < d.wx && sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz)
+        v = __ldg(occ + ((long)sz * d.ny + sy) * d.wx + sw);
+      so[i] = v;
+    }
+    __syncthreads();
+  }
+  const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
+  if (warp >= tc.TZ || lane >= tc.lanes || y > b.y1 || z > b.z1 || wx < b.wx0 || wx > b.wx1) return;
+  const long w = b.index(wx, y, z), nb = b.words();
+  const int base = ((z - z0 + R) * RY + (y - y0 + R)) * BX + (wx + 4);
+  const int e_end = min(n_off, (int)(blockIdx.y + 1) * kMaskChunk);
+  for (int e = blockIdx.y * kMaskChunk; e < e_end; ++e) {
+    const int s1 = __ldg(sc_start + e + 1);
+    uint32_t blocked = 0;
+    int i = __ldg(sc_start + e);
+    for (; i + 4 <= s1; i += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t t = __ldg(sctab + i + u);
+        const int a = base + (t >> 5);
+        blocked |= __funnelshift_r(so[a], so[a + 1], t & 31);
+      }
+    }
+    for (; i < s1; ++i) {
+      const int32_t t = __ldg(sctab + i);
+      const int a = base + (t >> 5);
+      blocked |= __funnelshift_r(so[a], so[a + 1], t & 31);
+    }
+    mask[(long)e * nb + w] = ~blocked;
+  }
+}
+
+size_t tma_mask_smem_bytes(const TileCfg& tc, int R, int BX) {
+  if (BX <= 0 || R > 31) return 0;
+  const size_t bytes = (size_t)BX * (tc.TY + 2 * R) * (tc.TZ + 2 * R) * 4 + 128;
+  return bytes <= (size_t)kTileOccSmemMax ? bytes : 0;
+}
+
+int tma_mask_pitch(const Dims& d) {
+  // rows must be a multiple of 16 bytes apart for a tensor map
+  if ((d.wx * 4) % 16 != 0) return 0;
+  return (d.wx + 5 + 3) / 4 * 4;
+}
+
+cudaError_t launch_edge_masks_tma(const Dims& d, const TileCfg& tc, const void* tmap, const uint32_t* occ,
+                                  const ShellDev& s, const MaskBox& b, uint32_t* mask, int* slow,
+                                  cudaStream_t st) {
+  const int n = (int)s.host.off.size();
+  if (n == 0 || b.words() <= 0) return cudaSuccess;
+  const int BX = tma_mask_pitch(d);
+  const size_t smem = tma_mask_smem_bytes(tc, s.reach, BX);
+  if (!smem || !s.d_sctab_tma) return cudaErrorInvalidValue;
+  const int tiles_y = (b.nyy() + tc.TY - 1) / tc.TY, tiles_z = (b.z1 - b.z0 + tc.TZ) / tc.TZ;
+  dim3 grid(tiles_y * tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
+  k_edge_masks_tma<<<grid, 256, smem, st>>>(*(const CUtensorMap*)tmap, d, tc, b, tiles_y, s.reach, n, BX, occ,
+                                            s.d_sc_start, s.d_sctab_tma, mask, slow);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
@@ -2391,6 +2516,9 @@ cudaError_t set_kernel_attributes() {
   const int bytes = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute((const void*)k_edge_masks_tile,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_edge_masks_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kTileOccSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);

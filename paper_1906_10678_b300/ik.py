@@ -34,6 +34,7 @@ IK_OPT_TILE_DEPTH = 2
 IK_OPT_DILATE_R2 = 3
 IK_OPT_WORK_LIST = 4
 IK_OPT_QUERY_PAIRS = 5
+IK_OPT_TMA_MASKS = 6
 IK_MAX_SEG = 16
 IK_MAX_LEN = 100
 
