@@ -404,8 +404,8 @@ def run_ours(args):
     # or fixed by --tile-depth
     if args.tile_depth == "auto":
         from paper_1906_10678_b300 import tune
-        tuning = tune.tile_depth(g.h, stream, sc.shape, sc.lengths, sc.root, boxes_d, targets_d, N_WAY,
-                                 (reach, found, poses, relax, status), delta=DELTA)
+        tuning = tune.tiling(g.h, stream, sc.shape, sc.lengths, sc.root, boxes_d, targets_d, N_WAY,
+                             (reach, found, poses, relax, status), delta=DELTA)
     else:
         ik.ik_set_option(g.h, ik.IK_OPT_TILE_DEPTH, int(args.tile_depth))
         tuning = {"depth": int(args.tile_depth), "fixed": True}

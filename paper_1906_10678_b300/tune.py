@@ -1,12 +1,15 @@
-"""Autotuner for the propagation tiling.
+"""Autotuner for the propagation and edge-mask tiling.
 
 For a grid shape and an arm it times one full reach + path batch with each
-candidate tile depth (8 or 16 output slices per block; see
-IK_OPT_TILE_DEPTH) and keeps the faster one.  Choices are cached in a JSON
-file (by default ``build/ik_tuning.json`` next to the package) keyed by the
-grid extents, the segment lengths and the batch shape, so a later process
-reuses them without measuring.  The results of every candidate are
-identical; only the time differs.
+candidate configuration and keeps the fastest: the tile depth (8 or 16
+output slices per block, IK_OPT_TILE_DEPTH), with depth 8 one or two
+queries per block on the dense levels (IK_OPT_QUERY_PAIRS), and the edge-mask
+brick staged by per-thread loads or by a TMA tensor copy (IK_OPT_TMA_MASKS,
+on grids whose rows allow it).  Choices are cached in a JSON file (by
+default ``build/ik_tuning.json`` next to the package) keyed by the grid
+extents, the segment lengths and the batch shape, so a later process reuses
+them without measuring.  The results of every candidate are identical; only
+the time differs.
 """
 from __future__ import annotations
 
@@ -16,14 +19,15 @@ from typing import Dict, Sequence
 
 from . import ik
 
-CANDIDATES = (8, 16)
+# (tile depth, query pairs); depth 16 has its own kernel, which takes one query
+CANDIDATES = ((8, 1), (8, 0), (16, 0))
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "build",
                              "ik_tuning.json")
 
 
 def _key(shape, lengths, n_targets: int, n_way: int) -> str:
     return "x".join(str(v) for v in shape) + "|" + ",".join(str(v) for v in lengths) + \
-        f"|{n_targets}|{n_way}"
+        f"|{n_targets}|{n_way}|v2"
 
 
 def load(path: str = DEFAULT_CACHE) -> Dict[str, dict]:
@@ -34,24 +38,35 @@ def load(path: str = DEFAULT_CACHE) -> Dict[str, dict]:
         return {}
 
 
-def tile_depth(grid_h: int, stream, shape, lengths: Sequence[int], root, boxes_d, targets_d, n_way: int,
-               outs, delta: int = 3, path: str = DEFAULT_CACHE, repeats: int = 2) -> dict:
-    """Best tile depth for this workload (measured once, then cached).
+def _apply(grid_h: int, cfg: dict) -> None:
+    ik.ik_set_option(grid_h, ik.IK_OPT_TILE_DEPTH, int(cfg["depth"]))
+    ik.ik_set_option(grid_h, ik.IK_OPT_QUERY_PAIRS, int(cfg["pairs"]))
+    ik.ik_set_option(grid_h, ik.IK_OPT_TMA_MASKS, int(cfg["tma"]))
+
+
+def tiling(grid_h: int, stream, shape, lengths: Sequence[int], root, boxes_d, targets_d, n_way: int,
+           outs, delta: int = 3, path: str = DEFAULT_CACHE, repeats: int = 2) -> dict:
+    """Best tiling for this workload (measured once, then cached).
 
     ``outs`` = (reach, found, poses, relax, status) CUDA tensors sized for
     ``targets_d``; ``stream`` the torch stream of the grid.  Leaves the
-    grid set to the chosen depth and returns {"depth", "ms": {...}}.
+    grid set to the chosen configuration and returns {"depth", "pairs",
+    "tma", "ms": {candidate: ms}}.
     """
     import torch
     cache = load(path)
     key = _key(shape, lengths, int(targets_d.shape[0]), n_way)
     if key in cache:
-        ik.ik_set_option(grid_h, ik.IK_OPT_TILE_DEPTH, cache[key]["depth"])
+        _apply(grid_h, cache[key])
         return dict(cache[key], cached=True)
     arm = ik.Arm(lengths)
+    tma_ok = (int(shape[0]) // 32 * 4) % 16 == 0
+    cands = [dict(depth=d, pairs=p, tma=t) for d, p in CANDIDATES for t in ((0, 1) if tma_ok else (0,))]
     times = {}
-    for depth in CANDIDATES:
-        ik.ik_set_option(grid_h, ik.IK_OPT_TILE_DEPTH, depth)
+    for cfg in cands:
+        _apply(grid_h, cfg)
+        name = f"depth{cfg['depth']}_pairs{cfg['pairs']}_tma{cfg['tma']}"
+
         def step():
             ik.ik_set_boxes(grid_h, boxes_d)
             ik.ik_reach_path_many_device(grid_h, arm, root, targets_d, n_way, *outs, delta=delta)
@@ -64,10 +79,10 @@ def tile_depth(grid_h: int, stream, shape, lengths: Sequence[int], root, boxes_d
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-        times[str(depth)] = e0.elapsed_time(e1) / repeats
-    best = min(CANDIDATES, key=lambda d: times[str(d)])
-    ik.ik_set_option(grid_h, ik.IK_OPT_TILE_DEPTH, best)
-    cache[key] = {"depth": best, "ms": times}
+        times[name] = e0.elapsed_time(e1) / repeats
+    best = min(cands, key=lambda c: times[f"depth{c['depth']}_pairs{c['pairs']}_tma{c['tma']}"])
+    _apply(grid_h, best)
+    cache[key] = dict(best, ms=times)
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         with open(path, "w") as f:
