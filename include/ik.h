@@ -142,10 +142,14 @@ IK_API int ik_destroy_grid(ik_grid g);
  * and one block per (tile, query) elsewhere; 0: one block per (tile, query)
  * on every level; 2: the work list on every level.  Results are identical. */
 #define IK_OPT_WORK_LIST 4
-/* IK_OPT_QUERY_PAIRS: 1 (default): on the levels of a batched backward pass
- * that run one block per tile (not the work list), with stored edge masks,
- * a block carries two queries, which share the output mask and the
- * edge-mask words; 0: one query per block.  Results are identical. */
+/* IK_OPT_QUERY_PAIRS: on the levels of a batched backward pass that run one
+ * block per tile (not the work list), with stored edge masks, a block
+ * carries two queries, which share the output mask and the edge-mask words:
+ * 1 (default) with padded source rows; 2 with source rows staged without
+ * pad words where a warp covers whole rows (conflict-free shared loads, the
+ * bits read across a row's end masked per offset: measured slower on the
+ * 128^3 step, 83.8 vs 79.1 ms, the masks cost more issue than the conflicts
+ * did), else as 1; 0: one query per block.  Results are identical. */
 #define IK_OPT_QUERY_PAIRS 5
 /* IK_OPT_TMA_MASKS: 1: the edge-mask kernel stages each tile's occupancy
  * brick with one TMA tensor copy where the grid allows it (rows a multiple of

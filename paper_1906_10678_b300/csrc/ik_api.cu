@@ -272,6 +272,19 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     const int delta = (vz * RY + vy) * g->tc.P + (vx >> 5);
     sctab[i] = (int32_t)((uint32_t)delta << 5) | (vx & 31);
   }
+  // and for rows staged without pad words (pitch wx), when a warp covers
+  // whole rows: the word offset, the sign of dx and the shift
+  std::vector<int32_t> tabw;
+  const int wxw = g->d.wx;
+  if (32 % wxw == 0) {
+    tabw.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+      const int32_t o = s->host.dev_off[i];
+      const int dx = unpack_x(o), dy = unpack_y(o);
+      const int delta = dy * wxw + (dx >> 5);
+      tabw[i] = (int32_t)(((uint32_t)delta << 6) | ((uint32_t)(dx < 0) << 5) | (uint32_t)(dx & 31));
+    }
+  }
   // and for the TMA-staged brick (pitch BX, word w at column w + 4)
   const int BX = tma_mask_pitch(g->d);
   std::vector<int32_t> sctab_tma;
@@ -288,6 +301,7 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
   if (e == cudaSuccess) e = cudaMalloc(&s->d_tab, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sctab, sctab.size() * 4);
   if (e == cudaSuccess && BX > 0) e = cudaMalloc(&s->d_sctab_tma, sctab_tma.size() * 4);
+  if (e == cudaSuccess && !tabw.empty()) e = cudaMalloc(&s->d_tabw, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
@@ -296,6 +310,7 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     cudaFree(s->d_tab);
     cudaFree(s->d_sctab);
     cudaFree(s->d_sctab_tma);
+    cudaFree(s->d_tabw);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -306,6 +321,8 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
   CK(cudaMemcpyAsync(s->d_sctab, sctab.data(), sctab.size() * 4, cudaMemcpyHostToDevice, g->st));
   if (BX > 0)
     CK(cudaMemcpyAsync(s->d_sctab_tma, sctab_tma.data(), sctab_tma.size() * 4, cudaMemcpyHostToDevice, g->st));
+  if (!tabw.empty())
+    CK(cudaMemcpyAsync(s->d_tabw, tabw.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_off, s->host.dev_off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_rows, s->host.rows.data(), s->host.rows.size() * 4, cudaMemcpyHostToDevice,
                      g->st));
@@ -488,6 +505,7 @@ void fill_seg(const ShellDev* s, const ik_grid g, bool masks, SegDev* sd) {
   sd->off = s->d_off;
   sd->rows = s->d_rows;
   sd->tab = s->d_tab;
+  sd->tabw = s->d_tabw;
   sd->sctab = s->d_sctab;
   sd->sc_start = s->d_sc_start;
   sd->sc = s->d_sc;
@@ -751,6 +769,7 @@ int ik_destroy_grid(ik_grid g) {
     cudaFree(s->d_tab);
     cudaFree(s->d_sctab);
     cudaFree(s->d_sctab_tma);
+    cudaFree(s->d_tabw);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -934,6 +953,7 @@ static int cone_arm(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int
   sd.off = s->d_off;
   sd.rows = s->d_rows;
   sd.tab = s->d_tab;
+  sd.tabw = s->d_tabw;
   sd.sctab = s->d_sctab;
   sd.sc_start = s->d_sc_start;
   sd.sc = s->d_sc;
@@ -1860,7 +1880,7 @@ int ik_set_option(ik_grid g, int option, int value) {
     return IK_OK;
   }
   if (option == IK_OPT_QUERY_PAIRS) {
-    if (value != 0 && value != 1) return IK_ERR_ARG;
+    if (value < 0 || value > 2) return IK_ERR_ARG;
     g->tc.pair = value;
     return IK_OK;
   }

@@ -83,6 +83,8 @@ struct SegDev {
   int lo2, hi2;
   int R;                   // max |component| of an offset
   const int32_t* tab;      // [n] shared-memory deltas for the tiled kernel, see TileCfg
+  const int32_t* tabw;     // [n] the same for rows staged without pad words (pitch wx):
+                           // ((dy * wx + (dx >> 5)) << 6) | (dx < 0) << 5 | (dx & 31); nullable
   const int32_t* sctab;    // [sc_start[n]] shared-memory deltas of the supercover voxels
   const uint32_t* occ;     // the grid's occupancy, for segment tests without stored masks
 };
@@ -97,7 +99,7 @@ struct SegDev {
 struct TileCfg {
   int TY, TZ, P, lanes, tiles_y, tiles_z;
   int depth = 8;  // output slices per tile of the propagation: 8 (one per warp) or 16 (two)
-  int pair = 1;   // two queries per block on the dense levels of a batched pass (IK_OPT_QUERY_PAIRS)
+  int pair = 1;   // IK_OPT_QUERY_PAIRS: 0 one query per block, 1 two (padded rows), 2 two (rows without pad)
 };
 TileCfg make_tile_cfg(const Dims& d);
 // Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).
@@ -133,6 +135,7 @@ struct ShellDev {
   int32_t* d_tab = nullptr;
   int32_t* d_sctab = nullptr;  // per supercover voxel: (shared-memory delta << 5) | (dx & 31)
   int32_t* d_sctab_tma = nullptr;  // the same for the TMA-staged brick (pitch tma_mask_pitch)
+  int32_t* d_tabw = nullptr;       // SegDev::tabw (grids whose rows fill a warp: wx = 1, 2, 4, 8, 16, 32)
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;

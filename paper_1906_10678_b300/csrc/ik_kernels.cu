@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(256, 3) k_propagate_tile_occ_list(Dims d, SegD
 // take bits from it.  The walk covers the union of the two queries' ranges
 // (a query's staged words outside its own box are zero).  Stored edge masks
 // only; results equal two one-query blocks.
-template <bool kCount>
+template <bool kCount, bool kWrap>
 __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg, TileCfg tc,
                                                              const uint32_t* __restrict__ X, long xs,
                                                              const uint32_t* __restrict__ mask,
@@ -841,14 +841,19 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
                                                              const int32_t* __restrict__ xbox,
                                                              int32_t* __restrict__ obox, long bs,
                                                              unsigned long long* __restrict__ counters) {
-  extern __shared__ uint2 s2[];
+  extern __shared__ uint2 s2_raw[];
+  // kWrap: rows staged at pitch wx without pad words (conflict-free 64-bit
+  // loads: a half warp reads 16 consecutive words), one spare word at both
+  // ends of the array; the words a row-end lane reads across the row's end
+  // belong to the neighbouring row and are masked off below
+  uint2* s2 = kWrap ? s2_raw + 1 : s2_raw;
   constexpr unsigned kFull = 0xffffffffu;
   const int tile = blockIdx.x;
   const int q0 = 2 * blockIdx.y, q1 = q0 + 1;
   const bool has1 = q1 < Q;
   const int y0 = (tile % tc.tiles_y) * tc.TY, z0 = (tile / tc.tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int R = seg.R, RY = tc.TY + 2 * R, P = tc.P;
+  const int R = seg.R, RY = tc.TY + 2 * R, P = kWrap ? d.wx : tc.P;
   const int z = z0 + warp, wx = lane % d.wx, y = y0 + lane / d.wx;
   const bool valid = warp < tc.TZ && lane < tc.lanes && y < d.ny && z < d.nz;
   const long w = valid ? ((long)z * d.ny + y) * d.wx + wx : 0;
@@ -887,7 +892,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
     const int sy0 = max(uy0 - tc.TY + 1, y0 - R), sy1 = min(uy1 + tc.TY - 1, y0 + tc.TY - 1 + R);
     const int ny_rows = sy1 - sy0 + 1, n_rows = (sz1 - sz0 + 1) * ny_rows;
     const int per_pass = 32 / P, nwarps = blockDim.x >> 5;
-    const int sub = lane / P, c = lane % P, sw = c - 1;
+    const int sub = lane / P, c = lane % P, sw = kWrap ? c : c - 1;
     if (ny_rows > 0 && sub < per_pass) {
       for (int r = warp * per_pass + sub; r < n_rows; r += nwarps * per_pass) {
         const int sy = sy0 + r % ny_rows, sz = sz0 + r / ny_rows;
@@ -909,7 +914,16 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
     const int ylast = min(y0 + tc.TY, d.ny) - 1;
     const int ez0 = max(uz0 - z, -R), ez1 = min(uz1 - z, R);
     const int ey0 = max(uy0 - ylast, -R), ey1 = min(uy1 - y0, R);
-    const int base = valid ? ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + 1) : (R * RY + R) * P + 1;
+    const int base = valid ? ((z - z0 + R) * RY + (y - y0 + R)) * P + (wx + (kWrap ? 0 : 1))
+                           : (R * RY + R) * P + 1;
+    // kWrap: the bits a row-end lane would take from across the row's end
+    const bool first = wx == 0, last = wx == d.wx - 1;
+    auto row_mask = [&](int32_t t) -> uint32_t {
+      if (!kWrap) return 0xffffffffu;
+      const int sh = t & 31;
+      if ((t >> 5) & 1) return first ? 0xffffffffu << (32 - sh) : 0xffffffffu;  // dx = sh - 32 < 0
+      return (last && sh) ? 0xffffffffu >> sh : 0xffffffffu;
+    };
     bool live0 = m != 0, live1 = has1 && m != 0;
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
       const int32_t* rowp = seg.rows + (ez + R) * side + R;
@@ -921,11 +935,12 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
         uint32_t xa[8], xb[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int32_t t = __ldg(seg.tab + e + i);
-          const int a = zb + (t >> 5);
+          const int32_t t = __ldg((kWrap ? seg.tabw : seg.tab) + e + i);
+          const int a = zb + (t >> (kWrap ? 6 : 5));
           const uint2 lo = s2[a], hi = s2[a + 1];
-          xa[i] = __funnelshift_r(lo.x, hi.x, t);  // shift taken mod 32
-          xb[i] = __funnelshift_r(lo.y, hi.y, t);
+          const uint32_t mk = row_mask(t);
+          xa[i] = __funnelshift_r(lo.x, hi.x, t) & mk;  // shift taken mod 32
+          xb[i] = __funnelshift_r(lo.y, hi.y, t) & mk;
         }
         const uint32_t want0 = m & ~acc0, want1 = m & ~acc1;
         uint32_t any = 0;
@@ -953,10 +968,11 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
         }
       }
       for (; e < e1; ++e) {
-        const int32_t t = __ldg(seg.tab + e);
-        const int a = zb + (t >> 5);
+        const int32_t t = __ldg((kWrap ? seg.tabw : seg.tab) + e);
+        const int a = zb + (t >> (kWrap ? 6 : 5));
         const uint2 lo = s2[a], hi = s2[a + 1];
-        const uint32_t x0 = __funnelshift_r(lo.x, hi.x, t), x1 = __funnelshift_r(lo.y, hi.y, t);
+        const uint32_t mk = row_mask(t);
+        const uint32_t x0 = __funnelshift_r(lo.x, hi.x, t) & mk, x1 = __funnelshift_r(lo.y, hi.y, t) & mk;
         if (kCount) {
           if (live0) {
             ++visited;
@@ -1319,12 +1335,26 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
   if (smem > 0 && seg.tab && seg.mask && !listed && Q >= 2 && mask_stride == 0 && tc.pair &&
       2 * smem <= (size_t)kTileOccSmemMax) {
     dim3 grid(tc.tiles_y * tc.tiles_z, (Q + 1) / 2);
+    if (tc.pair == 2 && seg.tabw && tc.lanes == 32) {
+      // rows without pad words: (TZ + 2R) (TY + 2R) wx words per query, one spare at each end
+      const size_t smem_w = ((size_t)(tc.TZ + 2 * seg.R) * (tc.TY + 2 * seg.R) * d.wx + 2) * 8;
+      if (counters)
+        k_propagate_tile_pair<true, true><<<grid, 256, smem_w, st>>>(d, seg, tc, X, x_stride, mask, occ, out,
+                                                                     out_stride, Q, xbox, obox, box_stride, counters);
+      else
+        k_propagate_tile_pair<false, true><<<grid, 256, smem_w, st>>>(d, seg, tc, X, x_stride, mask, occ, out,
+                                                                      out_stride, Q, xbox, obox, box_stride,
+                                                                      nullptr);
+      return cudaGetLastError();
+    }
     if (counters)
-      k_propagate_tile_pair<true><<<grid, 256, 2 * smem, st>>>(d, seg, tc, X, x_stride, mask, occ, out, out_stride,
-                                                               Q, xbox, obox, box_stride, counters);
+      k_propagate_tile_pair<true, false><<<grid, 256, 2 * smem, st>>>(d, seg, tc, X, x_stride, mask, occ, out,
+                                                                      out_stride, Q, xbox, obox, box_stride,
+                                                                      counters);
     else
-      k_propagate_tile_pair<false><<<grid, 256, 2 * smem, st>>>(d, seg, tc, X, x_stride, mask, occ, out,
-                                                                out_stride, Q, xbox, obox, box_stride, nullptr);
+      k_propagate_tile_pair<false, false><<<grid, 256, 2 * smem, st>>>(d, seg, tc, X, x_stride, mask, occ, out,
+                                                                       out_stride, Q, xbox, obox, box_stride,
+                                                                       nullptr);
     return cudaGetLastError();
   }
   if (smem > 0 && seg.tab && listed) {
@@ -2520,10 +2550,16 @@ cudaError_t set_kernel_attributes() {
     e = cudaFuncSetAttribute((const void*)k_edge_masks_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kTileOccSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<false>,
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile<true>,

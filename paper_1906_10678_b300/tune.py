@@ -19,8 +19,9 @@ from typing import Dict, Sequence
 
 from . import ik
 
-# (tile depth, query pairs); depth 16 has its own kernel, which takes one query
-CANDIDATES = ((8, 1), (8, 0), (16, 0))
+# (tile depth, query pairs: 0 one, 1 two with padded rows, 2 two with unpadded
+# rows); depth 16 has its own kernel, which takes one query
+CANDIDATES = ((8, 1), (8, 2), (8, 0), (16, 0))
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "build",
                              "ik_tuning.json")
 
