@@ -220,8 +220,30 @@ __global__ void __launch_bounds__(256) k_edge_masks_tile(Dims d, TileCfg tc, Mas
   const int y0 = b.y0 + (blockIdx.x % tiles_y) * tc.TY, z0 = b.z0 + (blockIdx.x / tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int RY = tc.TY + 2 * R, RZ = tc.TZ + 2 * R, P = tc.P;
-  {
-    const int n_rows = RZ * RY, per_pass = 32 / P;
+  const int n_rows = RZ * RY;
+  if ((d.wx & 3) == 0) {
+    // rows of 16-byte multiples: one thread per staged row, 128-bit loads
+    // (one per four words), the two pad words zero
+    for (int r = threadIdx.x; r < n_rows; r += blockDim.x) {
+      const int sy = y0 - R + r % RY, sz = z0 - R + r / RY;
+      uint32_t* dst = so + r * P;
+      dst[0] = 0u;
+      dst[d.wx + 1] = 0u;
+      if (sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz) {
+        const uint4* src = reinterpret_cast<const uint4*>(occ + ((long)sz * d.ny + sy) * d.wx);
+        for (int q = 0; q < (d.wx >> 2); ++q) {
+          const uint4 v = __ldg(src + q);
+          dst[1 + 4 * q] = v.x;
+          dst[2 + 4 * q] = v.y;
+          dst[3 + 4 * q] = v.z;
+          dst[4 + 4 * q] = v.w;
+        }
+      } else {
+        for (int c = 1; c <= d.wx; ++c) dst[c] = 0u;
+      }
+    }
+  } else {
+    const int per_pass = 32 / P;
     const int sub = lane / P, c = lane % P, sw = c - 1;
     if (sub < per_pass) {
       for (int r = warp * per_pass + sub; r < n_rows; r += 8 * per_pass) {
