@@ -53,6 +53,9 @@ struct ConeSpec {
 void build_shell(int lo2, int hi2, ShellHost* out, const ConeSpec* cone = nullptr);
 // Closed supercover of 0 -> d by incremental traversal; (z, y, x) order.
 void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
+// The same walk into a caller buffer of cap entries, allocating nothing:
+// returns the number of voxels, or -1 when they do not fit.
+int supercover_walk(int dx, int dy, int dz, int32_t* out, int cap);
 
 // A box of words {wx0..wx1} x {y0..y1} x {z0..z1} (inclusive) over which
 // edge masks are stored; a mask row holds its words in (z, y, x) order.

@@ -55,63 +55,6 @@ struct NaArm {
   int S;
 };
 
-// Supercover of 0 -> (dx, dy, dz) by the boundary-crossing walk (see
-// ik_tables.cpp), written to out (capacity cap) in (z, y, x) order.
-// Returns its size, or -1 when it does not fit.
-int na_supercover(int dx, int dy, int dz, int32_t* out, int cap) {
-  const int d[3] = {dx, dy, dz};
-  int n[3], s[3], k[3] = {0, 0, 0}, cur[3] = {0, 0, 0};
-  for (int i = 0; i < 3; ++i) {
-    n[i] = d[i] < 0 ? -d[i] : d[i];
-    s[i] = d[i] < 0 ? -1 : 1;
-  }
-  int cnt = 0;
-  auto push = [&](int x, int y, int z) {
-    if (cnt < cap) out[cnt] = ikb::pack3(x, y, z);
-    ++cnt;
-  };
-  push(0, 0, 0);
-  for (;;) {
-    int best = -1;
-    for (int i = 0; i < 3; ++i) {
-      if (k[i] >= n[i]) continue;
-      if (best < 0 || (long)(2 * k[i] + 1) * n[best] < (long)(2 * k[best] + 1) * n[i]) best = i;
-    }
-    if (best < 0) break;
-    int A[3], na = 0;
-    for (int i = 0; i < 3; ++i)
-      if (k[i] < n[i] && (long)(2 * k[i] + 1) * n[best] == (long)(2 * k[best] + 1) * n[i]) A[na++] = i;
-    for (int msk = 1; msk < (1 << na); ++msk) {
-      int v[3] = {cur[0], cur[1], cur[2]};
-      for (int b = 0; b < na; ++b)
-        if (msk & (1 << b)) v[A[b]] += s[A[b]];
-      push(v[0], v[1], v[2]);
-    }
-    for (int b = 0; b < na; ++b) {
-      cur[A[b]] += s[A[b]];
-      ++k[A[b]];
-    }
-  }
-  if (cnt > cap) return -1;
-  // order by (z, y, x) and drop repeats (insertion sort; lists are short)
-  auto key = [](int32_t v) {
-    return ((long)ikb::unpack_z(v) << 20) + ((long)ikb::unpack_y(v) << 10) + ikb::unpack_x(v);
-  };
-  for (int i = 1; i < cnt; ++i) {
-    int32_t v = out[i];
-    int j = i - 1;
-    while (j >= 0 && key(out[j]) > key(v)) {
-      out[j + 1] = out[j];
-      --j;
-    }
-    out[j + 1] = v;
-  }
-  int u = 0;
-  for (int i = 0; i < cnt; ++i)
-    if (u == 0 || out[u - 1] != out[i]) out[u++] = out[i];
-  return u;
-}
-
 // Fill the host staging tables for the arm; IK_ERR_UNSUPPORTED when they
 // exceed the scratch limits.
 int na_tables(const ik_arm* arm, NaArm* na, int* n_off, int* n_sc) {
@@ -134,7 +77,7 @@ int na_tables(const ik_arm* arm, NaArm* na, int* n_off, int* n_sc) {
           if (o >= kNaMaxOff) return IK_ERR_UNSUPPORTED;
           h_na_off[o] = ikb::pack3(x, y, z);
           h_na_start[o] = c;
-          const int m = na_supercover(x, y, z, h_na_sc + c, kNaMaxSc - c);
+          const int m = ikb::supercover_walk(x, y, z, h_na_sc + c, kNaMaxSc - c);
           if (m < 0) return IK_ERR_UNSUPPORTED;
           c += m;
           ++o;

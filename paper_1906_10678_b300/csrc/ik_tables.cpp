@@ -9,6 +9,7 @@
 // segment, so that no obstacle voxel can slip between sample points.
 
 #include <algorithm>
+#include <cstdlib>
 #include <array>
 #include <cmath>
 
@@ -43,17 +44,22 @@ static int isqrt_ceil(long v) {  // smallest r >= 0 with r*r >= v
 // Crossings are visited in increasing t (exact integer comparison).  At a
 // crossing time shared by the axes in A, the segment point lies on the faces
 // of every voxel cur + sum_{i in B} s_i e_i for B a subset of A, so all of
-// them are touched; then the walk steps to cur + sum_{i in A} s_i e_i.
-void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out) {
+// them are touched; then the walk steps to cur + sum_{i in A} s_i e_i.  The
+// voxels go to out (capacity cap, no allocation), sorted by (z, y, x)
+// without repeats; returns their number, or -1 when they do not fit.
+int supercover_walk(int dx, int dy, int dz, int32_t* out, int cap) {
   const int d[3] = {dx, dy, dz};
-  int n[3], s[3], k[3] = {0, 0, 0};
+  int n[3], s[3], k[3] = {0, 0, 0}, cur[3] = {0, 0, 0};
   for (int i = 0; i < 3; ++i) {
     n[i] = d[i] < 0 ? -d[i] : d[i];
     s[i] = d[i] < 0 ? -1 : 1;
   }
-  std::vector<std::array<int, 3>> vox;
-  int cur[3] = {0, 0, 0};
-  vox.push_back({0, 0, 0});
+  int cnt = 0;
+  auto push = [&](int x, int y, int z) {
+    if (cnt < cap) out[cnt] = pack3(x, y, z);
+    ++cnt;
+  };
+  push(0, 0, 0);
   for (;;) {
     // earliest pending crossing: compare (2k_i+1)/(2n_i) by cross-multiplying
     int best = -1;
@@ -63,29 +69,44 @@ void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out) {
     }
     if (best < 0) break;
     int A[3], na = 0;
-    for (int i = 0; i < 3; ++i) {
-      if (k[i] >= n[i]) continue;
-      if ((long)(2 * k[i] + 1) * n[best] == (long)(2 * k[best] + 1) * n[i]) A[na++] = i;
-    }
+    for (int i = 0; i < 3; ++i)
+      if (k[i] < n[i] && (long)(2 * k[i] + 1) * n[best] == (long)(2 * k[best] + 1) * n[i]) A[na++] = i;
     for (int mask = 1; mask < (1 << na); ++mask) {
-      std::array<int, 3> v = {cur[0], cur[1], cur[2]};
+      int v[3] = {cur[0], cur[1], cur[2]};
       for (int b = 0; b < na; ++b)
         if (mask & (1 << b)) v[A[b]] += s[A[b]];
-      vox.push_back(v);
+      push(v[0], v[1], v[2]);
     }
     for (int b = 0; b < na; ++b) {
       cur[A[b]] += s[A[b]];
       ++k[A[b]];
     }
   }
-  std::sort(vox.begin(), vox.end(), [](const std::array<int, 3>& a, const std::array<int, 3>& b) {
-    if (a[2] != b[2]) return a[2] < b[2];
-    if (a[1] != b[1]) return a[1] < b[1];
-    return a[0] < b[0];
-  });
-  vox.erase(std::unique(vox.begin(), vox.end()), vox.end());
-  out->clear();
-  for (auto& v : vox) out->push_back(pack3(v[0], v[1], v[2]));
+  if (cnt > cap) return -1;
+  // (z, y, x) order (the key keeps it: |x|, |y| < 512), then drop repeats;
+  // insertion sort, the lists are short
+  auto key = [](int32_t v) { return ((long)unpack_z(v) << 20) + ((long)unpack_y(v) << 10) + unpack_x(v); };
+  for (int i = 1; i < cnt; ++i) {
+    const int32_t v = out[i];
+    int j = i - 1;
+    while (j >= 0 && key(out[j]) > key(v)) {
+      out[j + 1] = out[j];
+      --j;
+    }
+    out[j + 1] = v;
+  }
+  int u = 0;
+  for (int i = 0; i < cnt; ++i)
+    if (u == 0 || out[u - 1] != out[i]) out[u++] = out[i];
+  return u;
+}
+
+void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out) {
+  // at most one voxel per crossing subset: 1 + 7 (|dx| + |dy| + |dz|)
+  const int cap = 8 + 7 * (std::abs(dx) + std::abs(dy) + std::abs(dz));
+  out->resize(cap);
+  const int n = supercover_walk(dx, dy, dz, out->data(), cap);
+  out->resize(n < 0 ? 0 : n);
 }
 
 static bool cone_keeps(const ConeSpec& c, long x, long y, long z) {
