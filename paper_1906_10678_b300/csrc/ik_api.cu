@@ -33,6 +33,10 @@ struct GridState;
 
 }  // namespace
 
+namespace ikb {
+void note_cuda_error(cudaError_t e) { g_last_error = cudaGetErrorString(e); }
+}  // namespace ikb
+
 struct ik_grid_s {
   int device = 0;
   Dims d{};

@@ -33,6 +33,7 @@ namespace {
 
 int cu(cudaError_t e) {
   if (e == cudaSuccess) return IK_OK;
+  note_cuda_error(e);
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? IK_ERR_OOM : IK_ERR_CUDA;
 }
@@ -133,7 +134,6 @@ struct ik_batch_engine_s {
   size_t pinned_bytes = 0;
   cudaEvent_t staged = nullptr;  // the last upload out of `pinned` is done
   cudaEvent_t t0 = nullptr, t1 = nullptr;
-  size_t smem_set = 0;
   long long timeout_ns = 20LL * 1000 * 1000 * 1000;
 
   ~ik_batch_engine_s() {
@@ -352,10 +352,7 @@ int run_wave(ik_batch_engine_s* E, const ik_problem* probs, const std::vector<Pr
   if ((rc = grow(E->state, (size_t)n * sizeof(int2)))) return rc;
   if ((rc = grow(E->boxes, std::max<size_t>(box_words, 1) * 4))) return rc;
   if (smem > batch_smem_limit()) return IK_ERR_UNSUPPORTED;
-  if (smem > E->smem_set) {
-    CKB(batch_set_smem(smem));
-    E->smem_set = smem;
-  }
+  CKB(batch_set_smem(smem));
   // host staging: descriptors, per-problem state, first items, boxes
   const size_t desc_b = (size_t)n * sizeof(BatchProb), state_b = (size_t)n * sizeof(int2);
   const size_t items_b = (size_t)n_first * sizeof(int4), boxes_b = box_words * 4;

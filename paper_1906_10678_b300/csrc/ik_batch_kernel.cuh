@@ -430,9 +430,21 @@ size_t batch_smem_limit() {
   return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
 }
 
+// The attribute belongs to the kernel, not to an engine: every engine of the
+// process shares it, so it only ever grows (per device, under a lock), and
+// a launch never finds it lowered by another engine.
 cudaError_t batch_set_smem(size_t bytes) {
-  return cudaFuncSetAttribute((const void*)k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  static std::mutex mu;
+  static size_t set_bytes[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (bytes <= set_bytes[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute((const void*)k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) set_bytes[dev] = bytes;
+  return e;
 }
 
 cudaError_t launch_batch_persistent(const BatchProb* probs, int n, const BatchQueue& q, const BatchRules& r,

@@ -289,6 +289,8 @@ cudaError_t launch_fold_last(const Dims& d, const SegDev& sg, int S, int P, int 
                              cudaStream_t st);
 // p[0 .. n) = v.
 cudaError_t launch_fill_i32(int32_t* p, long n, int32_t v, cudaStream_t st);
+// Records a CUDA error's text for ik_last_error_message (this thread).
+void note_cuda_error(cudaError_t e);
 // Opt-in to large dynamic shared memory for the tiled kernels (current device).
 cudaError_t set_kernel_attributes();
 cudaError_t launch_traceback_nearest_many(const Dims& d, const ArmDev& arm, const int32_t* root,

@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "ik_internal.h"
 

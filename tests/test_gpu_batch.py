@@ -307,3 +307,27 @@ def test_uneven_batch_timeout_is_reported_and_the_context_stays_usable(ik):
                               relax.cpu().numpy(), status.cpu().numpy())
     for a, b in zip(got, want):
         assert a["status"] == b["status"] and (a["poses"] == b["poses"]).all()
+
+
+def test_engines_share_the_kernels_shared_memory_setting(ik):
+    """Two engines on one device: one launches with the largest bricks (reach
+    24 on a 192^3 grid), the other with small ones, then the first again.
+    The kernel's shared-memory setting is shared by the engines and must not
+    be lowered under the first one's feet."""
+    import torch
+    sc = G.scaled_scene(192, (24, 16, 10, 6, 5), 150, 4, 24, 12, "big")
+    t = G.draw_targets(sc, 1, 12)[0]
+    big = [{"shape": sc.shape, "boxes": sc.boxes, "lengths": sc.lengths, "root": sc.root,
+            "target": tuple(int(v) for v in t), "n_way": 8}]
+    small = [_as_dict(p) for p in G.c4_problems(3, 9) if p.scene.shape[0] == 64][:1] or \
+        [_as_dict(G.c4_problems(1, 9)[0])]
+    want, _ = ik.ik_solve_batch(big)
+    with ik.BatchEngine() as e1, ik.BatchEngine() as e2:
+        for eng, probs in ((e1, big), (e2, small), (e1, big)):
+            found, reach, poses, relax, status, rc = _packed_outputs(ik, torch, probs)
+            eng.solve_async(probs, found, reach, poses, relax, status, rc)
+            torch.cuda.synchronize()
+            assert (rc.cpu().numpy() == ik.IK_OK).all()
+        got = ik.unpack_batch(big, found.cpu().numpy(), reach.cpu().numpy(), poses.cpu().numpy(),
+                              relax.cpu().numpy(), status.cpu().numpy())
+    assert got[0]["status"] == want[0]["status"] and (got[0]["poses"] == want[0]["poses"]).all()
