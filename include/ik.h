@@ -160,6 +160,17 @@ IK_API int ik_destroy_grid(ik_grid g);
  * masks takes 6.77 ms with it and 5.81 ms without (256^3: 16.3 / 13.9 ms).
  * Results are identical. */
 #define IK_OPT_TMA_MASKS 6
+/* IK_OPT_ROW_LANES (default 1): with stored edge masks, on grids whose rows
+ * are 1, 2 or 4 words (nx = 32, 64 or 128) and shells of reach at most 31,
+ * the levels of a batched pass (two or more queries) that run one block per
+ * tile (not the work list) use the row-lane kernel: a lane owns a whole
+ * row (two queries' words where IK_OPT_QUERY_PAIRS allows), each offset's
+ * source row comes from one conflict-free vector load of shared memory,
+ * and the rows that can still gain bits are packed into full warps before
+ * each plane of offsets.  On one B300 the 128^3 reach + path step takes
+ * 66.3 ms with it and 79.0 ms without.  0: the forms above.  Results are
+ * identical. */
+#define IK_OPT_ROW_LANES 7
 IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
 IK_API size_t ik_grid_words(ik_grid g);

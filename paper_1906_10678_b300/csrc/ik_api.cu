@@ -289,6 +289,31 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
       tabw[i] = (int32_t)(((uint32_t)delta << 6) | ((uint32_t)(dx < 0) << 5) | (uint32_t)(dx & 31));
     }
   }
+  // and for the row-lane propagation: per dz plane the runs dx < 0 and
+  // dx >= 0, each ordered by (dy, dx) (the device order within a row is by
+  // dx), with the run starts per dy
+  std::vector<int32_t> tabr, rowsr;
+  const int Rr = s->reach;
+  if (Rr <= 31) {
+    const int side = 2 * Rr + 1, rs = 2 * Rr + 2;
+    tabr.reserve(n);
+    rowsr.assign((size_t)side * 2 * rs, 0);
+    for (int dz = -Rr; dz <= Rr; ++dz)
+      for (int neg = 1; neg >= 0; --neg) {
+        int32_t* run = rowsr.data() + ((size_t)(dz + Rr) * 2 + (1 - neg)) * rs;
+        for (int dy = -Rr; dy <= Rr; ++dy) {
+          run[dy + Rr] = (int32_t)tabr.size();
+          const int r = (dz + Rr) * side + (dy + Rr);
+          for (int i = s->host.rows[r]; i < s->host.rows[r + 1]; ++i) {
+            const int32_t o = s->host.dev_off[i];
+            const int dx = unpack_x(o);
+            if ((dx < 0) != (neg == 1)) continue;
+            tabr.push_back((int32_t)(((uint32_t)i << 11) | ((uint32_t)(dy + 32) << 5) | (uint32_t)(dx & 31)));
+          }
+        }
+        run[2 * Rr + 1] = (int32_t)tabr.size();
+      }
+  }
   // and for the TMA-staged brick (pitch BX, word w at column w + 4)
   const int BX = tma_mask_pitch(g->d);
   std::vector<int32_t> sctab_tma;
@@ -306,6 +331,8 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sctab, sctab.size() * 4);
   if (e == cudaSuccess && BX > 0) e = cudaMalloc(&s->d_sctab_tma, sctab_tma.size() * 4);
   if (e == cudaSuccess && !tabw.empty()) e = cudaMalloc(&s->d_tabw, n * 4);
+  if (e == cudaSuccess && !tabr.empty()) e = cudaMalloc(&s->d_tabr, n * 4);
+  if (e == cudaSuccess && !tabr.empty()) e = cudaMalloc(&s->d_rowsr, rowsr.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
@@ -315,6 +342,8 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     cudaFree(s->d_sctab);
     cudaFree(s->d_sctab_tma);
     cudaFree(s->d_tabw);
+    cudaFree(s->d_tabr);
+    cudaFree(s->d_rowsr);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -327,6 +356,10 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     CK(cudaMemcpyAsync(s->d_sctab_tma, sctab_tma.data(), sctab_tma.size() * 4, cudaMemcpyHostToDevice, g->st));
   if (!tabw.empty())
     CK(cudaMemcpyAsync(s->d_tabw, tabw.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+  if (!tabr.empty()) {
+    CK(cudaMemcpyAsync(s->d_tabr, tabr.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+    CK(cudaMemcpyAsync(s->d_rowsr, rowsr.data(), rowsr.size() * 4, cudaMemcpyHostToDevice, g->st));
+  }
   CK(cudaMemcpyAsync(s->d_off, s->host.dev_off.data(), n * 4, cudaMemcpyHostToDevice, g->st));
   CK(cudaMemcpyAsync(s->d_rows, s->host.rows.data(), s->host.rows.size() * 4, cudaMemcpyHostToDevice,
                      g->st));
@@ -510,6 +543,8 @@ void fill_seg(const ShellDev* s, const ik_grid g, bool masks, SegDev* sd) {
   sd->rows = s->d_rows;
   sd->tab = s->d_tab;
   sd->tabw = s->d_tabw;
+  sd->tabr = s->d_tabr;
+  sd->rowsr = s->d_rowsr;
   sd->sctab = s->d_sctab;
   sd->sc_start = s->d_sc_start;
   sd->sc = s->d_sc;
@@ -774,6 +809,8 @@ int ik_destroy_grid(ik_grid g) {
     cudaFree(s->d_sctab);
     cudaFree(s->d_sctab_tma);
     cudaFree(s->d_tabw);
+    cudaFree(s->d_tabr);
+    cudaFree(s->d_rowsr);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -958,6 +995,8 @@ static int cone_arm(ik_grid g, const ik_arm* arm, const ik_cone* cone, const int
   sd.rows = s->d_rows;
   sd.tab = s->d_tab;
   sd.tabw = s->d_tabw;
+  sd.tabr = s->d_tabr;
+  sd.rowsr = s->d_rowsr;
   sd.sctab = s->d_sctab;
   sd.sc_start = s->d_sc_start;
   sd.sc = s->d_sc;
@@ -1886,6 +1925,11 @@ int ik_set_option(ik_grid g, int option, int value) {
   if (option == IK_OPT_QUERY_PAIRS) {
     if (value < 0 || value > 2) return IK_ERR_ARG;
     g->tc.pair = value;
+    return IK_OK;
+  }
+  if (option == IK_OPT_ROW_LANES) {
+    if (value != 0 && value != 1) return IK_ERR_ARG;
+    g->tc.rows = value;
     return IK_OK;
   }
   if (option == IK_OPT_TMA_MASKS) {

@@ -88,6 +88,12 @@ struct SegDev {
   const int32_t* tab;      // [n] shared-memory deltas for the tiled kernel, see TileCfg
   const int32_t* tabw;     // [n] the same for rows staged without pad words (pitch wx):
                            // ((dy * wx + (dx >> 5)) << 6) | (dx < 0) << 5 | (dx & 31); nullable
+  const int32_t* tabr;     // [n] the row-lane propagation's offsets: per dz plane those with dx < 0
+                           // ordered by (dy, dx), then those with dx >= 0; entry
+                           // (e << 11) | ((dy + 32) << 5) | (dx & 31), e the offset's index
+                           // above (its edge-mask row); nullable (reach above 31)
+  const int32_t* rowsr;    // [(2R+1) * 2 * (2R+2)] run starts of tabr: (dz, sign, dy), each
+                           // (dz, sign) run ending at its entry dy = R + 1
   const int32_t* sctab;    // [sc_start[n]] shared-memory deltas of the supercover voxels
   const uint32_t* occ;     // the grid's occupancy, for segment tests without stored masks
 };
@@ -103,6 +109,7 @@ struct TileCfg {
   int TY, TZ, P, lanes, tiles_y, tiles_z;
   int depth = 8;  // output slices per tile of the propagation: 8 (one per warp) or 16 (two)
   int pair = 1;   // IK_OPT_QUERY_PAIRS: 0 one query per block, 1 two (padded rows), 2 two (rows without pad)
+  int rows = 1;   // IK_OPT_ROW_LANES: the row-lane propagation where it applies
 };
 TileCfg make_tile_cfg(const Dims& d);
 // Shared-memory bytes of the tiled kernel for reach R (0 if it does not apply).
@@ -139,6 +146,8 @@ struct ShellDev {
   int32_t* d_sctab = nullptr;  // per supercover voxel: (shared-memory delta << 5) | (dx & 31)
   int32_t* d_sctab_tma = nullptr;  // the same for the TMA-staged brick (pitch tma_mask_pitch)
   int32_t* d_tabw = nullptr;       // SegDev::tabw (grids whose rows fill a warp: wx = 1, 2, 4, 8, 16, 32)
+  int32_t* d_tabr = nullptr;       // SegDev::tabr, rowsr (reach at most 31)
+  int32_t* d_rowsr = nullptr;
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "ik_internal.h"
 
@@ -1286,6 +1287,468 @@ __global__ void __launch_bounds__(256, 2) k_propagate_tile2(Dims d, SegDev seg, 
   }
 }
 
+// ------------------------------------------------------------ row lanes
+
+// Row-lane form of the stored-mask propagation, for grids whose rows are at
+// most four words (nx <= 128).  A lane owns one whole output row (the WX
+// words of one (y, z)), a warp 32 consecutive rows of one z slice, a block
+// 8 slices.  The source halo is staged as (8 + 2R) x (32 + 2R) rows of
+// exactly WX words: the words left of x = 0 and right of the row's end are
+// zero, so they are not stored, and a warp's 32 lanes read 32 consecutive
+// rows with one vector load each, free of bank conflicts.  An offset's
+// shifted source row then takes that one load and WX funnel shifts (the
+// neighbouring word is the same row's, or zero at its ends); its table
+// entry and edge-mask vector serve all WX words of the lane, and with
+// NQ = 2 both queries of the block (two planar halos, one output mask).
+// The offsets of each dz plane are walked as two runs over the dy range --
+// dx < 0, then dx >= 0 (table tabr, row starts rowsr) -- so that every
+// batch of offsets shifts the same way.  Results equal the other forms.
+template <int WX>
+__device__ __forceinline__ void row_ldg(const uint32_t* __restrict__ p, uint32_t (&v)[WX]) {
+  if constexpr (WX == 4) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else if constexpr (WX == 2) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = t.x, v[1] = t.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+
+template <int WX>
+__device__ __forceinline__ void row_lds(const uint32_t* p, uint32_t (&v)[WX]) {
+  if constexpr (WX == 4) {
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else if constexpr (WX == 2) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    v[0] = t.x, v[1] = t.y;
+  } else {
+    v[0] = *p;
+  }
+}
+
+template <int WX>
+__device__ __forceinline__ void row_st(uint32_t* p, const uint32_t (&v)[WX]) {
+  if constexpr (WX == 4)
+    *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  else if constexpr (WX == 2)
+    *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+  else
+    *p = v[0];
+}
+
+// The source row shifted by dx (dx & 31 = s): output bit b of word i takes
+// source voxel 32 i + b + dx.
+template <int WX, bool kNeg>
+__device__ __forceinline__ void row_shift(const uint32_t (&v)[WX], int s, uint32_t (&x)[WX]) {
+#pragma unroll
+  for (int i = 0; i < WX; ++i) {
+    if (kNeg)  // dx = s - 32: words i - 1 and i
+      x[i] = __funnelshift_r(i > 0 ? v[i > 0 ? i - 1 : 0] : 0u, v[i], s);
+    else  // dx = s: words i and i + 1
+      x[i] = __funnelshift_r(v[i], i + 1 < WX ? v[i + 1 < WX ? i + 1 : i] : 0u, s);
+  }
+}
+
+constexpr int kRowTY = 32, kRowTZ = 8, kRowUnits = kRowTY * kRowTZ;
+
+// The block's output rows are its units: unit t = (slice t / 32, row t %
+// 32), each carrying all NQ queries of the block.  The walk goes plane by
+// plane (dz) for the whole block: before each plane the units that can
+// still gain bits there (for some query, a free voxel not yet reached and a
+// source slice inside that query's box) are packed into a list, and each
+// warp takes 32 of them per pass, so a saturated row stops costing a lane
+// and a warp never waits on rows that are done.  A unit's accumulators and
+// output mask live in shared memory between planes.  qfast: blockIdx.x is
+// the query pair and blockIdx.y the tile, so the blocks resident together
+// work on the same tile and share its edge-mask words in L2.
+template <int WX, int NQ, bool kFullBox, bool kCount>
+__global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, int tiles_y, int qfast,
+                                                           const uint32_t* __restrict__ X, long xs,
+                                                           const uint32_t* __restrict__ mask, long ms,
+                                                           const uint32_t* __restrict__ occ,
+                                                           uint32_t* __restrict__ out, long os, int Q,
+                                                           const int32_t* __restrict__ xbox,
+                                                           int32_t* __restrict__ obox, long bs,
+                                                           unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(16) uint32_t sr[];
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr int TY = kRowTY, TZ = kRowTZ, NU = kRowUnits;
+  constexpr int kB = NQ == 1 ? 8 : 4;  // offsets per batch
+  __shared__ int s_cnt[8];
+  const int tile = qfast ? blockIdx.y : blockIdx.x;
+  const int qa = NQ * (qfast ? blockIdx.x : blockIdx.y);
+  const int y0 = (tile % tiles_y) * TY, z0 = (tile / tiles_y) * TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = seg.R, RY = TY + 2 * R;
+  const int HW = (TZ + 2 * R) * RY * WX;  // words of one query's halo
+  uint32_t* acc_s = sr + NQ * HW;                          // [NU][NQ][WX]
+  uint32_t* m_s = acc_s + NU * NQ * WX;                    // [NU][WX]
+  unsigned short* list = reinterpret_cast<unsigned short*>(m_s + NU * WX);  // [NU]
+  // the queries' source boxes (an empty box for a missing query)
+  int bx0[NQ], by0[NQ], bz0[NQ], bx1[NQ], by1[NQ], bz1[NQ];
+  bool has[NQ], touch = false;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    has[q] = qa + q < Q;
+    const int32_t* b = xbox + (long)(qa + q) * bs;
+    bx0[q] = has[q] ? __ldg(b + 0) : 0x7f7f7f7f;
+    by0[q] = has[q] ? __ldg(b + 1) : 0x7f7f7f7f;
+    bz0[q] = has[q] ? __ldg(b + 2) : 0x7f7f7f7f;
+    bx1[q] = has[q] ? -__ldg(b + 3) : -0x7f7f7f7f;
+    by1[q] = has[q] ? -__ldg(b + 4) : -0x7f7f7f7f;
+    bz1[q] = has[q] ? -__ldg(b + 5) : -0x7f7f7f7f;
+    touch = touch || (bx0[q] <= bx1[q] && by1[q] >= y0 - R && by0[q] <= y0 + TY - 1 + R &&
+                      bz1[q] >= z0 - R && bz0[q] <= z0 + TZ - 1 + R);
+  }
+  // this thread's row (slice warp, row lane): the output mask, shared by the queries
+  const int zt = z0 + warp, yt = y0 + lane;
+  const bool valid = yt < d.ny && zt < d.nz;
+  const long w0 = valid ? ((long)zt * d.ny + yt) * WX : 0;
+  bool m_any = false;
+  {
+    uint32_t m[WX];
+#pragma unroll
+    for (int i = 0; i < WX; ++i) m[i] = 0u;
+    if (valid) {
+      uint32_t o[WX];
+      row_ldg<WX>(occ + w0, o);
+      if (mask) row_ldg<WX>(mask + (long)qa * ms + w0, m);
+#pragma unroll
+      for (int i = 0; i < WX; ++i) {
+        m[i] = (mask ? m[i] : 0xffffffffu) & ~o[i];
+        m_any = m_any || m[i] != 0u;
+      }
+    }
+    row_st<WX>(m_s + threadIdx.x * WX, m);
+  }
+  if (!__syncthreads_or(touch && m_any)) {
+    if (valid) {
+      const uint32_t zero[WX] = {};
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (has[q]) row_st<WX>(out + (long)(qa + q) * os + w0, zero);
+    }
+    return;
+  }
+  // the union of the boxes in y and z (an empty box contributes nothing)
+  int uy0 = 0x7fffffff, uy1 = -0x7fffffff, uz0 = 0x7fffffff, uz1 = -0x7fffffff;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    if (bx0[q] <= bx1[q]) {
+      uy0 = min(uy0, by0[q]), uy1 = max(uy1, by1[q]);
+      uz0 = min(uz0, bz0[q]), uz1 = max(uz1, bz1[q]);
+    }
+  // Stage the halos: the rows the walk can read (slices of the union box in
+  // reach, rows at most TY - 1 outside its y range), one row per thread
+  // and pass; the words of each query's box are copied, the rest zeroed.
+  {
+    const int sz0 = max(uz0, z0 - R), sz1 = min(uz1, z0 + TZ - 1 + R);
+    const int sy0 = max(uy0 - TY + 1, y0 - R), sy1 = min(uy1 + TY - 1, y0 + TY - 1 + R);
+    const int nyr = sy1 - sy0 + 1, nr = (sz1 - sz0 + 1) * nyr;
+    if (nyr > 0)
+      for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        const int sy = sy0 + r % nyr, sz = sz0 + r / nyr;
+        const long row = ((long)sz * d.ny + sy) * WX;
+        uint32_t* dst = sr + ((sz - z0 + R) * RY + (sy - y0 + R)) * WX;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          uint32_t v[WX];
+#pragma unroll
+          for (int i = 0; i < WX; ++i) v[i] = 0u;
+          if (sy >= by0[q] && sy <= by1[q] && sz >= bz0[q] && sz <= bz1[q]) {
+            row_ldg<WX>(X + (long)(qa + q) * xs + row, v);
+#pragma unroll
+            for (int i = 0; i < WX; ++i)
+              if (i < bx0[q] || i > bx1[q]) v[i] = 0u;
+          }
+          row_st<WX>(dst + q * HW, v);
+        }
+      }
+    const uint32_t zero[WX] = {};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) row_st<WX>(acc_s + (threadIdx.x * NQ + q) * WX, zero);
+  }
+  __syncthreads();
+  unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0, passes = 0, pass_lanes = 0;
+  const int side = 2 * R + 2;  // row starts per (dz, sign) run, with its end
+  const int mx0 = kFullBox ? 0 : seg.mbox.wx0;
+  const unsigned mstr = (unsigned)seg.mbox.words();
+  const int EZ0 = max(uz0 - (z0 + TZ - 1), -R), EZ1 = min(uz1 - z0, R);
+  for (int ez = EZ0; ez <= EZ1; ++ez) {
+    // pack the units that can gain bits in this plane
+    bool act = false;
+    {
+      uint32_t m[WX];
+      row_lds<WX>(m_s + threadIdx.x * WX, m);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        uint32_t a[WX];
+        row_lds<WX>(acc_s + (threadIdx.x * NQ + q) * WX, a);
+        bool open = false;
+#pragma unroll
+        for (int i = 0; i < WX; ++i) open = open || (a[i] & m[i]) != m[i];
+        act = act || (open && zt + ez >= bz0[q] && zt + ez <= bz1[q]);
+      }
+    }
+    const unsigned bal = __ballot_sync(kFull, act);
+    if (lane == 0) s_cnt[warp] = __popc(bal);
+    __syncthreads();
+    int n_act = 0, pos = __popc(bal & ((1u << lane) - 1u));
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      n_act += s_cnt[c];
+      pos += c < warp ? s_cnt[c] : 0;
+    }
+    if (act) list[pos] = (unsigned short)threadIdx.x;
+    __syncthreads();
+    for (int p = warp * 32; p < n_act; p += 256) {
+      const bool hasu = p + lane < n_act;
+      const int t = hasu ? list[p + lane] : 0;
+      const int zu = z0 + t / 32, yu = y0 + t % 32;
+      uint32_t acc[NQ][WX], m[WX];
+      row_lds<WX>(m_s + t * WX, m);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) row_lds<WX>(acc_s + (t * NQ + q) * WX, acc[q]);
+      if (!hasu)
+#pragma unroll
+        for (int i = 0; i < WX; ++i) m[i] = 0u;
+      // the pass's union of the lanes' dy ranges
+      const int ey0 = __reduce_min_sync(kFull, hasu ? max(uy0 - yu, -R) : 0x7fffffff);
+      const int ey1 = __reduce_max_sync(kFull, hasu ? min(uy1 - yu, R) : -0x7fffffff);
+      const uint32_t* hz = sr + ((zu - z0 + R + ez) * RY + (yu - y0 + R)) * WX;
+      const uint32_t* mrow = seg.mask + (hasu ? seg.mbox.index(mx0, yu, zu) : 0);
+      // words still open at the pass's start (work counters only)
+      unsigned lw = 0;
+      if (kCount) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int i = 0; i < WX; ++i) lw |= (unsigned)((acc[q][i] & m[i]) != m[i]) << (q * WX + i);
+        if (lane == 0) {
+          ++passes;
+          pass_lanes += (unsigned long long)min(32, n_act - p);
+        }
+      }
+      // hz32: the lane's row at dy = -32 (the table stores dy + 32)
+      const uint32_t* hz32 = hz - 32 * WX;
+      // NB offsets from e on, all shifting the same way
+      auto batch = [&](auto neg_tag, auto nb_tag, int e) {
+        constexpr bool kNeg = decltype(neg_tag)::value;
+        constexpr int NB = decltype(nb_tag)::value;
+        uint32_t x[NB][NQ][WX];
+        int32_t tb[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          tb[b] = __ldg(seg.tabr + e + b);
+          const uint32_t* p2 = hz32 + ((tb[b] >> 5) & 63) * WX;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            uint32_t v[WX];
+            row_lds<WX>(p2 + q * HW, v);
+            row_shift<WX, kNeg>(v, tb[b] & 31, x[b][q]);
+          }
+        }
+        uint32_t want[NQ][WX];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int i = 0; i < WX; ++i) want[q][i] = m[i] & ~acc[q][i];
+        // need[b][i]: the bits offset b could add to word i of some query;
+        // with masks over whole rows only their union decides the load
+        constexpr int NW = kFullBox ? 1 : WX;
+        uint32_t need[NB][NW], any = 0u;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+#pragma unroll
+          for (int j = 0; j < NW; ++j) need[b][j] = 0u;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int i = 0; i < WX; ++i) need[b][kFullBox ? 0 : i] |= x[b][q][i] & want[q][i];
+#pragma unroll
+          for (int j = 0; j < NW; ++j) any |= need[b][j];
+        }
+        if (kCount) {
+          visited += (unsigned long long)NB * __popc(lw);
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+              for (int i = 0; i < WX; ++i) nonzero += ((lw >> (q * WX + i)) & 1u) && x[b][q][i] != 0u;
+        }
+        if (any) {
+          uint32_t mv[NB][WX];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const uint32_t* mp = mrow + (size_t)((unsigned)tb[b] >> 11) * mstr;
+            if (kFullBox) {
+              if (need[b][0]) {
+                row_ldg<WX>(mp, mv[b]);
+                if (kCount) mloads += WX;
+              } else {
+#pragma unroll
+                for (int i = 0; i < WX; ++i) mv[b][i] = 0u;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < WX; ++i) {
+                mv[b][i] = need[b][kFullBox ? 0 : i] ? __ldg(mp + (i - mx0)) : 0u;
+                if (kCount) mloads += need[b][kFullBox ? 0 : i] != 0u;
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+              for (int i = 0; i < WX; ++i) acc[q][i] |= x[b][q][i] & mv[b][i];
+        }
+      };
+      auto run = [&](auto neg_tag, int e, int e1) {
+        for (; e + kB <= e1; e += kB) batch(neg_tag, std::integral_constant<int, kB>{}, e);
+        for (; e < e1; ++e) batch(neg_tag, std::integral_constant<int, 1>{}, e);
+      };
+      if (ey0 <= ey1) {
+        const int32_t* rs = seg.rowsr + (ez + R) * 2 * side + R;
+        const int n0 = __ldg(rs + ey0), n1 = __ldg(rs + ey1 + 1);
+        const int p0 = __ldg(rs + side + ey0), p1 = __ldg(rs + side + ey1 + 1);
+        if (kCount && lane == 0) warp_iters += (unsigned long long)(n1 - n0 + p1 - p0);
+        run(std::true_type{}, n0, n1);
+        run(std::false_type{}, p0, p1);
+      }
+      if (hasu)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) row_st<WX>(acc_s + (t * NQ + q) * WX, acc[q]);
+    }
+    __syncthreads();
+  }
+  // outputs: this thread's row for each query
+  uint32_t m[WX];
+  row_lds<WX>(m_s + threadIdx.x * WX, m);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (!has[q]) continue;
+    uint32_t acc[WX];
+    row_lds<WX>(acc_s + (threadIdx.x * NQ + q) * WX, acc);
+    int lo = WX, hi = -1;
+#pragma unroll
+    for (int i = 0; i < WX; ++i) {
+      acc[i] &= m[i];
+      if (acc[i]) lo = min(lo, i), hi = i;
+    }
+    if (valid) row_st<WX>(out + (long)(qa + q) * os + w0, acc);
+    // the output's box: the lane's first and last non-zero word
+    int32_t* box = obox + (long)(qa + q) * bs;
+    const bool nz = hi >= 0;
+    if (__ballot_sync(kFull, nz)) {
+      const int big = 0x7fffffff;
+      const int v0 = __reduce_min_sync(kFull, nz ? lo : big);
+      const int v1 = __reduce_min_sync(kFull, nz ? yt : big);
+      const int v3 = __reduce_min_sync(kFull, nz ? -hi : big);
+      const int v4 = __reduce_min_sync(kFull, nz ? -yt : big);
+      if (lane == 0) {
+        atomicMin(box + 0, v0);
+        atomicMin(box + 1, v1);
+        atomicMin(box + 2, zt);
+        atomicMin(box + 3, v3);
+        atomicMin(box + 4, v4);
+        atomicMin(box + 5, -zt);
+      }
+    }
+  }
+  if (kCount) {
+    atomicAdd(counters + 0, visited);
+    atomicAdd(counters + 1, nonzero);
+    atomicAdd(counters + 2, mloads);
+    if (valid) {
+      unsigned long long live_words = 0;
+#pragma unroll
+      for (int i = 0; i < WX; ++i) live_words += m[i] != 0u;
+      int nq = 0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) nq += has[q];
+      atomicAdd(counters + 3, live_words * nq);
+    }
+    if (lane == 0) {
+      atomicAdd(counters + 4, warp_iters);
+      atomicAdd(counters + 6, passes);
+      atomicAdd(counters + 7, pass_lanes);
+    }
+    if (threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
+  }
+}
+
+size_t rows_smem_bytes(int wx, int R, int nq) {
+  if (R > 31 || (wx != 1 && wx != 2 && wx != 4)) return 0;
+  // the halos, the units' accumulators and output masks, the unit list
+  const size_t bytes = (size_t)nq * (kRowTZ + 2 * R) * (kRowTY + 2 * R) * wx * 4 +
+                       (size_t)(nq + 1) * kRowUnits * wx * 4 + (size_t)kRowUnits * 2;
+  return bytes <= (size_t)kTileOccSmemMax ? bytes : 0;
+}
+
+template <int WX, int NQ, bool kFullBox>
+cudaError_t launch_rows_t(const Dims& d, const SegDev& seg, const uint32_t* X, long xs, const uint32_t* mask,
+                          long ms, const uint32_t* occ, uint32_t* out, long os, int Q, const int32_t* xbox,
+                          int32_t* obox, long bs, cudaStream_t st, unsigned long long* counters, size_t smem) {
+  const int tiles_y = (d.ny + kRowTY - 1) / kRowTY, tiles_z = (d.nz + kRowTZ - 1) / kRowTZ;
+  const int tiles = tiles_y * tiles_z, groups = (Q + NQ - 1) / NQ;
+  // the query groups of one tile next to each other where the grid allows
+  const int qfast = tiles <= 65535 ? 1 : 0;
+  const dim3 grid = qfast ? dim3(groups, tiles) : dim3(tiles, groups);
+  if (counters)
+    k_propagate_rows<WX, NQ, kFullBox, true><<<grid, 256, smem, st>>>(d, seg, tiles_y, qfast, X, xs, mask, ms, occ,
+                                                                     out, os, Q, xbox, obox, bs, counters);
+  else
+    k_propagate_rows<WX, NQ, kFullBox, false><<<grid, 256, smem, st>>>(d, seg, tiles_y, qfast, X, xs, mask, ms,
+                                                                      occ, out, os, Q, xbox, obox, bs, nullptr);
+  return cudaGetLastError();
+}
+
+template <int WX>
+cudaError_t launch_rows_w(int nq, bool full, const Dims& d, const SegDev& seg, const uint32_t* X, long xs,
+                          const uint32_t* mask, long ms, const uint32_t* occ, uint32_t* out, long os, int Q,
+                          const int32_t* xbox, int32_t* obox, long bs, cudaStream_t st,
+                          unsigned long long* counters, size_t smem) {
+  if (nq == 2)
+    return full ? launch_rows_t<WX, 2, true>(d, seg, X, xs, mask, ms, occ, out, os, Q, xbox, obox, bs, st, counters, smem)
+                : launch_rows_t<WX, 2, false>(d, seg, X, xs, mask, ms, occ, out, os, Q, xbox, obox, bs, st, counters, smem);
+  return full ? launch_rows_t<WX, 1, true>(d, seg, X, xs, mask, ms, occ, out, os, Q, xbox, obox, bs, st, counters, smem)
+              : launch_rows_t<WX, 1, false>(d, seg, X, xs, mask, ms, occ, out, os, Q, xbox, obox, bs, st, counters, smem);
+}
+
+template <int WX>
+cudaError_t set_rows_attributes() {
+  cudaError_t e = cudaSuccess;
+  const void* fns[] = {(const void*)k_propagate_rows<WX, 1, false, false>, (const void*)k_propagate_rows<WX, 1, false, true>,
+                       (const void*)k_propagate_rows<WX, 1, true, false>,  (const void*)k_propagate_rows<WX, 1, true, true>,
+                       (const void*)k_propagate_rows<WX, 2, false, false>, (const void*)k_propagate_rows<WX, 2, false, true>,
+                       (const void*)k_propagate_rows<WX, 2, true, false>,  (const void*)k_propagate_rows<WX, 2, true, true>};
+  for (const void* f : fns)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  return e;
+}
+
+// Queries per block of the row-lane form for a launch, 0 where it does not
+// apply: stored edge masks, a batch of two or more queries (a single query,
+// the forward sets, measured faster on the other forms), rows of 1, 2 or 4
+// words, every row of every set aligned to its width, reach at most 31.
+int rows_queries(const Dims& d, const TileCfg& tc, const SegDev& seg, const uint32_t* X, long xs,
+                 const uint32_t* mask, long ms, const uint32_t* occ, const uint32_t* out, long os, int Q) {
+  if (!tc.rows || !seg.mask || !seg.tabr || !seg.rowsr || Q < 2) return 0;
+  const int wx = d.wx;
+  if (wx != 1 && wx != 2 && wx != 4) return 0;
+  const uintptr_t al = (uintptr_t)wx * 4 - 1;
+  if (((uintptr_t)X & al) || ((uintptr_t)out & al) || ((uintptr_t)mask & al) || ((uintptr_t)occ & al)) return 0;
+  if (xs % wx || os % wx || (mask && ms % wx)) return 0;
+  const int nq = (tc.pair && Q >= 2 && ms == 0) ? 2 : 1;
+  return rows_smem_bytes(wx, seg.R, nq) > 0 ? nq : 0;
+}
+
 size_t tile2_smem_bytes(const TileCfg& tc, int R) {
   if (R > 31 || tc.P > 31) return 0;
   const size_t bytes = (size_t)(16 + 2 * R) * (tc.TY + 2 * R) * tc.P * 4;
@@ -1353,6 +1816,21 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
                                                                occ, out, out_stride, xbox, obox, box_stride,
                                                                nullptr);
     return cudaGetLastError();
+  }
+  if (!listed) {
+    const int nq = rows_queries(d, tc, seg, X, x_stride, mask, mask_stride, occ, out, out_stride, Q);
+    if (nq) {
+      const size_t smem_r = rows_smem_bytes(d.wx, seg.R, nq);
+      const bool full = seg.mbox.wx0 == 0 && seg.mbox.wx1 == d.wx - 1;
+      if (d.wx == 4)
+        return launch_rows_w<4>(nq, full, d, seg, X, x_stride, mask, mask_stride, occ, out, out_stride, Q, xbox,
+                                obox, box_stride, st, counters, smem_r);
+      if (d.wx == 2)
+        return launch_rows_w<2>(nq, full, d, seg, X, x_stride, mask, mask_stride, occ, out, out_stride, Q, xbox,
+                                obox, box_stride, st, counters, smem_r);
+      return launch_rows_w<1>(nq, full, d, seg, X, x_stride, mask, mask_stride, occ, out, out_stride, Q, xbox,
+                              obox, box_stride, st, counters, smem_r);
+    }
   }
   const size_t smem = tile_smem_bytes(tc, seg.R);
   if (smem > 0 && seg.tab && seg.mask && !listed && Q >= 2 && mask_stride == 0 && tc.pair &&
@@ -2572,6 +3050,9 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_edge_masks_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kTileOccSmemMax);
+  if (e == cudaSuccess) e = set_rows_attributes<1>();
+  if (e == cudaSuccess) e = set_rows_attributes<2>();
+  if (e == cudaSuccess) e = set_rows_attributes<4>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);

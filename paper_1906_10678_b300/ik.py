@@ -35,6 +35,7 @@ IK_OPT_DILATE_R2 = 3
 IK_OPT_WORK_LIST = 4
 IK_OPT_QUERY_PAIRS = 5
 IK_OPT_TMA_MASKS = 6
+IK_OPT_ROW_LANES = 7
 IK_MAX_SEG = 16
 IK_MAX_LEN = 100
 

@@ -57,9 +57,10 @@ def test_tuner_cache_keys_and_missing_file(tmp_path):
     bad.write_text("{not json")
     assert tune.load(str(bad)) == {}
     k1 = tune._key((128, 128, 128), [20, 18], 64, 32)
-    assert k1 == "128x128x128|20,18|64|32|v2"
+    assert k1 == "128x128x128|20,18|64|32|v3"
     assert k1 != tune._key((128, 128, 128), [20, 18], 64, 16)
     good = tmp_path / "good.json"
-    good.write_text('{"%s": {"depth": 8, "pairs": 1, "tma": 0, "ms": {"depth8_pairs1_tma0": 1.0}}}' % k1)
+    good.write_text('{"%s": {"depth": 8, "pairs": 1, "rows": 1, "tma": 0, "ms": {"depth8_pairs1_rows1_tma0": 1.0}}}'
+                    % k1)
     got = tune.load(str(good))[k1]
-    assert got["depth"] == 8 and got["pairs"] == 1 and got["tma"] == 0
+    assert got["depth"] == 8 and got["pairs"] == 1 and got["rows"] == 1 and got["tma"] == 0
