@@ -1377,16 +1377,16 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
   constexpr unsigned kFull = 0xffffffffu;
   constexpr int TY = kRowTY, TZ = kRowTZ, NU = kRowUnits;
   constexpr int kB = NQ == 1 ? 8 : 4;  // offsets per batch
-  __shared__ int s_cnt[8];
+  __shared__ int s_cnt[8], s_next, s_plane[64];
   const int tile = qfast ? blockIdx.y : blockIdx.x;
   const int qa = NQ * (qfast ? blockIdx.x : blockIdx.y);
   const int y0 = (tile % tiles_y) * TY, z0 = (tile / tiles_y) * TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int R = seg.R, RY = TY + 2 * R;
   const int HW = (TZ + 2 * R) * RY * WX;  // words of one query's halo
-  uint32_t* acc_s = sr + NQ * HW;                          // [NU][NQ][WX]
+  uint32_t* acc_s = sr + NQ * HW;                          // [NQ][NU][WX]
   uint32_t* m_s = acc_s + NU * NQ * WX;                    // [NU][WX]
-  unsigned short* list = reinterpret_cast<unsigned short*>(m_s + NU * WX);  // [NU]
+  unsigned short* list = reinterpret_cast<unsigned short*>(m_s + NU * WX);  // [8][NU]: per warp
   // the queries' source boxes (an empty box for a missing query)
   int bx0[NQ], by0[NQ], bz0[NQ], bx1[NQ], by1[NQ], bz1[NQ];
   bool has[NQ], touch = false;
@@ -1469,7 +1469,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
       }
     const uint32_t zero[WX] = {};
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) row_st<WX>(acc_s + (threadIdx.x * NQ + q) * WX, zero);
+    for (int q = 0; q < NQ; ++q) row_st<WX>(acc_s + (q * NU + threadIdx.x) * WX, zero);
   }
   __syncthreads();
   unsigned long long visited = 0, nonzero = 0, mloads = 0, warp_iters = 0, passes = 0, pass_lanes = 0;
@@ -1477,153 +1477,222 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
   const int mx0 = kFullBox ? 0 : seg.mbox.wx0;
   const unsigned mstr = (unsigned)seg.mbox.words();
   const int EZ0 = max(uz0 - (z0 + TZ - 1), -R), EZ1 = min(uz1 - z0, R);
-  for (int ez = EZ0; ez <= EZ1; ++ez) {
-    // pack the units that can gain bits in this plane
-    bool act = false;
-    {
-      uint32_t m[WX];
-      row_lds<WX>(m_s + threadIdx.x * WX, m);
+  // One pass of a warp: the units lst[p .. p + 31] (of n_act) over plane
+  // ez.  merge: other warps may add to the same units meanwhile (their
+  // accumulators are OR-merged into shared memory); else the units are this
+  // pass's alone.
+  auto do_pass = [&](int ez, const unsigned short* lst, int n_act, int p, bool merge) {
+    const bool hasu = p + lane < n_act;
+    const int t = hasu ? lst[p + lane] : 0;
+    const int zu = z0 + t / 32, yu = y0 + t % 32;
+    uint32_t acc[NQ][WX], acc0[NQ][WX], m[WX];
+    row_lds<WX>(m_s + t * WX, m);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        uint32_t a[WX];
-        row_lds<WX>(acc_s + (threadIdx.x * NQ + q) * WX, a);
-        bool open = false;
+    for (int q = 0; q < NQ; ++q) {
+      row_lds<WX>(acc_s + (q * NU + t) * WX, acc[q]);
 #pragma unroll
-        for (int i = 0; i < WX; ++i) open = open || (a[i] & m[i]) != m[i];
-        act = act || (open && zt + ez >= bz0[q] && zt + ez <= bz1[q]);
+      for (int i = 0; i < WX; ++i) acc0[q][i] = acc[q][i];
+    }
+    if (!hasu)
+#pragma unroll
+      for (int i = 0; i < WX; ++i) m[i] = 0u;
+    // the pass's union of the lanes' dy ranges
+    const int ey0 = __reduce_min_sync(kFull, hasu ? max(uy0 - yu, -R) : 0x7fffffff);
+    const int ey1 = __reduce_max_sync(kFull, hasu ? min(uy1 - yu, R) : -0x7fffffff);
+    const uint32_t* hz = sr + ((zu - z0 + R + ez) * RY + (yu - y0 + R)) * WX;
+    const uint32_t* mrow = seg.mask + (hasu ? seg.mbox.index(mx0, yu, zu) : 0);
+    // words still open at the pass's start (work counters only)
+    unsigned lw = 0;
+    if (kCount) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int i = 0; i < WX; ++i) lw |= (unsigned)((acc[q][i] & m[i]) != m[i]) << (q * WX + i);
+      if (lane == 0) {
+        ++passes;
+        pass_lanes += (unsigned long long)min(32, n_act - p);
       }
     }
-    const unsigned bal = __ballot_sync(kFull, act);
-    if (lane == 0) s_cnt[warp] = __popc(bal);
-    __syncthreads();
-    int n_act = 0, pos = __popc(bal & ((1u << lane) - 1u));
+    // hz32: the lane's row at dy = -32 (the table stores dy + 32)
+    const uint32_t* hz32 = hz - 32 * WX;
+    // NB offsets from e on, all shifting the same way
+    auto batch = [&](auto neg_tag, auto nb_tag, int e) {
+      constexpr bool kNeg = decltype(neg_tag)::value;
+      constexpr int NB = decltype(nb_tag)::value;
+      uint32_t x[NB][NQ][WX];
+      int32_t tb[NB];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      n_act += s_cnt[c];
-      pos += c < warp ? s_cnt[c] : 0;
-    }
-    if (act) list[pos] = (unsigned short)threadIdx.x;
-    __syncthreads();
-    for (int p = warp * 32; p < n_act; p += 256) {
-      const bool hasu = p + lane < n_act;
-      const int t = hasu ? list[p + lane] : 0;
-      const int zu = z0 + t / 32, yu = y0 + t % 32;
-      uint32_t acc[NQ][WX], m[WX];
-      row_lds<WX>(m_s + t * WX, m);
+      for (int b = 0; b < NB; ++b) {
+        tb[b] = __ldg(seg.tabr + e + b);
+        const uint32_t* p2 = hz32 + ((tb[b] >> 5) & 63) * WX;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) row_lds<WX>(acc_s + (t * NQ + q) * WX, acc[q]);
-      if (!hasu)
+        for (int q = 0; q < NQ; ++q) {
+          uint32_t v[WX];
+          row_lds<WX>(p2 + q * HW, v);
+          row_shift<WX, kNeg>(v, tb[b] & 31, x[b][q]);
+        }
+      }
+      uint32_t want[NQ][WX];
 #pragma unroll
-        for (int i = 0; i < WX; ++i) m[i] = 0u;
-      // the pass's union of the lanes' dy ranges
-      const int ey0 = __reduce_min_sync(kFull, hasu ? max(uy0 - yu, -R) : 0x7fffffff);
-      const int ey1 = __reduce_max_sync(kFull, hasu ? min(uy1 - yu, R) : -0x7fffffff);
-      const uint32_t* hz = sr + ((zu - z0 + R + ez) * RY + (yu - y0 + R)) * WX;
-      const uint32_t* mrow = seg.mask + (hasu ? seg.mbox.index(mx0, yu, zu) : 0);
-      // words still open at the pass's start (work counters only)
-      unsigned lw = 0;
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int i = 0; i < WX; ++i) want[q][i] = m[i] & ~acc[q][i];
+      // need[b][i]: the bits offset b could add to word i of some query;
+      // with masks over whole rows only their union decides the load
+      constexpr int NW = kFullBox ? 1 : WX;
+      uint32_t need[NB][NW], any = 0u;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) need[b][j] = 0u;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int i = 0; i < WX; ++i) need[b][kFullBox ? 0 : i] |= x[b][q][i] & want[q][i];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) any |= need[b][j];
+      }
       if (kCount) {
+        visited += (unsigned long long)NB * __popc(lw);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-          for (int i = 0; i < WX; ++i) lw |= (unsigned)((acc[q][i] & m[i]) != m[i]) << (q * WX + i);
-        if (lane == 0) {
-          ++passes;
-          pass_lanes += (unsigned long long)min(32, n_act - p);
-        }
-      }
-      // hz32: the lane's row at dy = -32 (the table stores dy + 32)
-      const uint32_t* hz32 = hz - 32 * WX;
-      // NB offsets from e on, all shifting the same way
-      auto batch = [&](auto neg_tag, auto nb_tag, int e) {
-        constexpr bool kNeg = decltype(neg_tag)::value;
-        constexpr int NB = decltype(nb_tag)::value;
-        uint32_t x[NB][NQ][WX];
-        int32_t tb[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          tb[b] = __ldg(seg.tabr + e + b);
-          const uint32_t* p2 = hz32 + ((tb[b] >> 5) & 63) * WX;
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) {
-            uint32_t v[WX];
-            row_lds<WX>(p2 + q * HW, v);
-            row_shift<WX, kNeg>(v, tb[b] & 31, x[b][q]);
-          }
-        }
-        uint32_t want[NQ][WX];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-          for (int i = 0; i < WX; ++i) want[q][i] = m[i] & ~acc[q][i];
-        // need[b][i]: the bits offset b could add to word i of some query;
-        // with masks over whole rows only their union decides the load
-        constexpr int NW = kFullBox ? 1 : WX;
-        uint32_t need[NB][NW], any = 0u;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-#pragma unroll
-          for (int j = 0; j < NW; ++j) need[b][j] = 0u;
+        for (int b = 0; b < NB; ++b)
 #pragma unroll
           for (int q = 0; q < NQ; ++q)
 #pragma unroll
-            for (int i = 0; i < WX; ++i) need[b][kFullBox ? 0 : i] |= x[b][q][i] & want[q][i];
+            for (int i = 0; i < WX; ++i) nonzero += ((lw >> (q * WX + i)) & 1u) && x[b][q][i] != 0u;
+      }
+      if (any) {
+        uint32_t mv[NB][WX];
 #pragma unroll
-          for (int j = 0; j < NW; ++j) any |= need[b][j];
-        }
-        if (kCount) {
-          visited += (unsigned long long)NB * __popc(lw);
-#pragma unroll
-          for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-#pragma unroll
-              for (int i = 0; i < WX; ++i) nonzero += ((lw >> (q * WX + i)) & 1u) && x[b][q][i] != 0u;
-        }
-        if (any) {
-          uint32_t mv[NB][WX];
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const uint32_t* mp = mrow + (size_t)((unsigned)tb[b] >> 11) * mstr;
-            if (kFullBox) {
-              if (need[b][0]) {
-                row_ldg<WX>(mp, mv[b]);
-                if (kCount) mloads += WX;
-              } else {
-#pragma unroll
-                for (int i = 0; i < WX; ++i) mv[b][i] = 0u;
-              }
+        for (int b = 0; b < NB; ++b) {
+          const uint32_t* mp = mrow + (size_t)((unsigned)tb[b] >> 11) * mstr;
+          if (kFullBox) {
+            if (need[b][0]) {
+              row_ldg<WX>(mp, mv[b]);
+              if (kCount) mloads += WX;
             } else {
 #pragma unroll
-              for (int i = 0; i < WX; ++i) {
-                mv[b][i] = need[b][kFullBox ? 0 : i] ? __ldg(mp + (i - mx0)) : 0u;
-                if (kCount) mloads += need[b][kFullBox ? 0 : i] != 0u;
-              }
+              for (int i = 0; i < WX; ++i) mv[b][i] = 0u;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < WX; ++i) {
+              mv[b][i] = need[b][kFullBox ? 0 : i] ? __ldg(mp + (i - mx0)) : 0u;
+              if (kCount) mloads += need[b][kFullBox ? 0 : i] != 0u;
             }
           }
-#pragma unroll
-          for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-#pragma unroll
-              for (int i = 0; i < WX; ++i) acc[q][i] |= x[b][q][i] & mv[b][i];
         }
-      };
-      auto run = [&](auto neg_tag, int e, int e1) {
-        for (; e + kB <= e1; e += kB) batch(neg_tag, std::integral_constant<int, kB>{}, e);
-        for (; e < e1; ++e) batch(neg_tag, std::integral_constant<int, 1>{}, e);
-      };
-      if (ey0 <= ey1) {
-        const int32_t* rs = seg.rowsr + (ez + R) * 2 * side + R;
-        const int n0 = __ldg(rs + ey0), n1 = __ldg(rs + ey1 + 1);
-        const int p0 = __ldg(rs + side + ey0), p1 = __ldg(rs + side + ey1 + 1);
-        if (kCount && lane == 0) warp_iters += (unsigned long long)(n1 - n0 + p1 - p0);
-        run(std::true_type{}, n0, n1);
-        run(std::false_type{}, p0, p1);
-      }
-      if (hasu)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) row_st<WX>(acc_s + (t * NQ + q) * WX, acc[q]);
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int i = 0; i < WX; ++i) acc[q][i] |= x[b][q][i] & mv[b][i];
+      }
+    };
+    auto run = [&](auto neg_tag, int e, int e1) {
+      for (; e + kB <= e1; e += kB) batch(neg_tag, std::integral_constant<int, kB>{}, e);
+      for (; e < e1; ++e) batch(neg_tag, std::integral_constant<int, 1>{}, e);
+    };
+    if (ey0 <= ey1) {
+      const int32_t* rs = seg.rowsr + (ez + R) * 2 * side + R;
+      const int n0 = __ldg(rs + ey0), n1 = __ldg(rs + ey1 + 1);
+      const int p0 = __ldg(rs + side + ey0), p1 = __ldg(rs + side + ey1 + 1);
+      if (kCount && lane == 0) warp_iters += (unsigned long long)(n1 - n0 + p1 - p0);
+      run(std::true_type{}, n0, n1);
+      run(std::false_type{}, p0, p1);
+    }
+    if (hasu) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        if (merge) {
+#pragma unroll
+          for (int i = 0; i < WX; ++i)
+            if (acc[q][i] & ~acc0[q][i]) atomicOr(acc_s + (q * NU + t) * WX + i, acc[q][i]);
+        } else {
+          row_st<WX>(acc_s + (q * NU + t) * WX, acc[q]);
+        }
+      }
+    }
+  };
+  if (kCount) {
+    // the work counters count in plane order: the block takes each plane
+    // together (warps split its open units), with barriers between planes
+    for (int ez = EZ0; ez <= EZ1; ++ez) {
+      bool act = false;
+      {
+        uint32_t m[WX];
+        row_lds<WX>(m_s + threadIdx.x * WX, m);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          uint32_t a[WX];
+          row_lds<WX>(acc_s + (q * NU + threadIdx.x) * WX, a);
+          bool open = false;
+#pragma unroll
+          for (int i = 0; i < WX; ++i) open = open || (a[i] & m[i]) != m[i];
+          act = act || (open && zt + ez >= bz0[q] && zt + ez <= bz1[q]);
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, act);
+      if (lane == 0) s_cnt[warp] = __popc(bal);
+      __syncthreads();
+      int n_act = 0, pos = __popc(bal & ((1u << lane) - 1u));
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        n_act += s_cnt[c];
+        pos += c < warp ? s_cnt[c] : 0;
+      }
+      if (act) list[pos] = (unsigned short)threadIdx.x;
+      __syncthreads();
+      for (int p = warp * 32; p < n_act; p += 256) do_pass(ez, list, n_act, p, false);
+      __syncthreads();
+    }
+  } else {
+    // Warps take whole planes from a counter, the larger ones (nearest
+    // dz = 0) first, and each lists the units open for its plane: no block
+    // barrier between planes.  A unit's accumulator may lag bits that
+    // another warp is adding in another plane; it only gates loads, and the
+    // OR of all planes is the same in any order.
+    const int n_planes = EZ1 - EZ0 + 1;
+    if (threadIdx.x == 0) {
+      s_next = 0;
+      const int c = min(max(0, EZ0), EZ1);
+      int n = 0;
+      for (int k = 0; n < n_planes; ++k) {
+        if (c + k <= EZ1) s_plane[n++] = c + k;
+        if (k > 0 && c - k >= EZ0) s_plane[n++] = c - k;
+      }
+    }
+    __syncthreads();
+    unsigned short* wl = list + warp * NU;
+    for (;;) {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(&s_next, 1);
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= n_planes) break;
+      const int ez = s_plane[i];
+      int n_act = 0;
+      for (int c = 0; c < TZ; ++c) {
+        const int t = c * 32 + lane;
+        bool act = false;
+        uint32_t m[WX];
+        row_lds<WX>(m_s + t * WX, m);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          uint32_t a[WX];
+          row_lds<WX>(acc_s + (q * NU + t) * WX, a);
+          bool open = false;
+#pragma unroll
+          for (int k = 0; k < WX; ++k) open = open || (a[k] & m[k]) != m[k];
+          act = act || (open && z0 + c + ez >= bz0[q] && z0 + c + ez <= bz1[q]);
+        }
+        const unsigned bal = __ballot_sync(kFull, act);
+        if (act) wl[n_act + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)t;
+        n_act += __popc(bal);
+      }
+      __syncwarp();
+      for (int p = 0; p < n_act; p += 32) do_pass(ez, wl, n_act, p, true);
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -1634,7 +1703,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
   for (int q = 0; q < NQ; ++q) {
     if (!has[q]) continue;
     uint32_t acc[WX];
-    row_lds<WX>(acc_s + (threadIdx.x * NQ + q) * WX, acc);
+    row_lds<WX>(acc_s + (q * NU + threadIdx.x) * WX, acc);
     int lo = WX, hi = -1;
 #pragma unroll
     for (int i = 0; i < WX; ++i) {
@@ -1687,7 +1756,7 @@ size_t rows_smem_bytes(int wx, int R, int nq) {
   if (R > 31 || (wx != 1 && wx != 2 && wx != 4)) return 0;
   // the halos, the units' accumulators and output masks, the unit list
   const size_t bytes = (size_t)nq * (kRowTZ + 2 * R) * (kRowTY + 2 * R) * wx * 4 +
-                       (size_t)(nq + 1) * kRowUnits * wx * 4 + (size_t)kRowUnits * 2;
+                       (size_t)(nq + 1) * kRowUnits * wx * 4 + (size_t)8 * kRowUnits * 2;
   return bytes <= (size_t)kTileOccSmemMax ? bytes : 0;
 }
 
