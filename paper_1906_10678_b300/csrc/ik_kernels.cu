@@ -2637,10 +2637,22 @@ __device__ __forceinline__ OccBox word_box(const Box& a, const Box& b, uint32_t*
   return ob;
 }
 
+// The offset table and row starts a level's restricted words read: the
+// segment's own (global memory), or, with stored edge masks (the occupancy
+// buffer then free), the planes the level can use staged in shared memory,
+// so that the walk's table reads do not go to L2 behind the mask loads.
+// off[e] and rows[r] are valid for the staged e and r (plain loads).
+struct ChainTab {
+  const int32_t* off;
+  const int32_t* rows;
+};
+
 // Stages, for one level, the occupancy of the hull of boxes a and b and the
-// source set `src` (written earlier in this kernel: plain loads) over box sb.
+// source set `src` (written earlier in this kernel: plain loads) over box sb;
+// with tab, the table (see ChainTab) for outputs in a and sources in sb.
 __device__ void chain_stage(const Dims& d, const SegDev& sg, const Box& a, const Box& b, const Box& sb,
-                            const uint32_t* src, uint32_t* so, OccBox* ob, OccBox* xb) {
+                            const uint32_t* src, uint32_t* so, OccBox* ob, OccBox* xb,
+                            ChainTab* tab = nullptr) {
   int nz_o, nz_x;
   long tot_o, tot_x;
   // with stored edge masks one mask word per test beats a walk: no occupancy
@@ -2659,6 +2671,24 @@ __device__ void chain_stage(const Dims& d, const SegDev& sg, const Box& a, const
     for (int t = threadIdx.x; t < tot_x; t += blockDim.x) {
       const int ww = xb->w0 + t % xb->nw, yy = xb->y0 + (t / xb->nw) % xb->ny, zz = xb->z0 + t / (xb->nw * xb->ny);
       s[t] = (ww >= 0 && ww < d.wx) ? src[((long)zz * d.ny + yy) * d.wx + ww] : 0u;
+    }
+  }
+  if (tab) {
+    tab->off = sg.off;
+    tab->rows = sg.rows;
+    const int R = sg.R, side = 2 * R + 1;
+    const int pz0 = max(sb.z0 - a.z1, -R), pz1 = min(sb.z1 - a.z0, R);
+    if (sg.mask && !ob->ok && pz0 <= pz1) {
+      // rows of planes pz0 .. pz1 (and the end of the last), their offsets
+      const int r0 = (pz0 + R) * side, nr = (pz1 - pz0 + 1) * side + 1;
+      const int e0 = __ldg(sg.rows + r0), ne = __ldg(sg.rows + r0 + nr - 1) - e0;
+      if (nr + ne <= kChainOccWords) {
+        int32_t* s = reinterpret_cast<int32_t*>(so);
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) s[t] = __ldg(sg.rows + r0 + t);
+        for (int t = threadIdx.x; t < ne; t += blockDim.x) s[nr + t] = __ldg(sg.off + e0 + t);
+        tab->rows = s - r0;
+        tab->off = s + nr - e0;
+      }
     }
   }
   __syncthreads();
@@ -2702,9 +2732,9 @@ __device__ __forceinline__ uint32_t edge_word_box(const Dims& d, const SegDev& s
 // the group must call it (idle lanes pass m = 0).
 constexpr int kG = 8;
 
-__device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const OccBox& ob,
-                                                    const OccBox& xb, const uint32_t* src, const Box& sb,
-                                                    int wx, int y, int z, long w, uint32_t m,
+__device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev& sg, const ChainTab& tab,
+                                                    const OccBox& ob, const OccBox& xb, const uint32_t* src,
+                                                    const Box& sb, int wx, int y, int z, long w, uint32_t m,
                                                     unsigned long long* cnt) {
   const int g = threadIdx.x % kG;
   const unsigned gmask = ((1u << kG) - 1u) << ((threadIdx.x & 31) & ~(kG - 1));
@@ -2717,7 +2747,7 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
     const int exlo = sb.x0 - 32 * wx - 31, exhi = sb.x1 - 32 * wx;
     // the source word of an offset (0 when its voxels cannot lie in sb)
     auto source = [&](int e, int ez) -> uint32_t {
-      const int32_t o = __ldg(sg.off + e);
+      const int32_t o = tab.off[e];
       const int ex = unpack_x(o);
       if (ex < exlo || ex > exhi) return 0u;
       if (xb.ok) {
@@ -2728,9 +2758,9 @@ __device__ __forceinline__ uint32_t restricted_word(const Dims& d, const SegDev&
       return ld_shifted_rw(src, d, wx, y, z, ex, unpack_y(o), ez);
     };
     for (int ez = ez0; ez <= ez1 && ey0 <= ey1; ++ez) {
-      const int32_t* rowp = sg.rows + (ez + R) * side + R;
-      const int e1 = __ldg(rowp + ey1 + 1);
-      for (int e = __ldg(rowp + ey0) + g; e < e1; e += kG) {
+      const int32_t* rowp = tab.rows + (ez + R) * side + R;
+      const int e1 = rowp[ey1 + 1];
+      for (int e = rowp[ey0] + g; e < e1; e += kG) {
         const uint32_t x = source(e, ez);
         if (cnt) {
           ++visited;
@@ -2765,7 +2795,8 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
     uint32_t* dst = R + (long)k * d.nw;
     const long n = box_words(b);
     OccBox ob, xb;
-    chain_stage(d, sg, b, sb, sb, src, so, &ob, &xb);
+    ChainTab tab;
+    chain_stage(d, sg, b, sb, sb, src, so, &ob, &xb, &tab);
     int any = 0;
     // kG lanes per word; the loop bound is uniform per lane group
     for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
@@ -2778,7 +2809,7 @@ __device__ bool chain_forward(const Dims& d, const ArmDev& arm, ChainShared& sh,
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = (sh.r2[k] >= 0 ? ball_bits(wx, y, z, sh.ref[k], sh.r2[k]) : 0xffffffffu) & __ldg(Vk + w);
       }
-      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m, sh.cnt);
+      const uint32_t acc = restricted_word(d, sg, tab, ob, xb, src, sb, wx, y, z, w, m, sh.cnt);
       if (acc && threadIdx.x % kG == 0) {
         dst[w] = acc;
         any = 1;
@@ -2812,7 +2843,8 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
     uint32_t* dst = U + (long)k * d.nw;
     const long n = box_words(b);
     OccBox ob, xb;
-    chain_stage(d, sg, b, sb, sb, src, so, &ob, &xb);
+    ChainTab tab;
+    chain_stage(d, sg, b, sb, sb, src, so, &ob, &xb, &tab);
     for (long t0 = 0; t0 < n; t0 += blockDim.x / kG) {
       const long t = t0 + threadIdx.x / kG;
       int wx = 0, y = 0, z = 0;
@@ -2823,7 +2855,7 @@ __device__ void chain_backward(const Dims& d, const ArmDev& arm, ChainShared& sh
         w = ((long)z * d.ny + y) * d.wx + wx;
         m = Rk[w];
       }
-      const uint32_t acc = restricted_word(d, sg, ob, xb, src, sb, wx, y, z, w, m, sh.cnt);
+      const uint32_t acc = restricted_word(d, sg, tab, ob, xb, src, sb, wx, y, z, w, m, sh.cnt);
       if (acc && threadIdx.x % kG == 0) dst[w] = acc;
     }
     __syncthreads();
