@@ -38,10 +38,7 @@ def ik():
 
 
 def _load(name):
-    path = os.path.join(GOLDEN, name)
-    if not os.path.exists(path):
-        pytest.skip(f"{name} not written yet (tests/golden/make_full_size.py)")
-    return dict(np.load(path))
+    return dict(np.load(os.path.join(GOLDEN, name)))
 
 
 def test_c3_batch_reach_and_paths_exact(ik):
