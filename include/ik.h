@@ -454,6 +454,11 @@ IK_API int ik_batch_engine_set_budget(ik_batch_engine e, size_t pool_bytes);
  * item completing anywhere before it gives up: its blocks then stop taking
  * items and the unfinished problems report IK_ERR_TIMEOUT in job_rc. */
 IK_API int ik_batch_engine_set_timeout(ik_batch_engine e, int64_t ns);
+/* on = 1 (default): on the waypoint levels whose tiles leave room for a
+ * third halo in shared memory, a work item carries two waypoint queries of
+ * a problem, which share each segment test's supercover walk; 0: one query
+ * per item.  Results are identical. */
+IK_API int ik_batch_engine_set_pairs(ik_batch_engine e, int on);
 
 /* Solve n uneven problems (the systems pattern of batching, no paper
  * counterpart; every problem follows exactly the rules of ik_solve_reach +

@@ -135,6 +135,8 @@ struct ik_batch_engine_s {
   cudaEvent_t staged = nullptr;  // the last upload out of `pinned` is done
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   long long timeout_ns = 20LL * 1000 * 1000 * 1000;
+  int pairs = 1;          // ik_batch_engine_set_pairs
+  size_t smem_limit = 0;  // batch_smem_limit() of the device, at the first plan
 
   ~ik_batch_engine_s() {
     int prev = 0;
@@ -266,6 +268,7 @@ bool batch_tiling(const Dims& d, int R, TileCfg* out) {
 
 int plan_problems(ik_batch_engine_s* E, const ik_problem* probs, int n, std::vector<ProbPlan>* plans) {
   plans->resize(n);
+  if (!E->smem_limit) E->smem_limit = batch_smem_limit();
   size_t r = 0, p = 0, x = 0, b = 0;
   for (int i = 0; i < n; ++i) {
     const ik_problem& pr = probs[i];
@@ -288,8 +291,11 @@ int plan_problems(ik_batch_engine_s* E, const ik_problem* probs, int n, std::vec
       if (s->host.R > 31) return IK_ERR_UNSUPPORTED;  // the tiled bodies' x halo is one word
       TileCfg tc;
       if (!batch_tiling(pl.d, s->host.R, &tc)) return IK_ERR_UNSUPPORTED;
+      // the level's waypoint queries in pairs (one more halo) where it fits
+      const size_t occ_bytes = tile_occ_smem_bytes(tc, s->host.R), pair_bytes = 3 * (occ_bytes / 2);
+      tc.pair = E->pairs && pr.n_way >= 2 && pair_bytes <= E->smem_limit ? 1 : 0;
       pl.tcs[k] = tc;
-      pl.smem = std::max(pl.smem, tile_occ_smem_bytes(tc, s->host.R));
+      pl.smem = std::max(pl.smem, tc.pair ? pair_bytes : occ_bytes);
       int32_t *tab = nullptr, *sctab = nullptr;
       if ((rc = E->tables(s, tc, &tab, &sctab))) return rc;
       SegDev& sd = pl.arm.seg[k];
@@ -511,6 +517,13 @@ int ik_batch_engine_set_timeout(ik_batch_engine e, int64_t ns) {
   if (!e || ns < 1000) return IK_ERR_ARG;
   std::lock_guard<std::mutex> lock(e->mu);
   e->timeout_ns = ns;
+  return IK_OK;
+}
+
+int ik_batch_engine_set_pairs(ik_batch_engine e, int on) {
+  if (!e || (on != 0 && on != 1)) return IK_ERR_ARG;
+  std::lock_guard<std::mutex> lock(e->mu);
+  e->pairs = on;
   return IK_OK;
 }
 

@@ -181,13 +181,29 @@ __device__ void batch_advance(const BatchProb& P, int i, const BatchQueue& q) {
       mb = P.Fbox + 6 * (k - 1);
       R = P.arm.seg[k - 1].R;
     }
+    // waypoint levels whose tiling allows it take the queries in pairs
+    // (items (tile, pair): the union of both queries' tile ranges)
+    const bool pairs = kind == BK_WPROP && tc.pair;
+    auto range = [&](int qq, int* ty0, int* ty1, int* tz0, int* tz1) {
+      if (!pairs) return batch_tile_range(P.d, tc, R, xb0 + qq * qbs, mb, ty0, ty1, tz0, tz1);
+      int a0, a1, b0, b1, c0 = 0, c1 = -1, e0 = 0, e1 = -1;
+      const int ca = batch_tile_range(P.d, tc, R, xb0 + 2 * qq * qbs, mb, &a0, &a1, &b0, &b1);
+      const int cb = 2 * qq + 1 < W ? batch_tile_range(P.d, tc, R, xb0 + (2 * qq + 1) * qbs, mb, &c0, &c1, &e0, &e1)
+                                    : 0;
+      if (!ca && !cb) return 0;
+      if (!ca) a0 = c0, a1 = c1, b0 = e0, b1 = e1;
+      else if (cb) a0 = min(a0, c0), a1 = max(a1, c1), b0 = min(b0, e0), b1 = max(b1, e1);
+      *ty0 = a0, *ty1 = a1, *tz0 = b0, *tz1 = b1;
+      return (a1 - a0 + 1) * (b1 - b0 + 1);
+    };
+    if (pairs) Q = (W + 1) / 2;
     int total = 0;
     if (xb0) {
       // one query per thread and pass; items in query order
       for (int q0 = 0; q0 < Q; q0 += blockDim.x) {
         const int qq = q0 + threadIdx.x;
         int ty0, ty1, tz0, tz1, c = 0;
-        if (qq < Q) c = batch_tile_range(P.d, tc, R, xb0 + qq * qbs, mb, &ty0, &ty1, &tz0, &tz1);
+        if (qq < Q) c = range(qq, &ty0, &ty1, &tz0, &tz1);
         int part = 0;
         batch_scan(c, warp_sum, &part);
         total += part;
@@ -220,7 +236,7 @@ __device__ void batch_advance(const BatchProb& P, int i, const BatchQueue& q) {
       for (int q0 = 0; q0 < Q; q0 += blockDim.x) {
         const int qq = q0 + threadIdx.x;
         int ty0 = 0, ty1 = -1, tz0 = 0, tz1 = -1, c = 0;
-        if (qq < Q) c = batch_tile_range(P.d, tc, R, xb0 + qq * qbs, mb, &ty0, &ty1, &tz0, &tz1);
+        if (qq < Q) c = range(qq, &ty0, &ty1, &tz0, &tz1);
         int part = 0;
         const int off = batch_scan(c, warp_sum, &part);
         long long n = 0;
@@ -391,9 +407,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_persistent(const Bat
         const SegDev seg = P.arm.seg[k - 1];
         const TileCfg tc = P.tcs[k - 1];
         const long qs = (long)(S + 1) * d.nw;
-        propagate_tile_body<false, true, true>(d, seg, tc, P.Vw + (long)k * d.nw, qs, P.F + (long)(k - 1) * d.nw,
-                                              0, P.occ, P.Vw + (long)(k - 1) * d.nw, qs, P.Vwbox + 6 * k,
-                                              P.Vwbox + 6 * (k - 1), 6L * (S + 1), nullptr, it.w, it.z);
+        if (tc.pair)  // it.w: a pair of waypoint queries sharing the supercover walks
+          propagate_pair_body<false, false, true, true>(d, seg, tc, P.Vw + (long)k * d.nw, qs,
+                                                        P.F + (long)(k - 1) * d.nw, P.occ,
+                                                        P.Vw + (long)(k - 1) * d.nw, qs, P.W, P.Vwbox + 6 * k,
+                                                        P.Vwbox + 6 * (k - 1), 6L * (S + 1), nullptr, it.z, it.w);
+        else
+          propagate_tile_body<false, true, true>(d, seg, tc, P.Vw + (long)k * d.nw, qs, P.F + (long)(k - 1) * d.nw,
+                                                0, P.occ, P.Vw + (long)(k - 1) * d.nw, qs, P.Vwbox + 6 * k,
+                                                P.Vwbox + 6 * (k - 1), 6L * (S + 1), nullptr, it.w, it.z);
         break;
       }
       case BK_CHAIN:

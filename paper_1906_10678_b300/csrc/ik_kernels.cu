@@ -856,15 +856,18 @@ __global__ void __launch_bounds__(256, 3) k_propagate_tile_occ_list(Dims d, SegD
 // take bits from it.  The walk covers the union of the two queries' ranges
 // (a query's staged words outside its own box are zero).  Stored edge masks
 // only; results equal two one-query blocks.
-template <bool kCount, bool kWrap>
-__global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg, TileCfg tc,
-                                                             const uint32_t* __restrict__ X, long xs,
-                                                             const uint32_t* __restrict__ mask,
-                                                             const uint32_t* __restrict__ occ,
-                                                             uint32_t* __restrict__ out, long os, int Q,
-                                                             const int32_t* __restrict__ xbox,
-                                                             int32_t* __restrict__ obox, long bs,
-                                                             unsigned long long* __restrict__ counters) {
+// kCoh: the boxes were written earlier in the same kernel (the persistent
+// batch), read with coherent loads.
+template <bool kCount, bool kWrap, bool kOcc, bool kCoh>
+__device__ __forceinline__ void propagate_pair_body(const Dims& d, const SegDev& seg, const TileCfg& tc,
+                                                    const uint32_t* __restrict__ X, long xs,
+                                                    const uint32_t* __restrict__ mask,
+                                                    const uint32_t* __restrict__ occ,
+                                                    uint32_t* __restrict__ out, long os, int Q,
+                                                    const int32_t* __restrict__ xbox,
+                                                    int32_t* __restrict__ obox, long bs,
+                                                    unsigned long long* __restrict__ counters, int tile,
+                                                    int pair) {
   extern __shared__ uint2 s2_raw[];
   // kWrap: rows staged at pitch wx without pad words (conflict-free 64-bit
   // loads: a half warp reads 16 consecutive words), one spare word at both
@@ -872,8 +875,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
   // belong to the neighbouring row and are masked off below
   uint2* s2 = kWrap ? s2_raw + 1 : s2_raw;
   constexpr unsigned kFull = 0xffffffffu;
-  const int tile = blockIdx.x;
-  const int q0 = 2 * blockIdx.y, q1 = q0 + 1;
+  const int q0 = 2 * pair, q1 = q0 + 1;
   const bool has1 = q1 < Q;
   const int y0 = (tile % tc.tiles_y) * tc.TY, z0 = (tile / tc.tiles_y) * tc.TZ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -885,8 +887,8 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
   int b0[6], b1[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    b0[i] = __ldg(xbox + q0 * bs + i);
-    b1[i] = has1 ? __ldg(xbox + q1 * bs + i) : 0x7f7f7f7f;
+    b0[i] = ld_box<kCoh>(xbox + q0 * bs + i);
+    b1[i] = has1 ? ld_box<kCoh>(xbox + q1 * bs + i) : 0x7f7f7f7f;
   }
   const int ax0 = b0[0], ay0 = b0[1], az0 = b0[2], ax1 = -b0[3], ay1 = -b0[4], az1 = -b0[5];
   const int cx0 = b1[0], cy0 = b1[1], cz0 = b1[2], cx1 = -b1[3], cy1 = -b1[4], cz1 = -b1[5];
@@ -896,7 +898,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
   const bool t0 = touches(ax0, ay0, az0, ax1, ay1, az1), t1 = touches(cx0, cy0, cz0, cx1, cy1, cz1);
   uint32_t m = 0;
   if (valid) m = (mask ? __ldg(mask + w) : 0xffffffffu) & ~__ldg(occ + w);
-  const uint32_t* mrow = valid ? seg.mask + seg.mbox.index(wx, y, z) : nullptr;
+  const uint32_t* mrow = (!kOcc && valid) ? seg.mask + seg.mbox.index(wx, y, z) : nullptr;
   const long mstr = seg.mbox.words();
   if (!__syncthreads_or((t0 || t1) && m != 0)) {
     if (valid) {
@@ -927,6 +929,28 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
         if (sw >= cx0 && sw <= cx1 && sy >= cy0 && sy <= cy1 && sz >= cz0 && sz <= cz1)
           v.y = __ldg(X + q1 * xs + row);
         s2[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
+      }
+    }
+  }
+  // kOcc (no stored edge masks): the occupancy halo after the pair halo,
+  // same rows and pitch, one word per position; each edge test walks the
+  // offset's supercover there, once for both queries.  A supercover voxel
+  // lies between the output voxel and its source, so only the rows between
+  // the tile and the union box are staged (zero outside the grid).
+  uint32_t* so = reinterpret_cast<uint32_t*>(s2 + (tc.TZ + 2 * R) * RY * P);
+  if (kOcc) {
+    const int oz0 = max(z0 - R, min(z0, uz0)), oz1 = min(z0 + tc.TZ - 1 + R, max(z0 + tc.TZ - 1, uz1));
+    const int oy0 = max(y0 - R, min(y0, uy0)), oy1 = min(y0 + tc.TY - 1 + R, max(y0 + tc.TY - 1, uy1));
+    const int ny_rows = oy1 - oy0 + 1, n_rows = (oz1 - oz0 + 1) * ny_rows;
+    const int per_pass = 32 / P, nwarps = blockDim.x >> 5;
+    const int sub = lane / P, c = lane % P, sw = c - 1;
+    if (ny_rows > 0 && sub < per_pass) {
+      for (int r = warp * per_pass + sub; r < n_rows; r += nwarps * per_pass) {
+        const int sy = oy0 + r % ny_rows, sz = oz0 + r / ny_rows;
+        uint32_t v = 0u;
+        if (sw >= 0 && sw < d.wx && sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz)
+          v = __ldg(seg.occ + ((long)sz * d.ny + sy) * d.wx + sw);
+        so[((sz - z0 + R) * RY + (sy - y0 + R)) * P + c] = v;
       }
     }
   }
@@ -978,7 +1002,19 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
           }
           visited += 8 * ((int)live0 + (int)live1);
         }
-        if (any) {
+        if (any && kOcc) {
+          // supercover walks one at a time, each skipped once both
+          // accumulators hold the bits it could add
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if ((xa[i] & m & ~acc0) | (xb[i] & m & ~acc1)) {
+              if (kCount) ++mloads;
+              const uint32_t f = edge_word_tile(seg, e + i, so, base);
+              acc0 |= xa[i] & f;
+              acc1 |= xb[i] & f;
+            }
+          }
+        } else if (any) {
           uint32_t mv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i)
@@ -1010,7 +1046,7 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
         const uint32_t need = (x0 & m & ~acc0) | (x1 & m & ~acc1);
         if (need) {
           if (kCount) ++mloads;
-          const uint32_t mv = __ldg(mrow + (long)e * mstr);
+          const uint32_t mv = kOcc ? edge_word_tile(seg, e, so, base) : __ldg(mrow + (long)e * mstr);
           acc0 |= x0 & mv;
           acc1 |= x1 & mv;
         }
@@ -1038,6 +1074,19 @@ __global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg,
     if (lane == 0) atomicAdd(counters + 4, warp_iters);
     if (threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
   }
+}
+
+template <bool kCount, bool kWrap, bool kOcc = false>
+__global__ void __launch_bounds__(256) k_propagate_tile_pair(Dims d, SegDev seg, TileCfg tc,
+                                                             const uint32_t* __restrict__ X, long xs,
+                                                             const uint32_t* __restrict__ mask,
+                                                             const uint32_t* __restrict__ occ,
+                                                             uint32_t* __restrict__ out, long os, int Q,
+                                                             const int32_t* __restrict__ xbox,
+                                                             int32_t* __restrict__ obox, long bs,
+                                                             unsigned long long* __restrict__ counters) {
+  propagate_pair_body<kCount, kWrap, kOcc, false>(d, seg, tc, X, xs, mask, occ, out, os, Q, xbox, obox, bs,
+                                                  counters, blockIdx.x, blockIdx.y);
 }
 
 // The work list of one propagation: for every query q, the tiles whose
@@ -1872,6 +1921,18 @@ cudaError_t launch_propagate(const Dims& d, const TileCfg& tc, const SegDev& seg
       k_propagate_tile_occ_list<false><<<list_grid, 256, smem_o, st>>>(
           d, seg, tc, X, x_stride, mask, mask_stride, occ, out, out_stride, xbox, obox, box_stride, nullptr,
           wl->items, wl->count);
+    return cudaGetLastError();
+  }
+  // two queries per block without stored masks: the pair halo and the
+  // occupancy halo, the supercover walks shared by both queries
+  if (smem_o > 0 && seg.tab && Q >= 2 && tc.pair && mask_stride == 0 && 3 * (smem_o / 2) <= (size_t)kTileOccSmemMax) {
+    dim3 grid(tc.tiles_y * tc.tiles_z, (Q + 1) / 2);
+    if (counters)
+      k_propagate_tile_pair<true, false, true><<<grid, 256, 3 * (smem_o / 2), st>>>(
+          d, seg, tc, X, x_stride, mask, occ, out, out_stride, Q, xbox, obox, box_stride, counters);
+    else
+      k_propagate_tile_pair<false, false, true><<<grid, 256, 3 * (smem_o / 2), st>>>(
+          d, seg, tc, X, x_stride, mask, occ, out, out_stride, Q, xbox, obox, box_stride, nullptr);
     return cudaGetLastError();
   }
   if (smem_o > 0 && seg.tab) {
@@ -3151,6 +3212,12 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_edge_masks_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<true, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess) e = set_rows_attributes<1>();
   if (e == cudaSuccess) e = set_rows_attributes<2>();
   if (e == cudaSuccess) e = set_rows_attributes<4>();

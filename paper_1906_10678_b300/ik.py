@@ -126,6 +126,7 @@ _sig("ik_batch_engine_create", _i, [ctypes.POINTER(_vp)])
 _sig("ik_batch_engine_destroy", _i, [_vp])
 _sig("ik_batch_engine_set_budget", _i, [_vp, ctypes.c_size_t])
 _sig("ik_batch_engine_set_timeout", _i, [_vp, ctypes.c_int64])
+_sig("ik_batch_engine_set_pairs", _i, [_vp, _i])
 _sig("ik_solve_batch_async", _i, [_vp, _vp, _i, ctypes.POINTER(IkBatchParams), _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp])
 _sig("ik_batch_capture", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _i,
@@ -147,7 +148,8 @@ EXPORTED = [
     "ik_solve_reach", "ik_solve_reach_many", "ik_solve_reach_many_cone", "ik_solve_reach_set", "ik_set_segment_limits", "ik_guide", "ik_waypoint_sets", "ik_plan_path", "ik_plan_path_follow", "ik_plan_path_short",
     "ik_reach_path_many", "ik_plan_between", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_engine_create", "ik_batch_engine_destroy",
-    "ik_batch_engine_set_budget", "ik_batch_engine_set_timeout", "ik_solve_batch_async", "ik_batch_capture",
+    "ik_batch_engine_set_budget", "ik_batch_engine_set_timeout", "ik_batch_engine_set_pairs",
+    "ik_solve_batch_async", "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
@@ -605,6 +607,9 @@ class BatchEngine:
 
     def set_timeout(self, ns: int) -> None:
         _check(_lib.ik_batch_engine_set_timeout(self.h, int(ns)), "ik_batch_engine_set_timeout")
+
+    def set_pairs(self, on: int) -> None:
+        _check(_lib.ik_batch_engine_set_pairs(self.h, int(on)), "ik_batch_engine_set_pairs")
 
     def solve_async(self, problems, found, reach, poses, relax, status, job_rc, stream: int = 0,
                     delta: int = 3, eps2: int = 2, eps2_max: int = 8, max_relax: int = -1,

@@ -283,6 +283,30 @@ def test_uneven_batch_waves_equal_one_launch(ik):
         assert a["status"] == b["status"] and (a["poses"] == b["poses"]).all()
 
 
+def test_uneven_batch_query_pairs_equal_single_queries(ik):
+    """Waypoint items carrying two queries (sharing each supercover walk)
+    give exactly the results of one query per item, on problems of every
+    grid size and on one whose waypoint count is odd."""
+    import torch
+    probs = [_as_dict(p) for p in G.c4_problems(12, 7)]
+    assert any(p["n_way"] % 2 for p in probs) and len({p["shape"][0] for p in probs}) >= 3
+    outs = []
+    for pairs in (0, 1):
+        with ik.BatchEngine() as eng:
+            eng.set_pairs(pairs)
+            found, reach, poses, relax, status, rc = _packed_outputs(ik, torch, probs)
+            eng.solve_async(probs, found, reach, poses, relax, status, rc)
+            torch.cuda.synchronize()
+            assert (rc.cpu().numpy() == ik.IK_OK).all()
+            outs.append([t.cpu().numpy() for t in (found, reach, poses, relax, status)])
+    for a, b in zip(*outs):
+        assert (a == b).all()
+    with ik.BatchEngine() as eng:
+        for bad in (-1, 2):
+            with pytest.raises(Exception):
+                eng.set_pairs(bad)
+
+
 def test_uneven_batch_timeout_is_reported_and_the_context_stays_usable(ik):
     """With a wait limit too short for any work (1 microsecond) the
     persistent launch gives up on its own: unfinished problems report
