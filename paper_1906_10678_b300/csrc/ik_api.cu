@@ -314,6 +314,17 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
         run[2 * Rr + 1] = (int32_t)tabr.size();
       }
   }
+  // and for the row-lane edge masks (rows of 32 + 2R per halo slice)
+  std::vector<int32_t> sctabr;
+  if (Rr <= 31) {
+    const int RYr = 32 + 2 * Rr;
+    sctabr.resize(s->host.sc.size());
+    for (size_t i = 0; i < sctabr.size(); ++i) {
+      const int32_t v = s->host.sc[i];
+      const int vx = unpack_x(v), vy = unpack_y(v), vz = unpack_z(v);
+      sctabr[i] = (int32_t)(((uint32_t)(vz * RYr + vy) << 6) | (uint32_t)(vx + 32));
+    }
+  }
   // and for the TMA-staged brick (pitch BX, word w at column w + 4)
   const int BX = tma_mask_pitch(g->d);
   std::vector<int32_t> sctab_tma;
@@ -333,6 +344,7 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
   if (e == cudaSuccess && !tabw.empty()) e = cudaMalloc(&s->d_tabw, n * 4);
   if (e == cudaSuccess && !tabr.empty()) e = cudaMalloc(&s->d_tabr, n * 4);
   if (e == cudaSuccess && !tabr.empty()) e = cudaMalloc(&s->d_rowsr, rowsr.size() * 4);
+  if (e == cudaSuccess && !sctabr.empty()) e = cudaMalloc(&s->d_sctabr, sctabr.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, s->host.rows.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc_start, (n + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, s->host.sc.size() * 4);
@@ -344,6 +356,7 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     cudaFree(s->d_tabw);
     cudaFree(s->d_tabr);
     cudaFree(s->d_rowsr);
+    cudaFree(s->d_sctabr);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);
@@ -356,6 +369,8 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
     CK(cudaMemcpyAsync(s->d_sctab_tma, sctab_tma.data(), sctab_tma.size() * 4, cudaMemcpyHostToDevice, g->st));
   if (!tabw.empty())
     CK(cudaMemcpyAsync(s->d_tabw, tabw.data(), n * 4, cudaMemcpyHostToDevice, g->st));
+  if (!sctabr.empty())
+    CK(cudaMemcpyAsync(s->d_sctabr, sctabr.data(), sctabr.size() * 4, cudaMemcpyHostToDevice, g->st));
   if (!tabr.empty()) {
     CK(cudaMemcpyAsync(s->d_tabr, tabr.data(), n * 4, cudaMemcpyHostToDevice, g->st));
     CK(cudaMemcpyAsync(s->d_rowsr, rowsr.data(), rowsr.size() * 4, cudaMemcpyHostToDevice, g->st));
@@ -811,6 +826,7 @@ int ik_destroy_grid(ik_grid g) {
     cudaFree(s->d_tabw);
     cudaFree(s->d_tabr);
     cudaFree(s->d_rowsr);
+    cudaFree(s->d_sctabr);
     cudaFree(s->d_rows);
     cudaFree(s->d_sc_start);
     cudaFree(s->d_sc);

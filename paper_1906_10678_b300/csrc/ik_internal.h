@@ -148,6 +148,8 @@ struct ShellDev {
   int32_t* d_tabw = nullptr;       // SegDev::tabw (grids whose rows fill a warp: wx = 1, 2, 4, 8, 16, 32)
   int32_t* d_tabr = nullptr;       // SegDev::tabr, rowsr (reach at most 31)
   int32_t* d_rowsr = nullptr;
+  int32_t* d_sctabr = nullptr;     // per supercover voxel, for the row-lane edge masks (reach at most 31):
+                                   // ((vz * (32 + 2R) + vy) << 6) | (vx + 32)
   int32_t* d_sc_start = nullptr;
   int32_t* d_sc = nullptr;
   uint32_t* d_mask = nullptr;

@@ -408,10 +408,18 @@ cudaError_t launch_edge_masks_tma(const Dims& d, const TileCfg& tc, const void* 
   return cudaGetLastError();
 }
 
+cudaError_t launch_edge_masks_rows(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
+                                   const MaskBox& b, uint32_t* mask, cudaStream_t st, bool* done);
+
 cudaError_t launch_edge_masks(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
                               const MaskBox& b, uint32_t* mask, cudaStream_t st) {
   const int n = (int)s.host.off.size();
   if (n == 0 || b.words() <= 0) return cudaSuccess;
+  {
+    bool done = false;
+    const cudaError_t e = launch_edge_masks_rows(d, tc, occ, s, b, mask, st, &done);
+    if (done || e != cudaSuccess) return e;
+  }
   const size_t smem = tile_smem_bytes(tc, s.reach);
   if (smem > 0 && s.d_sctab) {
     const int tiles_y = (b.nyy() + tc.TY - 1) / tc.TY, tiles_z = (b.z1 - b.z0 + tc.TZ) / tc.TZ;
@@ -1799,6 +1807,101 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
     }
     if (threadIdx.x == 0) atomicAdd(counters + 5, 1ull);
   }
+}
+
+// Edge masks with row lanes (rows of 1, 2 or 4 words, reach at most 31): a
+// lane owns one row of the mask box, a block 32 rows x 8 slices.  The tile's
+// occupancy halo is staged at a pitch of exactly WX words (words outside the
+// grid are free, and a segment between two voxels of the grid never leaves
+// it), and each supercover voxel of an offset costs the lane one vector load
+// of shared memory and WX funnel shifts.  The voxels of one supercover are
+// the same for every lane, so the sign of their shift is warp-uniform.
+// sctabr[i] = ((vz * (32 + 2R) + vy) << 6) | (vx + 32).  Results equal
+// k_edge_masks_tile.
+template <int WX, bool kFull>
+__global__ void __launch_bounds__(256) k_edge_masks_rows(Dims d, MaskBox b, int tiles_y, int R, int n_off,
+                                                         const uint32_t* __restrict__ occ,
+                                                         const int32_t* __restrict__ sc_start,
+                                                         const int32_t* __restrict__ sctabr,
+                                                         uint32_t* __restrict__ mask) {
+  extern __shared__ __align__(16) uint32_t so[];
+  constexpr int TY = kRowTY, TZ = kRowTZ;
+  const int y0 = b.y0 + (blockIdx.x % tiles_y) * TY, z0 = b.z0 + (blockIdx.x / tiles_y) * TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RY = TY + 2 * R, RZ = TZ + 2 * R;
+  for (int r = threadIdx.x; r < RZ * RY; r += blockDim.x) {
+    const int sy = y0 - R + r % RY, sz = z0 - R + r / RY;
+    uint32_t v[WX];
+#pragma unroll
+    for (int i = 0; i < WX; ++i) v[i] = 0u;
+    if (sy >= 0 && sy < d.ny && sz >= 0 && sz < d.nz) row_ldg<WX>(occ + ((long)sz * d.ny + sy) * WX, v);
+    row_st<WX>(so + r * WX, v);
+  }
+  __syncthreads();
+  const int y = y0 + lane, z = z0 + warp;
+  if (y > b.y1 || z > b.z1) return;
+  const uint32_t* base = so + ((warp + R) * RY + (lane + R)) * WX;
+  const long nb = b.words();
+  uint32_t* mrow = mask + b.index(b.wx0, y, z);
+  const int e_end = min(n_off, (int)(blockIdx.y + 1) * kMaskChunk);
+  for (int e = blockIdx.y * kMaskChunk; e < e_end; ++e) {
+    const int i1 = __ldg(sc_start + e + 1);
+    uint32_t blk[WX];
+#pragma unroll
+    for (int i = 0; i < WX; ++i) blk[i] = 0u;
+#pragma unroll 4
+    for (int i = __ldg(sc_start + e); i < i1; ++i) {
+      const int32_t t = __ldg(sctabr + i);
+      uint32_t v[WX], x[WX];
+      row_lds<WX>(base + (t >> 6) * WX, v);
+      const int vx = (t & 63) - 32;
+      if (vx < 0)
+        row_shift<WX, true>(v, vx & 31, x);
+      else
+        row_shift<WX, false>(v, vx, x);
+#pragma unroll
+      for (int w = 0; w < WX; ++w) blk[w] |= x[w];
+    }
+    uint32_t* dst = mrow + (long)e * nb;
+    if (kFull) {
+      uint32_t o[WX];
+#pragma unroll
+      for (int w = 0; w < WX; ++w) o[w] = ~blk[w];
+      row_st<WX>(dst, o);
+    } else {
+#pragma unroll
+      for (int w = 0; w < WX; ++w)
+        if (w >= b.wx0 && w <= b.wx1) dst[w - b.wx0] = ~blk[w];
+    }
+  }
+}
+
+template <int WX>
+cudaError_t launch_edge_masks_rows_w(const Dims& d, const MaskBox& b, int R, int n, const uint32_t* occ,
+                                     const ShellDev& s, uint32_t* mask, cudaStream_t st) {
+  const int tiles_y = (b.nyy() + kRowTY - 1) / kRowTY, tiles_z = (b.z1 - b.z0 + kRowTZ) / kRowTZ;
+  const dim3 grid(tiles_y * tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
+  const size_t smem = (size_t)(kRowTZ + 2 * R) * (kRowTY + 2 * R) * WX * 4;
+  const bool full = b.wx0 == 0 && b.wx1 == d.wx - 1 && ((uintptr_t)mask & (WX * 4 - 1)) == 0;
+  if (full)
+    k_edge_masks_rows<WX, true><<<grid, 256, smem, st>>>(d, b, tiles_y, R, n, occ, s.d_sc_start, s.d_sctabr, mask);
+  else
+    k_edge_masks_rows<WX, false><<<grid, 256, smem, st>>>(d, b, tiles_y, R, n, occ, s.d_sc_start, s.d_sctabr,
+                                                          mask);
+  return cudaGetLastError();
+}
+
+// The row-lane edge masks where they apply (*done = false: use another form).
+cudaError_t launch_edge_masks_rows(const Dims& d, const TileCfg& tc, const uint32_t* occ, const ShellDev& s,
+                                   const MaskBox& b, uint32_t* mask, cudaStream_t st, bool* done) {
+  *done = false;
+  const int n = (int)s.host.off.size(), R = s.reach;
+  if (!tc.rows || !s.d_sctabr || R > 31 || (d.wx != 1 && d.wx != 2 && d.wx != 4)) return cudaSuccess;
+  if (((uintptr_t)occ & (d.wx * 4 - 1)) != 0) return cudaSuccess;
+  *done = true;
+  if (d.wx == 4) return launch_edge_masks_rows_w<4>(d, b, R, n, occ, s, mask, st);
+  if (d.wx == 2) return launch_edge_masks_rows_w<2>(d, b, R, n, occ, s, mask, st);
+  return launch_edge_masks_rows_w<1>(d, b, R, n, occ, s, mask, st);
 }
 
 size_t rows_smem_bytes(int wx, int R, int nq) {
@@ -3219,6 +3322,13 @@ cudaError_t set_kernel_attributes() {
     e = cudaFuncSetAttribute((const void*)k_propagate_tile_pair<false, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   if (e == cudaSuccess) e = set_rows_attributes<1>();
+  {
+    const void* fns[] = {(const void*)k_edge_masks_rows<1, false>, (const void*)k_edge_masks_rows<1, true>,
+                         (const void*)k_edge_masks_rows<2, false>, (const void*)k_edge_masks_rows<2, true>,
+                         (const void*)k_edge_masks_rows<4, false>, (const void*)k_edge_masks_rows<4, true>};
+    for (const void* f : fns)
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+  }
   if (e == cudaSuccess) e = set_rows_attributes<2>();
   if (e == cudaSuccess) e = set_rows_attributes<4>();
   if (e == cudaSuccess)
