@@ -1362,7 +1362,13 @@ __global__ void __launch_bounds__(256, 2) k_propagate_tile2(Dims d, SegDev seg, 
 // batch of offsets shifts the same way.  Results equal the other forms.
 template <int WX>
 __device__ __forceinline__ void row_ldg(const uint32_t* __restrict__ p, uint32_t (&v)[WX]) {
-  if constexpr (WX == 4) {
+  if constexpr (WX > 4 && WX % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < WX / 4; ++c) {
+      const uint4 t = __ldg(reinterpret_cast<const uint4*>(p) + c);
+      v[4 * c] = t.x, v[4 * c + 1] = t.y, v[4 * c + 2] = t.z, v[4 * c + 3] = t.w;
+    }
+  } else if constexpr (WX == 4) {
     const uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
     v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
   } else if constexpr (WX == 2) {
@@ -1375,7 +1381,13 @@ __device__ __forceinline__ void row_ldg(const uint32_t* __restrict__ p, uint32_t
 
 template <int WX>
 __device__ __forceinline__ void row_lds(const uint32_t* p, uint32_t (&v)[WX]) {
-  if constexpr (WX == 4) {
+  if constexpr (WX > 4 && WX % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < WX / 4; ++c) {
+      const uint4 t = reinterpret_cast<const uint4*>(p)[c];
+      v[4 * c] = t.x, v[4 * c + 1] = t.y, v[4 * c + 2] = t.z, v[4 * c + 3] = t.w;
+    }
+  } else if constexpr (WX == 4) {
     const uint4 t = *reinterpret_cast<const uint4*>(p);
     v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
   } else if constexpr (WX == 2) {
@@ -1388,7 +1400,11 @@ __device__ __forceinline__ void row_lds(const uint32_t* p, uint32_t (&v)[WX]) {
 
 template <int WX>
 __device__ __forceinline__ void row_st(uint32_t* p, const uint32_t (&v)[WX]) {
-  if constexpr (WX == 4)
+  if constexpr (WX > 4 && WX % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < WX / 4; ++c)
+      reinterpret_cast<uint4*>(p)[c] = make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  } else if constexpr (WX == 4)
     *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
   else if constexpr (WX == 2)
     *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
@@ -1882,7 +1898,7 @@ cudaError_t launch_edge_masks_rows_w(const Dims& d, const MaskBox& b, int R, int
   const int tiles_y = (b.nyy() + kRowTY - 1) / kRowTY, tiles_z = (b.z1 - b.z0 + kRowTZ) / kRowTZ;
   const dim3 grid(tiles_y * tiles_z, (n + kMaskChunk - 1) / kMaskChunk);
   const size_t smem = (size_t)(kRowTZ + 2 * R) * (kRowTY + 2 * R) * WX * 4;
-  const bool full = b.wx0 == 0 && b.wx1 == d.wx - 1 && ((uintptr_t)mask & (WX * 4 - 1)) == 0;
+  const bool full = b.wx0 == 0 && b.wx1 == d.wx - 1 && ((uintptr_t)mask & ((WX < 4 ? WX : 4) * 4 - 1)) == 0;
   if (full)
     k_edge_masks_rows<WX, true><<<grid, 256, smem, st>>>(d, b, tiles_y, R, n, occ, s.d_sc_start, s.d_sctabr, mask);
   else
@@ -1896,9 +1912,11 @@ cudaError_t launch_edge_masks_rows(const Dims& d, const TileCfg& tc, const uint3
                                    const MaskBox& b, uint32_t* mask, cudaStream_t st, bool* done) {
   *done = false;
   const int n = (int)s.host.off.size(), R = s.reach;
-  if (!tc.rows || !s.d_sctabr || R > 31 || (d.wx != 1 && d.wx != 2 && d.wx != 4)) return cudaSuccess;
-  if (((uintptr_t)occ & (d.wx * 4 - 1)) != 0) return cudaSuccess;
+  if (!tc.rows || !s.d_sctabr || R > 31 || (d.wx != 1 && d.wx != 2 && d.wx != 4 && d.wx != 8)) return cudaSuccess;
+  if (((uintptr_t)occ & (std::min(d.wx, 4) * 4 - 1)) != 0) return cudaSuccess;
+  if ((size_t)(kRowTZ + 2 * R) * (kRowTY + 2 * R) * d.wx * 4 > (size_t)kTileOccSmemMax) return cudaSuccess;
   *done = true;
+  if (d.wx == 8) return launch_edge_masks_rows_w<8>(d, b, R, n, occ, s, mask, st);
   if (d.wx == 4) return launch_edge_masks_rows_w<4>(d, b, R, n, occ, s, mask, st);
   if (d.wx == 2) return launch_edge_masks_rows_w<2>(d, b, R, n, occ, s, mask, st);
   return launch_edge_masks_rows_w<1>(d, b, R, n, occ, s, mask, st);
@@ -3325,7 +3343,8 @@ cudaError_t set_kernel_attributes() {
   {
     const void* fns[] = {(const void*)k_edge_masks_rows<1, false>, (const void*)k_edge_masks_rows<1, true>,
                          (const void*)k_edge_masks_rows<2, false>, (const void*)k_edge_masks_rows<2, true>,
-                         (const void*)k_edge_masks_rows<4, false>, (const void*)k_edge_masks_rows<4, true>};
+                         (const void*)k_edge_masks_rows<4, false>, (const void*)k_edge_masks_rows<4, true>,
+                         (const void*)k_edge_masks_rows<8, false>, (const void*)k_edge_masks_rows<8, true>};
     for (const void* f : fns)
       if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
   }
