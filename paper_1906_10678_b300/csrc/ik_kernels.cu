@@ -1426,6 +1426,16 @@ __device__ __forceinline__ void row_shift(const uint32_t (&v)[WX], int s, uint32
 }
 
 constexpr int kRowTY = 32, kRowTZ = 8, kRowUnits = kRowTY * kRowTZ;
+// dynamic shared memory a row-lane block may use (its static arrays take
+// up to 3 KiB of the 227 KiB a block may opt in to)
+constexpr int kRowSmemMax = 224 * 1024;
+
+// Bits r0 .. r0 + len - 1 (r0 < 64, len < 64) of the 96-bit row mask rb[0..2].
+__device__ __forceinline__ uint64_t row_window(const uint32_t* rb, int r0, int len) {
+  const uint64_t lo = ((uint64_t)rb[1] << 32) | rb[0], hi = rb[2];
+  const uint64_t w = r0 == 0 ? lo : ((lo >> r0) | (hi << (64 - r0)));
+  return w & ((1ull << len) - 1ull);
+}
 
 // The block's output rows are its units: unit t = (slice t / 32, row t %
 // 32), each carrying all NQ queries of the block.  The walk goes plane by
@@ -1451,6 +1461,8 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
   constexpr int TY = kRowTY, TZ = kRowTZ, NU = kRowUnits;
   constexpr int kB = NQ == 1 ? 8 : 4;  // offsets per batch
   __shared__ int s_cnt[8], s_next, s_plane[64];
+  // per staged slice: the halo rows holding a source word of either query
+  __shared__ uint32_t s_rowbits[(kRowTZ + 62) * 3];
   const int tile = qfast ? blockIdx.y : blockIdx.x;
   const int qa = NQ * (qfast ? blockIdx.x : blockIdx.y);
   const int y0 = (tile % tiles_y) * TY, z0 = (tile / tiles_y) * TZ;
@@ -1497,6 +1509,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
     }
     row_st<WX>(m_s + threadIdx.x * WX, m);
   }
+  for (int i = threadIdx.x; i < (TZ + 2 * R) * 3; i += blockDim.x) s_rowbits[i] = 0u;
   if (!__syncthreads_or(touch && m_any)) {
     if (valid) {
       const uint32_t zero[WX] = {};
@@ -1526,6 +1539,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
         const int sy = sy0 + r % nyr, sz = sz0 + r / nyr;
         const long row = ((long)sz * d.ny + sy) * WX;
         uint32_t* dst = sr + ((sz - z0 + R) * RY + (sy - y0 + R)) * WX;
+        uint32_t nz = 0u;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           uint32_t v[WX];
@@ -1537,7 +1551,13 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
             for (int i = 0; i < WX; ++i)
               if (i < bx0[q] || i > bx1[q]) v[i] = 0u;
           }
+#pragma unroll
+          for (int i = 0; i < WX; ++i) nz |= v[i];
           row_st<WX>(dst + q * HW, v);
+        }
+        if (nz) {
+          const int hr = sy - y0 + R;
+          atomicOr(s_rowbits + (sz - z0 + R) * 3 + (hr >> 5), 1u << (hr & 31));
         }
       }
     const uint32_t zero[WX] = {};
@@ -1570,8 +1590,18 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
 #pragma unroll
       for (int i = 0; i < WX; ++i) m[i] = 0u;
     // the pass's union of the lanes' dy ranges
-    const int ey0 = __reduce_min_sync(kFull, hasu ? max(uy0 - yu, -R) : 0x7fffffff);
-    const int ey1 = __reduce_max_sync(kFull, hasu ? min(uy1 - yu, R) : -0x7fffffff);
+    // the pass's union of the lanes' dy ranges: the rows of each lane's
+    // window (dy in [-R, R]) that hold a source word
+    int lo_dy = 0x7fffffff, hi_dy = -0x7fffffff;
+    if (hasu) {
+      const uint64_t win = row_window(s_rowbits + (zu - z0 + R + ez) * 3, yu - y0, 2 * R + 1);
+      if (win) {
+        lo_dy = __ffsll((long long)win) - 1 - R;
+        hi_dy = 63 - __clzll((long long)win) - R;
+      }
+    }
+    const int ey0 = __reduce_min_sync(kFull, lo_dy);
+    const int ey1 = __reduce_max_sync(kFull, hi_dy);
     const uint32_t* hz = sr + ((zu - z0 + R + ez) * RY + (yu - y0 + R)) * WX;
     const uint32_t* mrow = seg.mask + (hasu ? seg.mbox.index(mx0, yu, zu) : 0);
     // words still open at the pass's start (work counters only)
@@ -1706,6 +1736,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
           act = act || (open && zt + ez >= bz0[q] && zt + ez <= bz1[q]);
         }
       }
+      act = act && row_window(s_rowbits + (warp + R + ez) * 3, lane, 2 * R + 1) != 0ull;
       const unsigned bal = __ballot_sync(kFull, act);
       if (lane == 0) s_cnt[warp] = __popc(bal);
       __syncthreads();
@@ -1759,6 +1790,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
           for (int k = 0; k < WX; ++k) open = open || (a[k] & m[k]) != m[k];
           act = act || (open && z0 + c + ez >= bz0[q] && z0 + c + ez <= bz1[q]);
         }
+        act = act && row_window(s_rowbits + (c + R + ez) * 3, lane, 2 * R + 1) != 0ull;
         const unsigned bal = __ballot_sync(kFull, act);
         if (act) wl[n_act + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)t;
         n_act += __popc(bal);
@@ -1927,7 +1959,7 @@ size_t rows_smem_bytes(int wx, int R, int nq) {
   // the halos, the units' accumulators and output masks, the unit list
   const size_t bytes = (size_t)nq * (kRowTZ + 2 * R) * (kRowTY + 2 * R) * wx * 4 +
                        (size_t)(nq + 1) * kRowUnits * wx * 4 + (size_t)8 * kRowUnits * 2;
-  return bytes <= (size_t)kTileOccSmemMax ? bytes : 0;
+  return bytes <= (size_t)kRowSmemMax ? bytes : 0;
 }
 
 template <int WX, int NQ, bool kFullBox>
@@ -1968,7 +2000,7 @@ cudaError_t set_rows_attributes() {
                        (const void*)k_propagate_rows<WX, 2, false, false>, (const void*)k_propagate_rows<WX, 2, false, true>,
                        (const void*)k_propagate_rows<WX, 2, true, false>,  (const void*)k_propagate_rows<WX, 2, true, true>};
   for (const void* f : fns)
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileOccSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowSmemMax);
   return e;
 }
 
