@@ -1430,6 +1430,16 @@ constexpr int kRowTY = 32, kRowTZ = 8, kRowUnits = kRowTY * kRowTZ;
 // up to 3 KiB of the 227 KiB a block may opt in to)
 constexpr int kRowSmemMax = 224 * 1024;
 
+// The largest |dy| of an offset in plane dz of a shell with |d|^2 <= hi2
+// (at most R).
+__device__ __forceinline__ int plane_dy(int dz, int hi2, int R) {
+  const int v = max(0, hi2 - dz * dz);
+  int r = (int)sqrtf((float)v);
+  while ((r + 1) * (r + 1) <= v) ++r;
+  while (r * r > v) --r;
+  return min(r, R);
+}
+
 // Bits r0 .. r0 + len - 1 (r0 < 64, len < 64) of the 96-bit row mask rb[0..2].
 __device__ __forceinline__ uint64_t row_window(const uint32_t* rb, int r0, int len) {
   const uint64_t lo = ((uint64_t)rb[1] << 32) | rb[0], hi = rb[2];
@@ -1594,10 +1604,11 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
     // window (dy in [-R, R]) that hold a source word
     int lo_dy = 0x7fffffff, hi_dy = -0x7fffffff;
     if (hasu) {
-      const uint64_t win = row_window(s_rowbits + (zu - z0 + R + ez) * 3, yu - y0, 2 * R + 1);
+      const int dyx = plane_dy(ez, seg.hi2, R);
+      const uint64_t win = row_window(s_rowbits + (zu - z0 + R + ez) * 3, yu - y0 + R - dyx, 2 * dyx + 1);
       if (win) {
-        lo_dy = __ffsll((long long)win) - 1 - R;
-        hi_dy = 63 - __clzll((long long)win) - R;
+        lo_dy = __ffsll((long long)win) - 1 - dyx;
+        hi_dy = 63 - __clzll((long long)win) - dyx;
       }
     }
     const int ey0 = __reduce_min_sync(kFull, lo_dy);
@@ -1736,7 +1747,10 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
           act = act || (open && zt + ez >= bz0[q] && zt + ez <= bz1[q]);
         }
       }
-      act = act && row_window(s_rowbits + (warp + R + ez) * 3, lane, 2 * R + 1) != 0ull;
+      {
+        const int dyx = plane_dy(ez, seg.hi2, R);
+        act = act && row_window(s_rowbits + (warp + R + ez) * 3, lane + R - dyx, 2 * dyx + 1) != 0ull;
+      }
       const unsigned bal = __ballot_sync(kFull, act);
       if (lane == 0) s_cnt[warp] = __popc(bal);
       __syncthreads();
@@ -1775,6 +1789,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
       i = __shfl_sync(kFull, i, 0);
       if (i >= n_planes) break;
       const int ez = s_plane[i];
+      const int dyx = plane_dy(ez, seg.hi2, R);  // the plane's rows reach |dy| <= dyx
       int n_act = 0;
       for (int c = 0; c < TZ; ++c) {
         const int t = c * 32 + lane;
@@ -1790,7 +1805,7 @@ __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, i
           for (int k = 0; k < WX; ++k) open = open || (a[k] & m[k]) != m[k];
           act = act || (open && z0 + c + ez >= bz0[q] && z0 + c + ez <= bz1[q]);
         }
-        act = act && row_window(s_rowbits + (c + R + ez) * 3, lane, 2 * R + 1) != 0ull;
+        act = act && row_window(s_rowbits + (c + R + ez) * 3, lane + R - dyx, 2 * dyx + 1) != 0ull;
         const unsigned bal = __ballot_sync(kFull, act);
         if (act) wl[n_act + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)t;
         n_act += __popc(bal);
