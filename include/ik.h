@@ -138,8 +138,9 @@ IK_API int ik_destroy_grid(ik_grid g);
 /* IK_OPT_WORK_LIST: how a batched backward pass (16 or more queries) visits
  * the tiles of each level.  1 (default): a work list of the tiles a level's
  * bounding boxes reach, walked by a grid of resident blocks, on the levels
- * where a bound from the arm's reaches leaves at most an eighth of the tiles,
- * and one block per (tile, query) elsewhere; 0: one block per (tile, query)
+ * where a bound from the arm's reaches leaves at most an eighth of the tiles
+ * (a sixteenth where the row-lane kernel runs the other levels), and one
+ * block per (tile, query) elsewhere; 0: one block per (tile, query)
  * on every level; 2: the work list on every level.  Results are identical. */
 #define IK_OPT_WORK_LIST 4
 /* IK_OPT_QUERY_PAIRS: on the levels of a batched backward pass that run one

@@ -708,7 +708,12 @@ int backward_sets(ik_grid g, const ArmDev& ad, uint32_t* V, int Q, int prof_id, 
       };
       const long ty = std::min(tc.tiles_y, (span(g->f_root[1], d.ny) + tc.TY - 1) / tc.TY + 1);
       const long tz = std::min(tc.tiles_z, (span(g->f_root[2], d.nz) + tc.TZ - 1) / tc.TZ + 1);
-      if (8 * ty * tz <= (long)tc.tiles_y * tc.tiles_z) wk = wlp;
+      // with row lanes (which skip rows whose source windows are empty) the
+      // full grid pays down to sparser levels: the list then takes only the
+      // levels at most a 16th of whose tiles can be live (on the 128^3 step,
+      // levels 1 and 8; levels 2 and 7 measured faster on the full grid)
+      const bool rows = tc.rows && g->use_masks && (d.wx == 1 || d.wx == 2 || d.wx == 4) && ad.seg[k - 1].R <= 31;
+      if ((rows ? 16 : 8) * ty * tz <= (long)tc.tiles_y * tc.tiles_z) wk = wlp;
     }
     const SegDev& seg = ad.seg[k - 1];
     if (propagate_listed(g->tc, seg, Q, qs, wk)) {
