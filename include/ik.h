@@ -171,9 +171,10 @@ IK_API int ik_destroy_grid(ik_grid g);
  * row (two queries' words where IK_OPT_QUERY_PAIRS allows), each offset's
  * source row comes from one conflict-free vector load of shared memory,
  * and the warps of a block take planes of offsets (dz) one at a time, each
- * packing the rows that can still gain bits into full passes.  On one B300
- * the 128^3 reach + path step takes 60.2 ms with it and 79.0 ms without.
- * 0: the forms above.  Results are identical. */
+ * packing the rows that can still gain bits (and whose source rows hold a
+ * word) into full passes.  On one B300 the 128^3 reach + path step takes
+ * 52.7 ms with it and 78.5 ms without.  0: the forms above.  Results are
+ * identical. */
 #define IK_OPT_ROW_LANES 7
 IK_API int ik_set_option(ik_grid g, int option, int value);
 /* Number of uint32 words of one voxel set of this grid. */
