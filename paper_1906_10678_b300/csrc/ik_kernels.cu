@@ -1348,8 +1348,9 @@ __global__ void __launch_bounds__(256, 2) k_propagate_tile2(Dims d, SegDev seg, 
 
 // Row-lane form of the stored-mask propagation, for grids whose rows are at
 // most four words (nx <= 128).  A lane owns one whole output row (the WX
-// words of one (y, z)), a warp 32 consecutive rows of one z slice, a block
-// 8 slices.  The source halo is staged as (8 + 2R) x (32 + 2R) rows of
+// words of one (y, z)); a block covers 32 rows x 8 slices of a tile (the
+// helpers below also serve the row-lane edge masks, up to 8-word rows).
+// The source halo is staged as (8 + 2R) x (32 + 2R) rows of
 // exactly WX words: the words left of x = 0 and right of the row's end are
 // zero, so they are not stored, and a warp's 32 lanes read 32 consecutive
 // rows with one vector load each, free of bank conflicts.  An offset's
@@ -1448,15 +1449,20 @@ __device__ __forceinline__ uint64_t row_window(const uint32_t* rb, int r0, int l
 }
 
 // The block's output rows are its units: unit t = (slice t / 32, row t %
-// 32), each carrying all NQ queries of the block.  The walk goes plane by
-// plane (dz) for the whole block: before each plane the units that can
-// still gain bits there (for some query, a free voxel not yet reached and a
-// source slice inside that query's box) are packed into a list, and each
-// warp takes 32 of them per pass, so a saturated row stops costing a lane
-// and a warp never waits on rows that are done.  A unit's accumulators and
-// output mask live in shared memory between planes.  qfast: blockIdx.x is
-// the query pair and blockIdx.y the tile, so the blocks resident together
-// work on the same tile and share its edge-mask words in L2.
+// 32), each carrying all NQ queries of the block.  Warps take whole planes
+// of offsets (dz) from a counter, the larger planes first; for its plane a
+// warp lists the units that can still gain bits there (for some query, a
+// free voxel not yet reached, and a source row inside the plane's dy reach
+// that holds a word, from the per-slice source row masks recorded while
+// staging) and walks them 32 per pass, over the dy range of the pass's
+// non-empty source rows.  So a saturated row, or one without sources in
+// reach, costs no lane.  A unit's accumulators (OR-merged with shared
+// atomics: planes may overlap in time, and the OR over planes does not
+// depend on their order) and output mask live in shared memory.  The work
+// counters' run takes the planes in order with block barriers instead, so
+// that its counts do not depend on scheduling.  qfast: blockIdx.x is the
+// query pair and blockIdx.y the tile, so the blocks resident together work
+// on the same tile and share its edge-mask words in L2.
 template <int WX, int NQ, bool kFullBox, bool kCount>
 __global__ void __launch_bounds__(256, 2) k_propagate_rows(Dims d, SegDev seg, int tiles_y, int qfast,
                                                            const uint32_t* __restrict__ X, long xs,
