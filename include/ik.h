@@ -499,6 +499,30 @@ IK_API int ik_solve_batch(const ik_problem* probs, int n, const ik_batch_params*
                           int32_t* found_out, int32_t* reach_out, int32_t* poses_out,
                           int32_t* relax_out, int32_t* status_out, double* gpu_ms_out);
 
+/* The uneven batch as a CUDA graph: ik_batch_capture_uneven plans the n
+ * problems (as ik_solve_batch_async), copies their descriptors, boxes and
+ * initial work queue into device memory the graph owns (synchronously,
+ * before returning), and captures -- on a stream of its own -- the
+ * sequence that resets the queue, clears the problems' working memory,
+ * fills job_rc_dev with IK_ERR_TIMEOUT and runs the persistent kernel: one
+ * launch.  ik_batch_graph_launch replays it on cuda_stream (NULL: the
+ * legacy default stream) and returns without waiting; every replay writes
+ * the same outputs to the same device arrays (the layout of
+ * ik_batch_output_sizes), which must stay allocated while the graph
+ * exists.  The problems' data are copied at capture: the caller's arrays
+ * may change afterwards.  The whole batch must fit one launch (the
+ * engine's pool budget), else IK_ERR_UNSUPPORTED.  The graph takes the
+ * engine's timeout and query-pair setting at capture.  Returns IK_OK,
+ * IK_ERR_ARG, IK_ERR_UNSUPPORTED, IK_ERR_OOM or IK_ERR_CUDA; a graph
+ * handle is freed by ik_batch_graph_destroy (which waits for the device). */
+typedef struct ik_batch_graph_s* ik_batch_graph;
+IK_API int ik_batch_capture_uneven(ik_batch_engine e, const ik_problem* probs, int n, const ik_batch_params* bp,
+                                   int32_t* found_dev, int32_t* reach_dev, int32_t* poses_dev,
+                                   int32_t* relax_dev, int32_t* status_dev, int32_t* job_rc_dev,
+                                   ik_batch_graph* out);
+IK_API int ik_batch_graph_launch(ik_batch_graph g, void* cuda_stream);
+IK_API int ik_batch_graph_destroy(ik_batch_graph g);
+
 /* ------------------------------------------------------------- replan */
 /* Validity of n poses under the current occupancy: every joint inside the
  * grid, every offset in its shell, every segment obstacle-free.

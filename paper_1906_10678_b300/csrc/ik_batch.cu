@@ -337,6 +337,55 @@ long long item_bound(const ik_problem& p, const ProbPlan& pl) {
 }
 
 // Enqueues problems [lo, hi) as one persistent launch.
+// The device descriptor of problem i (index in the caller's arrays) whose
+// pool region starts at base and whose boxes go to dboxes (device) through
+// hboxes (host staging).
+void fill_desc(const ik_problem& p, const ProbPlan& pl, int i, uint32_t* base, int32_t* dboxes, int32_t* hboxes,
+               int32_t* found, int32_t* reach, int32_t* poses, int32_t* relax, int32_t* status, int32_t* rc_out,
+               BatchProb* out) {
+  BatchProb& B = *out;
+  memset(&B, 0, sizeof(B));
+  B.d = pl.d;
+  for (int k = 0; k < IK_MAX_SEG; ++k) B.tcs[k] = pl.tcs[k];
+  B.arm = pl.arm;
+  B.S = p.n_seg;
+  B.W = p.n_way;
+  B.n_boxes = p.n_boxes;
+  B.n_slabs = pl.n_slabs;
+  for (int c = 0; c < 3; ++c) {
+    B.root[c] = p.root[c];
+    B.target[c] = p.target[c];
+  }
+  if (p.n_boxes) memcpy(hboxes, p.boxes, (size_t)p.n_boxes * 24);
+  B.boxes = dboxes;
+  const Layout& L = pl.lay;
+  B.occ = base + L.occ;
+  B.F = base + L.F;
+  B.V = base + L.V;
+  B.Vw = base + L.Vw;
+  B.chain = base + L.chain;
+  B.Fbox = (int32_t*)(base + L.Fbox);
+  B.Vbox = (int32_t*)(base + L.Vbox);
+  B.Vwbox = (int32_t*)(base + L.Vwbox);
+  B.reach = (int32_t*)(base + L.reach);
+  B.found = (int32_t*)(base + L.found);
+  B.g = (int32_t*)(base + L.g);
+  B.eps = (int32_t*)(base + L.eps);
+  B.poses = (int32_t*)(base + L.poses);
+  B.relax = (int32_t*)(base + L.relax);
+  B.status = (int32_t*)(base + L.status);
+  for (int k = 0; k < p.n_seg; ++k) {
+    B.arm.seg[k].occ = B.occ;
+    B.arm.segf[k] = B.arm.seg[k];  // whole shells: symmetric
+  }
+  B.o_found = found + i;
+  B.o_reach = reach + pl.off_reach;
+  B.o_poses = poses + pl.off_poses;
+  B.o_relax = relax + pl.off_relax;
+  B.o_status = status + i;
+  B.o_rc = rc_out + i;
+}
+
 int run_wave(ik_batch_engine_s* E, const ik_problem* probs, const std::vector<ProbPlan>& plans, int lo, int hi,
              const ik_batch_params* bp, int32_t* found, int32_t* reach, int32_t* poses, int32_t* relax,
              int32_t* status, int32_t* rc_out, cudaStream_t st) {
@@ -374,54 +423,12 @@ int run_wave(ik_batch_engine_s* E, const ik_problem* probs, const std::vector<Pr
   size_t pw = 0, bw = 0;
   long long it = 0;
   for (int i = lo; i < hi; ++i) {
-    const ik_problem& p = probs[i];
-    const ProbPlan& pl = plans[i];
-    BatchProb& B = hd[i - lo];
-    memset(&B, 0, sizeof(B));
-    B.d = pl.d;
-    for (int k = 0; k < IK_MAX_SEG; ++k) B.tcs[k] = pl.tcs[k];
-    B.arm = pl.arm;
-    B.S = p.n_seg;
-    B.W = p.n_way;
-    B.n_boxes = p.n_boxes;
-    B.n_slabs = pl.n_slabs;
-    for (int c = 0; c < 3; ++c) {
-      B.root[c] = p.root[c];
-      B.target[c] = p.target[c];
-    }
-    if (p.n_boxes) memcpy(hb + bw, p.boxes, (size_t)p.n_boxes * 24);
-    B.boxes = dboxes + bw;
-    bw += align_words(6 * (size_t)p.n_boxes);
-    uint32_t* base = pool + pw;
-    const Layout& L = pl.lay;
-    B.occ = base + L.occ;
-    B.F = base + L.F;
-    B.V = base + L.V;
-    B.Vw = base + L.Vw;
-    B.chain = base + L.chain;
-    B.Fbox = (int32_t*)(base + L.Fbox);
-    B.Vbox = (int32_t*)(base + L.Vbox);
-    B.Vwbox = (int32_t*)(base + L.Vwbox);
-    B.reach = (int32_t*)(base + L.reach);
-    B.found = (int32_t*)(base + L.found);
-    B.g = (int32_t*)(base + L.g);
-    B.eps = (int32_t*)(base + L.eps);
-    B.poses = (int32_t*)(base + L.poses);
-    B.relax = (int32_t*)(base + L.relax);
-    B.status = (int32_t*)(base + L.status);
-    pw += L.total;
-    for (int k = 0; k < p.n_seg; ++k) {
-      B.arm.seg[k].occ = B.occ;
-      B.arm.segf[k] = B.arm.seg[k];  // whole shells: symmetric
-    }
-    B.o_found = found + i;
-    B.o_reach = reach + pl.off_reach;
-    B.o_poses = poses + pl.off_poses;
-    B.o_relax = relax + pl.off_relax;
-    B.o_status = status + i;
-    B.o_rc = rc_out + i;
-    hs[i - lo] = make_int2(0, pl.n_slabs);
-    for (int s = 0; s < pl.n_slabs; ++s) hi4[it++] = make_int4(i - lo + 1, 0, s, 0);
+    fill_desc(probs[i], plans[i], i, pool + pw, dboxes + bw, hb + bw, found, reach, poses, relax, status, rc_out,
+              &hd[i - lo]);
+    pw += plans[i].lay.total;
+    bw += align_words(6 * (size_t)probs[i].n_boxes);
+    hs[i - lo] = make_int2(0, plans[i].n_slabs);
+    for (int s = 0; s < plans[i].n_slabs; ++s) hi4[it++] = make_int4(i - lo + 1, 0, s, 0);
   }
   // uploads, cleared pool and queue, then the launch
   CKB(cudaMemcpyAsync(E->descs.p, hd, desc_b, cudaMemcpyHostToDevice, st));
@@ -486,6 +493,114 @@ ik_batch_engine_s* g_default[64] = {nullptr};
 }  // namespace
 
 extern "C" {
+
+// A captured uneven batch: its own pool, queue and descriptors, the initial
+// queue state kept on the device, and the graph that resets the queue,
+// clears the pool and runs the persistent kernel.
+struct ik_batch_graph_s {
+  int device = 0;
+  DevArr pool, descs, items, ctl, state, boxes, items0, state0, ctl0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+
+  ~ik_batch_graph_s() {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    cudaDeviceSynchronize();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    DevArr* all[] = {&pool, &descs, &items, &ctl, &state, &boxes, &items0, &state0, &ctl0};
+    for (DevArr* a : all) cudaFree(a->p);
+    cudaSetDevice(prev);
+  }
+};
+
+namespace {
+
+// Plans the batch, uploads its descriptors, boxes and initial queue into
+// the graph's buffers (synchronously, outside any capture) and captures the
+// launch sequence on a private stream.
+int capture_uneven(ik_batch_engine_s* E, const ik_problem* probs, int n, const ik_batch_params* bp,
+                   int32_t* found, int32_t* reach, int32_t* poses, int32_t* relax, int32_t* status,
+                   int32_t* rc_out, ik_batch_graph_s* G) {
+  std::vector<ProbPlan> plans;
+  int rc = plan_problems(E, probs, n, &plans);
+  if (rc) return rc;
+  if (E->budget == 0) {
+    size_t fr = 0, tot = 0;
+    CKB(cudaMemGetInfo(&fr, &tot));
+    E->budget = (size_t)(0.7 * (double)fr);
+  }
+  size_t pool_words = 0, box_words = 0, smem = 0;
+  long long n_items = 0, n_first = 0;
+  for (int i = 0; i < n; ++i) {
+    pool_words += plans[i].lay.total;
+    box_words += align_words(6 * (size_t)probs[i].n_boxes);
+    smem = std::max(smem, plans[i].smem);
+    n_items += item_bound(probs[i], plans[i]);
+    n_first += plans[i].n_slabs;
+  }
+  if (smem > batch_smem_limit() || pool_words * 4 > E->budget) return IK_ERR_UNSUPPORTED;
+  if ((rc = grow(G->pool, pool_words * 4))) return rc;
+  if ((rc = grow(G->descs, (size_t)n * sizeof(BatchProb)))) return rc;
+  if ((rc = grow(G->items, (size_t)n_items * sizeof(int4)))) return rc;
+  if ((rc = grow(G->items0, (size_t)n_first * sizeof(int4)))) return rc;
+  if ((rc = grow(G->ctl, 8 * sizeof(unsigned long long)))) return rc;
+  if ((rc = grow(G->ctl0, 8 * sizeof(unsigned long long)))) return rc;
+  if ((rc = grow(G->state, (size_t)n * sizeof(int2)))) return rc;
+  if ((rc = grow(G->state0, (size_t)n * sizeof(int2)))) return rc;
+  if ((rc = grow(G->boxes, std::max<size_t>(box_words, 1) * 4))) return rc;
+  CKB(batch_set_smem(smem));
+  std::vector<BatchProb> hd(n);
+  std::vector<int2> hs(n);
+  std::vector<int4> hi4((size_t)n_first);
+  std::vector<int32_t> hb(std::max<size_t>(box_words, 1));
+  uint32_t* pool = (uint32_t*)G->pool.p;
+  int32_t* dboxes = (int32_t*)G->boxes.p;
+  size_t pw = 0, bw = 0;
+  long long it = 0;
+  for (int i = 0; i < n; ++i) {
+    fill_desc(probs[i], plans[i], i, pool + pw, dboxes + bw, hb.data() + bw, found, reach, poses, relax, status,
+              rc_out, &hd[i]);
+    pw += plans[i].lay.total;
+    bw += align_words(6 * (size_t)probs[i].n_boxes);
+    hs[i] = make_int2(0, plans[i].n_slabs);
+    for (int s = 0; s < plans[i].n_slabs; ++s) hi4[it++] = make_int4(i + 1, 0, s, 0);
+  }
+  const unsigned long long ctl0[8] = {0, (unsigned long long)n_first, 0, 0, 0, 0, 0, 0};
+  CKB(cudaMemcpy(G->descs.p, hd.data(), (size_t)n * sizeof(BatchProb), cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(G->boxes.p, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(G->state0.p, hs.data(), (size_t)n * sizeof(int2), cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(G->items0.p, hi4.data(), hi4.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(G->ctl0.p, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice));
+  BatchQueue q;
+  q.items = (int4*)G->items.p;
+  q.cap = n_items;
+  q.ctl = (unsigned long long*)G->ctl.p;
+  q.state = (int2*)G->state.p;
+  BatchRules r{bp->delta, bp->eps2, bp->eps2_max, bp->max_relax};
+  const int per_sm = bp->blocks_per_sm > 0 ? bp->blocks_per_sm : 1;
+  cudaStream_t cs = nullptr;
+  CKB(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemcpyAsync(G->state.p, G->state0.p, (size_t)n * sizeof(int2), cudaMemcpyDeviceToDevice, cs);
+    cudaMemsetAsync(G->items.p, 0, (size_t)n_items * sizeof(int4), cs);
+    cudaMemcpyAsync(G->items.p, G->items0.p, hi4.size() * sizeof(int4), cudaMemcpyDeviceToDevice, cs);
+    cudaMemcpyAsync(G->ctl.p, G->ctl0.p, sizeof(ctl0), cudaMemcpyDeviceToDevice, cs);
+    cudaMemsetAsync(G->pool.p, 0, pool_words * 4, cs);
+    launch_fill_i32(rc_out, n, IK_ERR_TIMEOUT, cs);
+    launch_batch_persistent((const BatchProb*)G->descs.p, n, q, r, E->num_sms * per_sm, smem, E->timeout_ns, cs);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &G->graph);
+    e = e2 != cudaSuccess ? e2 : cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+  cudaStreamDestroy(cs);
+  return cu(e);
+}
+
+}  // namespace
 
 int ik_batch_engine_create(ik_batch_engine* out) {
   if (!out) return IK_ERR_ARG;
@@ -624,3 +739,42 @@ int ik_solve_batch(const ik_problem* probs, int n, const ik_batch_params* bp, in
 }
 
 }  // extern "C"
+
+int ik_batch_capture_uneven(ik_batch_engine e, const ik_problem* probs, int n, const ik_batch_params* bp,
+                            int32_t* found_dev, int32_t* reach_dev, int32_t* poses_dev, int32_t* relax_dev,
+                            int32_t* status_dev, int32_t* job_rc_dev, ik_batch_graph* out) {
+  if (!e || !out || n <= 0 || !probs || !found_dev || !reach_dev || !poses_dev || !relax_dev || !status_dev ||
+      !job_rc_dev)
+    return IK_ERR_ARG;
+  *out = nullptr;
+  int rc = check_params(bp);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i)
+    if ((rc = check_problem(probs[i]))) return rc;
+  std::lock_guard<std::mutex> lock(e->mu);
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return cu(cudaGetLastError());
+  if (prev != e->device) CKB(cudaSetDevice(e->device));
+  ik_batch_graph_s* G = new ik_batch_graph_s;
+  G->device = e->device;
+  rc = capture_uneven(e, probs, n, bp, found_dev, reach_dev, poses_dev, relax_dev, status_dev, job_rc_dev, G);
+  if (rc) delete G;
+  else *out = G;
+  if (prev != e->device) cudaSetDevice(prev);
+  return rc;
+}
+
+int ik_batch_graph_launch(ik_batch_graph g, void* cuda_stream) {
+  if (!g || !g->exec) return IK_ERR_ARG;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return cu(cudaGetLastError());
+  if (prev != g->device) CKB(cudaSetDevice(g->device));
+  const int rc = cu(cudaGraphLaunch(g->exec, (cudaStream_t)cuda_stream));
+  if (prev != g->device) cudaSetDevice(prev);
+  return rc;
+}
+
+int ik_batch_graph_destroy(ik_batch_graph g) {
+  delete g;
+  return IK_OK;
+}

@@ -129,6 +129,10 @@ _sig("ik_batch_engine_set_timeout", _i, [_vp, ctypes.c_int64])
 _sig("ik_batch_engine_set_pairs", _i, [_vp, _i])
 _sig("ik_solve_batch_async", _i, [_vp, _vp, _i, ctypes.POINTER(IkBatchParams), _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp])
+_sig("ik_batch_capture_uneven", _i, [_vp, _vp, _i, ctypes.POINTER(IkBatchParams), _vp, _vp, _vp, _vp, _vp, _vp,
+                                     ctypes.POINTER(_vp)])
+_sig("ik_batch_graph_launch", _i, [_vp, _vp])
+_sig("ik_batch_graph_destroy", _i, [_vp])
 _sig("ik_batch_capture", _i, [_vp, ctypes.POINTER(IkArm), _vp, _vp, _i, _vp, _i,
                               ctypes.POINTER(IkPathParams), _vp, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(_vp)])
@@ -149,7 +153,8 @@ EXPORTED = [
     "ik_reach_path_many", "ik_plan_between", "ik_validate_poses", "ik_replan", "ik_replan_many",
     "ik_batch_output_sizes", "ik_solve_batch", "ik_batch_engine_create", "ik_batch_engine_destroy",
     "ik_batch_engine_set_budget", "ik_batch_engine_set_timeout", "ik_batch_engine_set_pairs",
-    "ik_solve_batch_async", "ik_batch_capture",
+    "ik_solve_batch_async", "ik_batch_capture_uneven", "ik_batch_graph_launch", "ik_batch_graph_destroy",
+    "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
     "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
@@ -623,9 +628,51 @@ class BatchEngine:
                                          _dev_ptr(status), _dev_ptr(job_rc), _vp(stream) if stream else None),
                "ik_solve_batch_async")
 
+    def capture(self, problems, found, reach, poses, relax, status, job_rc, delta: int = 3, eps2: int = 2,
+                eps2_max: int = 8, max_relax: int = -1, blocks_per_sm: int = 0) -> "BatchGraph":
+        """The batch as a CUDA graph of one persistent launch writing into the
+        given CUDA tensors (ik_batch_capture_uneven); replay with .launch()."""
+        arr, keep = _problem_array(problems)
+        bp = IkBatchParams(delta, eps2, eps2_max, max_relax, blocks_per_sm)
+        h = _vp()
+        _check(_lib.ik_batch_capture_uneven(self.h, ctypes.cast(arr, _vp), len(problems), ctypes.byref(bp),
+                                            _dev_ptr(found), _dev_ptr(reach), _dev_ptr(poses), _dev_ptr(relax),
+                                            _dev_ptr(status), _dev_ptr(job_rc), ctypes.byref(h)),
+               "ik_batch_capture_uneven")
+        return BatchGraph(h.value, (found, reach, poses, relax, status, job_rc))
+
     def close(self) -> None:
         if self.h:
             _lib.ik_batch_engine_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchGraph:
+    """Owning wrapper of an ``ik_batch_graph`` (it keeps its output tensors
+    alive)."""
+
+    def __init__(self, h: int, outputs):
+        self.h = h
+        self._outputs = outputs
+
+    def launch(self, stream: int = 0) -> None:
+        _check(_lib.ik_batch_graph_launch(self.h, _vp(stream) if stream else None), "ik_batch_graph_launch")
+
+    def close(self) -> None:
+        if self.h:
+            _lib.ik_batch_graph_destroy(self.h)
             self.h = 0
 
     def __enter__(self):

@@ -307,6 +307,38 @@ def test_uneven_batch_query_pairs_equal_single_queries(ik):
                 eng.set_pairs(bad)
 
 
+def test_uneven_batch_captured_graph_replays_equal_sync(ik):
+    """The batch captured as a CUDA graph (one persistent launch) gives the
+    synchronous results on every replay, also after the caller's problem
+    arrays changed (they are copied at capture)."""
+    import torch
+    probs = [_as_dict(p) for p in G.c4_problems(10, 8)]
+    want, _ = ik.ik_solve_batch(probs)
+    stream = torch.cuda.Stream()
+    with ik.BatchEngine() as eng:
+        outs = _packed_outputs(ik, torch, probs)
+        with eng.capture(probs, *outs) as graph:
+            for p in probs:  # the caller's data may change after capture
+                p["boxes"] = np.zeros((0, 6), np.int32)
+            for _ in range(2):
+                for t in outs:
+                    t.fill_(-7)
+                torch.cuda.synchronize()
+                graph.launch(stream.cuda_stream)
+                stream.synchronize()
+                found, reach, poses, relax, status, rc = outs
+                assert (rc.cpu().numpy() == ik.IK_OK).all()
+                got = ik.unpack_batch([_as_dict(p) for p in G.c4_problems(10, 8)], found.cpu().numpy(),
+                                      reach.cpu().numpy(), poses.cpu().numpy(), relax.cpu().numpy(),
+                                      status.cpu().numpy())
+                for a, b in zip(got, want):
+                    assert a["found"] == b["found"] and a["status"] == b["status"]
+                    assert (a["reach"] == b["reach"]).all() and (a["poses"] == b["poses"]).all()
+                    assert (a["relax"] == b["relax"]).all()
+        with pytest.raises(Exception):
+            eng.capture([], *outs)
+
+
 def test_uneven_batch_timeout_is_reported_and_the_context_stays_usable(ik):
     """With a wait limit too short for any work (1 microsecond) the
     persistent launch gives up on its own: unfinished problems report
