@@ -131,8 +131,9 @@ def measured_peaks():
 
 
 # Algorithmic work per non-zero (offset, output word) pair of a propagation
-# (SURVEY-style W_alg with the supercover terms paid by the edge-mask
-# kernel): one AND with the edge-mask word and one OR into the output word;
+# (the method's word-op count with the supercover terms paid by the
+# edge-mask kernel): one AND with the edge-mask word and one OR into the
+# output word;
 # and two words read: the shifted source word (staged in shared memory) and
 # the edge-mask word.
 OPS_PER_PAIR = 2
