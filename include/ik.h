@@ -629,6 +629,19 @@ IK_API int ik_shell_offsets(int len, float tol, int32_t* lo2_hi2, int32_t* offs_
  * incremental integer traversal of the segment's boundary crossings),
  * ordered by (z, y, x).  Returns its size or a negative error code. */
 IK_API int ik_supercover_offsets(const int32_t d[3], int32_t* vox_out, int cap);
+/* The row-lane propagation's offset table of the shell of one segment
+ * length (IK_OPT_ROW_LANES), as the library builds it on the host: *R_out =
+ * the shell's reach; offs_out [n][3] = the offsets in device order (the
+ * order of the edge-mask rows: by (z, y, x)); tabr_out [n] = the entries,
+ * per dz plane the offsets with dx < 0 then those with dx >= 0, each run
+ * ordered by (dy, dx), entry (e << 11) | ((dy + 32) << 5) | (dx & 31), e
+ * the offset's device index; rowsr_out [(2R+1) * 2 * (2R+2)] = the start of
+ * each (dz, sign, dy) run, entry 2R+1 of a (dz, sign) run its end.  At most
+ * cap offsets and rowsr_cap starts are written (nullable outputs).  Returns
+ * n, IK_ERR_ARG, or IK_ERR_UNSUPPORTED when the reach exceeds 31 (no
+ * table). */
+IK_API int ik_row_table(int len, float tol, int32_t* R_out, int32_t* offs_out, int32_t* tabr_out, int cap,
+                        int32_t* rowsr_out, int rowsr_cap);
 
 #ifdef __cplusplus
 }

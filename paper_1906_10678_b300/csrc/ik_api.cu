@@ -34,6 +34,33 @@ struct GridState;
 }  // namespace
 
 namespace ikb {
+// The row-lane propagation's table of shell h (tabr, rowsr of SegDev),
+// empty when the reach exceeds 31: per dz plane the offsets with dx < 0,
+// then those with dx >= 0, each run ordered by (dy, dx) (the device order
+// within a (dz, dy) row is by dx), with the run starts per dy.
+void build_row_table(const ShellHost& h, std::vector<int32_t>* tabr, std::vector<int32_t>* rowsr) {
+  tabr->clear();
+  rowsr->clear();
+  const int R = h.R;
+  if (R > 31) return;
+  const int side = 2 * R + 1, rs = 2 * R + 2;
+  tabr->reserve(h.dev_off.size());
+  rowsr->assign((size_t)side * 2 * rs, 0);
+  for (int dz = -R; dz <= R; ++dz)
+    for (int neg = 1; neg >= 0; --neg) {
+      int32_t* run = rowsr->data() + ((size_t)(dz + R) * 2 + (1 - neg)) * rs;
+      for (int dy = -R; dy <= R; ++dy) {
+        run[dy + R] = (int32_t)tabr->size();
+        const int r = (dz + R) * side + (dy + R);
+        for (int i = h.rows[r]; i < h.rows[r + 1]; ++i) {
+          const int dx = unpack_x(h.dev_off[i]);
+          if ((dx < 0) != (neg == 1)) continue;
+          tabr->push_back((int32_t)(((uint32_t)i << 11) | ((uint32_t)(dy + 32) << 5) | (uint32_t)(dx & 31)));
+        }
+      }
+      run[2 * R + 1] = (int32_t)tabr->size();
+    }
+}
 void note_cuda_error(cudaError_t e) { g_last_error = cudaGetErrorString(e); }
 }  // namespace ikb
 
@@ -289,31 +316,10 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
       tabw[i] = (int32_t)(((uint32_t)delta << 6) | ((uint32_t)(dx < 0) << 5) | (uint32_t)(dx & 31));
     }
   }
-  // and for the row-lane propagation: per dz plane the runs dx < 0 and
-  // dx >= 0, each ordered by (dy, dx) (the device order within a row is by
-  // dx), with the run starts per dy
+  // and for the row-lane propagation (reach at most 31)
   std::vector<int32_t> tabr, rowsr;
   const int Rr = s->reach;
-  if (Rr <= 31) {
-    const int side = 2 * Rr + 1, rs = 2 * Rr + 2;
-    tabr.reserve(n);
-    rowsr.assign((size_t)side * 2 * rs, 0);
-    for (int dz = -Rr; dz <= Rr; ++dz)
-      for (int neg = 1; neg >= 0; --neg) {
-        int32_t* run = rowsr.data() + ((size_t)(dz + Rr) * 2 + (1 - neg)) * rs;
-        for (int dy = -Rr; dy <= Rr; ++dy) {
-          run[dy + Rr] = (int32_t)tabr.size();
-          const int r = (dz + Rr) * side + (dy + Rr);
-          for (int i = s->host.rows[r]; i < s->host.rows[r + 1]; ++i) {
-            const int32_t o = s->host.dev_off[i];
-            const int dx = unpack_x(o);
-            if ((dx < 0) != (neg == 1)) continue;
-            tabr.push_back((int32_t)(((uint32_t)i << 11) | ((uint32_t)(dy + 32) << 5) | (uint32_t)(dx & 31)));
-          }
-        }
-        run[2 * Rr + 1] = (int32_t)tabr.size();
-      }
-  }
+  build_row_table(s->host, &tabr, &rowsr);
   // and for the row-lane edge masks (rows of 32 + 2R per halo slice)
   std::vector<int32_t> sctabr;
   if (Rr <= 31) {
@@ -2054,6 +2060,30 @@ int ik_shell_offsets(int len, float tol, int32_t* lo2_hi2, int32_t* offs_out, in
     offs_out[3 * i + 1] = unpack_y(sh.off[i]);
     offs_out[3 * i + 2] = unpack_z(sh.off[i]);
   }
+  return n;
+}
+
+int ik_row_table(int len, float tol, int32_t* R_out, int32_t* offs_out, int32_t* tabr_out, int cap,
+                 int32_t* rowsr_out, int rowsr_cap) {
+  if (len < 1 || len > IK_MAX_LEN || !(tol >= 0.0f && tol < 1.0f)) return IK_ERR_ARG;
+  int lo2, hi2;
+  shell_bounds(len, (double)tol, &lo2, &hi2);
+  ShellHost sh;
+  build_shell(lo2, hi2, &sh);
+  if (R_out) *R_out = sh.R;
+  std::vector<int32_t> tabr, rowsr;
+  build_row_table(sh, &tabr, &rowsr);
+  if (tabr.empty()) return IK_ERR_UNSUPPORTED;
+  const int n = (int)sh.dev_off.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (offs_out) {
+      offs_out[3 * i] = unpack_x(sh.dev_off[i]);
+      offs_out[3 * i + 1] = unpack_y(sh.dev_off[i]);
+      offs_out[3 * i + 2] = unpack_z(sh.dev_off[i]);
+    }
+    if (tabr_out) tabr_out[i] = tabr[i];
+  }
+  for (int i = 0; i < (int)rowsr.size() && i < rowsr_cap && rowsr_out; ++i) rowsr_out[i] = rowsr[i];
   return n;
 }
 

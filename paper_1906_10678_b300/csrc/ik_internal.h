@@ -51,6 +51,8 @@ struct ConeSpec {
 // The shell lo2 <= |d|^2 <= hi2, or its part inside `cone` when given (R
 // stays floor(sqrt(hi2)), the reach of the whole shell).
 void build_shell(int lo2, int hi2, ShellHost* out, const ConeSpec* cone = nullptr);
+// The row-lane table of a shell (SegDev::tabr, rowsr); empty for reach > 31.
+void build_row_table(const ShellHost& h, std::vector<int32_t>* tabr, std::vector<int32_t>* rowsr);
 // Closed supercover of 0 -> d by incremental traversal; (z, y, x) order.
 void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
 // The same walk into a caller buffer of cap entries, allocating nothing:

@@ -144,6 +144,7 @@ _sig("ik_profile_read", _i, [_vp, _vp, _vp, _vp, _i])
 _sig("ik_profile_name", ctypes.c_char_p, [_i])
 _sig("ik_shell_offsets", _i, [_i, ctypes.c_float, _vp, _vp, _i])
 _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
+_sig("ik_row_table", _i, [_i, ctypes.c_float, _vp, _vp, _vp, _i, _vp, _i])
 _sig("ik_probe_peak", _i, [_i, _i, _i, _vp, _vp, _vp, _vp])
 
 EXPORTED = [
@@ -157,7 +158,7 @@ EXPORTED = [
     "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
-    "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets",
+    "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets", "ik_row_table",
     "ik_probe_peak",
 ]
 
@@ -817,6 +818,21 @@ def ik_shell_offsets(length: int, tol: float = 0.5) -> Tuple[Tuple[int, int], np
     out = np.zeros((max(n, 1), 3), np.int32)
     _lib.ik_shell_offsets(length, tol, _np_ptr(b), _np_ptr(out), n)
     return (int(b[0]), int(b[1])), out[:n]
+
+
+def ik_row_table(length: int, tol: float = 0.5):
+    """The row-lane propagation's table of one shell: (R, offsets [n][3] in
+    device order, tabr [n], rowsr [(2R+1) * 2 * (2R+2)])."""
+    R = np.zeros(1, np.int32)
+    n = _lib.ik_row_table(length, tol, _np_ptr(R), None, None, 0, None, 0)
+    if n < 0:
+        raise IkError(n, "ik_row_table")
+    r = int(R[0])
+    offs = np.zeros((max(n, 1), 3), np.int32)
+    tabr = np.zeros(max(n, 1), np.int32)
+    rowsr = np.zeros((2 * r + 1) * 2 * (2 * r + 2), np.int32)
+    _lib.ik_row_table(length, tol, _np_ptr(R), _np_ptr(offs), _np_ptr(tabr), n, _np_ptr(rowsr), len(rowsr))
+    return r, offs[:n], tabr[:n], rowsr
 
 
 def ik_supercover_offsets(d) -> np.ndarray:

@@ -85,3 +85,41 @@ def test_argument_errors_without_gpu(ik):
     with pytest.raises(ik.IkError):
         ik.ik_supercover_offsets([300, 0, 0])
     assert ik._lib.ik_strerror(-1) == b"invalid argument"
+
+
+@pytest.mark.parametrize("L", list(range(1, 25)) + [31])
+def test_row_lane_table_covers_the_shell_once_in_run_order(ik, L):
+    """The row-lane propagation's table (ik_row_table): every offset of the
+    shell exactly once; each entry decodes to its offset's dy and shift and
+    names its device (edge-mask row) index; the (dz, sign, dy) runs hold
+    exactly the offsets of that plane, sign and row, ordered by dx."""
+    R, offs, tabr, rowsr = ik.ik_row_table(L)
+    (lo2, hi2), shell = ik.ik_shell_offsets(L)
+    assert sorted(map(tuple, offs)) == sorted(map(tuple, shell))
+    assert R == np.abs(shell).max()
+    n = len(offs)
+    e = (tabr.astype(np.int64) & 0xFFFFFFFF) >> 11
+    dy = ((tabr >> 5) & 63) - 32
+    s = tabr & 31
+    assert sorted(e.tolist()) == list(range(n))
+    assert (dy == offs[e, 1]).all() and (s == (offs[e, 0] & 31)).all()
+    side = 2 * R + 2
+    runs = rowsr.reshape(2 * R + 1, 2, side)
+    for dz in range(-R, R + 1):
+        for sign in (0, 1):  # 0: dx < 0, 1: dx >= 0
+            r = runs[dz + R, sign]
+            assert (np.diff(r) >= 0).all()
+            for y in range(-R, R + 1):
+                got = offs[e[r[y + R]:r[y + R + 1]]]
+                want = shell[(shell[:, 2] == dz) & (shell[:, 1] == y) & ((shell[:, 0] >= 0) == (sign == 1))]
+                assert len(got) == len(want), (dz, sign, y)
+                assert (got[:, 2] == dz).all() and (got[:, 1] == y).all()
+                assert (np.diff(got[:, 0]) > 0).all()
+    # the runs tile the table in order: plane by plane, the dx < 0 run first
+    assert runs[0, 0, 0] == 0 and runs[-1, 1, -1] == n
+    assert (runs[:, 0, -1] == runs[:, 1, 0]).all() and (runs[1:, 0, 0] == runs[:-1, 1, -1]).all()
+
+
+def test_row_lane_table_refused_beyond_reach_31(ik):
+    with pytest.raises(Exception):
+        ik.ik_row_table(40)
