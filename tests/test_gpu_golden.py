@@ -4,14 +4,16 @@ written by tests/golden/make_full_size.py, which calls only the oracle).
 Each workload runs in the launch configuration the benchmark times:
 
 * 128^3 (64 targets, 32-waypoint paths): the whole 64 x 32 batch through
-  ik_reach_path_many (work list, query pairs and the autotuner's defaults);
+  ik_reach_path_many (the library's defaults: row lanes with two queries
+  per lane, row-lane edge masks, the work list on the sparsest levels);
   every reach pose and found flag, and the poses, relaxation records and
   status of 16 whole paths, element by element; and, for 4 paths at 5
   waypoints, every survivor set V_k^(j) compared by its SHA-256 over the
   packed bits (and its popcount) -- the oracle's byte sets packed the way
   the library packs words.
 * the uneven batch: the first 32 problems of the 1024-problem batch, solved
-  inside the full batch by the persistent launch, element by element.
+  inside the full batch by the persistent launch (waypoint items in query
+  pairs), element by element.
 * 256^3 (the serving scene after 5 ticks of the moving boxes): 8 reach poses
   and 2 whole paths, through a direct call and through the captured graph
   the server replays.
