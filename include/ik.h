@@ -642,6 +642,15 @@ IK_API int ik_supercover_offsets(const int32_t d[3], int32_t* vox_out, int cap);
  * table). */
 IK_API int ik_row_table(int len, float tol, int32_t* R_out, int32_t* offs_out, int32_t* tabr_out, int cap,
                         int32_t* rowsr_out, int rowsr_cap);
+/* The row-lane edge masks' supercover table of the same shell (section
+ * "Testing for collisions": the voxels a segment crosses), as the library
+ * builds it: sc_start_out [n + 1] = where each offset's voxels start (device
+ * order, as ik_row_table's offsets); sctabr_out [m] = per voxel v,
+ * ((v.z * (32 + 2R) + v.y) << 6) | (v.x + 32).  At most cap_off starts and
+ * cap_sc voxels are written (nullable outputs).  Returns m, IK_ERR_ARG, or
+ * IK_ERR_UNSUPPORTED when the reach exceeds 31. */
+IK_API int ik_row_mask_table(int len, float tol, int32_t* sc_start_out, int cap_off, int32_t* sctabr_out,
+                             int cap_sc);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,20 @@ void build_row_table(const ShellHost& h, std::vector<int32_t>* tabr, std::vector
       run[2 * R + 1] = (int32_t)tabr->size();
     }
 }
+// The row-lane edge masks' supercover table of shell h (empty when the
+// reach exceeds 31): per supercover voxel (v of h.sc, in its order),
+// ((vz * (32 + 2R) + vy) << 6) | (vx + 32).
+void build_row_mask_table(const ShellHost& h, std::vector<int32_t>* sctabr) {
+  sctabr->clear();
+  if (h.R > 31) return;
+  const int RY = 32 + 2 * h.R;
+  sctabr->resize(h.sc.size());
+  for (size_t i = 0; i < h.sc.size(); ++i) {
+    const int32_t v = h.sc[i];
+    const int vx = unpack_x(v), vy = unpack_y(v), vz = unpack_z(v);
+    (*sctabr)[i] = (int32_t)(((uint32_t)(vz * RY + vy) << 6) | (uint32_t)(vx + 32));
+  }
+}
 void note_cuda_error(cudaError_t e) { g_last_error = cudaGetErrorString(e); }
 }  // namespace ikb
 
@@ -318,19 +332,10 @@ int make_shell(ik_grid g, int lo2, int hi2, const ConeSpec* cone, ShellDev** out
   }
   // and for the row-lane propagation (reach at most 31)
   std::vector<int32_t> tabr, rowsr;
-  const int Rr = s->reach;
   build_row_table(s->host, &tabr, &rowsr);
   // and for the row-lane edge masks (rows of 32 + 2R per halo slice)
   std::vector<int32_t> sctabr;
-  if (Rr <= 31) {
-    const int RYr = 32 + 2 * Rr;
-    sctabr.resize(s->host.sc.size());
-    for (size_t i = 0; i < sctabr.size(); ++i) {
-      const int32_t v = s->host.sc[i];
-      const int vx = unpack_x(v), vy = unpack_y(v), vz = unpack_z(v);
-      sctabr[i] = (int32_t)(((uint32_t)(vz * RYr + vy) << 6) | (uint32_t)(vx + 32));
-    }
-  }
+  build_row_mask_table(s->host, &sctabr);
   // and for the TMA-staged brick (pitch BX, word w at column w + 4)
   const int BX = tma_mask_pitch(g->d);
   std::vector<int32_t> sctab_tma;
@@ -2085,6 +2090,20 @@ int ik_row_table(int len, float tol, int32_t* R_out, int32_t* offs_out, int32_t*
   }
   for (int i = 0; i < (int)rowsr.size() && i < rowsr_cap && rowsr_out; ++i) rowsr_out[i] = rowsr[i];
   return n;
+}
+
+int ik_row_mask_table(int len, float tol, int32_t* sc_start_out, int cap_off, int32_t* sctabr_out, int cap_sc) {
+  if (len < 1 || len > IK_MAX_LEN || !(tol >= 0.0f && tol < 1.0f)) return IK_ERR_ARG;
+  int lo2, hi2;
+  shell_bounds(len, (double)tol, &lo2, &hi2);
+  ShellHost sh;
+  build_shell(lo2, hi2, &sh);
+  std::vector<int32_t> sctabr;
+  build_row_mask_table(sh, &sctabr);
+  if (sctabr.empty()) return IK_ERR_UNSUPPORTED;
+  for (int i = 0; i <= (int)sh.dev_off.size() && i < cap_off && sc_start_out; ++i) sc_start_out[i] = sh.sc_start[i];
+  for (int i = 0; i < (int)sctabr.size() && i < cap_sc && sctabr_out; ++i) sctabr_out[i] = sctabr[i];
+  return (int)sctabr.size();
 }
 
 int ik_supercover_offsets(const int32_t d[3], int32_t* vox_out, int cap) {

@@ -53,6 +53,8 @@ struct ConeSpec {
 void build_shell(int lo2, int hi2, ShellHost* out, const ConeSpec* cone = nullptr);
 // The row-lane table of a shell (SegDev::tabr, rowsr); empty for reach > 31.
 void build_row_table(const ShellHost& h, std::vector<int32_t>* tabr, std::vector<int32_t>* rowsr);
+// The row-lane edge masks' supercover table (ShellDev::d_sctabr); empty for reach > 31.
+void build_row_mask_table(const ShellHost& h, std::vector<int32_t>* sctabr);
 // Closed supercover of 0 -> d by incremental traversal; (z, y, x) order.
 void supercover_traverse(int dx, int dy, int dz, std::vector<int32_t>* out);
 // The same walk into a caller buffer of cap entries, allocating nothing:

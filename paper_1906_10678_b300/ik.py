@@ -145,6 +145,7 @@ _sig("ik_profile_name", ctypes.c_char_p, [_i])
 _sig("ik_shell_offsets", _i, [_i, ctypes.c_float, _vp, _vp, _i])
 _sig("ik_supercover_offsets", _i, [_vp, _vp, _i])
 _sig("ik_row_table", _i, [_i, ctypes.c_float, _vp, _vp, _vp, _i, _vp, _i])
+_sig("ik_row_mask_table", _i, [_i, ctypes.c_float, _vp, _i, _vp, _i])
 _sig("ik_probe_peak", _i, [_i, _i, _i, _vp, _vp, _vp, _vp])
 
 EXPORTED = [
@@ -158,7 +159,7 @@ EXPORTED = [
     "ik_batch_capture",
     "ik_batch_launch", "ik_batch_destroy", "ik_forward_sets_noalloc",
     "ik_profile_enable",
-    "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets", "ik_row_table",
+    "ik_profile_read", "ik_profile_name", "ik_shell_offsets", "ik_supercover_offsets", "ik_row_table", "ik_row_mask_table",
     "ik_probe_peak",
 ]
 
@@ -833,6 +834,19 @@ def ik_row_table(length: int, tol: float = 0.5):
     rowsr = np.zeros((2 * r + 1) * 2 * (2 * r + 2), np.int32)
     _lib.ik_row_table(length, tol, _np_ptr(R), _np_ptr(offs), _np_ptr(tabr), n, _np_ptr(rowsr), len(rowsr))
     return r, offs[:n], tabr[:n], rowsr
+
+
+def ik_row_mask_table(length: int, tol: float = 0.5):
+    """The row-lane edge masks' supercover table of one shell:
+    (sc_start [n + 1], sctabr [m]), offsets in ik_row_table's device order."""
+    m = _lib.ik_row_mask_table(length, tol, None, 0, None, 0)
+    if m < 0:
+        raise IkError(m, "ik_row_mask_table")
+    n = len(ik_row_table(length, tol)[1])
+    start = np.zeros(n + 1, np.int32)
+    tab = np.zeros(max(m, 1), np.int32)
+    _lib.ik_row_mask_table(length, tol, _np_ptr(start), n + 1, _np_ptr(tab), m)
+    return start, tab[:m]
 
 
 def ik_supercover_offsets(d) -> np.ndarray:

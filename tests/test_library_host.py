@@ -123,3 +123,21 @@ def test_row_lane_table_covers_the_shell_once_in_run_order(ik, L):
 def test_row_lane_table_refused_beyond_reach_31(ik):
     with pytest.raises(Exception):
         ik.ik_row_table(40)
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 9, 14, 20, 24, 31])
+def test_row_mask_table_is_each_offsets_supercover(ik, L):
+    """The row-lane edge masks' table (ik_row_mask_table): the voxels listed
+    for each offset (in ik_row_table's device order) encode, row delta at
+    the halo pitch 32 + 2R and dx, exactly that offset's supercover as
+    ik_supercover_offsets builds it."""
+    R, offs, _, _ = ik.ik_row_table(L)
+    start, tab = ik.ik_row_mask_table(L)
+    assert start[0] == 0 and start[-1] == len(tab) and (np.diff(start) >= 0).all()
+    RY = 32 + 2 * R
+    for e, d in enumerate(offs):
+        sc = ik.ik_supercover_offsets(d)
+        want = ((sc[:, 2] * RY + sc[:, 1]) << 6) | (sc[:, 0] + 32)
+        got = tab[start[e]:start[e + 1]]
+        assert sorted(got.tolist()) == sorted(want.tolist()), (L, tuple(d))
+        assert (((got & 63) - 32) * np.sign(d[0]) >= 0).all()  # dx of one sign (or 0)
